@@ -1,0 +1,244 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module holds data synthesis only: flow fields, spectra and layouts.  It
+contains none of the decomposition's arithmetic and is the one module that the
+CUDA path's tests and the CPU oracle's tests share.
+
+Fields follow the paper's Taylor-Green vortex cases:
+  * 2D analytic TGV, Section 5.1:
+      u1 = sin(x1) cos(x2) exp(-2 nu t),  u2 = -cos(x1) sin(x2) exp(-2 nu t);
+  * 3D TGV initial condition of Section 5.2 (V0 = 1, L = 1, rho0 = 1,
+    p0 = 100), decayed as exp(-3 nu t), plus solenoidal Fourier modes with a
+    k^{-5/3} amplitude spectrum, each decaying as exp(-nu |k|^2 t) with a
+    drifting phase; density and pressure from rho = 1 + 0.01 |u|^2 and the
+    isentropic relation p = p0 (rho / rho0)^gamma, gamma = 1.4.
+
+Window layout ("blocks"): subdomain s is an m_s x n_s column-major matrix
+(column = snapshot) starting at element ``off[s]`` of one flat buffer with
+leading dimension ``ld[s]``.  Row order inside a 3D box is
+r = ((q * ez + z) * ey + y) * ex + x (x fastest, QoI slowest).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Window:
+    """A flat window plus its per-subdomain block descriptors."""
+    data: np.ndarray            # 1-D, float32 or float64
+    m: np.ndarray               # int64 [S]
+    n: np.ndarray               # int64 [S]
+    off: np.ndarray             # int64 [S]
+    ld: np.ndarray              # int64 [S]
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def num_sub(self) -> int:
+        return int(len(self.m))
+
+    def block(self, s: int) -> np.ndarray:
+        """View of subdomain s as an m_s x n_s array (column j = snapshot j)."""
+        m, n, off, ld = int(self.m[s]), int(self.n[s]), int(self.off[s]), int(self.ld[s])
+        cols = np.lib.stride_tricks.as_strided(
+            self.data[off:], shape=(n, m),
+            strides=(ld * self.data.itemsize, self.data.itemsize))
+        return cols.T
+
+    def nbytes_payload(self) -> int:
+        return int((self.m * self.n).sum()) * self.data.itemsize
+
+
+def pack_blocks(blocks, dtype=np.float32, layout: str = "subdomain", pad_to: int = 4) -> Window:
+    """Pack a list of m_s x n_s arrays into one flat window.
+
+    layout "subdomain": [s][j][r] (each subdomain contiguous, ld = m_s rounded
+    up to ``pad_to`` elements so every column starts 16-byte aligned).
+    layout "snapshot": [j][s][r] (each snapshot contiguous; all n_s equal;
+    ld = sum of padded m_s)."""
+    S = len(blocks)
+    m = np.array([b.shape[0] for b in blocks], dtype=np.int64)
+    n = np.array([b.shape[1] for b in blocks], dtype=np.int64)
+    mp = ((m + pad_to - 1) // pad_to) * pad_to
+    if layout == "subdomain":
+        ld = mp.copy()
+        off = np.concatenate([[0], np.cumsum(mp * n)[:-1]]).astype(np.int64)
+        total = int((mp * n).sum())
+    elif layout == "snapshot":
+        if len(set(n.tolist())) != 1:
+            raise ValueError("snapshot layout needs equal window lengths")
+        ld = np.full(S, int(mp.sum()), dtype=np.int64)
+        off = np.concatenate([[0], np.cumsum(mp)[:-1]]).astype(np.int64)
+        total = int(mp.sum()) * int(n[0])
+    else:
+        raise ValueError(layout)
+    data = np.zeros(total, dtype=dtype)
+    w = Window(data, m, n, off, ld, {"layout": layout})
+    for s, b in enumerate(blocks):
+        w.block(s)[...] = b
+    return w
+
+
+# --------------------------------------------------------------------------
+# 2D analytic Taylor-Green vortex (Section 5.1)
+# --------------------------------------------------------------------------
+def tgv2d(nx: int = 64, n: int = 128, nu: float = 0.01, t_end: float = 10.0,
+          noise: float = 1e-6, seed: int = 1) -> np.ndarray:
+    """A (2 nx^2 x n), rows = u1 then u2 on an nx x nx grid over [0, 2pi)^2
+    (x1 fastest), columns = snapshots at t_j = t_end j / (n - 1), plus i.i.d.
+    N(0, noise^2) entries drawn from PCG64(seed)."""
+    x = 2.0 * np.pi * np.arange(nx) / nx
+    X1, X2 = np.meshgrid(x, x, indexing="xy")      # X1[b, a] = x_a
+    t = t_end * np.arange(n) / max(n - 1, 1)
+    g = np.exp(-2.0 * nu * t)
+    u1 = (np.sin(X1) * np.cos(X2)).reshape(-1)
+    u2 = (-np.cos(X1) * np.sin(X2)).reshape(-1)
+    A = np.concatenate([u1, u2])[:, None] * g[None, :]
+    if noise > 0:
+        A = A + noise * np.random.default_rng(seed).standard_normal(A.shape)
+    return A
+
+
+# --------------------------------------------------------------------------
+# 3D TGV-like field with Fourier modes (Section 5.2 initial condition)
+# --------------------------------------------------------------------------
+@dataclass
+class FourierModes:
+    kvec: np.ndarray     # [K, 3] integer wavevectors
+    amp: np.ndarray      # [K]
+    dirn: np.ndarray     # [K, 3] unit vectors orthogonal to kvec
+    phase: np.ndarray    # [K]
+    omega: np.ndarray    # [K]
+
+
+def fourier_modes(count: int = 32, kmax: int = 8, eps_f: float = 0.05, seed: int = 2,
+                  omega_range: float = 0.5) -> FourierModes:
+    rng = np.random.default_rng(seed)
+    ks = []
+    while len(ks) < count:
+        kv = rng.integers(-kmax, kmax + 1, size=3)
+        if np.any(kv != 0):
+            ks.append(kv)
+    kvec = np.array(ks, dtype=np.float64)
+    kn = np.linalg.norm(kvec, axis=1)
+    spec = kn ** (-5.0 / 3.0)
+    amp = eps_f * spec / spec.max()
+    dirn = np.empty_like(kvec)
+    for i in range(count):
+        r = rng.standard_normal(3)
+        r -= kvec[i] * (r @ kvec[i]) / (kvec[i] @ kvec[i])
+        dirn[i] = r / np.linalg.norm(r)
+    phase = rng.uniform(0.0, 2.0 * np.pi, size=count)
+    omega = rng.uniform(-omega_range, omega_range, size=count)
+    return FourierModes(kvec, amp, dirn, phase, omega)
+
+
+def tgv3d_box(org, ext, grid: int, t: np.ndarray, modes: FourierModes, nu: float = 0.01,
+              p0: float = 100.0, gamma: float = 1.4, dtype=np.float32) -> np.ndarray:
+    """One box of the 3D field: (5 * ex * ey * ez) x len(t), QoIs (rho,u,v,w,p).
+
+    The box covers grid points org + [0, ext) of a periodic grid^3 grid over
+    [0, 2pi)^3 (indices wrap).  Velocity = TGV * exp(-3 nu t) + sum of modes;
+    each mode is a_k d_k exp(-nu |k|^2 t) cos(k.x + phi_k + omega_k t)."""
+    ex, ey, ez = (int(e) for e in ext)
+    h = 2.0 * np.pi / grid
+    xs = h * ((org[0] + np.arange(ex)) % grid)
+    ys = h * ((org[1] + np.arange(ey)) % grid)
+    zs = h * ((org[2] + np.arange(ez)) % grid)
+    Z, Yg, X = np.meshgrid(zs, ys, xs, indexing="ij")         # [z][y][x]
+    X, Yg, Z = X.reshape(-1), Yg.reshape(-1), Z.reshape(-1)
+    npts = X.size
+    K = modes.kvec.shape[0]
+    # spatial basis: [TGV, cos(k.x + phi), sin(k.x + phi)] -> npts x (1 + 2K)
+    arg = np.outer(X, modes.kvec[:, 0]) + np.outer(Yg, modes.kvec[:, 1]) \
+        + np.outer(Z, modes.kvec[:, 2]) + modes.phase[None, :]
+    cosb, sinb = np.cos(arg), np.sin(arg)
+    decay = np.exp(-nu * (modes.kvec ** 2).sum(1)[:, None] * t[None, :])   # K x n
+    tc = modes.amp[:, None] * decay * np.cos(np.outer(modes.omega, t))
+    ts = modes.amp[:, None] * decay * np.sin(np.outer(modes.omega, t))
+    g = np.exp(-3.0 * nu * t)
+    tgv = [np.sin(X) * np.cos(Yg) * np.cos(Z), -np.cos(X) * np.sin(Yg) * np.cos(Z),
+           np.zeros(npts)]
+    vel = []
+    for c in range(3):
+        basis = np.concatenate([tgv[c][:, None], cosb * modes.dirn[None, :, c],
+                                -sinb * modes.dirn[None, :, c]], axis=1)
+        tf = np.concatenate([g[None, :], tc, ts], axis=0)
+        vel.append(basis @ tf)
+    speed2 = vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2
+    rho = 1.0 + 0.01 * speed2
+    p = p0 * rho ** gamma
+    out = np.empty((5 * npts, t.size), dtype=dtype)
+    for q, f in enumerate([rho, vel[0], vel[1], vel[2], p]):
+        out[q * npts:(q + 1) * npts] = f
+    return out
+
+
+def tgv3d_window(grid: int = 64, box: int = 16, n: int = 512, t_end: float = 10.0,
+                 nu: float = 0.01, modes: FourierModes | None = None, seed: int = 2,
+                 dtype=np.float32, layout: str = "subdomain", boxes=None) -> Window:
+    """Equal cubic boxes of edge ``box`` tiling a grid^3 periodic grid (or the
+    first ``boxes`` of them), QoIs (rho,u,v,w,p), n snapshots on [0, t_end]."""
+    if modes is None:
+        modes = fourier_modes(seed=seed)
+    nb = grid // box
+    t = t_end * np.arange(n) / max(n - 1, 1)
+    origins = [(bx * box, by * box, bz * box) for bz in range(nb) for by in range(nb)
+               for bx in range(nb)]
+    if boxes is not None:
+        origins = origins[:boxes]
+    m = 5 * box ** 3
+    S = len(origins)
+    if layout == "subdomain":
+        data = np.empty(S * m * n, dtype=dtype)
+        for s, o in enumerate(origins):
+            data[s * m * n:(s + 1) * m * n] = tgv3d_box(o, (box,) * 3, grid, t, modes, nu,
+                                                        dtype=np.float64).T.reshape(-1)
+        w = Window(data, np.full(S, m, np.int64), np.full(S, n, np.int64),
+                   (np.arange(S, dtype=np.int64) * m * n), np.full(S, m, np.int64),
+                   {"layout": layout})
+    else:
+        blocks = [tgv3d_box(o, (box,) * 3, grid, t, modes, nu, dtype=np.float64)
+                  for o in origins]
+        w = pack_blocks(blocks, dtype=dtype, layout=layout)
+    w.meta.update({"grid": grid, "box": box, "t_end": t_end, "nu": nu, "origins": origins})
+    return w
+
+
+# --------------------------------------------------------------------------
+# Prescribed-spectrum matrices (Haar-orthonormal factors)
+# --------------------------------------------------------------------------
+def haar(rows: int, cols: int, rng: np.random.Generator) -> np.ndarray:
+    """rows x cols matrix with Haar-distributed orthonormal columns (QR of a
+    Gaussian with the sign of diag(R) fixed positive)."""
+    G = rng.standard_normal((rows, cols))
+    Q, R = np.linalg.qr(G)
+    return Q * np.sign(np.diag(R))[None, :]
+
+
+def spectrum_matrix(m: int, n: int, sigma, seed: int) -> np.ndarray:
+    """A = U diag(sigma) V^T, U (m x r) and V (n x r) Haar, r = len(sigma)."""
+    sigma = np.asarray(sigma, dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    U = haar(m, sigma.size, rng)
+    V = haar(n, sigma.size, rng)
+    return (U * sigma[None, :]) @ V.T
+
+
+def lowrank(m: int, n: int, r: int, seed: int) -> np.ndarray:
+    """Exactly rank-r Gaussian product G1 G2^T (FP64)."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((m, r)) @ rng.standard_normal((r, n))
+
+
+def separated_lowrank(m: int, n: int, r: int, seed: int, decay: float = 0.5,
+                      noise: float = 0.0) -> np.ndarray:
+    """Rank-r signal with geometrically decaying singular values plus optional
+    i.i.d. noise: pivots of its sketch are well separated for small r."""
+    sig = decay ** np.arange(r)
+    A = spectrum_matrix(m, n, sig, seed)
+    if noise > 0:
+        A = A + noise * np.random.default_rng(seed + 7919).standard_normal((m, n))
+    return A
