@@ -1,0 +1,330 @@
+"""Throughput of the sketched column-ID hot path on GB300.
+
+One step = one pass of the whole hot path over one window: Gaussian sketch
+(Omega regenerated on the fly), batched pivoted QR + rank decision +
+coefficients, and the fused reconstruction / relative Frobenius error, plus
+the compression factor.  Default workload: the 3D TGV + Fourier field on a
+64^3 grid split into 64 boxes of 16^3 x 5 QoIs (m = 20480), n = 512
+snapshots, k = 20, p = 10, FP32 data, TF32 tensor-core sketch.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+(the only reference this method has) on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "snapshot GB/s compressed at rel. err <=1e-3: mixed-prec batched vs plain FP32"
+WORKLOAD = ("TGV+Fourier 64^3 grid, 64 subdomains of 16^3 x 5 QoIs (m=20480), n=512 snapshots, "
+            "k=20, p=10, FP32 window")
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+            os.unlink(self.path)
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() in ("active", "1"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons),
+                       samples=len(sm))
+        return out
+
+
+def make_window(rank: int = 0, boxes=None):
+    from paper_2103_01380_gb300 import inputs
+    return inputs.tgv3d_window(grid=64, box=16, n=512, seed=2 + rank, boxes=boxes)
+
+
+def cpu_baseline(win, sample_subs: int, precision: str = "tf32"):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    idx = np.linspace(0, win.num_sub - 1, sample_subs).round().astype(int)
+    blocks = [win.block(int(s)) for s in idx]
+    from paper_2103_01380_gb300 import inputs
+    sub = inputs.pack_blocks(blocks, dtype=np.float64)
+    u = {"fp64": 2.0 ** -53, "fp32": 2.0 ** -24, "tf32": 2.0 ** -11}[precision]
+    t0 = time.perf_counter()
+    oracle.spid_batch(sub.data, sub.m, sub.n, sub.off, sub.ld, 30, 20, 0.0, u, 0x5EED0001)
+    dt = time.perf_counter() - t0
+    nbytes = 4.0 * float((sub.m * sub.n).sum())
+    return {"value": nbytes / dt / 1e9, "unit": "GB/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{sample_subs} of {win.num_sub} subdomains (m=20480, n=512), FP64 oracle "
+                      f"sketch+QR+coefficients+error, {dt:.2f} s wall"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    win = make_window(0, boxes=max(args.ref_subs, 1))
+    ts = []
+    nb = None
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        cb = cpu_baseline(win, args.ref_subs)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            ts.append(dt)
+            nb = cb
+    value = float(np.median([nb["value"]]))
+    sample_bytes = 4.0 * 20480 * 512 * args.ref_subs
+    ms = 1e3 * float(np.mean(ts))
+    line = {"impl": "reference", "metric": METRIC, "value": sample_bytes / (ms / 1e3) / 1e9,
+            "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_subdomains": args.ref_subs},
+            "cpu_baseline": {"kind": "oracle", "cores": nb["cores"], "sample": nb["sample"],
+                             "value": sample_bytes / (ms / 1e3) / 1e9, "unit": "GB/s"},
+            "e2e": {"value": sample_bytes / (ms / 1e3) / 1e9, "unit": "GB/s",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="tf32", choices=["tf32", "fp32"])
+    ap.add_argument("--ref-subs", type=int, default=16)
+    ap.add_argument("--cpu-sample", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    from paper_2103_01380_gb300 import build, spid
+    build.build()
+    spid.load_library()
+
+    win = make_window(rank)
+    nbytes = float(win.nbytes_payload())
+    host = torch.from_numpy(win.data).pin_memory()
+    dev = host.cuda()
+    stream = torch.cuda.current_stream()
+    err = torch.zeros(2 * win.num_sub, dtype=torch.float64, device="cuda")
+    tot = torch.zeros(4, dtype=torch.float64, device="cuda")
+
+    def make_plan(precision, flags=0):
+        return spid.Plan.for_window(win, k_max=20, p=10, tol=0.0, precision=precision,
+                                    seed=0x5EED0001, flags=flags)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(plan, steps, warmup, per_stage=True):
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+        for _ in range(warmup):
+            plan.sketch(dev); plan.finalize(); plan.error(dev, err, tot)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(steps):
+            ev[i][0].record(stream)
+            plan.sketch(dev)
+            ev[i][1].record(stream)
+            plan.finalize()
+            ev[i][2].record(stream)
+            plan.error(dev, err, tot)
+            ev[i][3].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        total_ms = t_start.elapsed_time(t_end)
+        sk = [e[0].elapsed_time(e[1]) for e in ev]
+        fi = [e[1].elapsed_time(e[2]) for e in ev]
+        er = [e[2].elapsed_time(e[3]) for e in ev]
+        return total_ms, sk, fi, er
+
+    plan = make_plan(args.precision)
+    with ClockSampler(local) as clk:
+        total_ms, sk, fi, er = timed(plan, args.steps, args.warmup)
+    clocks = clk.summary()
+    t = torch.tensor([total_ms], dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * nbytes * args.steps / (total_ms / 1e3) / 1e9
+
+    # global error / CF across ranks: a host-side sum of four doubles
+    totals = tot.detach().cpu().to(torch.float64)
+    if world > 1:
+        dist.all_reduce(totals)
+    rel_err = float(np.sqrt(totals[0] / totals[1]))
+    cf = float(totals[2] / totals[3])
+    k, J, C = plan.factors()
+
+    # end to end through the public API: pinned host window -> device, full
+    # path, device -> host read of the error sums, every step
+    host_tot = torch.zeros(4, dtype=torch.float64).pin_memory()
+    for _ in range(max(args.warmup, 1)):
+        dev.copy_(host, non_blocking=True)
+        plan.sketch(dev); plan.finalize(); plan.error(dev, err, tot)
+        host_tot.copy_(tot, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_steps = max(3, args.steps // 4)
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        dev.copy_(host, non_blocking=True)
+        plan.sketch(dev); plan.finalize(); plan.error(dev, err, tot)
+        host_tot.copy_(tot, non_blocking=True)
+        stream.synchronize()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    te = torch.tensor([e2e_ms], dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * nbytes / (float(te.item()) / 1e3) / 1e9
+
+    # comparator: plain FP32 (SIMT sketch, one launch per subdomain per stage, no graph)
+    comparator = None
+    if not args.no_comparator:
+        pl = make_plan("fp32", flags=spid.FLAG_PER_SUBDOMAIN)
+        c_ms, c_sk, c_fi, c_er = timed(pl, max(3, args.steps // 4), args.warmup)
+        torch.cuda.synchronize()
+        c_tot = tot.detach().cpu()
+        comparator = {"form": "plain FP32 (SIMT sketch, per-subdomain launches)",
+                      "value": nbytes * max(3, args.steps // 4) / (c_ms / 1e3) / 1e9,
+                      "sketch_gbs": nbytes / (statistics.mean(c_sk) / 1e3) / 1e9,
+                      "rel_err": float(np.sqrt(c_tot[0] / c_tot[1]))}
+        pl.close()
+        pb = make_plan("fp32")
+        b_ms, b_sk, b_fi, b_er = timed(pb, max(3, args.steps // 4), args.warmup)
+        comparator["batched_fp32_value"] = nbytes * max(3, args.steps // 4) / (b_ms / 1e3) / 1e9
+        comparator["batched_fp32_sketch_gbs"] = nbytes / (statistics.mean(b_sk) / 1e3) / 1e9
+        pb.close()
+
+    peak, peak_kind = load_peaks()
+    sk_ms, er_ms, fi_ms = statistics.mean(sk), statistics.mean(er), statistics.mean(fi)
+    dominant = "sketch" if sk_ms >= er_ms else "error"
+    dom_ms = max(sk_ms, er_ms)
+    # algorithmic bytes: sketch reads A once (4 B / element); the error pass reads
+    # A once plus the k skeleton columns of every subdomain
+    alg_bytes = nbytes if dominant == "sketch" else nbytes + 4.0 * 20 * float(win.m.sum())
+    achieved = alg_bytes / (dom_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None}
+
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (tf32 sketch)" if args.precision == "tf32" else "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": args.precision,
+                       "subdomains_per_gpu": win.num_sub, "bytes_per_step_per_gpu": nbytes,
+                       "l2": "inputs (2.68 GB) larger than L2; no flush"},
+            "stages_ms": {"sketch": sk_ms, "finalize": fi_ms, "error": er_ms},
+            "sketch_gbs": nbytes / (sk_ms / 1e3) / 1e9,
+            "error_gbs": nbytes / (er_ms / 1e3) / 1e9,
+            "rel_err": rel_err, "compression_factor": cf,
+            "k_mean": float(np.mean(k)), "k_max": int(np.max(k)),
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": int(nbytes),
+                    "d2h_bytes_per_step": 32},
+            "gpu_launches": 6 * args.steps,
+            "clocks": clocks,
+            "comparator": comparator}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(win, min(args.cpu_sample, win.num_sub))
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

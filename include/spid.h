@@ -1,0 +1,183 @@
+/*
+ * spid.h -- C ABI of the GB300 (sm_103a) sketched column interpolative
+ * decomposition library (libspid.so).
+ *
+ * The method (arXiv 2103.01380, Pacella, Dunton, Doostan, Iaccarino):
+ *   a data matrix A (m x n; rows = grid points x QoIs, columns = time
+ *   snapshots, Section 2) is compressed per spatial subdomain as
+ *   A ~ A(:,J) C.  A Gaussian sketch Y = Omega A (Omega l x m i.i.d. N(0,1),
+ *   l = k_max + p; Section 2, random projection) is accumulated as snapshot
+ *   columns arrive; a column-pivoted QR of Y picks the k skeleton columns J
+ *   (Section 2, A Z = Q R, Algorithm 1 step 3; adaptive rank per Remark 2.1)
+ *   and C = [I_k | R11^-1 R12] Z^T (Section 2, Eq. for C; Algorithms 1-2).
+ *   Subdomains are independent (Section 3.2) and are processed as one batch.
+ *
+ * Conventions shared by every entry point:
+ *   - Window layout ("blocks"): subdomain s is an m[s] x n[s] column-major
+ *     matrix (column j = snapshot j, contiguous rows) that starts at element
+ *     off[s] of one device buffer and has leading dimension ld[s] elements.
+ *     This covers both subdomain-major ([s][j][r]) and snapshot-major
+ *     ([j][s][r]) windows.  Elements are double for SPID_PREC_FP64 and float
+ *     otherwise.  off[s] and ld[s] must be multiples of 16 bytes / element
+ *     size, and the window base must be 16-byte aligned (checked).
+ *   - Omega(i, r), i < l, r < m, is never stored.  It is the Box-Muller
+ *     transform of Philox4x32-10 (Salmon et al., SC'11) with key =
+ *     (seed & 0xffffffff, seed >> 32) and counter = (r, i / 4, 0, 0); words
+ *     (x0, x1) give rows 4g, 4g+1 and (x2, x3) rows 4g+2, 4g+3 of group
+ *     g = i / 4, with u = (x + 0.5) 2^-32, g0 = sqrt(-2 ln ua) cos(2 pi ub),
+ *     g1 = sqrt(-2 ln ua) sin(2 pi ub).  The same Omega serves every
+ *     subdomain (subdomain s uses its first m[s] columns).
+ *   - Pointers named *_host are host memory; *_dev and window/out are device
+ *     memory.  The caller owns the window and every output buffer; the plan
+ *     owns its workspace (sketch Y, partial sums, factors, status word).
+ *   - Every call that takes a stream is asynchronous on that stream unless
+ *     stated otherwise.  A plan must be used from one stream at a time.
+ *   - Argument errors are returned synchronously and launch nothing.  Errors
+ *     found on the device (non-finite sketch, a bounded wait that timed out)
+ *     set a sticky status word read by spid_device_status().  No call ever
+ *     traps or aborts the process.
+ */
+#ifndef SPID_H
+#define SPID_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; 0 is the legacy default stream. */
+typedef struct CUstream_st* spid_stream_t;
+
+typedef struct spid_plan_s* spid_plan_t;
+
+typedef enum {
+  SPID_OK = 0,
+  SPID_ERR_INVALID_ARG = 1,  /* a size, pointer, alignment or mode is invalid */
+  SPID_ERR_CUDA = 2,         /* a CUDA runtime call failed (spid_last_error() says which) */
+  SPID_ERR_OOM = 3,          /* device allocation failed in spid_plan_create */
+  SPID_ERR_STATE = 4,        /* call out of order (e.g. factors before finalize) */
+  SPID_ERR_TIMEOUT = 5,      /* a bounded device wait gave up (device status) */
+  SPID_ERR_NONFINITE = 6,    /* NaN/Inf reached the sketch of some subdomain (device status) */
+  SPID_ERR_UNSUPPORTED = 7   /* valid request this build does not implement */
+} spid_status;
+
+typedef enum {
+  SPID_PREC_FP64 = 0,  /* FP64 window; sketch, QR, solve and error in FP64 (SIMT) */
+  SPID_PREC_FP32 = 1,  /* FP32 window; FP32 SIMT sketch; FP64 pivot norms and solve */
+  SPID_PREC_TF32 = 2   /* FP32 window; tcgen05 TF32 sketch (FP32 accumulate in TMEM,
+                          tiles staged by TMA); FP64 pivot norms and solve */
+} spid_precision;
+
+/* Plain (unbatched) form: one kernel launch per subdomain per stage. */
+#define SPID_FLAG_PER_SUBDOMAIN 1u
+
+typedef struct {
+  int32_t num_sub;        /* number of subdomains S >= 1 */
+  const int32_t* m;       /* host [S]: rows m_s >= 1 */
+  const int32_t* n;       /* host [S]: window length n_s >= 1 (columns) */
+  const int64_t* off;     /* host [S]: element offset of A_s(0,0) in the window */
+  const int64_t* ld;      /* host [S]: leading dimension (elements), >= m_s */
+  int32_t k_max;          /* maximum rank, 1 <= k_max; k_s <= min(k_max, n_s) */
+  int32_t p;              /* oversampling, p >= 0; l = k_max + p <= 64 */
+  double tol;             /* 0: fixed rank k_max.  > 0: smallest k with
+                             ||R22||_F <= tol ||Y||_F (Remark 2.1 reading) */
+  int32_t precision;      /* spid_precision */
+  uint32_t flags;         /* SPID_FLAG_* */
+  uint64_t seed;          /* Omega key */
+} spid_plan_desc;
+
+/* Create a plan: validates the descriptor and allocates ALL device
+ * workspace (later calls allocate nothing).  Rows m_s up to 2^31-1, columns
+ * up to 2^20 per subdomain.  Returns SPID_ERR_OOM if device memory runs out.
+ * The plan is bound to the current CUDA device. */
+spid_status spid_plan_create(const spid_plan_desc* desc, spid_plan_t* plan_out);
+
+/* Release every resource of the plan.  Synchronizes the device first. */
+spid_status spid_plan_destroy(spid_plan_t plan);
+
+/* l = k_max + p, l_pad (row stride of the stored sketch, a multiple of 16),
+ * and the plan's device workspace in bytes.  Any pointer may be NULL. */
+spid_status spid_plan_info(spid_plan_t plan, int32_t* l, int32_t* l_pad,
+                           int64_t* workspace_bytes);
+
+/* Sketch accumulation (Section 2, Y = Omega A), step a2 of the hot path:
+ * for every subdomain s, Y_s(:, j) = Omega(:, 0:m_s) A_s(:, j) for the
+ * window columns j in [col0, min(col0 + ncols, n_s)).  Columns are
+ * independent, so a window may be sketched in any number of calls (one per
+ * snapshot or per micro-batch); columns never sketched stay zero after
+ * spid_plan_create / spid_reset.  window: device, layout as above. */
+spid_status spid_sketch(spid_plan_t plan, const void* window, int32_t col0, int32_t ncols,
+                        spid_stream_t stream);
+
+/* Zero the stored sketch (start a new window).  Asynchronous. */
+spid_status spid_reset(spid_plan_t plan, spid_stream_t stream);
+
+/* Finalize (steps a3-a5): batched Householder QR with column pivoting of
+ * every Y_s (FP64 pivot norms, ties to the lowest column index), the rank
+ * decision (fixed k_max or adaptive tol, then the guard |R_jj| > 2 u |R_00|
+ * with u the unit roundoff of the sketch arithmetic), the FP64
+ * back-substitution T = R11^-1 R12 and C with C(:, J) = I exactly. */
+spid_status spid_finalize(spid_plan_t plan, spid_stream_t stream);
+
+/* Relative Frobenius error (Section 5.1; step a6): for every subdomain,
+ * err_dev[2 s] = ||A_s - A_s(:,J_s) C_s||_F^2 and err_dev[2 s + 1] =
+ * ||A_s||_F^2 (FP64 reduction in a fixed order), and total_dev[0..3] =
+ * {sum e2, sum a2, sum m_s n_s, sum k_s (m_s + n_s)}, so the global relative
+ * error is sqrt(total[0] / total[1]) and the compression factor (Section 2,
+ * Eq. for CF, aggregated over subdomains) is total[2] / total[3].
+ * err_dev may be NULL.  Requires spid_finalize. */
+spid_status spid_error(spid_plan_t plan, const void* window, double* err_dev, double* total_dev,
+                       spid_stream_t stream);
+
+/* Reconstruction A_hat_s = A_s(:, J_s) C_s written to out (same layout,
+ * offsets and leading dimensions as the window; rows between m_s and ld_s
+ * are not touched).  Requires spid_finalize. */
+spid_status spid_reconstruct(spid_plan_t plan, const void* window, void* out,
+                             spid_stream_t stream);
+
+/* Copy the factors to the host (synchronizes the stream): k_host[S],
+ * J_host[S * k_max] (pivot order, -1 past k_s), and C_host packed per
+ * subdomain as k_max x n_s row-major blocks, block s at element
+ * k_max * sum_{s' < s} n_{s'} (rows >= k_s are zero); element type as the
+ * window.  Any pointer may be NULL. */
+spid_status spid_get_factors(spid_plan_t plan, int32_t* k_host, int32_t* J_host, void* C_host,
+                             spid_stream_t stream);
+
+/* Copy the stored sketch to the host (synchronizes): Y_s as n_s x l_pad
+ * (row j = column j of Y_s, entries i >= l are zero), block s at element
+ * l_pad * sum_{s' < s} n_{s'}; element type as the window. */
+spid_status spid_get_sketch(spid_plan_t plan, void* Y_host, spid_stream_t stream);
+
+/* Synchronize the stream and return the sticky device status
+ * (SPID_OK, SPID_ERR_TIMEOUT or SPID_ERR_NONFINITE), then clear it. */
+spid_status spid_device_status(spid_plan_t plan, spid_stream_t stream);
+
+/* Omega(i, r0 + c) for i < l, c < nrows into out_dev as nrows x l row-major
+ * (row c holds Omega(:, r0 + c)); FP64 (precision SPID_PREC_FP64) or FP32
+ * (the value every FP32 sketch uses).  Step a1, exposed for checking. */
+spid_status spid_omega(uint64_t seed, int64_t r0, int32_t nrows, int32_t l, int32_t precision,
+                       void* out_dev, spid_stream_t stream);
+
+/* Philox4x32-10 of count counters (ctr_dev: count x 4 words) under the key
+ * {key0, key1}; out_dev: count x 4 words.  Exposed for checking. */
+spid_status spid_philox(const uint32_t* ctr_dev, uint32_t key0, uint32_t key1, uint32_t* out_dev,
+                        int64_t count, spid_stream_t stream);
+
+/* Aggregate compression factor (Section 2, Eq. for CF; Section 3.2):
+ * sum m_s n_s / sum k_s (m_s + n_s) over host arrays (step a7).  Host-only
+ * arithmetic; returns +inf when every k_s is 0. */
+double spid_compression_factor(int32_t num_sub, const int32_t* m, const int32_t* n,
+                               const int32_t* k);
+
+/* Human-readable name of a status code (static storage). */
+const char* spid_status_string(spid_status status);
+
+/* Detail of the last error raised on the calling thread ("" if none). */
+const char* spid_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPID_H */

@@ -1,0 +1,217 @@
+// error.cu -- reconstruction A_hat = A(:,J) C (Section 2, column ID form of
+// Algorithm 2) fused with the relative Frobenius error of Section 5.1:
+// ||A - A_hat||_F^2 and ||A||_F^2 per subdomain, reduced in FP64 in a fixed
+// order.
+//
+// A unit is (subdomain, 512-row block, 256-column block).  The CTA stages the
+// coefficient block C(:, cols) and, per 128-row tile, the skeleton rows
+// A(rows, J) in shared memory, then streams A once: lane l of warp w owns rows
+// 4l..4l+3 of the tile and 4 columns at a time, so each k-step is two shared
+// loads (one a broadcast) feeding 16 FMAs; A is read with 16-byte loads,
+// 512 contiguous bytes per warp per column.  Per-thread sums stay in the
+// working precision over 16 elements, then accumulate in FP64.
+#include "spid_internal.cuh"
+
+namespace spid {
+
+
+
+namespace {
+
+template <typename T> struct V4;   // 4 consecutive elements
+template <> struct V4<float> {
+  static __device__ __forceinline__ void load(const float* p, float (&v)[4]) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  }
+  static __device__ __forceinline__ void store(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  static __device__ __forceinline__ void lds(const float* p, float (&v)[4]) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  }
+};
+template <> struct V4<double> {
+  static __device__ __forceinline__ void load(const double* p, double (&v)[4]) {
+    const double2 x = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 y = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+  }
+  static __device__ __forceinline__ void store(double* p, const double (&v)[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+  static __device__ __forceinline__ void lds(const double* p, double (&v)[4]) {
+    const double2 x = reinterpret_cast<const double2*>(p)[0];
+    const double2 y = reinterpret_cast<const double2*>(p)[1];
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+  }
+};
+
+template <typename T, bool WRITE>
+__global__ void __launch_bounds__(256) error_kernel(ErrArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int u = blockIdx.x + a.unit_base;
+  const int s = a.unit_sub[u];
+  const int row0 = a.unit_row0[u], col0 = a.unit_col0[u];
+  const int m = a.m[s], n = a.n[s];
+  const int kk = a.k[s];
+  const int ncb = min(kErrColBlock, n - col0);
+  const int nrb = min(kErrRowBlock, m - row0);
+  T* Cs = reinterpret_cast<T*>(smem_raw);                 // [kk][kErrColBlock]
+  T* AJ = Cs + (size_t)a.k_max * kErrColBlock;             // [kk][kErrTile]
+  const T* A = static_cast<const T*>(a.window) + a.off[s];
+  const int64_t ld = a.ld[s];
+  const T* Cg = static_cast<const T*>(a.C) + a.coff[s];
+  const int32_t* Jg = a.J + (int64_t)s * a.k_max;
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+
+  for (int e = tid; e < kk * kErrColBlock; e += 256) {
+    const int p = e / kErrColBlock, jj = e % kErrColBlock;
+    Cs[e] = (jj < ncb) ? Cg[(int64_t)p * n + col0 + jj] : T(0);
+  }
+  double se = 0.0, sa = 0.0;
+  for (int t0 = 0; t0 < nrb; t0 += kErrTile) {
+    const int rt = row0 + t0;                       // first row of the tile
+    __syncthreads();
+    for (int e = tid; e < kk * kErrTile; e += 256) {
+      const int p = e / kErrTile, r = e % kErrTile;
+      AJ[e] = (rt + r < m) ? A[(int64_t)Jg[p] * ld + rt + r] : T(0);
+    }
+    __syncthreads();
+    const int r = rt + 4 * lane;                    // this lane's 4 rows
+    const bool full_rows = (r + 4 <= m);
+    for (int cg = 4 * warp; cg < ncb; cg += 32) {   // 4 columns per warp per pass
+      T acc[4][4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = T(0);
+      T av[4][4];   // A(r .. r+3, col0 + cg + y)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int col = col0 + cg + y;
+        const T* src = A + (int64_t)col * ld + r;
+        if (col < n && full_rows) {
+          V4<T>::load(src, av[y]);
+        } else {
+#pragma unroll
+          for (int x = 0; x < 4; ++x) av[y][x] = (col < n && r + x < m) ? src[x] : T(0);
+        }
+      }
+      for (int p = 0; p < kk; ++p) {
+        T aj[4], cc[4];
+        V4<T>::lds(AJ + p * kErrTile + 4 * lane, aj);
+        V4<T>::lds(Cs + p * kErrColBlock + cg, cc);
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = fma(aj[x], cc[y], acc[x][y]);
+      }
+      T le = T(0), la = T(0);
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          const T d = av[y][x] - acc[x][y];
+          le = fma(d, d, le);
+          la = fma(av[y][x], av[y][x], la);
+        }
+        if (WRITE) {
+          const int col = col0 + cg + y;
+          if (col < n) {
+            T* dst = static_cast<T*>(a.out) + a.off[s] + (int64_t)col * ld + r;
+            T o[4] = {acc[0][y], acc[1][y], acc[2][y], acc[3][y]};
+            if (full_rows) {
+              V4<T>::store(dst, o);
+            } else {
+#pragma unroll
+              for (int x = 0; x < 4; ++x)
+                if (r + x < m) dst[x] = o[x];
+            }
+          }
+        }
+      }
+      se += (double)le;
+      sa += (double)la;
+    }
+  }
+  // block reduction in a fixed order
+  __shared__ double red[2][8];
+  for (int o = 16; o > 0; o >>= 1) {
+    se += __shfl_down_sync(0xffffffffu, se, o);
+    sa += __shfl_down_sync(0xffffffffu, sa, o);
+  }
+  if (lane == 0) { red[0][warp] = se; red[1][warp] = sa; }
+  __syncthreads();
+  if (tid == 0) {
+    double te = 0.0, ta = 0.0;
+    for (int w = 0; w < 8; ++w) { te += red[0][w]; ta += red[1][w]; }
+    a.part[2 * (int64_t)u] = te;
+    a.part[2 * (int64_t)u + 1] = ta;
+  }
+}
+
+__global__ void error_finish_kernel(ErrFinishArgs a) {
+  // one thread per subdomain, then one warp-free serial total (fixed order)
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.S; s += gridDim.x * blockDim.x) {
+    double e = 0.0, q = 0.0;
+    for (int u = a.unit_ptr[s]; u < a.unit_ptr[s + 1]; ++u) {
+      e += a.part[2 * (int64_t)u];
+      q += a.part[2 * (int64_t)u + 1];
+    }
+    a.sub_err[2 * s] = e;
+    a.sub_err[2 * s + 1] = q;
+    if (a.err) { a.err[2 * s] = e; a.err[2 * s + 1] = q; }
+  }
+}
+
+__global__ void error_total_kernel(ErrFinishArgs a) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double te = 0.0, ta = 0.0, mn = 0.0, kd = 0.0;
+  for (int s = 0; s < a.S; ++s) {
+    te += a.sub_err[2 * s];
+    ta += a.sub_err[2 * s + 1];
+    mn += (double)a.m[s] * (double)a.n[s];
+    kd += (double)a.k[s] * ((double)a.m[s] + (double)a.n[s]);
+  }
+  if (a.total) { a.total[0] = te; a.total[1] = ta; a.total[2] = mn; a.total[3] = kd; }
+}
+
+}  // namespace
+
+size_t error_smem_bytes(int k_max, bool fp64) {
+  return (fp64 ? 8 : 4) * (size_t)k_max * (kErrColBlock + kErrTile) + 16;
+}
+
+cudaError_t launch_error(const ErrArgs& a, int units, bool fp64, cudaStream_t st) {
+  if (units <= 0) return cudaSuccess;
+  const size_t smem = error_smem_bytes(a.k_max, fp64);
+  cudaError_t e = cudaSuccess;
+#define SPID_LAUNCH_ERR(T, W)                                                               \
+  do {                                                                                      \
+    e = cudaFuncSetAttribute(error_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)smem);                                                    \
+    if (e != cudaSuccess) return e;                                                         \
+    error_kernel<T, W><<<units, 256, smem, st>>>(a);                                        \
+  } while (0)
+  const bool w = a.out != nullptr;
+  if (fp64) {
+    if (w) SPID_LAUNCH_ERR(double, true); else SPID_LAUNCH_ERR(double, false);
+  } else {
+    if (w) SPID_LAUNCH_ERR(float, true); else SPID_LAUNCH_ERR(float, false);
+  }
+#undef SPID_LAUNCH_ERR
+  return cudaGetLastError();
+}
+
+cudaError_t launch_error_finish(const ErrFinishArgs& a, cudaStream_t st) {
+  error_finish_kernel<<<(a.S + 127) / 128, 128, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  error_total_kernel<<<1, 32, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace spid

@@ -1,0 +1,221 @@
+// sketch_simt.cu -- Gaussian sketch Y = Omega A on the CUDA cores (FP64 and
+// plain FP32 forms), Section 2 (random projection B = Omega A).
+//
+// Work decomposition (shared with the tensor-core kernel): the host splits
+// every problem (subdomain x column group) into chunks of 32 rows and hands
+// each CTA a contiguous, byte-balanced range of chunks ("segments").  A CTA
+// keeps the whole column group's partial sketch in registers while it walks
+// its rows, regenerating Omega(:, rows) once per chunk and reusing it for all
+// columns of the group; at the end of a segment it writes its partial to a
+// private slot, and spid_reduce_partials sums the slots in a fixed order.
+#include "spid_internal.cuh"
+
+namespace spid {
+
+namespace {
+
+template <typename T> struct Vec;
+template <> struct Vec<float> { using type = float4; static constexpr int width = 4; };
+template <> struct Vec<double> { using type = double2; static constexpr int width = 2; };
+
+template <typename T>
+__device__ __forceinline__ void store_vec(T* dst, const typename Vec<T>::type& v);
+template <>
+__device__ __forceinline__ void store_vec<float>(float* d, const float4& v) {
+  *reinterpret_cast<float4*>(d) = v;
+}
+template <>
+__device__ __forceinline__ void store_vec<double>(double* d, const double2& v) {
+  *reinterpret_cast<double2*>(d) = v;
+}
+
+constexpr int kThreads = 256;
+constexpr int kJGroups = 64;  // thread = (i-group in 0..3) x (j-group in 0..63)
+
+// TI: Omega rows per thread (l_pad = 4 TI); TJ: columns per thread (the
+// column group holds up to 64 TJ columns).
+template <typename T, int TI, int TJ>
+__global__ void __launch_bounds__(kThreads, (TI * TJ <= 64) ? 2 : 1)
+sketch_simt_kernel(SketchArgs args) {
+  constexpr int LP = 4 * TI;
+  constexpr int CG = kJGroups * TJ;
+  constexpr int CGP = CG + 1;  // odd row stride: conflict-free transposed stores
+  constexpr int VW = Vec<T>::width;
+  constexpr int VPC = kChunkRows / VW;  // vectors per column per chunk
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* As = reinterpret_cast<T*>(smem_raw);       // [kChunkRows][CGP]
+  T* Om = As + kChunkRows * CGP;                // [kChunkRows][LP]
+  // Om must be 16-byte aligned for vector loads
+  Om = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(Om) + 15) & ~uintptr_t(15));
+
+  const int tid = threadIdx.x;
+  const int ig = tid / kJGroups;
+  const int jg = tid % kJGroups;
+  const int cta = blockIdx.x + args.cta_base;
+  const uint2 key = philox_key(args.seed);
+  const T* window = static_cast<const T*>(args.window);
+  T* partial = static_cast<T*>(args.partial);
+  const int l = args.l;
+
+  const int s0 = args.seg_ptr[cta], s1 = args.seg_ptr[cta + 1];
+  for (int si = s0; si < s1; ++si) {
+    const Segment seg = args.segs[si];
+    const Problem pb = args.probs[seg.prob];
+    const T* A = window + pb.off + (int64_t)pb.col0 * pb.ld;
+    const int nc = pb.ncols;
+
+    T acc[TJ][TI];
+#pragma unroll
+    for (int u = 0; u < TJ; ++u)
+#pragma unroll
+      for (int v = 0; v < TI; ++v) acc[u][v] = T(0);
+
+    for (int ch = seg.chunk0; ch < seg.chunk1; ++ch) {
+      const int r0 = ch * kChunkRows;
+      // ---- stage A(r0 : r0+32, col group) transposed into As[row][col]
+      for (int v = tid; v < nc * VPC; v += kThreads) {
+        const int c = v / VPC, q = v % VPC;
+        const int r = r0 + q * VW;
+        const T* src = A + (int64_t)c * pb.ld + r;
+        T vals[VW];
+        if (r + VW <= pb.m) {
+          const typename Vec<T>::type x = __ldg(reinterpret_cast<const typename Vec<T>::type*>(src));
+          const T* xs = reinterpret_cast<const T*>(&x);
+#pragma unroll
+          for (int u = 0; u < VW; ++u) vals[u] = xs[u];
+        } else {
+#pragma unroll
+          for (int u = 0; u < VW; ++u) vals[u] = (r + u < pb.m) ? src[u] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < VW; ++u) As[(q * VW + u) * CGP + c] = vals[u];
+      }
+      // columns of the group past nc stay stale: their accumulators are never stored
+      // ---- Omega(:, r0 : r0+32) into Om[row][i]
+      for (int task = tid; task < kChunkRows * (LP / 4); task += kThreads) {
+        const int k = task % kChunkRows, g = task / kChunkRows;
+        T w[4] = {T(0), T(0), T(0), T(0)};
+        if (4 * g < l && r0 + k < pb.m) {
+          omega_group<T>(key, (uint32_t)(r0 + k), (uint32_t)g, w);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (4 * g + u >= l) w[u] = T(0);
+        }
+        typename Vec<T>::type* dst = reinterpret_cast<typename Vec<T>::type*>(Om + k * LP + 4 * g);
+        if constexpr (VW == 4) {
+          dst[0] = make_float4(w[0], w[1], w[2], w[3]);
+        } else {
+          dst[0] = make_double2(w[0], w[1]);
+          dst[1] = make_double2(w[2], w[3]);
+        }
+      }
+      __syncthreads();
+      // ---- acc[j][i] += A(r, j) Omega(i, r), rows in ascending order
+#pragma unroll 4
+      for (int k = 0; k < kChunkRows; ++k) {
+        T a[TJ], w[TI];
+#pragma unroll
+        for (int u = 0; u < TJ; ++u) a[u] = As[k * CGP + jg + kJGroups * u];
+#pragma unroll
+        for (int v = 0; v < TI; v += VW) {
+          const typename Vec<T>::type x =
+              *reinterpret_cast<const typename Vec<T>::type*>(Om + k * LP + ig * TI + v);
+          const T* xs = reinterpret_cast<const T*>(&x);
+#pragma unroll
+          for (int u = 0; u < VW; ++u) w[v + u] = xs[u];
+        }
+#pragma unroll
+        for (int u = 0; u < TJ; ++u)
+#pragma unroll
+          for (int v = 0; v < TI; ++v) acc[u][v] = fma(a[u], w[v], acc[u][v]);
+      }
+      __syncthreads();
+    }
+    // ---- partial slot: [col][l_pad]
+    T* out = partial + args.slot_off[seg.slot];
+#pragma unroll
+    for (int u = 0; u < TJ; ++u) {
+      const int j = jg + kJGroups * u;
+      if (j < nc) {
+#pragma unroll
+        for (int v = 0; v < TI; v += VW) {
+          typename Vec<T>::type x;
+          T* xs = reinterpret_cast<T*>(&x);
+#pragma unroll
+          for (int q = 0; q < VW; ++q) xs[q] = acc[u][v + q];
+          store_vec<T>(out + (int64_t)j * LP + ig * TI + v, x);
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int TI, int TJ>
+cudaError_t launch_one(const SketchArgs& a, int grid, cudaStream_t st) {
+  constexpr int LP = 4 * TI;
+  constexpr int CGP = kJGroups * TJ + 1;
+  const size_t smem = sizeof(T) * (size_t)kChunkRows * (CGP + LP) + 16;
+  auto k = sketch_simt_kernel<T, TI, TJ>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Column-group size of the SIMT sketch for a given element size.
+int sketch_simt_group_cols(bool fp64) { return fp64 ? kJGroups * 4 : kJGroups * 8; }
+
+cudaError_t launch_sketch_simt(const SketchArgs& a, int grid, bool fp64, cudaStream_t st) {
+  if (grid <= 0) return cudaSuccess;
+  if (fp64) {
+    switch (a.l_pad) {
+      case 16: return launch_one<double, 4, 4>(a, grid, st);
+      case 32: return launch_one<double, 8, 4>(a, grid, st);
+      case 48: return launch_one<double, 12, 4>(a, grid, st);
+      case 64: return launch_one<double, 16, 4>(a, grid, st);
+    }
+  } else {
+    switch (a.l_pad) {
+      case 16: return launch_one<float, 4, 8>(a, grid, st);
+      case 32: return launch_one<float, 8, 8>(a, grid, st);
+      case 48: return launch_one<float, 12, 8>(a, grid, st);
+      case 64: return launch_one<float, 16, 8>(a, grid, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-order reduction of partial slots into the stored sketch:
+// Y_s(:, col0 + j) = sum over the problem's slots (in schedule order).
+// ---------------------------------------------------------------------------
+
+
+template <typename T>
+__global__ void __launch_bounds__(256) reduce_partials_kernel(ReduceArgs a) {
+  const int p = blockIdx.x + a.prob_base;
+  const Problem pb = a.probs[p];
+  const int q0 = a.pslot_ptr[p], q1 = a.pslot_ptr[p + 1];
+  const T* part = static_cast<const T*>(a.partial);
+  T* Y = static_cast<T*>(a.Y) + a.yoff[pb.sub] + (int64_t)pb.col0 * a.l_pad;
+  const int64_t total = (int64_t)pb.ncols * a.l_pad;
+  for (int64_t e = threadIdx.x + (int64_t)blockIdx.y * blockDim.x; e < total;
+       e += (int64_t)blockDim.x * gridDim.y) {
+    T s = T(0);
+    for (int q = q0; q < q1; ++q) s += part[a.slot_off[a.pslots[q]] + e];
+    Y[e] = s;
+  }
+}
+
+cudaError_t launch_reduce_partials(const ReduceArgs& a, int nprob, bool fp64, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  dim3 grid(nprob, 4);
+  if (fp64) reduce_partials_kernel<double><<<grid, 256, 0, st>>>(a);
+  else reduce_partials_kernel<float><<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace spid

@@ -1,0 +1,377 @@
+// sketch_tc.cu -- Gaussian sketch Y = Omega A (Section 2, random projection
+// B = Omega A) on the 5th-generation tensor cores of sm_103a.
+//
+// The contraction is computed transposed, Y^T = A^T Omega^T:
+//   MMA M = 128 window columns (snapshots), N = l_pad (rows of Omega),
+//   K = rows of A, 32 rows (one 128-byte swizzle row of FP32) per chunk.
+// A's columns are contiguous in rows, so a [32 rows x 128 columns] box loaded
+// by TMA with 128-byte swizzling is exactly the K-major canonical layout the
+// MMA reads; Omega(:, rows) is regenerated from Philox each chunk by four
+// warps directly into the same swizzled K-major layout and reused for every
+// 128-column tile of the column group; the accumulators live in TMEM.
+//
+// Warp roles (192 threads):
+//   warp 0      TMA producer (one elected lane)
+//   warp 1      TMEM allocator + MMA issuer (one elected lane)
+//   warps 2..5  Omega generators, then the TMEM -> partial-slot epilogue
+//               (warp w reads TMEM lanes 32 (w % 4) .. +31)
+// Every mbarrier wait is bounded (kWaitLimitNs); on timeout the CTA records
+// kStatusTimeout, drains its own copies and MMAs (again bounded), frees TMEM
+// and returns.
+#include <cuda.h>
+
+#include "spid_internal.cuh"
+
+namespace spid {
+
+namespace {
+
+constexpr int kTcThreads = 192;
+constexpr int kTileCols = 128;                 // MMA M
+constexpr int kTileBytes = kTileCols * 128;    // 128 columns x 32 FP32 rows
+constexpr int kMaxStages = 8;
+
+struct TcArgs {
+  SketchArgs s;
+  int32_t stages;      // pipeline depth
+  int32_t max_tiles;   // 128-column tiles per column group (<= 4)
+  int32_t acc_stride;  // TMEM columns per tile accumulator (multiple of 32 >= l_pad)
+  int32_t tmem_cols;   // power of two >= max_tiles * acc_stride
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase with the given parity; false on timeout or abort.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                       int* status, bool honour_abort = true) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 127u) == 0) {
+      if (honour_abort && *abort_flag) return false;
+      if (globaltimer_ns() - t0 > kWaitLimitNs) {
+        *abort_flag = 1;
+        raise_status(status, kStatusTimeout);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// K-major operand, 128-byte swizzle: 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu)       // start address
+         | ((uint64_t)1 << 16)                    // leading byte offset (unused when swizzled)
+         | ((uint64_t)(1024 >> 4) << 32)          // stride byte offset
+         | ((uint64_t)1 << 46)                    // descriptor version
+         | ((uint64_t)2 << 61);                   // SWIZZLE_128B
+}
+
+// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major.
+__device__ __forceinline__ uint32_t tf32_idesc(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32"
+      " {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) sketch_tf32_kernel(const TcArgs args) {
+  extern __shared__ unsigned char smem_raw[];
+  // 1024-byte alignment for the 128-byte swizzle atoms
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const SketchArgs& a = args.s;
+  const int S = args.stages;
+  const int l_pad = a.l_pad;
+  const int omega_bytes = l_pad * 128;
+  unsigned char* smem_A = smem;                                        // S x max_tiles x 16 KB
+  unsigned char* smem_O = smem_A + (size_t)S * args.max_tiles * kTileBytes;  // S x l_pad x 128 B
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_O + (size_t)S * omega_bytes);
+  uint64_t* full = bars;                       // [S] TMA bytes landed
+  uint64_t* empty = bars + kMaxStages;         // [S] MMAs that read the stage completed
+  uint64_t* ofull = bars + 2 * kMaxStages;     // [S] Omega written (128 arrivals)
+  uint64_t* accum = bars + 3 * kMaxStages;     // accumulators of a segment complete
+  uint64_t* drain = bars + 3 * kMaxStages + 1; // abort path: every issued MMA complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kMaxStages + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  const int cta = blockIdx.x + a.cta_base;
+  const int seg0 = a.seg_ptr[cta], seg1 = a.seg_ptr[cta + 1];
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_addr(&full[s]), 1);
+      mbar_init(smem_addr(&empty[s]), 1);
+      mbar_init(smem_addr(&ofull[s]), 128);
+    }
+    mbar_init(smem_addr(accum), 1);
+    mbar_init(smem_addr(drain), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(tmem_slot)),
+                 "r"(args.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      const CUtensorMap* tmaps = static_cast<const CUtensorMap*>(a.tmaps);
+      for (int si = seg0; si < seg1 && ok; ++si) {
+        const Segment seg = a.segs[si];
+        const Problem pb = a.probs[seg.prob];
+        const int nt = (pb.ncols + kTileCols - 1) / kTileCols;
+        const CUtensorMap* tm = tmaps + pb.sub;
+        for (int ch = seg.chunk0; ch < seg.chunk1; ++ch, ++it) {
+          const int st = it % S;
+          const uint32_t ph = (uint32_t)(it / S) & 1u;
+          if (!mbar_wait(smem_addr(&empty[st]), ph ^ 1u, abort_flag, a.status)) { ok = false; break; }
+          const uint32_t fb = smem_addr(&full[st]);
+          mbar_arrive_expect_tx(fb, (uint32_t)(nt * kTileBytes));
+          for (int t = 0; t < nt; ++t)
+            tma_load_2d(smem_addr(smem_A + ((size_t)st * args.max_tiles + t) * kTileBytes), tm,
+                        ch * kChunkRows, pb.col0 + t * kTileCols, fb);
+        }
+      }
+      // Drain: every issued stage's bytes must have landed before the CTA exits.
+      const int first = it - S > 0 ? it - S : 0;
+      for (int j = first; j < it; ++j)
+        mbar_wait(smem_addr(&full[j % S]), (uint32_t)(j / S) & 1u, abort_flag, a.status, false);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true, issued = false;
+      const uint32_t idesc = tf32_idesc(kTileCols, l_pad);
+      for (int si = seg0; si < seg1 && ok; ++si) {
+        const Segment seg = a.segs[si];
+        const Problem pb = a.probs[seg.prob];
+        const int nt = (pb.ncols + kTileCols - 1) / kTileCols;
+        for (int ch = seg.chunk0; ch < seg.chunk1; ++ch, ++it) {
+          const int st = it % S;
+          const uint32_t ph = (uint32_t)(it / S) & 1u;
+          if (!mbar_wait(smem_addr(&full[st]), ph, abort_flag, a.status)) { ok = false; break; }
+          if (!mbar_wait(smem_addr(&ofull[st]), ph, abort_flag, a.status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a0 = smem_addr(smem_A + (size_t)st * args.max_tiles * kTileBytes);
+          const uint32_t b0 = smem_addr(smem_O + (size_t)st * omega_bytes);
+          for (int t = 0; t < nt; ++t) {
+            const uint64_t ad = sw128_kmajor_desc(a0 + t * kTileBytes);
+            const uint64_t bd = sw128_kmajor_desc(b0);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)   // K = 8 TF32 (32 bytes) per MMA
+              umma_tf32(tmem_base + (uint32_t)(t * args.acc_stride), ad + 2 * kk, bd + 2 * kk,
+                        idesc, (ch > seg.chunk0 || kk > 0) ? 1u : 0u);
+          }
+          issued = true;
+          umma_commit(smem_addr(&empty[st]));
+          if (ch == seg.chunk1 - 1) umma_commit(smem_addr(accum));
+        }
+      }
+      // Every issued MMA must be complete before TMEM is released.
+      if (issued) {
+        umma_commit(smem_addr(drain));
+        mbar_wait(smem_addr(drain), 0u, abort_flag, a.status, false);
+      }
+    }
+  } else {
+    // ------------------------------------------------ Omega generators + epilogue
+    const int gtid = threadIdx.x - 64;            // 0..127
+    const int quad = warp & 3;                    // TMEM lane quadrant of this warp
+    const uint2 key = philox_key(a.seed);
+    const int groups = l_pad / 4;
+    float* partial = static_cast<float*>(a.partial);
+    int it = 0, segi = 0;
+    bool ok = true;
+    auto epilogue = [&](const Segment& seg, int seg_index) -> bool {
+      if (!mbar_wait(smem_addr(accum), (uint32_t)seg_index & 1u, abort_flag, a.status))
+        return false;
+      tc_fence_after();
+      const Problem pb = a.probs[seg.prob];
+      const int nt = (pb.ncols + kTileCols - 1) / kTileCols;
+      float* out = partial + a.slot_off[seg.slot];
+      for (int t = 0; t < nt; ++t) {
+        const int j = t * kTileCols + quad * 32 + lane;
+        for (int c = 0; c < l_pad; c += 16) {
+          uint32_t r[16];
+          __syncwarp();
+          tmem_ld16(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(t * args.acc_stride + c),
+                    r);
+          tmem_ld_wait();
+          if (j < pb.ncols) {
+            float4* dst = reinterpret_cast<float4*>(out + (int64_t)j * l_pad + c);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                   __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+          }
+        }
+      }
+      tc_fence_before();
+      return true;
+    };
+    for (int si = seg0; si < seg1 && ok; ++si, ++segi) {
+      const Segment seg = a.segs[si];
+      if (si > seg0 && !epilogue(a.segs[si - 1], segi - 1)) { ok = false; break; }
+      const Problem pb = a.probs[seg.prob];
+      for (int ch = seg.chunk0; ch < seg.chunk1; ++ch, ++it) {
+        const int st = it % S;
+        const uint32_t ph = (uint32_t)(it / S) & 1u;
+        if (!mbar_wait(smem_addr(&empty[st]), ph ^ 1u, abort_flag, a.status)) { ok = false; break; }
+        unsigned char* ob = smem_O + (size_t)st * omega_bytes;
+        const int r0 = ch * kChunkRows;
+        for (int task = gtid; task < kChunkRows * groups; task += 128) {
+          const int k = task % kChunkRows, g = task / kChunkRows;
+          float w[4] = {0.f, 0.f, 0.f, 0.f};
+          if (4 * g < a.l && r0 + k < pb.m) {
+            omega_group<float>(key, (uint32_t)(r0 + k), (uint32_t)g, w);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (4 * g + u >= a.l) w[u] = 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = 4 * g + u;   // row of Omega = MMA N index
+            const uint32_t off = (uint32_t)((i >> 3) * 1024 + (i & 7) * 128 +
+                                            ((((k >> 2) ^ (i & 7))) << 4) + ((k & 3) << 2));
+            *reinterpret_cast<float*>(ob + off) = w[u];
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(smem_addr(&ofull[st]));
+      }
+    }
+    if (ok && seg1 > seg0) epilogue(a.segs[seg1 - 1], segi - 1);
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(args.tmem_cols)
+                 : "memory");
+  }
+}
+
+}  // namespace
+
+int sketch_tc_group_cols() { return 4 * kTileCols; }
+
+// Dynamic shared memory the TF32 sketch needs for a pipeline of `stages`.
+size_t sketch_tc_smem_bytes(int stages, int max_tiles, int l_pad) {
+  return 1024 + (size_t)stages * ((size_t)max_tiles * kTileBytes + (size_t)l_pad * 128) +
+         (3 * kMaxStages + 2) * sizeof(uint64_t) + 16;
+}
+
+int sketch_tc_max_stages() { return kMaxStages; }
+
+cudaError_t launch_sketch_tc(const SketchArgs& s, int grid, int stages, int max_tiles,
+                             cudaStream_t st) {
+  if (grid <= 0) return cudaSuccess;
+  TcArgs a;
+  a.s = s;
+  a.stages = stages;
+  a.max_tiles = max_tiles;
+  a.acc_stride = (s.l_pad + 31) / 32 * 32;
+  int need = max_tiles * a.acc_stride;
+  int cols = 32;
+  while (cols < need) cols *= 2;
+  a.tmem_cols = cols;
+  if (cols > 512 || stages < 1 || stages > kMaxStages || max_tiles < 1 || max_tiles > 4)
+    return cudaErrorInvalidValue;
+  const size_t smem = sketch_tc_smem_bytes(stages, max_tiles, s.l_pad);
+  cudaError_t e = cudaFuncSetAttribute(sketch_tf32_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  sketch_tf32_kernel<<<grid, kTcThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace spid

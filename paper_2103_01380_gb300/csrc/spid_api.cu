@@ -1,0 +1,786 @@
+// spid_api.cu -- the C ABI of libspid (include/spid.h): plan creation, the
+// per-call work schedules and the kernel launches of the hot path
+//   sketch (a1-a2) -> finalize (a3-a5) -> error / reconstruct (a6), CF (a7).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/spid.h"
+#include "spid_internal.cuh"
+
+
+using namespace spid;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+spid_status fail(spid_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+#define SPID_CUDA(call)                                                                    \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(e_ == cudaErrorMemoryAllocation ? SPID_ERR_OOM : SPID_ERR_CUDA,          \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+  } while (0)
+
+// One sketch launch plan for a window column range.
+struct Schedule {
+  int grid = 0;            // CTAs per launch (per subdomain in per-subdomain mode)
+  int nprob = 0;
+  int max_tiles = 1;       // 128-column tiles of the widest problem (TF32)
+  int stages = 1;          // TF32 pipeline depth
+  std::vector<int> cta_base_of_sub, prob_base_of_sub, nprob_of_sub;
+  void* dev = nullptr;     // one device block holding every table below
+  const Problem* probs = nullptr;
+  const Segment* segs = nullptr;
+  const int32_t* seg_ptr = nullptr;
+  const int64_t* slot_off = nullptr;
+  const int32_t* pslot_ptr = nullptr;
+  const int32_t* pslots = nullptr;
+  int64_t partial_elems = 0;
+};
+
+}  // namespace
+
+struct spid_plan_s {
+  int device = 0;
+  int num_sms = 0;
+  size_t smem_optin = 0;
+  int S = 0;
+  std::vector<int32_t> m, n;
+  std::vector<int64_t> off, ld;
+  int n_max = 0;
+  int k_max = 0, p = 0, l = 0, l_pad = 0;
+  double tol = 0.0;
+  int prec = SPID_PREC_FP32;
+  uint32_t flags = 0;
+  uint64_t seed = 0;
+  size_t esz = 4;
+  bool fp64() const { return prec == SPID_PREC_FP64; }
+  bool per_sub() const { return (flags & SPID_FLAG_PER_SUBDOMAIN) != 0; }
+  double u_mode() const {
+    return prec == SPID_PREC_FP64 ? std::ldexp(1.0, -53)
+                                  : (prec == SPID_PREC_TF32 ? std::ldexp(1.0, -11) : std::ldexp(1.0, -24));
+  }
+
+  // device state
+  int32_t* d_m = nullptr;
+  int32_t* d_n = nullptr;
+  int64_t* d_off = nullptr;
+  int64_t* d_ld = nullptr;
+  int64_t* d_yoff = nullptr;
+  int64_t* d_coff = nullptr;
+  void* d_Y = nullptr;
+  void* d_C = nullptr;
+  int32_t* d_J = nullptr;
+  int32_t* d_k = nullptr;
+  int* d_status = nullptr;
+  int32_t* d_unit_sub = nullptr;
+  int32_t* d_unit_row0 = nullptr;
+  int32_t* d_unit_col0 = nullptr;
+  int32_t* d_unit_ptr = nullptr;
+  double* d_err_part = nullptr;
+  double* d_sub_err = nullptr;
+  void* d_tmaps = nullptr;
+  void* d_partial = nullptr;
+  int64_t partial_cap = 0;
+  int units = 0;
+  std::vector<int32_t> unit_ptr;
+  int64_t y_elems = 0, c_elems = 0;
+  int64_t workspace = 0;
+
+  const void* bound_window = nullptr;
+  std::map<std::pair<int, int>, Schedule> schedules;
+  std::vector<void*> allocs;
+  std::mutex mu;
+
+  cudaError_t alloc(void** p, size_t bytes) {
+    bytes = std::max<size_t>(bytes, 16);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) {
+      allocs.push_back(*p);
+      workspace += (int64_t)bytes;
+    }
+    return e;
+  }
+  int group_cols() const {
+    return prec == SPID_PREC_TF32 ? sketch_tc_group_cols() : sketch_simt_group_cols(fp64());
+  }
+  int sketch_grid() const {
+    if (prec == SPID_PREC_TF32) return num_sms;
+    return (!fp64() && l_pad <= 32) || (fp64() && l_pad <= 16) ? 2 * num_sms : num_sms;
+  }
+};
+
+namespace {
+
+// Build the sketch schedule for window columns [col0, col0 + ncols).
+spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
+  const int CG = P->group_cols();
+  const int G = P->sketch_grid();
+  std::vector<Problem> probs;
+  std::vector<int> prob_sub_first(P->S + 1, 0);
+  for (int s = 0; s < P->S; ++s) {
+    prob_sub_first[s] = (int)probs.size();
+    const int end = std::min<int64_t>((int64_t)col0 + ncols, P->n[s]);
+    for (int c = col0; c < end; c += CG) {
+      Problem pb;
+      pb.sub = s;
+      pb.col0 = c;
+      pb.ncols = std::min(CG, end - c);
+      pb.m = P->m[s];
+      pb.off = P->off[s];
+      pb.ld = P->ld[s];
+      probs.push_back(pb);
+    }
+  }
+  prob_sub_first[P->S] = (int)probs.size();
+  std::vector<Segment> segs;
+  std::vector<int32_t> seg_ptr;
+  std::vector<int64_t> slot_off;
+  int64_t slot_total = 0;
+  std::vector<std::vector<int32_t>> slots_of_prob(probs.size());
+  int max_tiles = 1;
+  for (const Problem& pb : probs) max_tiles = std::max(max_tiles, (pb.ncols + 127) / 128);
+
+  // Partition the chunk sequence of problems [p0, p1) over G CTAs, balanced by
+  // bytes (chunk weight = columns of its problem).
+  // Chunk i of the concatenated sequence goes to the CTA whose equal share of
+  // the total weight contains the chunk's midpoint; consecutive chunks of one
+  // problem on one CTA form a segment.  Appends G + 1 entries to seg_ptr.
+  auto partition = [&](int p0, int p1) {
+    double W = 0.0;
+    for (int p = p0; p < p1; ++p)
+      W += (double)((probs[p].m + kChunkRows - 1) / kChunkRows) * probs[p].ncols;
+    std::vector<std::vector<Segment>> per_cta(G);
+    double acc = 0.0;
+    for (int p = p0; p < p1; ++p) {
+      const int nch = (probs[p].m + kChunkRows - 1) / kChunkRows;
+      const double w = probs[p].ncols;
+      for (int ch = 0; ch < nch; ++ch) {
+        int c = (int)((acc + 0.5 * w) * G / W);
+        c = std::min(std::max(c, 0), G - 1);
+        std::vector<Segment>& v = per_cta[c];
+        if (!v.empty() && v.back().prob == p && v.back().chunk1 == ch) {
+          v.back().chunk1 = ch + 1;
+        } else {
+          Segment sg;
+          sg.prob = p;
+          sg.chunk0 = ch;
+          sg.chunk1 = ch + 1;
+          sg.slot = -1;
+          v.push_back(sg);
+        }
+        acc += w;
+      }
+    }
+    for (int c = 0; c < G; ++c) {
+      seg_ptr.push_back((int32_t)segs.size());
+      for (Segment sg : per_cta[c]) {
+        sg.slot = (int32_t)slot_off.size();
+        slot_off.push_back(slot_total);
+        slot_total += (int64_t)probs[sg.prob].ncols * P->l_pad;
+        slots_of_prob[sg.prob].push_back(sg.slot);
+        segs.push_back(sg);
+      }
+    }
+    seg_ptr.push_back((int32_t)segs.size());
+  };
+  sc.cta_base_of_sub.assign(P->S, 0);
+  sc.prob_base_of_sub.assign(P->S, 0);
+  sc.nprob_of_sub.assign(P->S, 0);
+  if (P->per_sub()) {
+    // one launch of G CTAs per subdomain: seg_ptr has S blocks of G + 1 entries
+    for (int s = 0; s < P->S; ++s) {
+      sc.cta_base_of_sub[s] = (int)seg_ptr.size();
+      sc.prob_base_of_sub[s] = prob_sub_first[s];
+      sc.nprob_of_sub[s] = prob_sub_first[s + 1] - prob_sub_first[s];
+      partition(prob_sub_first[s], prob_sub_first[s + 1]);
+    }
+  } else {
+    partition(0, (int)probs.size());
+  }
+  std::vector<int32_t> pslot_ptr(probs.size() + 1, 0), pslots;
+  for (size_t p = 0; p < probs.size(); ++p) {
+    pslot_ptr[p] = (int32_t)pslots.size();
+    for (int32_t q : slots_of_prob[p]) pslots.push_back(q);
+  }
+  pslot_ptr[probs.size()] = (int32_t)pslots.size();
+
+  sc.grid = G;
+  sc.nprob = (int)probs.size();
+  sc.max_tiles = max_tiles;
+  sc.partial_elems = slot_total;
+  if (slot_total > P->partial_cap)
+    return fail(SPID_ERR_INVALID_ARG, "sketch schedule exceeds the partial workspace");
+  // one device block for all tables (16-byte aligned pieces)
+  auto al = [](size_t b) { return (b + 15) / 16 * 16; };
+  const size_t b_probs = al(sizeof(Problem) * std::max<size_t>(probs.size(), 1));
+  const size_t b_segs = al(sizeof(Segment) * std::max<size_t>(segs.size(), 1));
+  const size_t b_segp = al(sizeof(int32_t) * seg_ptr.size());
+  const size_t b_slot = al(sizeof(int64_t) * std::max<size_t>(slot_off.size(), 1));
+  const size_t b_pptr = al(sizeof(int32_t) * pslot_ptr.size());
+  const size_t b_psl = al(sizeof(int32_t) * std::max<size_t>(pslots.size(), 1));
+  const size_t total = b_probs + b_segs + b_segp + b_slot + b_pptr + b_psl;
+  std::vector<unsigned char> host(total, 0);
+  size_t o = 0;
+  auto put = [&](const void* src, size_t bytes, size_t span) {
+    if (bytes) std::memcpy(host.data() + o, src, bytes);
+    size_t at = o;
+    o += span;
+    return at;
+  };
+  const size_t o_probs = put(probs.data(), sizeof(Problem) * probs.size(), b_probs);
+  const size_t o_segs = put(segs.data(), sizeof(Segment) * segs.size(), b_segs);
+  const size_t o_segp = put(seg_ptr.data(), sizeof(int32_t) * seg_ptr.size(), b_segp);
+  const size_t o_slot = put(slot_off.data(), sizeof(int64_t) * slot_off.size(), b_slot);
+  const size_t o_pptr = put(pslot_ptr.data(), sizeof(int32_t) * pslot_ptr.size(), b_pptr);
+  const size_t o_psl = put(pslots.data(), sizeof(int32_t) * pslots.size(), b_psl);
+  SPID_CUDA(P->alloc(&sc.dev, total));
+  SPID_CUDA(cudaMemcpy(sc.dev, host.data(), total, cudaMemcpyHostToDevice));
+  unsigned char* d = static_cast<unsigned char*>(sc.dev);
+  sc.probs = reinterpret_cast<const Problem*>(d + o_probs);
+  sc.segs = reinterpret_cast<const Segment*>(d + o_segs);
+  sc.seg_ptr = reinterpret_cast<const int32_t*>(d + o_segp);
+  sc.slot_off = reinterpret_cast<const int64_t*>(d + o_slot);
+  sc.pslot_ptr = reinterpret_cast<const int32_t*>(d + o_pptr);
+  sc.pslots = reinterpret_cast<const int32_t*>(d + o_psl);
+  if (P->prec == SPID_PREC_TF32) {
+    const size_t per_stage = (size_t)max_tiles * 128 * 128 + (size_t)P->l_pad * 128;
+    const size_t fixed = sketch_tc_smem_bytes(0, max_tiles, P->l_pad);
+    int stages = (int)((P->smem_optin - fixed) / per_stage);
+    stages = std::min(stages, sketch_tc_max_stages());
+    if (stages < 2) return fail(SPID_ERR_UNSUPPORTED, "not enough shared memory for the TF32 pipeline");
+    sc.stages = stages;
+  }
+  return SPID_OK;
+}
+
+spid_status get_schedule(spid_plan_t P, int col0, int ncols, Schedule** out) {
+  std::lock_guard<std::mutex> g(P->mu);
+  auto key = std::make_pair(col0, ncols);
+  auto it = P->schedules.find(key);
+  if (it == P->schedules.end()) {
+    Schedule sc;
+    spid_status st = build_schedule(P, col0, ncols, sc);
+    if (st != SPID_OK) return st;
+    it = P->schedules.emplace(key, sc).first;
+  }
+  *out = &it->second;
+  return SPID_OK;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Encode one 2-D tensor map per subdomain over the window: dim0 = rows
+// (contiguous), dim1 = window columns, box = 32 rows x 128 columns, 128-byte
+// swizzle, zero fill outside [0, m) x [0, n).
+spid_status bind_window(spid_plan_t P, const void* window, cudaStream_t st) {
+  if (P->bound_window == window) return SPID_OK;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return fail(SPID_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  std::vector<CUtensorMap> maps(P->S);
+  for (int s = 0; s < P->S; ++s) {
+    void* base = const_cast<char*>(static_cast<const char*>(window)) + P->off[s] * P->esz;
+    cuuint64_t dims[2] = {(cuuint64_t)P->m[s], (cuuint64_t)P->n[s]};
+    cuuint64_t strides[1] = {(cuuint64_t)P->ld[s] * P->esz};
+    cuuint32_t box[2] = {32, 128};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&maps[s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+      return fail(SPID_ERR_INVALID_ARG, "cuTensorMapEncodeTiled failed for subdomain " +
+                                            std::to_string(s) + " (code " + std::to_string((int)r) + ")");
+  }
+  // previous maps may still be read by work in flight on this stream
+  SPID_CUDA(cudaStreamSynchronize(st));
+  SPID_CUDA(cudaMemcpy(P->d_tmaps, maps.data(), sizeof(CUtensorMap) * P->S, cudaMemcpyHostToDevice));
+  P->bound_window = window;
+  return SPID_OK;
+}
+
+spid_status check_plan(spid_plan_t P) {
+  if (!P) return fail(SPID_ERR_INVALID_ARG, "plan is NULL");
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != P->device) {
+    SPID_CUDA(cudaSetDevice(P->device));
+  }
+  return SPID_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* spid_status_string(spid_status s) {
+  switch (s) {
+    case SPID_OK: return "SPID_OK";
+    case SPID_ERR_INVALID_ARG: return "SPID_ERR_INVALID_ARG";
+    case SPID_ERR_CUDA: return "SPID_ERR_CUDA";
+    case SPID_ERR_OOM: return "SPID_ERR_OOM";
+    case SPID_ERR_STATE: return "SPID_ERR_STATE";
+    case SPID_ERR_TIMEOUT: return "SPID_ERR_TIMEOUT";
+    case SPID_ERR_NONFINITE: return "SPID_ERR_NONFINITE";
+    case SPID_ERR_UNSUPPORTED: return "SPID_ERR_UNSUPPORTED";
+  }
+  return "SPID_ERR_UNKNOWN";
+}
+
+const char* spid_last_error(void) { return g_last_error.c_str(); }
+
+double spid_compression_factor(int32_t num_sub, const int32_t* m, const int32_t* n,
+                               const int32_t* k) {
+  double num = 0.0, den = 0.0;
+  for (int32_t s = 0; s < num_sub; ++s) {
+    num += (double)m[s] * (double)n[s];
+    den += (double)k[s] * ((double)m[s] + (double)n[s]);
+  }
+  return den > 0.0 ? num / den : INFINITY;
+}
+
+spid_status spid_plan_create(const spid_plan_desc* d, spid_plan_t* out) {
+  g_last_error.clear();
+  if (!d || !out) return fail(SPID_ERR_INVALID_ARG, "desc/out is NULL");
+  *out = nullptr;
+  if (d->num_sub < 1 || !d->m || !d->n || !d->off || !d->ld)
+    return fail(SPID_ERR_INVALID_ARG, "num_sub < 1 or a descriptor array is NULL");
+  if (d->precision < SPID_PREC_FP64 || d->precision > SPID_PREC_TF32)
+    return fail(SPID_ERR_INVALID_ARG, "unknown precision");
+  if (d->k_max < 1 || d->p < 0 || d->k_max + d->p > 64)
+    return fail(SPID_ERR_INVALID_ARG, "need k_max >= 1, p >= 0, k_max + p <= 64");
+  if (!(d->tol >= 0.0) || !std::isfinite(d->tol)) return fail(SPID_ERR_INVALID_ARG, "tol must be >= 0");
+  const size_t esz = d->precision == SPID_PREC_FP64 ? 8 : 4;
+  const int align = (int)(16 / esz);
+  int n_max = 0;
+  for (int s = 0; s < d->num_sub; ++s) {
+    if (d->m[s] < 1 || d->n[s] < 1 || d->n[s] > (1 << 20) || d->ld[s] < d->m[s] || d->off[s] < 0)
+      return fail(SPID_ERR_INVALID_ARG, "bad size for subdomain " + std::to_string(s));
+    if (d->off[s] % align || d->ld[s] % align)
+      return fail(SPID_ERR_INVALID_ARG, "off/ld of subdomain " + std::to_string(s) +
+                                            " not a multiple of 16 bytes");
+    n_max = std::max(n_max, d->n[s]);
+  }
+  spid_plan_s* P = new spid_plan_s();
+  auto bail = [&](spid_status st) {
+    spid_plan_destroy(P);
+    return st;
+  };
+  P->S = d->num_sub;
+  P->m.assign(d->m, d->m + P->S);
+  P->n.assign(d->n, d->n + P->S);
+  P->off.assign(d->off, d->off + P->S);
+  P->ld.assign(d->ld, d->ld + P->S);
+  P->n_max = n_max;
+  P->k_max = d->k_max;
+  P->p = d->p;
+  P->l = d->k_max + d->p;
+  P->l_pad = (P->l + 15) / 16 * 16;
+  P->tol = d->tol;
+  P->prec = d->precision;
+  P->flags = d->flags;
+  P->seed = d->seed;
+  P->esz = esz;
+  if (qrcp_cols_per_thread(n_max, P->l_pad, P->fp64()) == 0) {
+    delete P;
+    return fail(SPID_ERR_UNSUPPORTED, "window length / oversampled rank beyond the QR kernel's range");
+  }
+  cudaError_t e = cudaGetDevice(&P->device);
+  if (e != cudaSuccess) { delete P; return fail(SPID_ERR_CUDA, cudaGetErrorString(e)); }
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, P->device);
+  if (e != cudaSuccess) { delete P; return fail(SPID_ERR_CUDA, cudaGetErrorString(e)); }
+  P->num_sms = prop.multiProcessorCount;
+  P->smem_optin = prop.sharedMemPerBlockOptin;
+  if (P->prec == SPID_PREC_TF32 && prop.major < 10) {
+    delete P;
+    return fail(SPID_ERR_UNSUPPORTED, "TF32 tensor-core sketch needs sm_100 or newer");
+  }
+
+  // offsets of Y and C
+  std::vector<int64_t> yoff(P->S), coff(P->S);
+  int64_t ysum = 0, csum = 0;
+  for (int s = 0; s < P->S; ++s) {
+    yoff[s] = ysum;
+    coff[s] = csum;
+    ysum += (int64_t)P->n[s] * P->l_pad;
+    csum += (int64_t)P->n[s] * P->k_max;
+  }
+  P->y_elems = ysum;
+  P->c_elems = csum;
+  // error units: (subdomain, 512-row block, 256-column block)
+  std::vector<int32_t> usub, urow, ucol;
+  P->unit_ptr.assign(P->S + 1, 0);
+  for (int s = 0; s < P->S; ++s) {
+    P->unit_ptr[s] = (int32_t)usub.size();
+    for (int r = 0; r < P->m[s]; r += kErrRowBlock)
+      for (int c = 0; c < P->n[s]; c += kErrColBlock) {
+        usub.push_back(s);
+        urow.push_back(r);
+        ucol.push_back(c);
+      }
+  }
+  P->unit_ptr[P->S] = (int32_t)usub.size();
+  P->units = (int)usub.size();
+  // partial workspace bound: (CTAs + problems) slots of one column group each
+  const int CG = P->group_cols();
+  int64_t nprob_full = 0;
+  for (int s = 0; s < P->S; ++s) nprob_full += (P->n[s] + CG - 1) / CG;
+  const int64_t ctas = (int64_t)P->sketch_grid() * (P->per_sub() ? P->S : 1);
+  P->partial_cap = (ctas + nprob_full) * (int64_t)CG * P->l_pad;
+
+#define SPID_ALLOC(ptr, bytes)                                                            \
+  do {                                                                                    \
+    cudaError_t e_ = P->alloc(reinterpret_cast<void**>(&(ptr)), (bytes));                 \
+    if (e_ != cudaSuccess) {                                                              \
+      g_last_error = std::string("cudaMalloc: ") + cudaGetErrorString(e_);                \
+      return bail(e_ == cudaErrorMemoryAllocation ? SPID_ERR_OOM : SPID_ERR_CUDA);        \
+    }                                                                                     \
+  } while (0)
+  SPID_ALLOC(P->d_m, sizeof(int32_t) * P->S);
+  SPID_ALLOC(P->d_n, sizeof(int32_t) * P->S);
+  SPID_ALLOC(P->d_off, sizeof(int64_t) * P->S);
+  SPID_ALLOC(P->d_ld, sizeof(int64_t) * P->S);
+  SPID_ALLOC(P->d_yoff, sizeof(int64_t) * P->S);
+  SPID_ALLOC(P->d_coff, sizeof(int64_t) * P->S);
+  SPID_ALLOC(P->d_Y, esz * P->y_elems);
+  SPID_ALLOC(P->d_C, esz * P->c_elems);
+  SPID_ALLOC(P->d_J, sizeof(int32_t) * P->S * P->k_max);
+  SPID_ALLOC(P->d_k, sizeof(int32_t) * P->S);
+  SPID_ALLOC(P->d_status, sizeof(int));
+  SPID_ALLOC(P->d_unit_sub, sizeof(int32_t) * P->units);
+  SPID_ALLOC(P->d_unit_row0, sizeof(int32_t) * P->units);
+  SPID_ALLOC(P->d_unit_col0, sizeof(int32_t) * P->units);
+  SPID_ALLOC(P->d_unit_ptr, sizeof(int32_t) * (P->S + 1));
+  SPID_ALLOC(P->d_err_part, sizeof(double) * 2 * P->units);
+  SPID_ALLOC(P->d_sub_err, sizeof(double) * 2 * P->S);
+  SPID_ALLOC(P->d_partial, esz * P->partial_cap);
+  if (P->prec == SPID_PREC_TF32) SPID_ALLOC(P->d_tmaps, sizeof(CUtensorMap) * P->S);
+#undef SPID_ALLOC
+#define SPID_H2D(dst, src, bytes)                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = cudaMemcpy((dst), (src), (bytes), cudaMemcpyHostToDevice);            \
+    if (e_ != cudaSuccess) {                                                               \
+      g_last_error = std::string("cudaMemcpy: ") + cudaGetErrorString(e_);                 \
+      return bail(SPID_ERR_CUDA);                                                          \
+    }                                                                                      \
+  } while (0)
+  SPID_H2D(P->d_m, P->m.data(), sizeof(int32_t) * P->S);
+  SPID_H2D(P->d_n, P->n.data(), sizeof(int32_t) * P->S);
+  SPID_H2D(P->d_off, P->off.data(), sizeof(int64_t) * P->S);
+  SPID_H2D(P->d_ld, P->ld.data(), sizeof(int64_t) * P->S);
+  SPID_H2D(P->d_yoff, yoff.data(), sizeof(int64_t) * P->S);
+  SPID_H2D(P->d_coff, coff.data(), sizeof(int64_t) * P->S);
+  SPID_H2D(P->d_unit_sub, usub.data(), sizeof(int32_t) * P->units);
+  SPID_H2D(P->d_unit_row0, urow.data(), sizeof(int32_t) * P->units);
+  SPID_H2D(P->d_unit_col0, ucol.data(), sizeof(int32_t) * P->units);
+  SPID_H2D(P->d_unit_ptr, P->unit_ptr.data(), sizeof(int32_t) * (P->S + 1));
+#undef SPID_H2D
+  if (cudaMemset(P->d_Y, 0, esz * P->y_elems) != cudaSuccess ||
+      cudaMemset(P->d_status, 0, sizeof(int)) != cudaSuccess ||
+      cudaMemset(P->d_k, 0, sizeof(int32_t) * P->S) != cudaSuccess)
+    return bail(fail(SPID_ERR_CUDA, "cudaMemset failed"));
+  // the whole-window schedule is built now so that steady-state calls allocate nothing
+  Schedule* sc = nullptr;
+  spid_status st = get_schedule(P, 0, n_max, &sc);
+  if (st != SPID_OK) return bail(st);
+  if (cudaDeviceSynchronize() != cudaSuccess) return bail(fail(SPID_ERR_CUDA, "sync failed"));
+  *out = P;
+  return SPID_OK;
+}
+
+spid_status spid_plan_destroy(spid_plan_t P) {
+  if (!P) return SPID_OK;
+  cudaSetDevice(P->device);
+  cudaDeviceSynchronize();
+  for (void* p : P->allocs) cudaFree(p);
+  delete P;
+  return SPID_OK;
+}
+
+spid_status spid_plan_info(spid_plan_t P, int32_t* l, int32_t* l_pad, int64_t* ws) {
+  if (!P) return fail(SPID_ERR_INVALID_ARG, "plan is NULL");
+  if (l) *l = P->l;
+  if (l_pad) *l_pad = P->l_pad;
+  if (ws) *ws = P->workspace;
+  return SPID_OK;
+}
+
+spid_status spid_reset(spid_plan_t P, spid_stream_t stream) {
+  spid_status st = check_plan(P);
+  if (st != SPID_OK) return st;
+  SPID_CUDA(cudaMemsetAsync(P->d_Y, 0, P->esz * P->y_elems, (cudaStream_t)stream));
+  return SPID_OK;
+}
+
+spid_status spid_sketch(spid_plan_t P, const void* window, int32_t col0, int32_t ncols,
+                        spid_stream_t stream) {
+  spid_status st = check_plan(P);
+  if (st != SPID_OK) return st;
+  if (!window) return fail(SPID_ERR_INVALID_ARG, "window is NULL");
+  if (reinterpret_cast<uintptr_t>(window) % 16)
+    return fail(SPID_ERR_INVALID_ARG, "window must be 16-byte aligned");
+  if (col0 < 0 || ncols < 0) return fail(SPID_ERR_INVALID_ARG, "negative column range");
+  if (ncols == 0 || col0 >= P->n_max) return SPID_OK;
+  ncols = std::min(ncols, P->n_max - col0);
+  cudaStream_t cs = (cudaStream_t)stream;
+  Schedule* sc = nullptr;
+  st = get_schedule(P, col0, ncols, &sc);
+  if (st != SPID_OK) return st;
+  if (P->prec == SPID_PREC_TF32) {
+    st = bind_window(P, window, cs);
+    if (st != SPID_OK) return st;
+  }
+  SketchArgs a;
+  a.probs = sc->probs;
+  a.segs = sc->segs;
+  a.seg_ptr = sc->seg_ptr;
+  a.slot_off = sc->slot_off;
+  a.partial = P->d_partial;
+  a.window = window;
+  a.tmaps = P->d_tmaps;
+  a.cta_base = 0;
+  a.l = P->l;
+  a.l_pad = P->l_pad;
+  a.seed = P->seed;
+  a.status = P->d_status;
+  ReduceArgs r;
+  r.probs = sc->probs;
+  r.pslot_ptr = sc->pslot_ptr;
+  r.pslots = sc->pslots;
+  r.slot_off = sc->slot_off;
+  r.partial = P->d_partial;
+  r.Y = P->d_Y;
+  r.yoff = P->d_yoff;
+  r.l_pad = P->l_pad;
+  r.prob_base = 0;
+  const int nlaunch = P->per_sub() ? P->S : 1;
+  for (int q = 0; q < nlaunch; ++q) {
+    a.cta_base = P->per_sub() ? sc->cta_base_of_sub[q] : 0;
+    cudaError_t e = (P->prec == SPID_PREC_TF32)
+                        ? launch_sketch_tc(a, sc->grid, sc->stages, sc->max_tiles, cs)
+                        : launch_sketch_simt(a, sc->grid, P->fp64(), cs);
+    if (e != cudaSuccess) return fail(SPID_ERR_CUDA, std::string("sketch launch: ") + cudaGetErrorString(e));
+  }
+  for (int q = 0; q < nlaunch; ++q) {
+    r.prob_base = P->per_sub() ? sc->prob_base_of_sub[q] : 0;
+    const int np = P->per_sub() ? sc->nprob_of_sub[q] : sc->nprob;
+    cudaError_t e = launch_reduce_partials(r, np, P->fp64(), cs);
+    if (e != cudaSuccess) return fail(SPID_ERR_CUDA, std::string("reduce launch: ") + cudaGetErrorString(e));
+  }
+  return SPID_OK;
+}
+
+spid_status spid_finalize(spid_plan_t P, spid_stream_t stream) {
+  spid_status st = check_plan(P);
+  if (st != SPID_OK) return st;
+  QrcpArgs a;
+  a.Y = P->d_Y;
+  a.yoff = P->d_yoff;
+  a.n = P->d_n;
+  a.C = P->d_C;
+  a.coff = P->d_coff;
+  a.J = P->d_J;
+  a.k_out = P->d_k;
+  a.l = P->l;
+  a.k_max = P->k_max;
+  a.tol = P->tol;
+  a.u_mode = P->u_mode();
+  a.sub_base = 0;
+  a.status = P->d_status;
+  cudaStream_t cs = (cudaStream_t)stream;
+  if (P->per_sub()) {
+    for (int s = 0; s < P->S; ++s) {
+      a.sub_base = s;
+      cudaError_t e = launch_qrcp(a, 1, P->n[s], P->l_pad, P->fp64(), cs);
+      if (e != cudaSuccess) return fail(SPID_ERR_CUDA, std::string("qrcp launch: ") + cudaGetErrorString(e));
+    }
+  } else {
+    cudaError_t e = launch_qrcp(a, P->S, P->n_max, P->l_pad, P->fp64(), cs);
+    if (e != cudaSuccess) return fail(SPID_ERR_CUDA, std::string("qrcp launch: ") + cudaGetErrorString(e));
+  }
+  return SPID_OK;
+}
+
+static spid_status run_error(spid_plan_t P, const void* window, void* out, double* err_dev,
+                             double* total_dev, cudaStream_t cs) {
+  if (!window) return fail(SPID_ERR_INVALID_ARG, "window is NULL");
+  if (reinterpret_cast<uintptr_t>(window) % 16 || (out && reinterpret_cast<uintptr_t>(out) % 16))
+    return fail(SPID_ERR_INVALID_ARG, "window/out must be 16-byte aligned");
+  ErrArgs a;
+  a.window = window;
+  a.out = out;
+  a.m = P->d_m;
+  a.n = P->d_n;
+  a.off = P->d_off;
+  a.ld = P->d_ld;
+  a.C = P->d_C;
+  a.coff = P->d_coff;
+  a.J = P->d_J;
+  a.k = P->d_k;
+  a.k_max = P->k_max;
+  a.unit_sub = P->d_unit_sub;
+  a.unit_row0 = P->d_unit_row0;
+  a.unit_col0 = P->d_unit_col0;
+  a.part = P->d_err_part;
+  a.unit_base = 0;
+  if (P->per_sub()) {
+    for (int s = 0; s < P->S; ++s) {
+      a.unit_base = P->unit_ptr[s];
+      cudaError_t e = launch_error(a, P->unit_ptr[s + 1] - P->unit_ptr[s], P->fp64(), cs);
+      if (e != cudaSuccess) return fail(SPID_ERR_CUDA, std::string("error launch: ") + cudaGetErrorString(e));
+    }
+  } else {
+    cudaError_t e = launch_error(a, P->units, P->fp64(), cs);
+    if (e != cudaSuccess) return fail(SPID_ERR_CUDA, std::string("error launch: ") + cudaGetErrorString(e));
+  }
+  ErrFinishArgs f;
+  f.unit_ptr = P->d_unit_ptr;
+  f.part = P->d_err_part;
+  f.err = err_dev;
+  f.sub_err = P->d_sub_err;
+  f.total = total_dev;
+  f.m = P->d_m;
+  f.n = P->d_n;
+  f.k = P->d_k;
+  f.S = P->S;
+  cudaError_t e = launch_error_finish(f, cs);
+  if (e != cudaSuccess) return fail(SPID_ERR_CUDA, std::string("error finish: ") + cudaGetErrorString(e));
+  return SPID_OK;
+}
+
+spid_status spid_error(spid_plan_t P, const void* window, double* err_dev, double* total_dev,
+                       spid_stream_t stream) {
+  spid_status st = check_plan(P);
+  if (st != SPID_OK) return st;
+  return run_error(P, window, nullptr, err_dev, total_dev, (cudaStream_t)stream);
+}
+
+spid_status spid_reconstruct(spid_plan_t P, const void* window, void* out, spid_stream_t stream) {
+  spid_status st = check_plan(P);
+  if (st != SPID_OK) return st;
+  if (!out) return fail(SPID_ERR_INVALID_ARG, "out is NULL");
+  return run_error(P, window, out, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+spid_status spid_get_factors(spid_plan_t P, int32_t* k_host, int32_t* J_host, void* C_host,
+                             spid_stream_t stream) {
+  spid_status st = check_plan(P);
+  if (st != SPID_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  SPID_CUDA(cudaStreamSynchronize(cs));
+  if (k_host) SPID_CUDA(cudaMemcpy(k_host, P->d_k, sizeof(int32_t) * P->S, cudaMemcpyDeviceToHost));
+  if (J_host)
+    SPID_CUDA(cudaMemcpy(J_host, P->d_J, sizeof(int32_t) * P->S * P->k_max, cudaMemcpyDeviceToHost));
+  if (C_host) SPID_CUDA(cudaMemcpy(C_host, P->d_C, P->esz * P->c_elems, cudaMemcpyDeviceToHost));
+  return SPID_OK;
+}
+
+spid_status spid_get_sketch(spid_plan_t P, void* Y_host, spid_stream_t stream) {
+  spid_status st = check_plan(P);
+  if (st != SPID_OK) return st;
+  if (!Y_host) return fail(SPID_ERR_INVALID_ARG, "Y_host is NULL");
+  SPID_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  SPID_CUDA(cudaMemcpy(Y_host, P->d_Y, P->esz * P->y_elems, cudaMemcpyDeviceToHost));
+  return SPID_OK;
+}
+
+spid_status spid_device_status(spid_plan_t P, spid_stream_t stream) {
+  spid_status st = check_plan(P);
+  if (st != SPID_OK) return st;
+  SPID_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  int v = 0;
+  SPID_CUDA(cudaMemcpy(&v, P->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  SPID_CUDA(cudaMemset(P->d_status, 0, sizeof(int)));
+  if (v & kStatusTimeout) return fail(SPID_ERR_TIMEOUT, "a bounded device wait timed out");
+  if (v & kStatusNonfinite) return fail(SPID_ERR_NONFINITE, "non-finite values reached a sketch");
+  return SPID_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Omega and Philox exposed for checking
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename T>
+__global__ void omega_kernel(uint64_t seed, int64_t r0, int32_t nrows, int32_t l, T* out) {
+  const uint2 key = philox_key(seed);
+  const int groups = (l + 3) / 4;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nrows * groups;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = t / groups;
+    const int g = (int)(t % groups);
+    T w[4];
+    omega_group<T>(key, (uint32_t)(r0 + c), (uint32_t)g, w);
+    for (int u = 0; u < 4; ++u)
+      if (4 * g + u < l) out[c * l + 4 * g + u] = w[u];
+  }
+}
+
+__global__ void philox_kernel(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
+                              int64_t count) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 c = make_uint4(ctr[4 * t], ctr[4 * t + 1], ctr[4 * t + 2], ctr[4 * t + 3]);
+    const uint4 x = philox4x32_10(c, make_uint2(k0, k1));
+    out[4 * t] = x.x;
+    out[4 * t + 1] = x.y;
+    out[4 * t + 2] = x.z;
+    out[4 * t + 3] = x.w;
+  }
+}
+
+}  // namespace
+
+extern "C" spid_status spid_omega(uint64_t seed, int64_t r0, int32_t nrows, int32_t l,
+                                  int32_t precision, void* out_dev, spid_stream_t stream) {
+  if (!out_dev || nrows < 0 || l < 1 || r0 < 0 || r0 + nrows > ((int64_t)1 << 32))
+    return fail(SPID_ERR_INVALID_ARG, "bad omega arguments");
+  if (nrows == 0) return SPID_OK;
+  const int64_t work = (int64_t)nrows * ((l + 3) / 4);
+  const int grid = (int)std::min<int64_t>((work + 255) / 256, 4096);
+  if (precision == SPID_PREC_FP64)
+    omega_kernel<double><<<grid, 256, 0, (cudaStream_t)stream>>>(seed, r0, nrows, l, (double*)out_dev);
+  else
+    omega_kernel<float><<<grid, 256, 0, (cudaStream_t)stream>>>(seed, r0, nrows, l, (float*)out_dev);
+  SPID_CUDA(cudaGetLastError());
+  return SPID_OK;
+}
+
+extern "C" spid_status spid_philox(const uint32_t* ctr_dev, uint32_t key0, uint32_t key1,
+                                   uint32_t* out_dev, int64_t count, spid_stream_t stream) {
+  if (!ctr_dev || !out_dev || count < 0) return fail(SPID_ERR_INVALID_ARG, "bad philox arguments");
+  if (count == 0) return SPID_OK;
+  const int grid = (int)std::min<int64_t>((count + 255) / 256, 4096);
+  philox_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(ctr_dev, key0, key1, out_dev, count);
+  SPID_CUDA(cudaGetLastError());
+  return SPID_OK;
+}

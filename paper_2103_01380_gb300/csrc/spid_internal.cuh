@@ -1,0 +1,205 @@
+// spid_internal.cuh -- types shared by the host side of libspid and its
+// kernels, plus the device helpers every kernel uses (Philox4x32-10,
+// Box-Muller, bounded waits, status word).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace spid {
+
+// Sticky device status bits (OR-ed into the plan's status word).
+enum : int {
+  kStatusTimeout = 1,
+  kStatusNonfinite = 2,
+};
+
+// Every spin on an mbarrier gives up after this many nanoseconds, records
+// kStatusTimeout and lets the kernel unwind.
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
+
+// Rows of A handled per sketch chunk: one 128-byte swizzle row of FP32.
+constexpr int kChunkRows = 32;
+
+// A "problem" is one subdomain restricted to a group of window columns.
+struct Problem {
+  int32_t sub;     // subdomain index
+  int32_t col0;    // first window column
+  int32_t ncols;   // number of columns (<= the kernel's column-group size)
+  int32_t m;       // rows of the subdomain
+  int64_t off;     // element offset of A_s(0,0) in the window
+  int64_t ld;      // leading dimension in elements
+};
+
+// A contiguous range of row chunks of one problem, processed by one CTA; its
+// partial sketch goes to partial slot `slot`.
+struct Segment {
+  int32_t prob;
+  int32_t chunk0;
+  int32_t chunk1;
+  int32_t slot;
+};
+
+// Sketch schedule arguments (both sketch kernels).
+struct SketchArgs {
+  const Problem* probs;
+  const Segment* segs;
+  const int32_t* seg_ptr;     // CTA c owns segs[seg_ptr[c] .. seg_ptr[c+1])
+  const int64_t* slot_off;    // element offset of each partial slot
+  void* partial;              // float or double partial sums [slot][ncols][l_pad]
+  const void* window;
+  const void* tmaps;          // CUtensorMap per subdomain (TF32 kernel only)
+  int32_t cta_base;           // first schedule CTA of this launch
+  int32_t l;
+  int32_t l_pad;
+  uint64_t seed;
+  int* status;
+};
+
+// Fixed-order reduction of a schedule's partial slots into the stored sketch.
+struct ReduceArgs {
+  const Problem* probs;
+  const int32_t* pslot_ptr;   // problem p owns pslots[pslot_ptr[p] .. pslot_ptr[p+1])
+  const int32_t* pslots;
+  const int64_t* slot_off;
+  const void* partial;
+  void* Y;
+  const int64_t* yoff;        // element offset of Y_s
+  int32_t l_pad;
+  int32_t prob_base;
+};
+
+// Batched pivoted QR + rank + coefficients.
+struct QrcpArgs {
+  const void* Y;          // sketches: Y_s at yoff[s], [n_s][l_pad]
+  const int64_t* yoff;
+  const int32_t* n;
+  void* C;                // C_s at coff[s], k_max x n_s row-major
+  const int64_t* coff;
+  int32_t* J;             // [S][k_max]
+  int32_t* k_out;         // [S]
+  int32_t l;
+  int32_t k_max;
+  double tol;
+  double u_mode;
+  int32_t sub_base;
+  int* status;
+};
+
+// Fused reconstruction / error pass.
+constexpr int kErrRowBlock = 512;
+constexpr int kErrColBlock = 256;
+constexpr int kErrTile = 128;
+
+struct ErrArgs {
+  const void* window;
+  void* out;                  // reconstruction (same layout), or nullptr
+  const int32_t* m;
+  const int32_t* n;
+  const int64_t* off;
+  const int64_t* ld;
+  const void* C;
+  const int64_t* coff;
+  const int32_t* J;
+  const int32_t* k;
+  int32_t k_max;
+  const int32_t* unit_sub;
+  const int32_t* unit_row0;
+  const int32_t* unit_col0;
+  double* part;               // [unit][2] = {e2, a2}
+  int32_t unit_base;
+};
+
+struct ErrFinishArgs {
+  const int32_t* unit_ptr;    // subdomain s owns units [unit_ptr[s], unit_ptr[s+1])
+  const double* part;
+  double* err;                // [S][2] or nullptr
+  double* sub_err;            // plan copy [S][2]
+  double* total;              // [4] or nullptr
+  const int32_t* m;
+  const int32_t* n;
+  const int32_t* k;
+  int32_t S;
+};
+
+// Launchers (one translation unit each).
+int sketch_simt_group_cols(bool fp64);
+cudaError_t launch_sketch_simt(const SketchArgs& a, int grid, bool fp64, cudaStream_t st);
+cudaError_t launch_reduce_partials(const ReduceArgs& a, int nprob, bool fp64, cudaStream_t st);
+int sketch_tc_group_cols();
+size_t sketch_tc_smem_bytes(int stages, int max_tiles, int l_pad);
+int sketch_tc_max_stages();
+cudaError_t launch_sketch_tc(const SketchArgs& s, int grid, int stages, int max_tiles,
+                             cudaStream_t st);
+int qrcp_cols_per_thread(int n_max, int l_pad, bool fp64);
+cudaError_t launch_qrcp(const QrcpArgs& a, int grid, int n_max, int l_pad, bool fp64,
+                        cudaStream_t st);
+size_t error_smem_bytes(int k_max, bool fp64);
+cudaError_t launch_error(const ErrArgs& a, int units, bool fp64, cudaStream_t st);
+cudaError_t launch_error_finish(const ErrFinishArgs& a, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the Philox
+// S-box on a 4 x 32-bit counter, with a Weyl-sequence key schedule.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint2 philox_key(uint64_t seed) {
+  return make_uint2((uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32));
+}
+
+// Box-Muller on a pair of words, FP32: u = (x + 0.5) 2^-32.
+__device__ __forceinline__ void box_muller(uint32_t xa, uint32_t xb, float& g0, float& g1) {
+  const float ua = fmaf(__uint2float_rn(xa), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+  const float ub = fmaf(__uint2float_rn(xb), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+  const float rad = sqrtf(-2.0f * logf(ua));
+  float s, c;
+  sincospif(2.0f * ub, &s, &c);
+  g0 = rad * c;
+  g1 = rad * s;
+}
+
+// Box-Muller on a pair of words, FP64.
+__device__ __forceinline__ void box_muller(uint32_t xa, uint32_t xb, double& g0, double& g1) {
+  const double ua = ((double)xa + 0.5) * 2.3283064365386963e-10;
+  const double ub = ((double)xb + 0.5) * 2.3283064365386963e-10;
+  const double rad = sqrt(-2.0 * log(ua));
+  double s, c;
+  sincospi(2.0 * ub, &s, &c);
+  g0 = rad * c;
+  g1 = rad * s;
+}
+
+// Omega(4g .. 4g+3, r) from one Philox call with counter (r, g, 0, 0).
+template <typename T>
+__device__ __forceinline__ void omega_group(uint2 key, uint32_t r, uint32_t g, T out[4]) {
+  const uint4 x = philox4x32_10(make_uint4(r, g, 0u, 0u), key);
+  box_muller(x.x, x.y, out[0], out[1]);
+  box_muller(x.z, x.w, out[2], out[3]);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void raise_status(int* status, int bit) {
+  if (status) atomicOr(status, bit);
+}
+
+}  // namespace spid

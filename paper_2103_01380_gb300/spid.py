@@ -1,0 +1,238 @@
+"""Python binding of libspid (include/spid.h).
+
+Argument marshalling only: every step of the decomposition runs in the CUDA
+kernels behind the C ABI.  Device buffers are torch CUDA tensors (PyTorch is
+used for device memory and streams); host results come back as numpy arrays.
+There is no CPU fallback: if libspid.so is missing or cannot be loaded, every
+entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libspid.so")
+
+SPID_OK = 0
+STATUS_NAMES = {0: "SPID_OK", 1: "SPID_ERR_INVALID_ARG", 2: "SPID_ERR_CUDA", 3: "SPID_ERR_OOM",
+                4: "SPID_ERR_STATE", 5: "SPID_ERR_TIMEOUT", 6: "SPID_ERR_NONFINITE",
+                7: "SPID_ERR_UNSUPPORTED"}
+PREC = {"fp64": 0, "fp32": 1, "tf32": 2}
+FLAG_PER_SUBDOMAIN = 1
+
+# every symbol include/spid.h declares
+EXPORTS = ["spid_plan_create", "spid_plan_destroy", "spid_plan_info", "spid_sketch", "spid_reset",
+           "spid_finalize", "spid_error", "spid_reconstruct", "spid_get_factors",
+           "spid_get_sketch", "spid_device_status", "spid_omega", "spid_philox",
+           "spid_compression_factor", "spid_status_string", "spid_last_error"]
+
+
+class SpidError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} {detail}".strip())
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("num_sub", ctypes.c_int32),
+                ("m", ctypes.POINTER(ctypes.c_int32)),
+                ("n", ctypes.POINTER(ctypes.c_int32)),
+                ("off", ctypes.POINTER(ctypes.c_int64)),
+                ("ld", ctypes.POINTER(ctypes.c_int64)),
+                ("k_max", ctypes.c_int32),
+                ("p", ctypes.c_int32),
+                ("tol", ctypes.c_double),
+                ("precision", ctypes.c_int32),
+                ("flags", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libspid.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libspid.so not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        c = ctypes
+        vp, i32, i64, u32, u64, dbl = (c.c_void_p, c.c_int32, c.c_int64, c.c_uint32, c.c_uint64,
+                                       c.c_double)
+        sig = {
+            "spid_plan_create": ([c.POINTER(_Desc), c.POINTER(vp)], c.c_int),
+            "spid_plan_destroy": ([vp], c.c_int),
+            "spid_plan_info": ([vp, c.POINTER(i32), c.POINTER(i32), c.POINTER(i64)], c.c_int),
+            "spid_sketch": ([vp, vp, i32, i32, vp], c.c_int),
+            "spid_reset": ([vp, vp], c.c_int),
+            "spid_finalize": ([vp, vp], c.c_int),
+            "spid_error": ([vp, vp, vp, vp, vp], c.c_int),
+            "spid_reconstruct": ([vp, vp, vp, vp], c.c_int),
+            "spid_get_factors": ([vp, vp, vp, vp, vp], c.c_int),
+            "spid_get_sketch": ([vp, vp, vp], c.c_int),
+            "spid_device_status": ([vp, vp], c.c_int),
+            "spid_omega": ([u64, i64, i32, i32, i32, vp, vp], c.c_int),
+            "spid_philox": ([vp, u32, u32, vp, i64, vp], c.c_int),
+            "spid_compression_factor": ([i32, vp, vp, vp], dbl),
+            "spid_status_string": ([c.c_int], c.c_char_p),
+            "spid_last_error": ([], c.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str):
+    if status != SPID_OK:
+        detail = load_library().spid_last_error().decode(errors="replace")
+        raise SpidError(status, where, detail)
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if not t.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        return t.data_ptr()
+    return int(t)
+
+
+class Plan:
+    """Batched sketched column-ID plan over a window of subdomains.
+
+    m, n, off, ld: per-subdomain rows, columns, element offset and leading
+    dimension of the column-major blocks inside one flat window buffer."""
+
+    def __init__(self, m, n, off, ld, k_max: int, p: int = 10, tol: float = 0.0,
+                 precision: str = "tf32", seed: int = 0x5EED0001, flags: int = 0):
+        lib = load_library()
+        self.m = np.ascontiguousarray(m, dtype=np.int32)
+        self.n = np.ascontiguousarray(n, dtype=np.int32)
+        self.off = np.ascontiguousarray(off, dtype=np.int64)
+        self.ld = np.ascontiguousarray(ld, dtype=np.int64)
+        self.S = int(len(self.m))
+        self.k_max = int(k_max)
+        self.p = int(p)
+        self.precision = precision
+        self.dtype = np.float64 if precision == "fp64" else np.float32
+        d = _Desc()
+        d.num_sub = self.S
+        d.m = self.m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        d.n = self.n.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        d.off = self.off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        d.ld = self.ld.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        d.k_max = self.k_max
+        d.p = self.p
+        d.tol = float(tol)
+        d.precision = PREC[precision]
+        d.flags = int(flags)
+        d.seed = int(seed)
+        h = ctypes.c_void_p()
+        _check(lib.spid_plan_create(ctypes.byref(d), ctypes.byref(h)), "spid_plan_create")
+        self._h = h
+        l = ctypes.c_int32()
+        lp = ctypes.c_int32()
+        ws = ctypes.c_int64()
+        _check(lib.spid_plan_info(h, ctypes.byref(l), ctypes.byref(lp), ctypes.byref(ws)),
+               "spid_plan_info")
+        self.l, self.l_pad, self.workspace_bytes = int(l.value), int(lp.value), int(ws.value)
+
+    @classmethod
+    def for_window(cls, win, **kw) -> "Plan":
+        return cls(win.m, win.n, win.off, win.ld, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().spid_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- hot path
+    def sketch(self, window, col0: int = 0, ncols: int | None = None, stream=None):
+        if ncols is None:
+            ncols = int(self.n.max()) - col0
+        _check(load_library().spid_sketch(self._h, _ptr(window), int(col0), int(ncols),
+                                          _stream_handle(stream)), "spid_sketch")
+
+    def reset(self, stream=None):
+        _check(load_library().spid_reset(self._h, _stream_handle(stream)), "spid_reset")
+
+    def finalize(self, stream=None):
+        _check(load_library().spid_finalize(self._h, _stream_handle(stream)), "spid_finalize")
+
+    def error(self, window, err=None, total=None, stream=None):
+        _check(load_library().spid_error(self._h, _ptr(window), _ptr(err), _ptr(total),
+                                         _stream_handle(stream)), "spid_error")
+
+    def reconstruct(self, window, out, stream=None):
+        _check(load_library().spid_reconstruct(self._h, _ptr(window), _ptr(out),
+                                               _stream_handle(stream)), "spid_reconstruct")
+
+    # ---------------------------------------------------------------- results
+    def factors(self, stream=None):
+        """(k [S], J [S, k_max], C list of k_max x n_s arrays)."""
+        k = np.zeros(self.S, dtype=np.int32)
+        J = np.zeros((self.S, self.k_max), dtype=np.int32)
+        C = np.zeros(self.k_max * int(self.n.sum()), dtype=self.dtype)
+        _check(load_library().spid_get_factors(self._h, k.ctypes.data, J.ctypes.data,
+                                               C.ctypes.data, _stream_handle(stream)),
+               "spid_get_factors")
+        coff = np.concatenate([[0], np.cumsum(self.n)]) * self.k_max
+        Cs = [C[coff[s]:coff[s + 1]].reshape(self.k_max, int(self.n[s])) for s in range(self.S)]
+        return k, J, Cs
+
+    def sketches(self, stream=None):
+        """List of Y_s as l x n_s arrays."""
+        Y = np.zeros(self.l_pad * int(self.n.sum()), dtype=self.dtype)
+        _check(load_library().spid_get_sketch(self._h, Y.ctypes.data, _stream_handle(stream)),
+               "spid_get_sketch")
+        yoff = np.concatenate([[0], np.cumsum(self.n)]) * self.l_pad
+        return [Y[yoff[s]:yoff[s + 1]].reshape(int(self.n[s]), self.l_pad)[:, :self.l].T
+                for s in range(self.S)]
+
+    def device_status(self, stream=None) -> int:
+        return int(load_library().spid_device_status(self._h, _stream_handle(stream)))
+
+
+def omega(seed: int, r0: int, nrows: int, l: int, precision: str, out, stream=None):
+    _check(load_library().spid_omega(int(seed), int(r0), int(nrows), int(l), PREC[precision],
+                                     _ptr(out), _stream_handle(stream)), "spid_omega")
+
+
+def philox(ctr, key0: int, key1: int, out, stream=None):
+    _check(load_library().spid_philox(_ptr(ctr), int(key0), int(key1), _ptr(out),
+                                      int(ctr.numel() // 4), _stream_handle(stream)), "spid_philox")
+
+
+def compression_factor(m, n, k) -> float:
+    m = np.ascontiguousarray(m, dtype=np.int32)
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    k = np.ascontiguousarray(k, dtype=np.int32)
+    return float(load_library().spid_compression_factor(len(m), m.ctypes.data, n.ctypes.data,
+                                                        k.ctypes.data))

@@ -1,0 +1,46 @@
+"""Shared test helpers: oracle runs, separation of pivots, relative errors."""
+import numpy as np
+
+import oracle
+
+U_MODE = {"fp64": 2.0 ** -53, "fp32": 2.0 ** -24, "tf32": 2.0 ** -11}
+
+
+def rel_fro(a, b) -> float:
+    """||a - b||_F / ||b||_F (0 when both are zero)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return float(np.linalg.norm(a))
+    return float(np.linalg.norm(a - b) / nb)
+
+
+def separated_prefix(Y: np.ndarray, k: int, gap: float) -> int:
+    """Number of leading pivot steps of the oracle's pivoted QR of Y at which the
+    best residual norm^2 beats the runner-up by a relative margin >= gap.  J must
+    agree bit-exactly over this prefix; past it several pivots are valid."""
+    Y = np.asarray(Y, dtype=np.float64)
+    l, n = Y.shape
+    J, R, kk, _ = oracle.qrcp_mgs(Y, k)
+    col2 = (Y * Y).sum(0)
+    for j in range(kk):
+        nu = col2 - (R[:j] ** 2).sum(0) if j > 0 else col2.copy()
+        nu[J[:j]] = -np.inf
+        order = np.sort(nu)[::-1]
+        best = order[0]
+        second = order[1] if n - j > 1 else -np.inf
+        if not (best > 0) or (best - second) / best < gap:
+            return j
+    return kk
+
+
+def oracle_window(win, l, kmax, tol, precision, seed):
+    """Oracle SPID over every subdomain of a window (values taken exactly into FP64)."""
+    return oracle.spid_batch(win.data, win.m, win.n, win.off, win.ld, l, kmax, tol,
+                             U_MODE[precision], seed, want_y=True)
+
+
+def oracle_reconstruction(A: np.ndarray, J, C, k: int) -> np.ndarray:
+    Ahat, _, _ = oracle.reconstruct_error(A, np.asarray(J[:k], dtype=np.int32), C[:k])
+    return Ahat

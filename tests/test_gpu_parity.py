@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on
+the same seeded inputs.
+
+Tolerances (element-wise relative Frobenius norms unless stated):
+  * Philox words: bit-exact.  Omega: FP64 <= 1e-13 abs, FP32 <= 2e-5 abs.
+  * Sketch Y: FP64 <= 1e-13, FP32 <= 2e-6, TF32 <= 3e-3 (FP32 data truncated
+    to TF32's 10-bit mantissa, two roundings of ~2^-11 each, random signs).
+  * J: identical over the oracle's separated pivot prefix (gap 1e-6 FP64,
+    1e-3 FP32, 2e-2 TF32); past it several pivots are valid and only the
+    reconstruction is compared.
+  * C and A_hat: <= 1e-10 in FP64 mode, <= 1e-5 in FP32 mode (on inputs whose
+    R11 is well conditioned for C; A_hat always).
+  * Relative error sqrt(e2/a2): |gpu - oracle| <= the A_hat difference bound.
+  * TF32: final relative error <= max(1e-3, 2 x oracle) on the workloads here.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2103_01380_gb300 import inputs, spid
+from _helpers import oracle_window, rel_fro, separated_prefix, U_MODE
+
+pytestmark = pytest.mark.gpu
+
+GAP = {"fp64": 1e-6, "fp32": 1e-3, "tf32": 2e-2}
+Y_TOL = {"fp64": 1e-13, "fp32": 2e-6, "tf32": 3e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_01380_gb300 import build
+    build.build()
+    spid.load_library()
+    torch.cuda.init()
+
+
+def _dev(win):
+    return torch.from_numpy(win.data).cuda()
+
+
+def run_gpu(win, precision, k_max, p=10, tol=0.0, seed=0x5EED0001, flags=0, window=None,
+            batches=None, reconstruct=True):
+    plan = spid.Plan.for_window(win, k_max=k_max, p=p, tol=tol, precision=precision, seed=seed,
+                                flags=flags)
+    w = _dev(win) if window is None else window
+    if batches is None:
+        plan.sketch(w)
+    else:
+        for c0 in range(0, int(win.n.max()), batches):
+            plan.sketch(w, c0, batches)
+    plan.finalize()
+    err = torch.zeros(2 * win.num_sub, dtype=torch.float64, device="cuda")
+    tot = torch.zeros(4, dtype=torch.float64, device="cuda")
+    plan.error(w, err, tot)
+    out = torch.zeros_like(w) if reconstruct else None
+    if reconstruct:
+        plan.reconstruct(w, out)
+    torch.cuda.synchronize()
+    k, J, C = plan.factors()
+    Y = plan.sketches()
+    res = {"k": k, "J": J, "C": C, "Y": Y, "err": err.cpu().numpy().reshape(-1, 2),
+           "total": tot.cpu().numpy(), "status": plan.device_status(), "plan": plan}
+    if reconstruct:
+        ow = inputs.Window(out.cpu().numpy(), win.m, win.n, win.off, win.ld)
+        res["Ahat"] = [ow.block(s).copy() for s in range(win.num_sub)]
+    return res
+
+
+def check_parity(win, precision, k_max, p=10, tol=0.0, seed=0x5EED0001, c_tol=None,
+                 ahat_tol=None, **kw):
+    g = run_gpu(win, precision, k_max, p, tol, seed, **kw)
+    o = oracle_window(win, k_max + p, k_max, tol, precision, seed)
+    assert g["status"] == 0
+    for s in range(win.num_sub):
+        A = win.block(s).astype(np.float64)
+        Yo = o["Y"][s]
+        assert rel_fro(g["Y"][s], Yo) <= Y_TOL[precision], (s, rel_fro(g["Y"][s], Yo))
+        ko, kg = int(o["k"][s]), int(g["k"][s])
+        pre = min(separated_prefix(Yo, max(ko, 1), GAP[precision]), ko)
+        assert list(g["J"][s][:pre]) == list(o["J"][s][:pre]), (s, g["J"][s], o["J"][s], pre)
+        Jg = g["J"][s][:kg]
+        if kg:
+            # C(:, J) = I exactly (Lemma A.1 item 1)
+            assert np.array_equal(g["C"][s][:kg][:, Jg], np.eye(kg, dtype=g["C"][s].dtype))
+        if kg == ko and list(Jg) == list(o["J"][s][:ko]):
+            if c_tol is not None:
+                assert rel_fro(g["C"][s][:kg], o["C"][s][:ko]) <= c_tol, (s, rel_fro(g["C"][s][:kg], o["C"][s][:ko]))
+            if ahat_tol is not None and "Ahat" in g:
+                Ahat_o, e2, a2 = oracle.reconstruct_error(A, o["J"][s][:ko], o["C"][s][:ko])
+                d = rel_fro(g["Ahat"][s], Ahat_o)
+                assert d <= ahat_tol, (s, d)
+                eg = np.sqrt(g["err"][s, 0] / g["err"][s, 1])
+                eo = np.sqrt(e2 / a2)
+                assert abs(eg - eo) <= ahat_tol * 1.01 + 1e-7 * eo, (s, eg, eo)
+                assert g["err"][s, 1] == pytest.approx(a2, rel=1e-6 if precision != "fp64" else 1e-12)
+    return g, o
+
+
+# ---------------------------------------------------------------- RNG
+def test_philox_bitexact():
+    rng = np.random.default_rng(3)
+    ctr = rng.integers(0, 2 ** 32, size=(20000, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:3] = [[0, 0, 0, 0], [0xffffffff] * 4, [0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344]]
+    for key in [(0, 0), (0xffffffff, 0xffffffff), (0xa4093822, 0x299f31d0), (12345, 678)]:
+        out = torch.zeros(ctr.size, dtype=torch.int32, device="cuda")
+        spid.philox(torch.from_numpy(ctr.view(np.int32)).cuda(), key[0], key[1], out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint32).reshape(-1, 4)
+        want = oracle.philox4x32_10(ctr, key)
+        assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 2e-5)])
+def test_omega_matches_oracle(precision, tol):
+    seed, r0, nrows, l = 0x5EED0002, 12345, 4000, 42
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    out = torch.zeros(nrows * l, dtype=dt, device="cuda")
+    spid.omega(seed, r0, nrows, l, precision, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64).reshape(nrows, l).T
+    want = oracle.omega(seed, r0, nrows, l)
+    assert np.max(np.abs(got - want)) <= tol
+
+
+# ---------------------------------------------------------------- whole path
+def _lowrank_window(S, m, n, r, seed, noise=1e-4, dtype=np.float32, layout="subdomain", decay=0.5):
+    blocks = [inputs.separated_lowrank(m[s] if np.ndim(m) else m, n[s] if np.ndim(n) else n, r,
+                                       seed + s, decay=decay, noise=noise) for s in range(S)]
+    return inputs.pack_blocks(blocks, dtype=dtype, layout=layout)
+
+
+def test_fp64_parity_tgv2d_full_config():
+    # 2D analytic TGV + 1e-6 noise, m = 8192, n = 128, k = 10, p = 10 (Section 5.1 case)
+    A = inputs.tgv2d(nx=64, n=128, noise=1e-6, seed=1)
+    win = inputs.pack_blocks([A], dtype=np.float64)
+    g, o = check_parity(win, "fp64", 10, c_tol=1e-10, ahat_tol=1e-10, seed=0x5EED0001)
+    assert g["k"][0] == 10
+    rel = np.sqrt(g["total"][0] / g["total"][1])
+    assert rel < 1e-5
+    assert g["total"][2] / g["total"][3] == pytest.approx(8192 * 128 / (10 * (8192 + 128)))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_parity_ragged_multi_subdomain(precision):
+    # several subdomains with ragged rows (not a multiple of 32) and columns
+    # crossing 128-column tiles and column groups
+    m = [33, 200, 1000, 517]
+    n = [40, 300, 130, 600] if precision == "fp32" else [40, 300, 130, 257]
+    dt = np.float64 if precision == "fp64" else np.float32
+    win = _lowrank_window(4, m, n, 6, seed=10, dtype=dt)
+    tol = 1e-10 if precision == "fp64" else 1e-5
+    check_parity(win, precision, 5, p=8, c_tol=tol, ahat_tol=tol)
+
+
+def test_tf32_sketch_accuracy_and_parity():
+    m = [33, 200, 1000, 4099]
+    n = [40, 300, 130, 600]
+    win = _lowrank_window(4, m, n, 6, seed=20, noise=1e-3)
+    g, o = check_parity(win, "tf32", 5, p=8)
+    for s in range(4):
+        eg = np.sqrt(g["err"][s, 0] / g["err"][s, 1])
+        eo = np.sqrt(o["e2"][s] / o["a2"][s])
+        assert eg <= max(1e-3, 2.0 * eo), (s, eg, eo)
+
+
+def test_snapshot_major_layout():
+    # [j][s][r] window: every snapshot contiguous, ld = sum of padded rows
+    win = _lowrank_window(3, [100, 64, 257], [90, 90, 90], 5, seed=30, layout="snapshot")
+    for prec in ("fp32", "tf32"):
+        check_parity(win, prec, 4, p=6, ahat_tol=1e-5 if prec == "fp32" else None)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32"])
+def test_edge_cases(precision):
+    # n < k_max, n = 1, m < 32, k_max = 1
+    blocks = [inputs.separated_lowrank(20, 3, 2, 1), inputs.separated_lowrank(5, 1, 1, 2),
+              inputs.separated_lowrank(70, 50, 4, 3)]
+    win = inputs.pack_blocks(blocks)
+    g, o = check_parity(win, precision, 6, p=4)
+    assert g["k"][0] <= 3 and g["k"][1] == 1
+    g1, o1 = check_parity(win, precision, 1, p=4)
+    assert list(g1["k"]) == [1, 1, 1]
+
+
+def test_zero_window_gives_rank_zero():
+    win = inputs.pack_blocks([np.zeros((64, 20)), np.zeros((40, 10))])
+    g = run_gpu(win, "fp32", 4, p=4)
+    assert list(g["k"]) == [0, 0]
+    assert np.all(g["J"] == -1)
+    assert np.all(g["err"] == 0.0)
+    assert g["status"] == 0
+
+
+def test_nonfinite_input_is_reported():
+    A = inputs.separated_lowrank(64, 20, 3, 1)
+    A[5, 7] = np.nan
+    win = inputs.pack_blocks([A, inputs.separated_lowrank(64, 20, 3, 2)])
+    g = run_gpu(win, "fp32", 4, p=4, reconstruct=False)
+    assert g["status"] == 6            # SPID_ERR_NONFINITE
+    assert g["k"][0] == 0 and g["k"][1] > 0
+
+
+def test_adaptive_rank_geometric_spectrum():
+    # sigma_i = 10^{-i/4}: adaptive tolerance 1e-3 (Remark 2.1 reading)
+    sig = 10.0 ** (-np.arange(1, 129) / 4.0)
+    blocks = [inputs.spectrum_matrix(2048, 128, sig, seed=3 + s) for s in range(3)]
+    win = inputs.pack_blocks(blocks)
+    for prec in ("fp32", "tf32"):
+        g, o = check_parity(win, prec, 32, p=10, tol=1e-3,
+                            ahat_tol=1e-5 if prec == "fp32" else None)
+        for s in range(3):
+            assert abs(int(g["k"][s]) - int(o["k"][s])) <= (0 if prec == "fp32" else 2)
+            assert np.sqrt(g["err"][s, 0] / g["err"][s, 1]) <= 3e-3
+
+
+def test_per_subdomain_launches_match_batched():
+    win = _lowrank_window(5, [300, 129, 640, 64, 1000], [200, 64, 100, 513, 77], 5, seed=40)
+    for prec in ("fp32", "tf32"):
+        a = run_gpu(win, prec, 5, p=6)
+        b = run_gpu(win, prec, 5, p=6, flags=spid.FLAG_PER_SUBDOMAIN)
+        for s in range(5):
+            assert rel_fro(a["Y"][s], b["Y"][s]) <= 1e-6
+            assert list(a["J"][s]) == list(b["J"][s])
+            assert rel_fro(a["Ahat"][s], b["Ahat"][s]) <= 1e-5
+
+
+def test_streamed_micro_batches_match_one_shot():
+    win = _lowrank_window(3, [500, 777, 256], [256, 200, 130], 5, seed=50)
+    for prec in ("fp32", "tf32"):
+        a = run_gpu(win, prec, 5, p=6)
+        b = run_gpu(win, prec, 5, p=6, batches=64)
+        c = run_gpu(win, prec, 5, p=6, batches=1)
+        for s in range(3):
+            assert rel_fro(b["Y"][s], a["Y"][s]) <= 1e-6
+            assert rel_fro(c["Y"][s], a["Y"][s]) <= 1e-6
+            assert list(b["J"][s]) == list(a["J"][s])
+
+
+def test_sketch_is_scale_equivariant_fp64():
+    # Omega fixed, so Y(2^7 A) = 2^7 Y(A) exactly and J, C are unchanged
+    A = inputs.separated_lowrank(300, 40, 5, 9, noise=1e-3)
+    w1 = inputs.pack_blocks([A], dtype=np.float64)
+    w2 = inputs.pack_blocks([A * 2.0 ** 7], dtype=np.float64)
+    a = run_gpu(w1, "fp64", 4, p=6)
+    b = run_gpu(w2, "fp64", 4, p=6)
+    assert np.array_equal(b["Y"][0], a["Y"][0] * 2.0 ** 7)
+    assert list(a["J"][0]) == list(b["J"][0])
+    assert np.array_equal(a["C"][0], b["C"][0])
+
+
+@pytest.mark.parametrize("precision", ["tf32", "fp32"])
+def test_tgv3d_full_size_sampled_parity(precision):
+    # 64 boxes of 16^3 x 5 QoIs (m = 20480), n = 512, k = 20, p = 10: the whole
+    # window on the GPU, the oracle on three sampled subdomains.
+    win = inputs.tgv3d_window(grid=64, box=16, n=512)
+    g = run_gpu(win, precision, 20, p=10, reconstruct=False)
+    assert g["status"] == 0
+    rel = np.sqrt(g["total"][0] / g["total"][1])
+    assert rel <= 1e-3, rel
+    for s in (0, 27, 63):
+        A = win.block(s).astype(np.float64)
+        o = oracle.spid(A, 30, 20, 0.0, U_MODE[precision], 0x5EED0001, want_y=True)
+        assert rel_fro(g["Y"][s], o["Y"]) <= Y_TOL[precision]
+        pre = min(separated_prefix(o["Y"], max(o["k"], 1), GAP[precision]), o["k"])
+        assert list(g["J"][s][:pre]) == list(o["J"][:pre])
+        eg = np.sqrt(g["err"][s, 0] / g["err"][s, 1])
+        eo = np.sqrt(o["e2"] / o["a2"])
+        assert eg <= max(1e-3, 2 * eo)
