@@ -160,7 +160,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="tf32", choices=["tf32", "fp32"])
     ap.add_argument("--ref-subs", type=int, default=16)
-    ap.add_argument("--cpu-sample", type=int, default=32)
+    ap.add_argument("--cpu-sample", type=int, default=64)
+    ap.add_argument("--boxes", type=int, default=None,
+                    help="first N boxes only (small profiling case; not the bench workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     args = ap.parse_args()
@@ -179,7 +181,7 @@ def main():
     build.build()
     spid.load_library()
 
-    win = make_window(rank)
+    win = make_window(rank, boxes=args.boxes)
     nbytes = float(win.nbytes_payload())
     host = torch.from_numpy(win.data).pin_memory()
     dev = host.cuda()
@@ -237,6 +239,7 @@ def main():
     totals = tot.detach().cpu().to(torch.float64)
     if world > 1:
         dist.all_reduce(totals)
+    totals = totals.numpy()
     rel_err = float(np.sqrt(totals[0] / totals[1]))
     cf = float(totals[2] / totals[3])
     k, J, C = plan.factors()
@@ -274,7 +277,7 @@ def main():
         pl = make_plan("fp32", flags=spid.FLAG_PER_SUBDOMAIN)
         c_ms, c_sk, c_fi, c_er = timed(pl, max(3, args.steps // 4), args.warmup)
         torch.cuda.synchronize()
-        c_tot = tot.detach().cpu()
+        c_tot = tot.detach().cpu().numpy()
         comparator = {"form": "plain FP32 (SIMT sketch, per-subdomain launches)",
                       "value": nbytes * max(3, args.steps // 4) / (c_ms / 1e3) / 1e9,
                       "sketch_gbs": nbytes / (statistics.mean(c_sk) / 1e3) / 1e9,
@@ -302,7 +305,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 (tf32 sketch)" if args.precision == "tf32" else "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": args.precision,
+            "config": {"workload": WORKLOAD if args.boxes is None else
+                       f"first {args.boxes} boxes of: " + WORKLOAD, "precision": args.precision,
                        "subdomains_per_gpu": win.num_sub, "bytes_per_step_per_gpu": nbytes,
                        "l2": "inputs (2.68 GB) larger than L2; no flush"},
             "stages_ms": {"sketch": sk_ms, "finalize": fi_ms, "error": er_ms},

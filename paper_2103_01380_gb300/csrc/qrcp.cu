@@ -9,8 +9,9 @@
 // plus a dot product and an axpy per column.  Pivoting never moves data: the
 // pivot column's owner publishes the reflector, and the column is retired.
 //   - pivot = largest residual norm^2, kept in FP64 by downdating
-//     (nu -= R(j,c)^2) and recomputed from scratch in FP64 whenever it has
-//     lost two digits; ties go to the lowest column index;
+//     (nu -= R(j,c)^2) and recomputed from the remaining rows (accumulated in
+//     the working precision) whenever it has lost two digits; the argmax is
+//     exact in FP64 with ties to the lowest column index;
 //   - adaptive stop: smallest k with sum of residual norms^2 <= tol^2 ||Y||_F^2;
 //   - rank guard: keep leading pivots with |R_jj| > 2 u |R_00|;
 //   - T = R11^-1 R12 by FP64 back-substitution, one thread per column, in
@@ -25,17 +26,37 @@ namespace {
 
 constexpr int kMaxWarps = 16;
 
+// Exact FP64 argmax with ties to the lowest column: the bit pattern of a
+// non-negative double orders like the value, so the warp reduces the high
+// word, then the low word among the leaders, then the column among the exact
+// winners, with three integer redux.sync operations.
+struct PivotKey {
+  uint32_t hi, lo, col;
+};
+
+__device__ __forceinline__ PivotKey warp_pivot(double nu, uint32_t col) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(nu);
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  const uint32_t mhi = __reduce_max_sync(0xffffffffu, hi);
+  const uint32_t mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+  const uint32_t mcol = __reduce_min_sync(0xffffffffu, (hi == mhi && lo == mlo) ? col : 0xffffffffu);
+  return {mhi, mlo, mcol};
+}
+
+__device__ __forceinline__ bool key_better(const PivotKey& a, const PivotKey& b) {
+  if (a.hi != b.hi) return a.hi > b.hi;
+  if (a.lo != b.lo) return a.lo > b.lo;
+  return a.col < b.col;
+}
+
 template <typename T, int LP, int CPT>
 __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
-  __shared__ T vs[LP];                 // Householder vector of the current step
-  __shared__ double beta_s;
+  __shared__ T vs[2][LP];              // Householder vector, double-buffered by step parity
+  __shared__ T beta_s[2];
   __shared__ double R11[LP][LP];       // R11(i, p) = R(i, J[p])
   __shared__ int Js[LP];
-  __shared__ double red_nu[kMaxWarps];
-  __shared__ int red_col[kMaxWarps];
-  __shared__ double red_rest[kMaxWarps];
-  __shared__ double b_nu, b_rest;
-  __shared__ int b_col;
+  __shared__ uint4 red_key[2][kMaxWarps];
+  __shared__ double red_rest[2][kMaxWarps];
 
   const int s = blockIdx.x + a.sub_base;
   const int n = a.n[s];
@@ -45,25 +66,26 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
   int kcap = a.k_max;
   if (kcap > a.l) kcap = a.l;
   if (kcap > n) kcap = n;
+  const bool adaptive = a.tol > 0.0;
 
   const T* Y = static_cast<const T*>(a.Y) + a.yoff[s];
   T y[CPT][LP];
-  double nu[CPT], nuref[CPT];
+  double nu[CPT], nu_floor[CPT];
   int step_of[CPT];
   bool bad = false;
 #pragma unroll
   for (int c = 0; c < CPT; ++c) {
     const int col = tid + c * NT;
     step_of[c] = (col < n) ? -1 : -2;   // -1 active, -2 no column, >= 0 pivot step
-    double acc = 0.0;
+    T acc = T(0);
 #pragma unroll
     for (int i = 0; i < LP; ++i) {
       y[c][i] = (col < n) ? Y[(int64_t)col * LP + i] : T(0);
-      if (!isfinite((double)y[c][i])) bad = true;
-      acc += (double)y[c][i] * (double)y[c][i];
+      if (!isfinite(y[c][i])) bad = true;
+      acc = fma(y[c][i], y[c][i], acc);
     }
-    nu[c] = acc;
-    nuref[c] = acc;
+    nu[c] = (double)acc;
+    nu_floor[c] = 1e-2 * nu[c];
   }
   T* C = static_cast<T*>(a.C) + a.coff[s];
   if (__syncthreads_or(bad)) {
@@ -75,109 +97,98 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
     for (int64_t e = tid; e < (int64_t)a.k_max * n; e += NT) C[e] = T(0);
     return;
   }
-  // ||Y||_F^2 (fixed-order block sum)
-  {
+  // ||Y||_F^2, fixed-order block sum (adaptive mode only)
+  double normY2 = 0.0;
+  if (adaptive) {
     double t = 0.0;
 #pragma unroll
     for (int c = 0; c < CPT; ++c)
       if (step_of[c] == -1) t += nu[c];
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    if (lane == 0) red_rest[warp] = t;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red_rest[1][warp] = t;
     __syncthreads();
-    if (tid == 0) {
-      double tot = 0.0;
-      for (int w = 0; w < nwarps; ++w) tot += red_rest[w];
-      b_rest = tot;
-    }
-    __syncthreads();
+    for (int w = 0; w < nwarps; ++w) normY2 += red_rest[1][w];
   }
-  const double normY2 = b_rest;
   const double tol2 = a.tol * a.tol;
 
   int k = 0;
   for (int j = 0; j < kcap; ++j) {
-    // ---- argmax of the residual norms (ties -> lowest column), and their sum
+    const int par = j & 1;
+    // ---- argmax of the residual norms^2 (exact FP64, ties -> lowest column)
     double bnu = -1.0, rest = 0.0;
-    int bcol = 0x7fffffff;
+    uint32_t bcol = 0xffffffffu;
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
       if (step_of[c] != -1) continue;
-      const int col = tid + c * NT;
       rest += nu[c];
-      if (nu[c] > bnu || (nu[c] == bnu && col < bcol)) { bnu = nu[c]; bcol = col; }
+      if (nu[c] > bnu) { bnu = nu[c]; bcol = (uint32_t)(tid + c * NT); }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      const double on = __shfl_down_sync(0xffffffffu, bnu, o);
-      const int oc = __shfl_down_sync(0xffffffffu, bcol, o);
-      rest += __shfl_down_sync(0xffffffffu, rest, o);
-      if (on > bnu || (on == bnu && oc < bcol)) { bnu = on; bcol = oc; }
-    }
-    if (lane == 0) { red_nu[warp] = bnu; red_col[warp] = bcol; red_rest[warp] = rest; }
-    __syncthreads();
-    if (tid == 0) {
-      double gn = -1.0, gr = 0.0;
-      int gc = 0x7fffffff;
-      for (int w = 0; w < nwarps; ++w) {
-        gr += red_rest[w];
-        if (red_nu[w] > gn || (red_nu[w] == gn && red_col[w] < gc)) { gn = red_nu[w]; gc = red_col[w]; }
-      }
-      b_nu = gn; b_col = gc; b_rest = gr;
+    const PivotKey wk = warp_pivot(bnu > 0.0 ? bnu : 0.0, bcol);
+    if (adaptive)
+      for (int o = 16; o > 0; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
+    if (lane == 0) {
+      red_key[par][warp] = make_uint4(wk.hi, wk.lo, wk.col, 0u);
+      red_rest[par][warp] = rest;
     }
     __syncthreads();
-    if (a.tol > 0.0 && b_rest <= tol2 * normY2) break;
-    if (!(b_nu > 0.0)) break;
-    const int pcol = b_col;
+    PivotKey best = {0u, 0u, 0xffffffffu};
+    double trest = 0.0;
+    for (int w = 0; w < nwarps; ++w) {
+      const uint4 q = red_key[par][w];
+      const PivotKey kq = {q.x, q.y, q.z};
+      if (key_better(kq, best)) best = kq;
+      if (adaptive) trest += red_rest[par][w];
+    }
+    if (adaptive && trest <= tol2 * normY2) break;
+    if ((best.hi | best.lo) == 0u || best.col == 0xffffffffu) break;   // residual is zero
+    const int pcol = (int)best.col;
     // ---- the owner of the pivot column builds the reflector
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
       if (tid + c * NT != pcol) continue;
-      double sig = 0.0;
+      double sig = 0.0, xj = 0.0;
 #pragma unroll
-      for (int i = 0; i < LP; ++i)
+      for (int i = 0; i < LP; ++i) {
         if (i > j) sig += (double)y[c][i] * (double)y[c][i];
-      double xj = 0.0;
-#pragma unroll
-      for (int i = 0; i < LP; ++i)
         if (i == j) xj = (double)y[c][i];
+      }
       const double norm = sqrt(xj * xj + sig);
       const double alpha = (xj >= 0.0) ? -norm : norm;
       const double vj = xj - alpha;
       const double vtv = vj * vj + sig;
-      beta_s = (vtv > 0.0) ? 2.0 / vtv : 0.0;
+      beta_s[par] = (T)((vtv > 0.0) ? 2.0 / vtv : 0.0);
 #pragma unroll
       for (int i = 0; i < LP; ++i) {
-        if (i < j) { vs[i] = T(0); R11[i][j] = (double)y[c][i]; }
-        else if (i == j) { vs[i] = (T)vj; R11[j][j] = alpha; }
-        else vs[i] = y[c][i];
+        if (i < j) { vs[par][i] = T(0); R11[i][j] = (double)y[c][i]; }
+        else if (i == j) { vs[par][i] = (T)vj; R11[j][j] = alpha; }
+        else vs[par][i] = y[c][i];
       }
       Js[j] = pcol;
       step_of[c] = j;
     }
     __syncthreads();
-    // ---- apply H_j = I - beta v v^T to every remaining column
-    const T beta = (T)beta_s;
+    // ---- apply H_j = I - beta v v^T to every remaining column; downdate the
+    // FP64 norm; recompute it from the remaining rows once it lost two digits
+    const T beta = beta_s[par];
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
       if (step_of[c] != -1) continue;
       T dot = T(0);
 #pragma unroll
       for (int i = 0; i < LP; ++i)
-        if (i >= j) dot = fma(vs[i], y[c][i], dot);
+        if (i >= j) dot = fma(vs[par][i], y[c][i], dot);
       const T f = beta * dot;
-      double rj = 0.0;
+      T rj = T(0), tail = T(0);
 #pragma unroll
       for (int i = 0; i < LP; ++i) {
-        if (i >= j) y[c][i] = fma(-f, vs[i], y[c][i]);
-        if (i == j) rj = (double)y[c][i];
+        if (i >= j) y[c][i] = fma(-f, vs[par][i], y[c][i]);
+        if (i == j) rj = y[c][i];
+        if (i > j) tail = fma(y[c][i], y[c][i], tail);
       }
-      nu[c] -= rj * rj;
-      if (nu[c] < 1e-2 * nuref[c]) {
-        double t = 0.0;
-#pragma unroll
-        for (int i = 0; i < LP; ++i)
-          if (i > j) t += (double)y[c][i] * (double)y[c][i];
-        nu[c] = t;
-        nuref[c] = t;
+      nu[c] -= (double)(rj * rj);
+      if (nu[c] < nu_floor[c]) {
+        nu[c] = (double)tail;
+        nu_floor[c] = 1e-2 * nu[c];
       }
     }
     k = j + 1;
@@ -196,7 +207,7 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
   }
   if (tid == 0) a.k_out[s] = keff;
   for (int i = tid; i < a.k_max; i += NT) a.J[(int64_t)s * a.k_max + i] = (i < keff) ? Js[i] : -1;
-  // ---- coefficients
+  // ---- coefficients: FP64 back-substitution R11 t = R(0:keff, col), in place
 #pragma unroll
   for (int c = 0; c < CPT; ++c) {
     const int col = tid + c * NT;
@@ -205,7 +216,6 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
       for (int i = 0; i < a.k_max; ++i) C[(int64_t)i * n + col] = (i == step_of[c]) ? T(1) : T(0);
       continue;
     }
-    // back-substitution R11 t = R(0:keff, col), in place over y[c][0:keff]
 #pragma unroll
     for (int ii = LP - 1; ii >= 0; --ii) {
       if (ii < keff) {

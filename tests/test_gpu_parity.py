@@ -20,7 +20,7 @@ torch = pytest.importorskip("torch")
 
 import oracle
 from paper_2103_01380_gb300 import inputs, spid
-from _helpers import oracle_window, rel_fro, separated_prefix, U_MODE
+from _helpers import adaptive_margin, oracle_window, r11_condition, rel_fro, separated_prefix, U_MODE
 
 pytestmark = pytest.mark.gpu
 
@@ -75,27 +75,38 @@ def check_parity(win, precision, k_max, p=10, tol=0.0, seed=0x5EED0001, c_tol=No
     g = run_gpu(win, precision, k_max, p, tol, seed, **kw)
     o = oracle_window(win, k_max + p, k_max, tol, precision, seed)
     assert g["status"] == 0
+    u = U_MODE[precision]
     for s in range(win.num_sub):
         A = win.block(s).astype(np.float64)
         Yo = o["Y"][s]
-        assert rel_fro(g["Y"][s], Yo) <= Y_TOL[precision], (s, rel_fro(g["Y"][s], Yo))
+        dy = rel_fro(g["Y"][s], Yo)
+        assert dy <= Y_TOL[precision], ("Y", s, dy)
         ko, kg = int(o["k"][s]), int(g["k"][s])
-        pre = min(separated_prefix(Yo, max(ko, 1), GAP[precision]), ko)
-        assert list(g["J"][s][:pre]) == list(o["J"][s][:pre]), (s, g["J"][s], o["J"][s], pre)
+        if tol > 0 and kg != ko:
+            # adaptive stop taken on both sides in FP64 from sketches that differ by
+            # rounding: a different k is valid only near the threshold
+            margin = adaptive_margin(Yo, k_max, tol, ko)
+            assert abs(kg - ko) <= 1 and margin <= 64 * Y_TOL[precision], ("k", s, kg, ko, margin)
+        pre = min(separated_prefix(Yo, max(ko, 1), GAP[precision], u), ko, kg)
+        assert list(g["J"][s][:pre]) == list(o["J"][s][:pre]), ("J", s, g["J"][s], o["J"][s], pre)
         Jg = g["J"][s][:kg]
         if kg:
             # C(:, J) = I exactly (Lemma A.1 item 1)
             assert np.array_equal(g["C"][s][:kg][:, Jg], np.eye(kg, dtype=g["C"][s].dtype))
         if kg == ko and list(Jg) == list(o["J"][s][:ko]):
             if c_tol is not None:
-                assert rel_fro(g["C"][s][:kg], o["C"][s][:ko]) <= c_tol, (s, rel_fro(g["C"][s][:kg], o["C"][s][:ko]))
+                # C = R11^-1 R12 moves by about cond(R11) u under rounding
+                ct = max(c_tol, 8.0 * r11_condition(Yo, ko) * u)
+                dc = rel_fro(g["C"][s][:kg], o["C"][s][:ko])
+                assert dc <= ct, ("C", s, dc, ct)
             if ahat_tol is not None and "Ahat" in g:
                 Ahat_o, e2, a2 = oracle.reconstruct_error(A, o["J"][s][:ko], o["C"][s][:ko])
                 d = rel_fro(g["Ahat"][s], Ahat_o)
-                assert d <= ahat_tol, (s, d)
+                assert d <= ahat_tol, ("Ahat", s, d)
                 eg = np.sqrt(g["err"][s, 0] / g["err"][s, 1])
                 eo = np.sqrt(e2 / a2)
-                assert abs(eg - eo) <= ahat_tol * 1.01 + 1e-7 * eo, (s, eg, eo)
+                # triangle inequality: |e_gpu - e_oracle| <= ||Ahat_gpu - Ahat_oracle|| / ||A||
+                assert abs(eg - eo) <= d * 1.01 + 4 * u * np.sqrt(A.size), ("err", s, eg, eo)
                 assert g["err"][s, 1] == pytest.approx(a2, rel=1e-6 if precision != "fp64" else 1e-12)
     return g, o
 
@@ -213,7 +224,8 @@ def test_adaptive_rank_geometric_spectrum():
         g, o = check_parity(win, prec, 32, p=10, tol=1e-3,
                             ahat_tol=1e-5 if prec == "fp32" else None)
         for s in range(3):
-            assert abs(int(g["k"][s]) - int(o["k"][s])) <= (0 if prec == "fp32" else 2)
+            if prec == "tf32":
+                assert abs(int(g["k"][s]) - int(o["k"][s])) <= 2
             assert np.sqrt(g["err"][s, 0] / g["err"][s, 1]) <= 3e-3
 
 
@@ -265,7 +277,8 @@ def test_tgv3d_full_size_sampled_parity(precision):
         A = win.block(s).astype(np.float64)
         o = oracle.spid(A, 30, 20, 0.0, U_MODE[precision], 0x5EED0001, want_y=True)
         assert rel_fro(g["Y"][s], o["Y"]) <= Y_TOL[precision]
-        pre = min(separated_prefix(o["Y"], max(o["k"], 1), GAP[precision]), o["k"])
+        pre = min(separated_prefix(o["Y"], max(o["k"], 1), GAP[precision], U_MODE[precision]),
+                  o["k"], int(g["k"][s]))
         assert list(g["J"][s][:pre]) == list(o["J"][:pre])
         eg = np.sqrt(g["err"][s, 0] / g["err"][s, 1])
         eo = np.sqrt(o["e2"] / o["a2"])
