@@ -170,6 +170,36 @@ spid_status spid_philox(const uint32_t* ctr_dev, uint32_t key0, uint32_t key1, u
 double spid_compression_factor(int32_t num_sub, const int32_t* m, const int32_t* n,
                                const int32_t* k);
 
+/* ---- Allocation-free sketch -------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory when they need a sketch: an in-situ
+ * simulation that reserves nearly all GPU memory for its own fields through
+ * its own pool at start-up, or whose time loop must not call cudaMalloc /
+ * cudaFree (they may synchronize the whole device).  Such a caller cannot
+ * create a plan mid-run, because spid_plan_create allocates its workspace.
+ *
+ * spid_sketch_fp32_noalloc computes the FP32 sketch of ONE subdomain,
+ * Y(:, j) = Omega(:, 0:m) A(:, j) for j < n (Omega as defined above, same
+ * values as the FP32 entry points), with A an m x n column-major FP32 matrix
+ * at device pointer A (16-byte aligned, leading dimension ld >= m, a multiple
+ * of 4), and writes Y(i, j) to device memory Y[j * ldy + i] for i < l
+ * (ldy >= l); 1 <= l <= 64.  It allocates nothing and calls no allocating
+ * routine: its split-K partial sums live in one file-scope device array of
+ * SPID_NOALLOC_SCRATCH_FLOATS floats (8 MiB) that every GPU loading this
+ * library holds until the process exits.  Limit: ceil(n / 512) * 512 * l_pad
+ * <= SPID_NOALLOC_SCRATCH_FLOATS (l_pad = l rounded up to 16), i.e. n <= 65536
+ * for l <= 32; larger requests return SPID_ERR_INVALID_ARG with nothing
+ * launched.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call shares the array and leaves its
+ * contents behind (each call overwrites every slot it reads, so nothing needs
+ * clearing); calls that overlap on the GPU -- on different streams, or from
+ * host threads without ordering -- race on the array and must be serialized
+ * by the caller.  Asynchronous on `stream`. */
+#define SPID_NOALLOC_SCRATCH_FLOATS (1u << 21)
+spid_status spid_sketch_fp32_noalloc(const float* A, int32_t m, int32_t n, int64_t ld, int32_t l,
+                                     uint64_t seed, float* Y, int32_t ldy, spid_stream_t stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* spid_status_string(spid_status status);
 

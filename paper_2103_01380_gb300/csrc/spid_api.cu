@@ -56,6 +56,8 @@ struct Schedule {
 
 }  // namespace
 
+void spid::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 struct spid_plan_s {
   int device = 0;
   int num_sms = 0;

@@ -122,6 +122,9 @@ struct ErrFinishArgs {
   int32_t S;
 };
 
+// Detail message returned by spid_last_error() on the calling thread.
+void set_last_error(const char* msg);
+
 // Launchers (one translation unit each).
 int sketch_simt_group_cols(bool fp64);
 cudaError_t launch_sketch_simt(const SketchArgs& a, int grid, bool fp64, cudaStream_t st);

@@ -28,7 +28,8 @@ FLAG_PER_SUBDOMAIN = 1
 EXPORTS = ["spid_plan_create", "spid_plan_destroy", "spid_plan_info", "spid_sketch", "spid_reset",
            "spid_finalize", "spid_error", "spid_reconstruct", "spid_get_factors",
            "spid_get_sketch", "spid_device_status", "spid_omega", "spid_philox",
-           "spid_compression_factor", "spid_status_string", "spid_last_error"]
+           "spid_compression_factor", "spid_status_string", "spid_last_error",
+           "spid_sketch_fp32_noalloc"]
 
 
 class SpidError(RuntimeError):
@@ -84,6 +85,7 @@ def load_library(path: str = LIB_PATH):
             "spid_compression_factor": ([i32, vp, vp, vp], dbl),
             "spid_status_string": ([c.c_int], c.c_char_p),
             "spid_last_error": ([], c.c_char_p),
+            "spid_sketch_fp32_noalloc": ([vp, i32, i32, i64, i32, u64, vp, i32, vp], c.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -236,3 +238,17 @@ def compression_factor(m, n, k) -> float:
     k = np.ascontiguousarray(k, dtype=np.int32)
     return float(load_library().spid_compression_factor(len(m), m.ctypes.data, n.ctypes.data,
                                                         k.ctypes.data))
+
+
+def sketch_fp32_noalloc(A, m: int, n: int, ld: int, l: int, seed: int, Y, ldy: int, stream=None):
+    """FP32 sketch of one subdomain through the allocation-free entry point.
+
+    For callers that cannot allocate device memory mid-run (an in-situ solver
+    that owns nearly all GPU memory through its own pool, or whose time loop
+    must avoid cudaMalloc/cudaFree and their device-wide synchronization): the
+    split-K partials live in the library's fixed 8 MiB static device array, so
+    concurrent calls on different streams race and must be serialized."""
+    _check(load_library().spid_sketch_fp32_noalloc(_ptr(A), int(m), int(n), int(ld), int(l),
+                                                   int(seed), _ptr(Y), int(ldy),
+                                                   _stream_handle(stream)),
+           "spid_sketch_fp32_noalloc")
