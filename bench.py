@@ -317,7 +317,7 @@ def main():
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": int(nbytes),
                     "d2h_bytes_per_step": 32},
-            "gpu_launches": 6 * args.steps,
+            "gpu_launches": 3 * args.steps,
             "clocks": clocks,
             "comparator": comparator}
     if rank == 0 and not args.no_cpu_baseline:

@@ -1,20 +1,26 @@
 // error.cu -- reconstruction A_hat = A(:,J) C (Section 2, column ID form of
 // Algorithm 2) fused with the relative Frobenius error of Section 5.1:
-// ||A - A_hat||_F^2 and ||A||_F^2 per subdomain, reduced in FP64 in a fixed
-// order.
+// ||A - A_hat||_F^2 and ||A||_F^2 per subdomain and over the window, plus the
+// compression-factor sums (Section 2, Eq. for CF).
 //
 // A unit is (subdomain, 512-row block, 256-column block).  The CTA stages the
 // coefficient block C(:, cols) and, per 128-row tile, the skeleton rows
 // A(rows, J) in shared memory, then streams A once: lane l of warp w owns rows
 // 4l..4l+3 of the tile and 4 columns at a time, so each k-step is two shared
 // loads (one a broadcast) feeding 16 FMAs; A is read with 16-byte loads,
-// 512 contiguous bytes per warp per column.  Per-thread sums stay in the
-// working precision over 16 elements, then accumulate in FP64.
+// 512 contiguous bytes per warp per column.
+//
+// Reductions keep FP64 off the per-element path (GB300 runs FP64 at 1/64 of
+// FP32): per-thread sums are Kahan-compensated in the working precision, warps
+// reduce in the working precision, and only the per-CTA, per-subdomain and
+// window totals are FP64.  The last CTA of each subdomain (an atomic counter,
+// after a device-wide fence) sums that subdomain's unit partials in a fixed
+// order, and the last subdomain to finish sums the window totals; every
+// counter is reset by the CTA that completes it, so results are deterministic
+// and the plan is ready for the next call.
 #include "spid_internal.cuh"
 
 namespace spid {
-
-
 
 namespace {
 
@@ -49,9 +55,20 @@ template <> struct V4<double> {
   }
 };
 
+// Kahan-compensated running sum.
+template <typename T>
+__device__ __forceinline__ void kahan_add(T& s, T& c, T x) {
+  const T y = x - c;
+  const T t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
 template <typename T, bool WRITE>
 __global__ void __launch_bounds__(256) error_kernel(ErrArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[2][8];
+  __shared__ int last_sub;
   const int u = blockIdx.x + a.unit_base;
   const int s = a.unit_sub[u];
   const int row0 = a.unit_row0[u], col0 = a.unit_col0[u];
@@ -71,7 +88,7 @@ __global__ void __launch_bounds__(256) error_kernel(ErrArgs a) {
     const int p = e / kErrColBlock, jj = e % kErrColBlock;
     Cs[e] = (jj < ncb) ? Cg[(int64_t)p * n + col0 + jj] : T(0);
   }
-  double se = 0.0, sa = 0.0;
+  T se = T(0), ce = T(0), sa = T(0), ca = T(0);   // Kahan sums of e^2 and a^2
   for (int t0 = 0; t0 < nrb; t0 += kErrTile) {
     const int rt = row0 + t0;                       // first row of the tile
     __syncthreads();
@@ -133,50 +150,72 @@ __global__ void __launch_bounds__(256) error_kernel(ErrArgs a) {
           }
         }
       }
-      se += (double)le;
-      sa += (double)la;
+      kahan_add(se, ce, le);
+      kahan_add(sa, ca, la);
     }
   }
-  // block reduction in a fixed order
-  __shared__ double red[2][8];
+  // warp tree in the working precision, then FP64 across the 8 warps
+  T we = se - ce, wa = sa - ca;
   for (int o = 16; o > 0; o >>= 1) {
-    se += __shfl_down_sync(0xffffffffu, se, o);
-    sa += __shfl_down_sync(0xffffffffu, sa, o);
+    we += __shfl_xor_sync(0xffffffffu, we, o);
+    wa += __shfl_xor_sync(0xffffffffu, wa, o);
   }
-  if (lane == 0) { red[0][warp] = se; red[1][warp] = sa; }
+  if (lane == 0) { red[0][warp] = (double)we; red[1][warp] = (double)wa; }
   __syncthreads();
   if (tid == 0) {
     double te = 0.0, ta = 0.0;
     for (int w = 0; w < 8; ++w) { te += red[0][w]; ta += red[1][w]; }
     a.part[2 * (int64_t)u] = te;
     a.part[2 * (int64_t)u + 1] = ta;
+    __threadfence();
+    const int units_s = a.unit_ptr[s + 1] - a.unit_ptr[s];
+    last_sub = (atomicAdd(&a.sub_cnt[s], 1) == units_s - 1);
   }
-}
-
-__global__ void error_finish_kernel(ErrFinishArgs a) {
-  // one thread per subdomain, then one warp-free serial total (fixed order)
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.S; s += gridDim.x * blockDim.x) {
-    double e = 0.0, q = 0.0;
-    for (int u = a.unit_ptr[s]; u < a.unit_ptr[s + 1]; ++u) {
-      e += a.part[2 * (int64_t)u];
-      q += a.part[2 * (int64_t)u + 1];
-    }
-    a.sub_err[2 * s] = e;
-    a.sub_err[2 * s + 1] = q;
-    if (a.err) { a.err[2 * s] = e; a.err[2 * s + 1] = q; }
+  __syncthreads();
+  if (!last_sub || warp != 0) return;
+  // ---- this CTA completed subdomain s: fixed-order sum of its unit partials
+  __threadfence();
+  const int u0 = a.unit_ptr[s], u1 = a.unit_ptr[s + 1];
+  double es = 0.0, as = 0.0;
+  for (int q = u0 + lane; q < u1; q += 32) {
+    es += __ldcg(a.part + 2 * (int64_t)q);
+    as += __ldcg(a.part + 2 * (int64_t)q + 1);
   }
-}
-
-__global__ void error_total_kernel(ErrFinishArgs a) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int o = 16; o > 0; o >>= 1) {
+    es += __shfl_xor_sync(0xffffffffu, es, o);
+    as += __shfl_xor_sync(0xffffffffu, as, o);
+  }
+  int last_all = 0;
+  if (lane == 0) {
+    a.sub_err[2 * s] = es;
+    a.sub_err[2 * s + 1] = as;
+    if (a.err) { a.err[2 * s] = es; a.err[2 * s + 1] = as; }
+    a.sub_cnt[s] = 0;
+    __threadfence();
+    last_all = (atomicAdd(a.all_cnt, 1) == a.S - 1);
+  }
+  last_all = __shfl_sync(0xffffffffu, last_all, 0);
+  if (!last_all) return;
+  // ---- last subdomain of the window: fixed-order window totals
+  __threadfence();
   double te = 0.0, ta = 0.0, mn = 0.0, kd = 0.0;
-  for (int s = 0; s < a.S; ++s) {
-    te += a.sub_err[2 * s];
-    ta += a.sub_err[2 * s + 1];
-    mn += (double)a.m[s] * (double)a.n[s];
-    kd += (double)a.k[s] * ((double)a.m[s] + (double)a.n[s]);
+  for (int q = lane; q < a.S; q += 32) {
+    te += __ldcg(a.sub_err + 2 * (int64_t)q);
+    ta += __ldcg(a.sub_err + 2 * (int64_t)q + 1);
+    const double mq = (double)a.m[q], nq = (double)a.n[q];
+    mn += mq * nq;
+    kd += (double)a.k[q] * (mq + nq);
   }
-  if (a.total) { a.total[0] = te; a.total[1] = ta; a.total[2] = mn; a.total[3] = kd; }
+  for (int o = 16; o > 0; o >>= 1) {
+    te += __shfl_xor_sync(0xffffffffu, te, o);
+    ta += __shfl_xor_sync(0xffffffffu, ta, o);
+    mn += __shfl_xor_sync(0xffffffffu, mn, o);
+    kd += __shfl_xor_sync(0xffffffffu, kd, o);
+  }
+  if (lane == 0) {
+    if (a.total) { a.total[0] = te; a.total[1] = ta; a.total[2] = mn; a.total[3] = kd; }
+    *a.all_cnt = 0;
+  }
 }
 
 }  // namespace
@@ -203,14 +242,6 @@ cudaError_t launch_error(const ErrArgs& a, int units, bool fp64, cudaStream_t st
     if (w) SPID_LAUNCH_ERR(float, true); else SPID_LAUNCH_ERR(float, false);
   }
 #undef SPID_LAUNCH_ERR
-  return cudaGetLastError();
-}
-
-cudaError_t launch_error_finish(const ErrFinishArgs& a, cudaStream_t st) {
-  error_finish_kernel<<<(a.S + 127) / 128, 128, 0, st>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  error_total_kernel<<<1, 32, 0, st>>>(a);
   return cudaGetLastError();
 }
 

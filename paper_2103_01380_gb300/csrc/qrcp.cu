@@ -8,10 +8,14 @@
 // Householder step costs one broadcast of the reflector through shared memory
 // plus a dot product and an axpy per column.  Pivoting never moves data: the
 // pivot column's owner publishes the reflector, and the column is retired.
-//   - pivot = largest residual norm^2, kept in FP64 by downdating
-//     (nu -= R(j,c)^2) and recomputed from the remaining rows (accumulated in
-//     the working precision) whenever it has lost two digits; the argmax is
-//     exact in FP64 with ties to the lowest column index;
+//   - pivot = largest residual norm^2, ties to the lowest column index.  The
+//     norms carry FP64-class precision without the FP64 pipe (GB300 runs FP64
+//     at 1/64 of FP32): in FP32 modes each norm is an unevaluated sum of two
+//     floats (hi + lo, ~48-bit significand) built from exact products
+//     (fma) and error-free additions; it is downdated by the exact square of
+//     the new R entry at every step and recomputed from the remaining rows
+//     whenever it has lost two digits.  In FP64 mode the norms are doubles.
+//     The argmax compares the (hi, lo) pairs exactly with integer redux.
 //   - adaptive stop: smallest k with sum of residual norms^2 <= tol^2 ||Y||_F^2;
 //   - rank guard: keep leading pivots with |R_jj| > 2 u |R_00|;
 //   - T = R11^-1 R12 by FP64 back-substitution, one thread per column, in
@@ -20,32 +24,90 @@
 
 namespace spid {
 
-
-
 namespace {
 
 constexpr int kMaxWarps = 16;
 
-// Exact FP64 argmax with ties to the lowest column: the bit pattern of a
-// non-negative double orders like the value, so the warp reduces the high
-// word, then the low word among the leaders, then the column among the exact
-// winners, with three integer redux.sync operations.
-struct PivotKey {
-  uint32_t hi, lo, col;
+// ---------------------------------------------------------------------------
+// Residual norms: a double-float in FP32 modes, a double in FP64 mode.
+// ---------------------------------------------------------------------------
+template <typename T> struct Norm;
+
+template <> struct Norm<float> {
+  float hi, lo;
+  // error-free a + b = s + e (Knuth two-sum)
+  static __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+  }
+  __device__ __forceinline__ void set_zero() { hi = 0.f; lo = 0.f; }
+  // += y^2 with the product exact (fma) and the sum compensated
+  __device__ __forceinline__ void add_square(float y) {
+    const float p = y * y;
+    const float pe = fmaf(y, y, -p);
+    float s, e;
+    two_sum(hi, p, s, e);
+    e += lo + pe;
+    hi = s + e;
+    lo = e - (hi - s);
+  }
+  // -= y^2, exactly rounded to the pair
+  __device__ __forceinline__ void sub_square(float y) {
+    const float p = y * y;
+    const float pe = fmaf(y, y, -p);
+    float s, e;
+    two_sum(hi, -p, s, e);
+    e += lo - pe;
+    hi = s + e;
+    lo = e - (hi - s);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+  __device__ __forceinline__ bool below(const Norm& floor) const { return hi < floor.hi; }
+  __device__ __forceinline__ Norm scaled(float f) const { return Norm{hi * f, lo * f}; }
+  // order-preserving 64-bit key of a non-negative value (hi, then lo)
+  static __device__ __forceinline__ uint32_t okey(float x) {
+    const uint32_t b = __float_as_uint(x);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+  }
+  __device__ __forceinline__ void key(uint32_t& k0, uint32_t& k1) const {
+    if (!(hi > 0.f)) { k0 = 0u; k1 = 0u; return; }
+    k0 = okey(hi);
+    k1 = okey(lo);
+  }
 };
 
-__device__ __forceinline__ PivotKey warp_pivot(double nu, uint32_t col) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(nu);
-  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
-  const uint32_t mhi = __reduce_max_sync(0xffffffffu, hi);
-  const uint32_t mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
-  const uint32_t mcol = __reduce_min_sync(0xffffffffu, (hi == mhi && lo == mlo) ? col : 0xffffffffu);
-  return {mhi, mlo, mcol};
+template <> struct Norm<double> {
+  double hi;
+  __device__ __forceinline__ void set_zero() { hi = 0.0; }
+  __device__ __forceinline__ void add_square(double y) { hi = fma(y, y, hi); }
+  __device__ __forceinline__ void sub_square(double y) { hi = fma(-y, y, hi); }
+  __device__ __forceinline__ double value() const { return hi; }
+  __device__ __forceinline__ bool below(const Norm& floor) const { return hi < floor.hi; }
+  __device__ __forceinline__ Norm scaled(double f) const { return Norm{hi * f}; }
+  __device__ __forceinline__ void key(uint32_t& k0, uint32_t& k1) const {
+    if (!(hi > 0.0)) { k0 = 0u; k1 = 0u; return; }
+    const unsigned long long b = (unsigned long long)__double_as_longlong(hi);
+    k0 = (uint32_t)(b >> 32);
+    k1 = (uint32_t)b;
+  }
+};
+
+struct PivotKey {
+  uint32_t k0, k1, col;
+};
+
+// Warp argmax of (k0, k1) with ties to the lowest column: three integer redux.
+__device__ __forceinline__ PivotKey warp_pivot(uint32_t k0, uint32_t k1, uint32_t col) {
+  const uint32_t m0 = __reduce_max_sync(0xffffffffu, k0);
+  const uint32_t m1 = __reduce_max_sync(0xffffffffu, k0 == m0 ? k1 : 0u);
+  const uint32_t mc = __reduce_min_sync(0xffffffffu, (k0 == m0 && k1 == m1) ? col : 0xffffffffu);
+  return {m0, m1, mc};
 }
 
 __device__ __forceinline__ bool key_better(const PivotKey& a, const PivotKey& b) {
-  if (a.hi != b.hi) return a.hi > b.hi;
-  if (a.lo != b.lo) return a.lo > b.lo;
+  if (a.k0 != b.k0) return a.k0 > b.k0;
+  if (a.k1 != b.k1) return a.k1 > b.k1;
   return a.col < b.col;
 }
 
@@ -70,22 +132,21 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
 
   const T* Y = static_cast<const T*>(a.Y) + a.yoff[s];
   T y[CPT][LP];
-  double nu[CPT], nu_floor[CPT];
+  Norm<T> nu[CPT], nu_floor[CPT];
   int step_of[CPT];
   bool bad = false;
 #pragma unroll
   for (int c = 0; c < CPT; ++c) {
     const int col = tid + c * NT;
     step_of[c] = (col < n) ? -1 : -2;   // -1 active, -2 no column, >= 0 pivot step
-    T acc = T(0);
+    nu[c].set_zero();
 #pragma unroll
     for (int i = 0; i < LP; ++i) {
       y[c][i] = (col < n) ? Y[(int64_t)col * LP + i] : T(0);
       if (!isfinite(y[c][i])) bad = true;
-      acc = fma(y[c][i], y[c][i], acc);
+      nu[c].add_square(y[c][i]);
     }
-    nu[c] = (double)acc;
-    nu_floor[c] = 1e-2 * nu[c];
+    nu_floor[c] = nu[c].scaled(T(1e-2));
   }
   T* C = static_cast<T*>(a.C) + a.coff[s];
   if (__syncthreads_or(bad)) {
@@ -103,7 +164,7 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
     double t = 0.0;
 #pragma unroll
     for (int c = 0; c < CPT; ++c)
-      if (step_of[c] == -1) t += nu[c];
+      if (step_of[c] == -1) t += nu[c].value();
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (lane == 0) red_rest[1][warp] = t;
     __syncthreads();
@@ -114,81 +175,86 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
   int k = 0;
   for (int j = 0; j < kcap; ++j) {
     const int par = j & 1;
-    // ---- argmax of the residual norms^2 (exact FP64, ties -> lowest column)
-    double bnu = -1.0, rest = 0.0;
-    uint32_t bcol = 0xffffffffu;
+    // ---- argmax of the residual norms^2 (exact on the pairs, ties -> lowest column)
+    uint32_t b0 = 0u, b1 = 0u, bcol = 0xffffffffu;
+    double rest = 0.0;
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
       if (step_of[c] != -1) continue;
-      rest += nu[c];
-      if (nu[c] > bnu) { bnu = nu[c]; bcol = (uint32_t)(tid + c * NT); }
+      uint32_t k0, k1;
+      nu[c].key(k0, k1);
+      if (adaptive) rest += nu[c].value();
+      if (bcol == 0xffffffffu || k0 > b0 || (k0 == b0 && k1 > b1)) {
+        b0 = k0; b1 = k1; bcol = (uint32_t)(tid + c * NT);
+      }
     }
-    const PivotKey wk = warp_pivot(bnu > 0.0 ? bnu : 0.0, bcol);
+    const PivotKey wk = warp_pivot(b0, b1, bcol);
     if (adaptive)
       for (int o = 16; o > 0; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
     if (lane == 0) {
-      red_key[par][warp] = make_uint4(wk.hi, wk.lo, wk.col, 0u);
+      red_key[par][warp] = make_uint4(wk.k0, wk.k1, wk.col, 0u);
       red_rest[par][warp] = rest;
     }
     __syncthreads();
-    PivotKey best = {0u, 0u, 0xffffffffu};
-    double trest = 0.0;
-    for (int w = 0; w < nwarps; ++w) {
-      const uint4 q = red_key[par][w];
-      const PivotKey kq = {q.x, q.y, q.z};
-      if (key_better(kq, best)) best = kq;
-      if (adaptive) trest += red_rest[par][w];
+    // every warp reduces the per-warp winners itself (no second barrier)
+    const uint4 q = (lane < nwarps) ? red_key[par][lane] : make_uint4(0u, 0u, 0xffffffffu, 0u);
+    const PivotKey best = warp_pivot(q.x, q.y, q.z);
+    if (adaptive) {
+      double trest = 0.0;
+      for (int w = 0; w < nwarps; ++w) trest += red_rest[par][w];
+      if (trest <= tol2 * normY2) break;
     }
-    if (adaptive && trest <= tol2 * normY2) break;
-    if ((best.hi | best.lo) == 0u || best.col == 0xffffffffu) break;   // residual is zero
+    if ((best.k0 | best.k1) == 0u || best.col == 0xffffffffu) break;   // residual is zero
     const int pcol = (int)best.col;
-    // ---- the owner of the pivot column builds the reflector
+    // ---- the owner of the pivot column builds the reflector (working precision)
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
       if (tid + c * NT != pcol) continue;
-      double sig = 0.0, xj = 0.0;
+      T sig = T(0), xj = T(0);
 #pragma unroll
       for (int i = 0; i < LP; ++i) {
-        if (i > j) sig += (double)y[c][i] * (double)y[c][i];
-        if (i == j) xj = (double)y[c][i];
+        if (i > j) sig = fma(y[c][i], y[c][i], sig);
+        if (i == j) xj = y[c][i];
       }
-      const double norm = sqrt(xj * xj + sig);
-      const double alpha = (xj >= 0.0) ? -norm : norm;
-      const double vj = xj - alpha;
-      const double vtv = vj * vj + sig;
-      beta_s[par] = (T)((vtv > 0.0) ? 2.0 / vtv : 0.0);
+      const T norm = sqrt(fma(xj, xj, sig));
+      const T alpha = (xj >= T(0)) ? -norm : norm;
+      const T vj = xj - alpha;
+      const T vtv = fma(vj, vj, sig);
+      beta_s[par] = (vtv > T(0)) ? T(2) / vtv : T(0);
 #pragma unroll
       for (int i = 0; i < LP; ++i) {
         if (i < j) { vs[par][i] = T(0); R11[i][j] = (double)y[c][i]; }
-        else if (i == j) { vs[par][i] = (T)vj; R11[j][j] = alpha; }
+        else if (i == j) { vs[par][i] = vj; R11[j][j] = (double)alpha; }
         else vs[par][i] = y[c][i];
       }
       Js[j] = pcol;
       step_of[c] = j;
     }
     __syncthreads();
-    // ---- apply H_j = I - beta v v^T to every remaining column; downdate the
-    // FP64 norm; recompute it from the remaining rows once it lost two digits
+    // ---- apply H_j = I - beta v v^T to every remaining column (v is zero
+    // above row j, so no row predicate is needed); downdate the norm by the
+    // new R entry; recompute it from the remaining rows once it lost two digits
     const T beta = beta_s[par];
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
       if (step_of[c] != -1) continue;
       T dot = T(0);
 #pragma unroll
-      for (int i = 0; i < LP; ++i)
-        if (i >= j) dot = fma(vs[par][i], y[c][i], dot);
+      for (int i = 0; i < LP; ++i) dot = fma(vs[par][i], y[c][i], dot);
       const T f = beta * dot;
-      T rj = T(0), tail = T(0);
+      T rj = T(0);
 #pragma unroll
       for (int i = 0; i < LP; ++i) {
-        if (i >= j) y[c][i] = fma(-f, vs[par][i], y[c][i]);
-        if (i == j) rj = y[c][i];
-        if (i > j) tail = fma(y[c][i], y[c][i], tail);
+        y[c][i] = fma(-f, vs[par][i], y[c][i]);
+        rj = (i == j) ? y[c][i] : rj;
       }
-      nu[c] -= (double)(rj * rj);
-      if (nu[c] < nu_floor[c]) {
-        nu[c] = (double)tail;
-        nu_floor[c] = 1e-2 * nu[c];
+      nu[c].sub_square(rj);
+      if (nu[c].below(nu_floor[c])) {
+        nu[c].set_zero();
+#pragma unroll
+        for (int i = 0; i < LP; ++i)
+          if (i > j) nu[c].add_square(y[c][i]);
+        nu_floor[c] = nu[c].scaled(T(1e-2));
       }
     }
     k = j + 1;

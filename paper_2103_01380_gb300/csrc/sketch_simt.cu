@@ -7,7 +7,8 @@
 // keeps the whole column group's partial sketch in registers while it walks
 // its rows, regenerating Omega(:, rows) once per chunk and reusing it for all
 // columns of the group; at the end of a segment it writes its partial to a
-// private slot, and spid_reduce_partials sums the slots in a fixed order.
+// private slot, and the CTA that completes a problem (an atomic count after a
+// device-wide fence) sums that problem's slots in schedule order into Y.
 #include "spid_internal.cuh"
 
 namespace spid {
@@ -44,6 +45,7 @@ sketch_simt_kernel(SketchArgs args) {
   constexpr int VPC = kChunkRows / VW;  // vectors per column per chunk
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int last_flag;
   T* As = reinterpret_cast<T*>(smem_raw);       // [kChunkRows][CGP]
   T* Om = As + kChunkRows * CGP;                // [kChunkRows][LP]
   // Om must be 16-byte aligned for vector loads
@@ -148,6 +150,19 @@ sketch_simt_kernel(SketchArgs args) {
         }
       }
     }
+    // ---- the CTA that completes a problem sums its slots (fixed order)
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      const int nslots = args.pslot_ptr[seg.prob + 1] - args.pslot_ptr[seg.prob];
+      last_flag = (atomicAdd(&args.prob_cnt[seg.prob], 1) == nslots - 1);
+    }
+    __syncthreads();
+    if (last_flag) {
+      __threadfence();
+      reduce_problem_slots<T>(args, seg.prob, tid, kThreads);
+      if (tid == 0) args.prob_cnt[seg.prob] = 0;
+    }
   }
 }
 
@@ -186,36 +201,6 @@ cudaError_t launch_sketch_simt(const SketchArgs& a, int grid, bool fp64, cudaStr
     }
   }
   return cudaErrorInvalidValue;
-}
-
-// ---------------------------------------------------------------------------
-// Fixed-order reduction of partial slots into the stored sketch:
-// Y_s(:, col0 + j) = sum over the problem's slots (in schedule order).
-// ---------------------------------------------------------------------------
-
-
-template <typename T>
-__global__ void __launch_bounds__(256) reduce_partials_kernel(ReduceArgs a) {
-  const int p = blockIdx.x + a.prob_base;
-  const Problem pb = a.probs[p];
-  const int q0 = a.pslot_ptr[p], q1 = a.pslot_ptr[p + 1];
-  const T* part = static_cast<const T*>(a.partial);
-  T* Y = static_cast<T*>(a.Y) + a.yoff[pb.sub] + (int64_t)pb.col0 * a.l_pad;
-  const int64_t total = (int64_t)pb.ncols * a.l_pad;
-  for (int64_t e = threadIdx.x + (int64_t)blockIdx.y * blockDim.x; e < total;
-       e += (int64_t)blockDim.x * gridDim.y) {
-    T s = T(0);
-    for (int q = q0; q < q1; ++q) s += part[a.slot_off[a.pslots[q]] + e];
-    Y[e] = s;
-  }
-}
-
-cudaError_t launch_reduce_partials(const ReduceArgs& a, int nprob, bool fp64, cudaStream_t st) {
-  if (nprob <= 0) return cudaSuccess;
-  dim3 grid(nprob, 4);
-  if (fp64) reduce_partials_kernel<double><<<grid, 256, 0, st>>>(a);
-  else reduce_partials_kernel<float><<<grid, 256, 0, st>>>(a);
-  return cudaGetLastError();
 }
 
 }  // namespace spid

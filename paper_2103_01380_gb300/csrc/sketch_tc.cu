@@ -143,12 +143,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr));
 }
 
+// Barrier among `count` threads (whole warps) on hardware barrier `id` (0 is
+// __syncthreads).
+__device__ __forceinline__ void named_bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1) sketch_tf32_kernel(const TcArgs args) {
   extern __shared__ unsigned char smem_raw[];
+  __shared__ int epi_last;
   // 1024-byte alignment for the 128-byte swizzle atoms
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -293,6 +300,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) sketch_tf32_kernel(const TcArgs
         }
       }
       tc_fence_before();
+      // the CTA that completes a problem sums its slots in schedule order
+      __threadfence();
+      named_bar_sync(1, 128);
+      if (gtid == 0) {
+        const int nslots = a.pslot_ptr[seg.prob + 1] - a.pslot_ptr[seg.prob];
+        epi_last = (atomicAdd(&a.prob_cnt[seg.prob], 1) == nslots - 1);
+      }
+      named_bar_sync(1, 128);
+      if (epi_last) {
+        __threadfence();
+        reduce_problem_slots<float>(a, seg.prob, gtid, 128);
+        if (gtid == 0) a.prob_cnt[seg.prob] = 0;
+      }
+      named_bar_sync(1, 128);   // epi_last is reused by the next segment
       return true;
     };
     for (int si = seg0; si < seg1 && ok; ++si, ++segi) {

@@ -51,6 +51,7 @@ struct Schedule {
   const int64_t* slot_off = nullptr;
   const int32_t* pslot_ptr = nullptr;
   const int32_t* pslots = nullptr;
+  int* prob_cnt = nullptr;   // per-problem completed-segment counters
   int64_t partial_elems = 0;
 };
 
@@ -97,6 +98,7 @@ struct spid_plan_s {
   int32_t* d_unit_ptr = nullptr;
   double* d_err_part = nullptr;
   double* d_sub_err = nullptr;
+  int* d_err_cnt = nullptr;     // [S + 1] error-pass completion counters
   void* d_tmaps = nullptr;
   void* d_partial = nullptr;
   int64_t partial_cap = 0;
@@ -237,7 +239,8 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   const size_t b_slot = al(sizeof(int64_t) * std::max<size_t>(slot_off.size(), 1));
   const size_t b_pptr = al(sizeof(int32_t) * pslot_ptr.size());
   const size_t b_psl = al(sizeof(int32_t) * std::max<size_t>(pslots.size(), 1));
-  const size_t total = b_probs + b_segs + b_segp + b_slot + b_pptr + b_psl;
+  const size_t b_cnt = al(sizeof(int) * std::max<size_t>(probs.size(), 1));
+  const size_t total = b_probs + b_segs + b_segp + b_slot + b_pptr + b_psl + b_cnt;
   std::vector<unsigned char> host(total, 0);
   size_t o = 0;
   auto put = [&](const void* src, size_t bytes, size_t span) {
@@ -252,6 +255,7 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   const size_t o_slot = put(slot_off.data(), sizeof(int64_t) * slot_off.size(), b_slot);
   const size_t o_pptr = put(pslot_ptr.data(), sizeof(int32_t) * pslot_ptr.size(), b_pptr);
   const size_t o_psl = put(pslots.data(), sizeof(int32_t) * pslots.size(), b_psl);
+  const size_t o_cnt = put(nullptr, 0, b_cnt);   // problem counters start at zero
   SPID_CUDA(P->alloc(&sc.dev, total));
   SPID_CUDA(cudaMemcpy(sc.dev, host.data(), total, cudaMemcpyHostToDevice));
   unsigned char* d = static_cast<unsigned char*>(sc.dev);
@@ -261,6 +265,7 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   sc.slot_off = reinterpret_cast<const int64_t*>(d + o_slot);
   sc.pslot_ptr = reinterpret_cast<const int32_t*>(d + o_pptr);
   sc.pslots = reinterpret_cast<const int32_t*>(d + o_psl);
+  sc.prob_cnt = reinterpret_cast<int*>(d + o_cnt);
   if (P->prec == SPID_PREC_TF32) {
     const size_t per_stage = (size_t)max_tiles * 128 * 128 + (size_t)P->l_pad * 128;
     const size_t fixed = sketch_tc_smem_bytes(0, max_tiles, P->l_pad);
@@ -326,6 +331,17 @@ spid_status bind_window(spid_plan_t P, const void* window, cudaStream_t st) {
   SPID_CUDA(cudaMemcpy(P->d_tmaps, maps.data(), sizeof(CUtensorMap) * P->S, cudaMemcpyHostToDevice));
   P->bound_window = window;
   return SPID_OK;
+}
+
+// Zero every completion counter (schedules and error pass).  Needed only after
+// a kernel gave up on a timeout and left a counter part-way.
+cudaError_t reset_counters(spid_plan_t P, cudaStream_t st) {
+  for (auto& kv : P->schedules) {
+    cudaError_t e = cudaMemsetAsync(kv.second.prob_cnt, 0,
+                                    sizeof(int) * std::max(kv.second.nprob, 1), st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaMemsetAsync(P->d_err_cnt, 0, sizeof(int) * (P->S + 1), st);
 }
 
 spid_status check_plan(spid_plan_t P) {
@@ -482,6 +498,7 @@ spid_status spid_plan_create(const spid_plan_desc* d, spid_plan_t* out) {
   SPID_ALLOC(P->d_unit_ptr, sizeof(int32_t) * (P->S + 1));
   SPID_ALLOC(P->d_err_part, sizeof(double) * 2 * P->units);
   SPID_ALLOC(P->d_sub_err, sizeof(double) * 2 * P->S);
+  SPID_ALLOC(P->d_err_cnt, sizeof(int) * (P->S + 1));
   SPID_ALLOC(P->d_partial, esz * P->partial_cap);
   if (P->prec == SPID_PREC_TF32) SPID_ALLOC(P->d_tmaps, sizeof(CUtensorMap) * P->S);
 #undef SPID_ALLOC
@@ -506,6 +523,7 @@ spid_status spid_plan_create(const spid_plan_desc* d, spid_plan_t* out) {
 #undef SPID_H2D
   if (cudaMemset(P->d_Y, 0, esz * P->y_elems) != cudaSuccess ||
       cudaMemset(P->d_status, 0, sizeof(int)) != cudaSuccess ||
+      cudaMemset(P->d_err_cnt, 0, sizeof(int) * (P->S + 1)) != cudaSuccess ||
       cudaMemset(P->d_k, 0, sizeof(int32_t) * P->S) != cudaSuccess)
     return bail(fail(SPID_ERR_CUDA, "cudaMemset failed"));
   // the whole-window schedule is built now so that steady-state calls allocate nothing
@@ -538,6 +556,7 @@ spid_status spid_reset(spid_plan_t P, spid_stream_t stream) {
   spid_status st = check_plan(P);
   if (st != SPID_OK) return st;
   SPID_CUDA(cudaMemsetAsync(P->d_Y, 0, P->esz * P->y_elems, (cudaStream_t)stream));
+  SPID_CUDA(reset_counters(P, (cudaStream_t)stream));
   return SPID_OK;
 }
 
@@ -572,16 +591,11 @@ spid_status spid_sketch(spid_plan_t P, const void* window, int32_t col0, int32_t
   a.l_pad = P->l_pad;
   a.seed = P->seed;
   a.status = P->d_status;
-  ReduceArgs r;
-  r.probs = sc->probs;
-  r.pslot_ptr = sc->pslot_ptr;
-  r.pslots = sc->pslots;
-  r.slot_off = sc->slot_off;
-  r.partial = P->d_partial;
-  r.Y = P->d_Y;
-  r.yoff = P->d_yoff;
-  r.l_pad = P->l_pad;
-  r.prob_base = 0;
+  a.pslot_ptr = sc->pslot_ptr;
+  a.pslots = sc->pslots;
+  a.prob_cnt = sc->prob_cnt;
+  a.Y = P->d_Y;
+  a.yoff = P->d_yoff;
   const int nlaunch = P->per_sub() ? P->S : 1;
   for (int q = 0; q < nlaunch; ++q) {
     a.cta_base = P->per_sub() ? sc->cta_base_of_sub[q] : 0;
@@ -589,12 +603,6 @@ spid_status spid_sketch(spid_plan_t P, const void* window, int32_t col0, int32_t
                         ? launch_sketch_tc(a, sc->grid, sc->stages, sc->max_tiles, cs)
                         : launch_sketch_simt(a, sc->grid, P->fp64(), cs);
     if (e != cudaSuccess) return fail(SPID_ERR_CUDA, std::string("sketch launch: ") + cudaGetErrorString(e));
-  }
-  for (int q = 0; q < nlaunch; ++q) {
-    r.prob_base = P->per_sub() ? sc->prob_base_of_sub[q] : 0;
-    const int np = P->per_sub() ? sc->nprob_of_sub[q] : sc->nprob;
-    cudaError_t e = launch_reduce_partials(r, np, P->fp64(), cs);
-    if (e != cudaSuccess) return fail(SPID_ERR_CUDA, std::string("reduce launch: ") + cudaGetErrorString(e));
   }
   return SPID_OK;
 }
@@ -652,6 +660,13 @@ static spid_status run_error(spid_plan_t P, const void* window, void* out, doubl
   a.unit_col0 = P->d_unit_col0;
   a.part = P->d_err_part;
   a.unit_base = 0;
+  a.unit_ptr = P->d_unit_ptr;
+  a.sub_cnt = P->d_err_cnt;
+  a.all_cnt = P->d_err_cnt + P->S;
+  a.err = err_dev;
+  a.sub_err = P->d_sub_err;
+  a.total = total_dev;
+  a.S = P->S;
   if (P->per_sub()) {
     for (int s = 0; s < P->S; ++s) {
       a.unit_base = P->unit_ptr[s];
@@ -662,18 +677,6 @@ static spid_status run_error(spid_plan_t P, const void* window, void* out, doubl
     cudaError_t e = launch_error(a, P->units, P->fp64(), cs);
     if (e != cudaSuccess) return fail(SPID_ERR_CUDA, std::string("error launch: ") + cudaGetErrorString(e));
   }
-  ErrFinishArgs f;
-  f.unit_ptr = P->d_unit_ptr;
-  f.part = P->d_err_part;
-  f.err = err_dev;
-  f.sub_err = P->d_sub_err;
-  f.total = total_dev;
-  f.m = P->d_m;
-  f.n = P->d_n;
-  f.k = P->d_k;
-  f.S = P->S;
-  cudaError_t e = launch_error_finish(f, cs);
-  if (e != cudaSuccess) return fail(SPID_ERR_CUDA, std::string("error finish: ") + cudaGetErrorString(e));
   return SPID_OK;
 }
 
@@ -720,7 +723,11 @@ spid_status spid_device_status(spid_plan_t P, spid_stream_t stream) {
   int v = 0;
   SPID_CUDA(cudaMemcpy(&v, P->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   SPID_CUDA(cudaMemset(P->d_status, 0, sizeof(int)));
-  if (v & kStatusTimeout) return fail(SPID_ERR_TIMEOUT, "a bounded device wait timed out");
+  if (v & kStatusTimeout) {
+    SPID_CUDA(reset_counters(P, (cudaStream_t)stream));
+    SPID_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return fail(SPID_ERR_TIMEOUT, "a bounded device wait timed out");
+  }
   if (v & kStatusNonfinite) return fail(SPID_ERR_NONFINITE, "non-finite values reached a sketch");
   return SPID_OK;
 }

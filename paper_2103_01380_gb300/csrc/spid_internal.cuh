@@ -54,20 +54,30 @@ struct SketchArgs {
   int32_t l_pad;
   uint64_t seed;
   int* status;
-};
-
-// Fixed-order reduction of a schedule's partial slots into the stored sketch.
-struct ReduceArgs {
-  const Problem* probs;
+  // fixed-order reduction of the partial slots into the stored sketch, done by
+  // the CTA that completes each problem
   const int32_t* pslot_ptr;   // problem p owns pslots[pslot_ptr[p] .. pslot_ptr[p+1])
   const int32_t* pslots;
-  const int64_t* slot_off;
-  const void* partial;
-  void* Y;
-  const int64_t* yoff;        // element offset of Y_s
-  int32_t l_pad;
-  int32_t prob_base;
+  int* prob_cnt;              // [problems] completed-segment counters (zero between calls)
+  void* Y;                    // stored sketches, Y_s at yoff[s], [n_s][l_pad]
+  const int64_t* yoff;
 };
+
+// Sum problem p's partial slots in schedule order into Y (called by the CTA
+// that completed p, after a device-wide fence): threads [t0, t0 + nt).
+template <typename T>
+__device__ __forceinline__ void reduce_problem_slots(const SketchArgs& a, int p, int t, int nt) {
+  const Problem pb = a.probs[p];
+  const int q0 = a.pslot_ptr[p], q1 = a.pslot_ptr[p + 1];
+  const T* part = static_cast<const T*>(a.partial);
+  T* Y = static_cast<T*>(a.Y) + a.yoff[pb.sub] + (int64_t)pb.col0 * a.l_pad;
+  const int64_t total = (int64_t)pb.ncols * a.l_pad;
+  for (int64_t e = t; e < total; e += nt) {
+    T s = T(0);
+    for (int q = q0; q < q1; ++q) s += __ldcg(part + a.slot_off[a.pslots[q]] + e);
+    Y[e] = s;
+  }
+}
 
 // Batched pivoted QR + rank + coefficients.
 struct QrcpArgs {
@@ -108,17 +118,12 @@ struct ErrArgs {
   const int32_t* unit_col0;
   double* part;               // [unit][2] = {e2, a2}
   int32_t unit_base;
-};
-
-struct ErrFinishArgs {
   const int32_t* unit_ptr;    // subdomain s owns units [unit_ptr[s], unit_ptr[s+1])
-  const double* part;
+  int* sub_cnt;               // [S] completed-unit counters (zero between calls)
+  int* all_cnt;               // completed-subdomain counter (zero between calls)
   double* err;                // [S][2] or nullptr
   double* sub_err;            // plan copy [S][2]
   double* total;              // [4] or nullptr
-  const int32_t* m;
-  const int32_t* n;
-  const int32_t* k;
   int32_t S;
 };
 
@@ -128,7 +133,6 @@ void set_last_error(const char* msg);
 // Launchers (one translation unit each).
 int sketch_simt_group_cols(bool fp64);
 cudaError_t launch_sketch_simt(const SketchArgs& a, int grid, bool fp64, cudaStream_t st);
-cudaError_t launch_reduce_partials(const ReduceArgs& a, int nprob, bool fp64, cudaStream_t st);
 int sketch_tc_group_cols();
 size_t sketch_tc_smem_bytes(int stages, int max_tiles, int l_pad);
 int sketch_tc_max_stages();
@@ -139,7 +143,6 @@ cudaError_t launch_qrcp(const QrcpArgs& a, int grid, int n_max, int l_pad, bool 
                         cudaStream_t st);
 size_t error_smem_bytes(int k_max, bool fp64);
 cudaError_t launch_error(const ErrArgs& a, int units, bool fp64, cudaStream_t st);
-cudaError_t launch_error_finish(const ErrFinishArgs& a, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the Philox
