@@ -105,17 +105,67 @@ __device__ __forceinline__ PivotKey warp_pivot(uint32_t k0, uint32_t k1, uint32_
   return {m0, m1, mc};
 }
 
-__device__ __forceinline__ bool key_better(const PivotKey& a, const PivotKey& b) {
-  if (a.k0 != b.k0) return a.k0 > b.k0;
-  if (a.k1 != b.k1) return a.k1 > b.k1;
-  return a.col < b.col;
+
+// T = R11^-1 r in place over r[0 .. keff), FP64-class accuracy.
+// FP32 data: every t_l is carried as an unevaluated pair (hi in r, lo in tl),
+// each product R_il t_l is split exactly with fma, and the running residual is
+// an error-free double-float sum; the division is corrected by one residual
+// step.  All on the FP32 pipe.  FP64 data: plain FP64.
+template <int LP>
+__device__ __forceinline__ void back_substitute(float (&r)[LP], const float (&R)[LP][LP],
+                                                int keff) {
+  float tl[LP];
+#pragma unroll
+  for (int ii = LP - 1; ii >= 0; --ii) {
+    tl[ii] = 0.f;
+    if (ii < keff) {
+      float hi = r[ii], lo = 0.f;
+#pragma unroll
+      for (int ll = ii + 1; ll < LP; ++ll) {
+        if (ll < keff) {
+          const float Rv = R[ii][ll];
+          const float p = Rv * r[ll];
+          float pe = fmaf(Rv, r[ll], -p);
+          pe = fmaf(Rv, tl[ll], pe);
+          // (hi, lo) -= (p, pe)
+          const float s = hi - p;
+          const float bb = s - hi;
+          float e = (hi - (s - bb)) + (-p - bb);
+          e += lo - pe;
+          hi = s + e;
+          lo = e - (hi - s);
+        }
+      }
+      const float d = R[ii][ii];
+      const float q = hi / d;
+      const float res = fmaf(-q, d, hi) + lo;
+      const float ql = res / d;
+      r[ii] = q + ql;
+      tl[ii] = ql - (r[ii] - q);
+    }
+  }
+}
+
+template <int LP>
+__device__ __forceinline__ void back_substitute(double (&r)[LP], const double (&R)[LP][LP],
+                                                int keff) {
+#pragma unroll
+  for (int ii = LP - 1; ii >= 0; --ii) {
+    if (ii < keff) {
+      double acc = r[ii];
+#pragma unroll
+      for (int ll = ii + 1; ll < LP; ++ll)
+        if (ll < keff) acc = fma(-R[ii][ll], r[ll], acc);
+      r[ii] = acc / R[ii][ii];
+    }
+  }
 }
 
 template <typename T, int LP, int CPT>
 __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
-  __shared__ T vs[2][LP];              // Householder vector, double-buffered by step parity
+  __shared__ __align__(16) T vs[2][LP];   // Householder vector, double-buffered by step parity
   __shared__ T beta_s[2];
-  __shared__ double R11[LP][LP];       // R11(i, p) = R(i, J[p])
+  __shared__ T R11[LP][LP];            // R11(i, p) = R(i, J[p])
   __shared__ int Js[LP];
   __shared__ uint4 red_key[2][kMaxWarps];
   __shared__ double red_rest[2][kMaxWarps];
@@ -210,12 +260,13 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
       if (tid + c * NT != pcol) continue;
-      T sig = T(0), xj = T(0);
+      T sp[4] = {T(0), T(0), T(0), T(0)}, xj = T(0);   // four chains: short latency
 #pragma unroll
       for (int i = 0; i < LP; ++i) {
-        if (i > j) sig = fma(y[c][i], y[c][i], sig);
+        if (i > j) sp[i & 3] = fma(y[c][i], y[c][i], sp[i & 3]);
         if (i == j) xj = y[c][i];
       }
+      const T sig = (sp[0] + sp[1]) + (sp[2] + sp[3]);
       const T norm = sqrt(fma(xj, xj, sig));
       const T alpha = (xj >= T(0)) ? -norm : norm;
       const T vj = xj - alpha;
@@ -223,8 +274,8 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
       beta_s[par] = (vtv > T(0)) ? T(2) / vtv : T(0);
 #pragma unroll
       for (int i = 0; i < LP; ++i) {
-        if (i < j) { vs[par][i] = T(0); R11[i][j] = (double)y[c][i]; }
-        else if (i == j) { vs[par][i] = vj; R11[j][j] = (double)alpha; }
+        if (i < j) { vs[par][i] = T(0); R11[i][j] = y[c][i]; }
+        else if (i == j) { vs[par][i] = vj; R11[j][j] = alpha; }
         else vs[par][i] = y[c][i];
       }
       Js[j] = pcol;
@@ -238,10 +289,16 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
 #pragma unroll
     for (int c = 0; c < CPT; ++c) {
       if (step_of[c] != -1) continue;
-      T dot = T(0);
+      T dp[4] = {T(0), T(0), T(0), T(0)};
+      constexpr int VW = 16 / sizeof(T);
 #pragma unroll
-      for (int i = 0; i < LP; ++i) dot = fma(vs[par][i], y[c][i], dot);
-      const T f = beta * dot;
+      for (int i4 = 0; i4 < LP; i4 += VW) {
+        const typename Vec16<T>::type x = *reinterpret_cast<const typename Vec16<T>::type*>(&vs[par][i4]);
+        const T* xs = reinterpret_cast<const T*>(&x);
+#pragma unroll
+        for (int u = 0; u < VW; ++u) dp[(i4 + u) & 3] = fma(xs[u], y[c][i4 + u], dp[(i4 + u) & 3]);
+      }
+      const T f = beta * ((dp[0] + dp[1]) + (dp[2] + dp[3]));
       T rj = T(0);
 #pragma unroll
       for (int i = 0; i < LP; ++i) {
@@ -263,10 +320,10 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
   // ---- rank guard
   int keff = 0;
   if (k > 0) {
-    const double r00 = fabs(R11[0][0]);
-    if (r00 > 0.0) {
+    const T thr = (T)(2.0 * a.u_mode) * abs(R11[0][0]);
+    if (thr > T(0)) {
       for (int j = 0; j < k; ++j) {
-        if (fabs(R11[j][j]) > 2.0 * a.u_mode * r00) keff = j + 1;
+        if (abs(R11[j][j]) > thr) keff = j + 1;
         else break;
       }
     }
@@ -282,16 +339,7 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
       for (int i = 0; i < a.k_max; ++i) C[(int64_t)i * n + col] = (i == step_of[c]) ? T(1) : T(0);
       continue;
     }
-#pragma unroll
-    for (int ii = LP - 1; ii >= 0; --ii) {
-      if (ii < keff) {
-        double acc = (double)y[c][ii];
-#pragma unroll
-        for (int ll = ii + 1; ll < LP; ++ll)
-          if (ll < keff) acc -= R11[ii][ll] * (double)y[c][ll];
-        y[c][ii] = (T)(acc / R11[ii][ii]);
-      }
-    }
+    back_substitute(y[c], R11, keff);
 #pragma unroll
     for (int i = 0; i < LP; ++i)
       if (i < a.k_max) C[(int64_t)i * n + col] = (i < keff) ? y[c][i] : T(0);
