@@ -97,6 +97,32 @@ class ClockSampler:
         return out
 
 
+def bind_to_gpu_numa_node(device: int):
+    """Pin this process to the CPUs local to the GPU, so that pinned host
+    buffers are first-touched on the memory node attached to the GPU (on a
+    Grace-based GB300 the other socket's memory is reached through the CPU-CPU
+    link and halves host->device bandwidth).  Returns what was done."""
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(device)
+        bus = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        base = f"/sys/bus/pci/devices/{bus}"
+        node = int(open(f"{base}/numa_node").read().strip())
+        cpus = set()
+        for part in open(f"{base}/local_cpulist").read().strip().split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+        return {"pci": bus, "numa_node": node, "cpus": len(cpus)}
+    except Exception as exc:  # sysfs layout differs: leave affinity alone
+        return {"error": type(exc).__name__}
+
+
 def make_window(rank: int = 0, boxes=None):
     from paper_2103_01380_gb300 import inputs
     return inputs.tgv3d_window(grid=64, box=16, n=512, seed=2 + rank, boxes=boxes)
@@ -177,6 +203,7 @@ def main():
     if world > 1:
         dist.init_process_group("gloo")
     torch.cuda.set_device(local)
+    numa = bind_to_gpu_numa_node(local)
     from paper_2103_01380_gb300 import build, spid
     build.build()
     spid.load_library()
@@ -257,15 +284,20 @@ def main():
     t0 = time.perf_counter()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    hc = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(e2e_steps)]
     e0.record(stream)
-    for _ in range(e2e_steps):
+    for i in range(e2e_steps):
+        hc[i][0].record(stream)
         dev.copy_(host, non_blocking=True)
+        hc[i][1].record(stream)
         plan.sketch(dev); plan.finalize(); plan.error(dev, err, tot)
         host_tot.copy_(tot, non_blocking=True)
         stream.synchronize()
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    h2d_ms = statistics.mean(a.elapsed_time(b) for a, b in hc)
     te = torch.tensor([e2e_ms], dtype=torch.float64)
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
@@ -316,7 +348,8 @@ def main():
             "k_mean": float(np.mean(k)), "k_max": int(np.max(k)),
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": int(nbytes),
-                    "d2h_bytes_per_step": 32},
+                    "d2h_bytes_per_step": 32, "ms_per_step": e2e_ms, "h2d_ms_per_step": h2d_ms,
+                    "h2d_gbs": nbytes / (h2d_ms / 1e3) / 1e9, "host_binding": numa},
             "gpu_launches": 3 * args.steps,
             "clocks": clocks,
             "comparator": comparator}

@@ -168,6 +168,8 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
   __shared__ T R11[LP][LP];            // R11(i, p) = R(i, J[p])
   __shared__ int Js[LP];
   __shared__ uint4 red_key[2][kMaxWarps];
+  __shared__ T guard_thr;              // 2 u |R_00|
+  __shared__ int stop_s[2];            // the pivot of this step failed the rank guard
   __shared__ double red_rest[2][kMaxWarps];
 
   const int s = blockIdx.x + a.sub_base;
@@ -269,6 +271,12 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
       const T sig = (sp[0] + sp[1]) + (sp[2] + sp[3]);
       const T norm = sqrt(fma(xj, xj, sig));
       const T alpha = (xj >= T(0)) ? -norm : norm;
+      // rank guard, applied as the pivots are produced: it keeps a leading
+      // prefix, so the first R_jj at or below 2 u |R_00| ends the factorization
+      if (j == 0) guard_thr = (T)(2.0 * a.u_mode) * abs(alpha);
+      const bool stop = (j == 0) ? !(abs(alpha) > T(0)) : !(abs(alpha) > guard_thr);
+      stop_s[par] = stop ? 1 : 0;
+      if (stop) continue;
       const T vj = xj - alpha;
       const T vtv = fma(vj, vj, sig);
       beta_s[par] = (vtv > T(0)) ? T(2) / vtv : T(0);
@@ -282,6 +290,7 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
       step_of[c] = j;
     }
     __syncthreads();
+    if (stop_s[par]) break;
     // ---- apply H_j = I - beta v v^T to every remaining column (v is zero
     // above row j, so no row predicate is needed); downdate the norm by the
     // new R entry; recompute it from the remaining rows once it lost two digits
@@ -307,10 +316,14 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
       }
       nu[c].sub_square(rj);
       if (nu[c].below(nu_floor[c])) {
-        nu[c].set_zero();
+        // the downdate lost two digits: take the norm of the rows that remain
+        // (four independent chains; the stored rows are what the next step sees)
+        T sq[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
         for (int i = 0; i < LP; ++i)
-          if (i > j) nu[c].add_square(y[c][i]);
+          if (i > j) sq[i & 3] = fma(y[c][i], y[c][i], sq[i & 3]);
+        nu[c].set_zero();
+        nu[c].hi = (sq[0] + sq[1]) + (sq[2] + sq[3]);
         nu_floor[c] = nu[c].scaled(T(1e-2));
       }
     }
