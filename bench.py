@@ -263,12 +263,9 @@ def main():
     value = world * nbytes * args.steps / (total_ms / 1e3) / 1e9
 
     # global error / CF across ranks: a host-side sum of four doubles
-    totals = tot.detach().cpu().to(torch.float64)
-    if world > 1:
-        dist.all_reduce(totals)
-    totals = totals.numpy()
-    rel_err = float(np.sqrt(totals[0] / totals[1]))
-    cf = float(totals[2] / totals[3])
+    # global error / CF across ranks: one host-side sum of four doubles
+    from paper_2103_01380_gb300 import shard
+    rel_err, cf, _ = shard.combine_totals(tot.detach().cpu().numpy())
     k, J, C = plan.factors()
 
     # end to end through the public API: pinned host window -> device, full
