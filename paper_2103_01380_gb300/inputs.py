@@ -207,6 +207,37 @@ def tgv3d_window(grid: int = 64, box: int = 16, n: int = 512, t_end: float = 10.
     return w
 
 
+def uneven_boxes(count: int, edges=(8, 12, 16, 24, 32), n_range=(64, 1024), grid: int = 256,
+                 t_end: float = 10.0, nu: float = 0.01, seed: int = 4,
+                 modes: FourierModes | None = None):
+    """Descriptors of `count` cubic boxes with uniformly drawn edges and window
+    lengths, each at a uniformly random periodic offset of a grid^3 field:
+    list of (origin, edge, n)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        e = int(rng.choice(edges))
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        org = tuple(int(x) for x in rng.integers(0, grid, size=3))
+        out.append((org, e, n))
+    return out
+
+
+def uneven_window(boxes, grid: int = 256, t_end: float = 10.0, nu: float = 0.01,
+                  modes: FourierModes | None = None, seed: int = 2, dtype=np.float32) -> Window:
+    """Window of the boxes described by `uneven_boxes` (subdomain-major); each
+    box's snapshots sample t in [0, t_end] at its own n points."""
+    if modes is None:
+        modes = fourier_modes(seed=seed)
+    blocks = []
+    for org, e, n in boxes:
+        t = t_end * np.arange(n) / max(n - 1, 1)
+        blocks.append(tgv3d_box(org, (e, e, e), grid, t, modes, nu, dtype=np.float64))
+    w = pack_blocks(blocks, dtype=dtype)
+    w.meta.update({"grid": grid, "boxes": boxes})
+    return w
+
+
 # --------------------------------------------------------------------------
 # Prescribed-spectrum matrices (Haar-orthonormal factors)
 # --------------------------------------------------------------------------
