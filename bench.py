@@ -33,6 +33,30 @@ WORKLOAD = ("TGV+Fourier 64^3 grid, 64 subdomains of 16^3 x 5 QoIs (m=20480), n=
             "k=20, p=10, FP32 window")
 
 
+# DRAM bytes (read + write) of one launch of each hot kernel on the default
+# workload, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`
+# (profiles/dram_traffic_tf32_tgv3d_64sub.md).  A figure is reported only while
+# the kernel's sources hash to the value they had when it was measured.
+MEASURED_TRAFFIC = {
+    "sketch": {"bytes": 2.69e9 + 7.07e6, "sources": ("sketch_tc.cu", "spid_internal.cuh"),
+               "sha256_16": "73839046242937e9"},
+    "error": {"bytes": 2.69e9 + 0.212e6, "sources": ("error.cu", "spid_internal.cuh"),
+              "sha256_16": "e9556cc92f9e01aa"},
+}
+
+
+def measured_traffic(kernel: str):
+    import hashlib
+    rec = MEASURED_TRAFFIC.get(kernel)
+    if rec is None:
+        return None
+    m = hashlib.sha256()
+    for f in rec["sources"]:
+        with open(os.path.join(ROOT, "paper_2103_01380_gb300", "csrc", f), "rb") as fh:
+            m.update(fh.read())
+    return rec["bytes"] if m.hexdigest()[:16] == rec["sha256_16"] else None
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -324,10 +348,13 @@ def main():
     dom_ms = max(sk_ms, er_ms)
     # algorithmic bytes: sketch reads A once (4 B / element); the error pass reads
     # A once plus the k skeleton columns of every subdomain
-    alg_bytes = nbytes if dominant == "sketch" else nbytes + 4.0 * 20 * float(win.m.sum())
+    alg_bytes = nbytes if dominant == "sketch" else nbytes + 4.0 * float((k * win.m).sum())
     achieved = alg_bytes / (dom_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
-            "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None}
+            "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+            "traffic": measured_traffic(dominant) if (args.boxes is None and
+                                                      args.precision == "tf32") else None,
+            "alg_bytes": alg_bytes}
 
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
