@@ -62,11 +62,20 @@ typedef enum {
   SPID_ERR_UNSUPPORTED = 7   /* valid request this build does not implement */
 } spid_status;
 
+/* Every FP32-window mode factors the sketch with FP32 Householder reflectors,
+ * pivot norms held as FP32 pairs (hi + lo, ~48-bit significand, exact
+ * argmax) and a pair-precision back-substitution: FP64-class accuracy without
+ * GB300's 1:64-rate FP64 pipe.  The unit roundoff u of each mode sets its rank
+ * guard |R_jj| > 2 u |R_00|. */
 typedef enum {
-  SPID_PREC_FP64 = 0,  /* FP64 window; sketch, QR, solve and error in FP64 (SIMT) */
-  SPID_PREC_FP32 = 1,  /* FP32 window; FP32 SIMT sketch; FP64 pivot norms and solve */
-  SPID_PREC_TF32 = 2   /* FP32 window; tcgen05 TF32 sketch (FP32 accumulate in TMEM,
-                          tiles staged by TMA); FP64 pivot norms and solve */
+  SPID_PREC_FP64 = 0,   /* FP64 window; sketch, QR, solve and error in FP64 (SIMT); u = 2^-53 */
+  SPID_PREC_FP32 = 1,   /* FP32 window; FP32 SIMT sketch; u = 2^-24 */
+  SPID_PREC_TF32 = 2,   /* FP32 window; tcgen05 TF32 sketch (FP32 accumulate in TMEM, tiles
+                           staged by TMA); u = 2^-11 */
+  SPID_PREC_BF16 = 3,   /* FP32 window; tcgen05 BF16 sketch (A and Omega rounded to BF16,
+                           FP32 accumulate); u = 2^-9 */
+  SPID_PREC_BF16X3 = 4  /* FP32 window; tcgen05 3xBF16 sketch (two-term BF16 splits of A and
+                           Omega, three products, FP32 accumulate); u = 2^-16 */
 } spid_precision;
 
 /* Plain (unbatched) form: one kernel launch per subdomain per stage. */

@@ -75,9 +75,16 @@ struct spid_plan_s {
   size_t esz = 4;
   bool fp64() const { return prec == SPID_PREC_FP64; }
   bool per_sub() const { return (flags & SPID_FLAG_PER_SUBDOMAIN) != 0; }
+  bool tensor_core() const { return prec >= SPID_PREC_TF32; }
+  bool bf16() const { return prec == SPID_PREC_BF16 || prec == SPID_PREC_BF16X3; }
   double u_mode() const {
-    return prec == SPID_PREC_FP64 ? std::ldexp(1.0, -53)
-                                  : (prec == SPID_PREC_TF32 ? std::ldexp(1.0, -11) : std::ldexp(1.0, -24));
+    switch (prec) {
+      case SPID_PREC_FP64: return std::ldexp(1.0, -53);
+      case SPID_PREC_TF32: return std::ldexp(1.0, -11);
+      case SPID_PREC_BF16: return std::ldexp(1.0, -9);
+      case SPID_PREC_BF16X3: return std::ldexp(1.0, -16);
+      default: return std::ldexp(1.0, -24);
+    }
   }
 
   // device state
@@ -122,10 +129,10 @@ struct spid_plan_s {
     return e;
   }
   int group_cols() const {
-    return prec == SPID_PREC_TF32 ? sketch_tc_group_cols() : sketch_simt_group_cols(fp64());
+    return tensor_core() ? sketch_tc_group_cols() : sketch_simt_group_cols(fp64());
   }
   int sketch_grid() const {
-    if (prec == SPID_PREC_TF32) return num_sms;
+    if (tensor_core()) return num_sms;
     return (!fp64() && l_pad <= 32) || (fp64() && l_pad <= 16) ? 2 * num_sms : num_sms;
   }
 };
@@ -266,9 +273,12 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   sc.pslot_ptr = reinterpret_cast<const int32_t*>(d + o_pptr);
   sc.pslots = reinterpret_cast<const int32_t*>(d + o_psl);
   sc.prob_cnt = reinterpret_cast<int*>(d + o_cnt);
-  if (P->prec == SPID_PREC_TF32) {
-    const size_t per_stage = (size_t)max_tiles * 128 * 128 + (size_t)P->l_pad * 128;
-    const size_t fixed = sketch_tc_smem_bytes(0, max_tiles, P->l_pad);
+  if (P->tensor_core()) {
+    const bool split = P->prec == SPID_PREC_BF16X3;
+    const size_t fixed = P->bf16() ? sketch_bf16_smem_bytes(0, max_tiles, P->l_pad, split)
+                                   : sketch_tc_smem_bytes(0, max_tiles, P->l_pad);
+    const size_t per_stage = (P->bf16() ? sketch_bf16_smem_bytes(1, max_tiles, P->l_pad, split)
+                                        : sketch_tc_smem_bytes(1, max_tiles, P->l_pad)) - fixed;
     int stages = (int)((P->smem_optin - fixed) / per_stage);
     stages = std::min(stages, sketch_tc_max_stages());
     if (stages < 2) return fail(SPID_ERR_UNSUPPORTED, "not enough shared memory for the TF32 pipeline");
@@ -389,7 +399,7 @@ spid_status spid_plan_create(const spid_plan_desc* d, spid_plan_t* out) {
   *out = nullptr;
   if (d->num_sub < 1 || !d->m || !d->n || !d->off || !d->ld)
     return fail(SPID_ERR_INVALID_ARG, "num_sub < 1 or a descriptor array is NULL");
-  if (d->precision < SPID_PREC_FP64 || d->precision > SPID_PREC_TF32)
+  if (d->precision < SPID_PREC_FP64 || d->precision > SPID_PREC_BF16X3)
     return fail(SPID_ERR_INVALID_ARG, "unknown precision");
   if (d->k_max < 1 || d->p < 0 || d->k_max + d->p > 64)
     return fail(SPID_ERR_INVALID_ARG, "need k_max >= 1, p >= 0, k_max + p <= 64");
@@ -436,9 +446,9 @@ spid_status spid_plan_create(const spid_plan_desc* d, spid_plan_t* out) {
   if (e != cudaSuccess) { delete P; return fail(SPID_ERR_CUDA, cudaGetErrorString(e)); }
   P->num_sms = prop.multiProcessorCount;
   P->smem_optin = prop.sharedMemPerBlockOptin;
-  if (P->prec == SPID_PREC_TF32 && prop.major < 10) {
+  if (P->tensor_core() && prop.major < 10) {
     delete P;
-    return fail(SPID_ERR_UNSUPPORTED, "TF32 tensor-core sketch needs sm_100 or newer");
+    return fail(SPID_ERR_UNSUPPORTED, "the tensor-core sketch needs sm_100 or newer");
   }
 
   // offsets of Y and C
@@ -500,7 +510,7 @@ spid_status spid_plan_create(const spid_plan_desc* d, spid_plan_t* out) {
   SPID_ALLOC(P->d_sub_err, sizeof(double) * 2 * P->S);
   SPID_ALLOC(P->d_err_cnt, sizeof(int) * (P->S + 1));
   SPID_ALLOC(P->d_partial, esz * P->partial_cap);
-  if (P->prec == SPID_PREC_TF32) SPID_ALLOC(P->d_tmaps, sizeof(CUtensorMap) * P->S);
+  if (P->tensor_core()) SPID_ALLOC(P->d_tmaps, sizeof(CUtensorMap) * P->S);
 #undef SPID_ALLOC
 #define SPID_H2D(dst, src, bytes)                                                          \
   do {                                                                                     \
@@ -574,7 +584,7 @@ spid_status spid_sketch(spid_plan_t P, const void* window, int32_t col0, int32_t
   Schedule* sc = nullptr;
   st = get_schedule(P, col0, ncols, &sc);
   if (st != SPID_OK) return st;
-  if (P->prec == SPID_PREC_TF32) {
+  if (P->tensor_core()) {
     st = bind_window(P, window, cs);
     if (st != SPID_OK) return st;
   }
@@ -599,9 +609,11 @@ spid_status spid_sketch(spid_plan_t P, const void* window, int32_t col0, int32_t
   const int nlaunch = P->per_sub() ? P->S : 1;
   for (int q = 0; q < nlaunch; ++q) {
     a.cta_base = P->per_sub() ? sc->cta_base_of_sub[q] : 0;
-    cudaError_t e = (P->prec == SPID_PREC_TF32)
-                        ? launch_sketch_tc(a, sc->grid, sc->stages, sc->max_tiles, cs)
-                        : launch_sketch_simt(a, sc->grid, P->fp64(), cs);
+    cudaError_t e =
+        P->bf16() ? launch_sketch_bf16(a, sc->grid, sc->stages, sc->max_tiles,
+                                       P->prec == SPID_PREC_BF16X3, cs)
+        : P->tensor_core() ? launch_sketch_tc(a, sc->grid, sc->stages, sc->max_tiles, cs)
+                           : launch_sketch_simt(a, sc->grid, P->fp64(), cs);
     if (e != cudaSuccess) return fail(SPID_ERR_CUDA, std::string("sketch launch: ") + cudaGetErrorString(e));
   }
   return SPID_OK;

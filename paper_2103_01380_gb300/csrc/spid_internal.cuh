@@ -169,6 +169,9 @@ cudaError_t launch_sketch_simt(const SketchArgs& a, int grid, bool fp64, cudaStr
 int sketch_tc_group_cols();
 size_t sketch_tc_smem_bytes(int stages, int max_tiles, int l_pad);
 int sketch_tc_max_stages();
+size_t sketch_bf16_smem_bytes(int stages, int max_tiles, int l_pad, bool split);
+cudaError_t launch_sketch_bf16(const SketchArgs& s, int grid, int stages, int max_tiles, bool split,
+                               cudaStream_t st);
 cudaError_t launch_sketch_tc(const SketchArgs& s, int grid, int stages, int max_tiles,
                              cudaStream_t st);
 int qrcp_cols_per_thread(int n_max, int l_pad, bool fp64);

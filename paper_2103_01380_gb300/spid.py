@@ -21,7 +21,7 @@ SPID_OK = 0
 STATUS_NAMES = {0: "SPID_OK", 1: "SPID_ERR_INVALID_ARG", 2: "SPID_ERR_CUDA", 3: "SPID_ERR_OOM",
                 4: "SPID_ERR_STATE", 5: "SPID_ERR_TIMEOUT", 6: "SPID_ERR_NONFINITE",
                 7: "SPID_ERR_UNSUPPORTED"}
-PREC = {"fp64": 0, "fp32": 1, "tf32": 2}
+PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "bf16x3": 4}
 FLAG_PER_SUBDOMAIN = 1
 
 # every symbol include/spid.h declares

@@ -3,7 +3,8 @@ import numpy as np
 
 import oracle
 
-U_MODE = {"fp64": 2.0 ** -53, "fp32": 2.0 ** -24, "tf32": 2.0 ** -11}
+U_MODE = {"fp64": 2.0 ** -53, "fp32": 2.0 ** -24, "tf32": 2.0 ** -11, "bf16": 2.0 ** -9,
+          "bf16x3": 2.0 ** -16}
 
 
 def rel_fro(a, b) -> float:

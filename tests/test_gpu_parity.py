@@ -24,8 +24,13 @@ from _helpers import adaptive_margin, oracle_window, r11_condition, rel_fro, sep
 
 pytestmark = pytest.mark.gpu
 
-GAP = {"fp64": 1e-6, "fp32": 1e-3, "tf32": 2e-2}
-Y_TOL = {"fp64": 1e-13, "fp32": 2e-6, "tf32": 3e-3}
+GAP = {"fp64": 1e-6, "fp32": 1e-3, "tf32": 2e-2, "bf16": 1e-1, "bf16x3": 1e-3}
+# BF16 keeps 8 significand bits of A and Omega (two roundings of up to 2^-9);
+# 3xBF16 drops only the lo x lo product and the 16-bit tails (~2^-16)
+Y_TOL = {"fp64": 1e-13, "fp32": 2e-6, "tf32": 3e-3, "bf16": 1.5e-2, "bf16x3": 1e-4}
+# final relative error the low-precision sketches must reach on the separated
+# low-rank inputs here (data noise 1e-3 sets the oracle's own error)
+ERR_CAP = {"tf32": 1e-3, "bf16x3": 1e-3, "bf16": 1e-2}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -167,25 +172,27 @@ def test_parity_ragged_multi_subdomain(precision):
     check_parity(win, precision, 5, p=8, c_tol=tol, ahat_tol=tol)
 
 
-def test_tf32_sketch_accuracy_and_parity():
+@pytest.mark.parametrize("precision", ["tf32", "bf16x3", "bf16"])
+def test_tensor_core_sketch_accuracy_and_parity(precision):
     m = [33, 200, 1000, 4099]
     n = [40, 300, 130, 600]
     win = _lowrank_window(4, m, n, 6, seed=20, noise=1e-3)
-    g, o = check_parity(win, "tf32", 5, p=8)
+    g, o = check_parity(win, precision, 5, p=8,
+                        ahat_tol=1e-4 if precision == "bf16x3" else None)
     for s in range(4):
         eg = np.sqrt(g["err"][s, 0] / g["err"][s, 1])
         eo = np.sqrt(o["e2"][s] / o["a2"][s])
-        assert eg <= max(1e-3, 2.0 * eo), (s, eg, eo)
+        assert eg <= max(ERR_CAP[precision], 2.0 * eo), (s, eg, eo)
 
 
 def test_snapshot_major_layout():
     # [j][s][r] window: every snapshot contiguous, ld = sum of padded rows
     win = _lowrank_window(3, [100, 64, 257], [90, 90, 90], 5, seed=30, layout="snapshot")
-    for prec in ("fp32", "tf32"):
-        check_parity(win, prec, 4, p=6, ahat_tol=1e-5 if prec == "fp32" else None)
+    for prec in ("fp32", "tf32", "bf16x3"):
+        check_parity(win, prec, 4, p=6, ahat_tol={"fp32": 1e-5, "bf16x3": 1e-4}.get(prec))
 
 
-@pytest.mark.parametrize("precision", ["fp32", "tf32"])
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16", "bf16x3"])
 def test_edge_cases(precision):
     # n < k_max, n = 1, m < 32, k_max = 1
     blocks = [inputs.separated_lowrank(20, 3, 2, 1), inputs.separated_lowrank(5, 1, 1, 2),
@@ -220,18 +227,18 @@ def test_adaptive_rank_geometric_spectrum():
     sig = 10.0 ** (-np.arange(1, 129) / 4.0)
     blocks = [inputs.spectrum_matrix(2048, 128, sig, seed=3 + s) for s in range(3)]
     win = inputs.pack_blocks(blocks)
-    for prec in ("fp32", "tf32"):
+    for prec in ("fp32", "tf32", "bf16x3"):
         g, o = check_parity(win, prec, 32, p=10, tol=1e-3,
-                            ahat_tol=1e-5 if prec == "fp32" else None)
+                            ahat_tol={"fp32": 1e-5, "bf16x3": 1e-4}.get(prec))
         for s in range(3):
-            if prec == "tf32":
+            if prec != "fp32":
                 assert abs(int(g["k"][s]) - int(o["k"][s])) <= 2
             assert np.sqrt(g["err"][s, 0] / g["err"][s, 1]) <= 3e-3
 
 
 def test_per_subdomain_launches_match_batched():
     win = _lowrank_window(5, [300, 129, 640, 64, 1000], [200, 64, 100, 513, 77], 5, seed=40)
-    for prec in ("fp32", "tf32"):
+    for prec in ("fp32", "tf32", "bf16x3"):
         a = run_gpu(win, prec, 5, p=6)
         b = run_gpu(win, prec, 5, p=6, flags=spid.FLAG_PER_SUBDOMAIN)
         for s in range(5):
@@ -242,7 +249,7 @@ def test_per_subdomain_launches_match_batched():
 
 def test_streamed_micro_batches_match_one_shot():
     win = _lowrank_window(3, [500, 777, 256], [256, 200, 130], 5, seed=50)
-    for prec in ("fp32", "tf32"):
+    for prec in ("fp32", "tf32", "bf16", "bf16x3"):
         a = run_gpu(win, prec, 5, p=6)
         b = run_gpu(win, prec, 5, p=6, batches=64)
         c = run_gpu(win, prec, 5, p=6, batches=1)

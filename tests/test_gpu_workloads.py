@@ -49,17 +49,38 @@ def check_sampled(win, g, precision, k_max, p, tol, samples, seed=0x5EED0001, er
         assert eg <= max(err_target or 0.0, 2.0 * eo, 1e-6), ("err", s, eg, eo)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "tf32"])
+_SPECTRUM_WINDOW = {}
+
+
+def _spectrum_window():
+    if "w" not in _SPECTRUM_WINDOW:
+        sig = 10.0 ** (-np.arange(1, 257) / 4.0)
+        blocks = [inputs.spectrum_matrix(16384, 256, sig, seed=3 + s) for s in range(4)]
+        _SPECTRUM_WINDOW["w"] = inputs.pack_blocks(blocks)
+    return _SPECTRUM_WINDOW["w"]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16x3"])
 def test_geometric_spectrum_adaptive_full_size(precision):
-    sig = 10.0 ** (-np.arange(1, 257) / 4.0)
-    blocks = [inputs.spectrum_matrix(16384, 256, sig, seed=3 + s) for s in range(4)]
-    win = inputs.pack_blocks(blocks)
+    win = _spectrum_window()
     g = run_gpu(win, precision, 32, p=10, tol=1e-3, reconstruct=False)
     assert g["status"] == 0
     check_sampled(win, g, precision, 32, 10, 1e-3, samples=(0, 3), err_target=3e-3)
     # the best rank-12 error sits at 1e-3: adaptive ranks land just above it
     assert 10 <= int(np.median(g["k"])) <= 18
     assert np.sqrt(g["total"][0] / g["total"][1]) <= 3e-3
+
+
+def test_geometric_spectrum_bf16_hits_its_noise_floor():
+    # single-pass BF16 rounds A and Omega to 8 significand bits: the sketch's
+    # noise (~1e-3 of ||Y||) sits at the tolerance, the rank guard (2^-8 |R_00|)
+    # stops near sigma_10, and the error lands above 1e-3 -- reported, not hidden
+    win = _spectrum_window()
+    g = run_gpu(win, "bf16", 32, p=10, tol=1e-3, reconstruct=False)
+    assert g["status"] == 0
+    check_sampled(win, g, "bf16", 32, 10, 1e-3, samples=(1,), err_target=3e-2)
+    rel = np.sqrt(g["total"][0] / g["total"][1])
+    assert rel <= 3e-2
 
 
 @pytest.mark.parametrize("precision", ["fp32", "tf32"])
