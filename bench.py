@@ -38,10 +38,11 @@ WORKLOAD = ("TGV+Fourier 64^3 grid, 64 subdomains of 16^3 x 5 QoIs (m=20480), n=
 # (profiles/dram_traffic_tf32_tgv3d_64sub.md).  A figure is reported only while
 # the kernel's sources hash to the value they had when it was measured.
 MEASURED_TRAFFIC = {
-    "sketch": {"bytes": 2.69e9 + 7.07e6, "sources": ("sketch_tc.cu", "spid_internal.cuh"),
-               "sha256_16": "73839046242937e9"},
-    "error": {"bytes": 2.69e9 + 0.212e6, "sources": ("error.cu", "spid_internal.cuh"),
-              "sha256_16": "e9556cc92f9e01aa"},
+    "sketch": {"bytes": 2693607424 + 7129856,
+               "sources": ("sketch_tc.cu", "tcgen05_ptx.cuh", "spid_internal.cuh"),
+               "sha256_16": "ab4f1f584cc52fb7"},
+    "error": {"bytes": 2684970240 + 400640, "sources": ("error.cu", "spid_internal.cuh"),
+              "sha256_16": "d659a1baed82867a"},
 }
 
 
@@ -208,7 +209,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="tf32", choices=["tf32", "fp32"])
+    ap.add_argument("--precision", default="tf32", choices=["tf32", "bf16x3", "bf16", "fp32"])
     ap.add_argument("--ref-subs", type=int, default=16)
     ap.add_argument("--cpu-sample", type=int, default=64)
     ap.add_argument("--boxes", type=int, default=None,
@@ -359,7 +360,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 (tf32 sketch)" if args.precision == "tf32" else "f32",
+            "dtype": "f32" if args.precision == "fp32" else f"f32 ({args.precision} sketch)",
             "data": "synthetic",
             "config": {"workload": WORKLOAD if args.boxes is None else
                        f"first {args.boxes} boxes of: " + WORKLOAD, "precision": args.precision,
