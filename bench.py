@@ -203,6 +203,241 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------------------
+# Other workloads of the paper-derived configuration list (one GPU each)
+# ----------------------------------------------------------------------------
+def _stage_times(torch, plan, window, steps, warmup, err, tot, sketch_calls):
+    """Mean sketch / finalize / error times (ms) over `steps` CUDA-event-timed
+    steps on the current stream; sketch_calls = list of (col0, ncols)."""
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for c0, nc in sketch_calls:
+            plan.sketch(window, c0, nc)
+        plan.finalize()
+        plan.error(window, err, tot)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for i in range(steps):
+        ev[i][0].record(stream)
+        for c0, nc in sketch_calls:
+            plan.sketch(window, c0, nc)
+        ev[i][1].record(stream)
+        plan.finalize()
+        ev[i][2].record(stream)
+        plan.error(window, err, tot)
+        ev[i][3].record(stream)
+    torch.cuda.synchronize()
+    sk = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    fi = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    er = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
+    return sk, fi, er
+
+
+def _summary(plan, tot):
+    t = tot.detach().cpu().numpy()
+    k, _, _ = plan.factors()
+    return {"rel_err": float(np.sqrt(t[0] / t[1])), "compression_factor": float(t[2] / t[3]),
+            "k_mean": float(np.mean(k)), "k_max": int(np.max(k))}
+
+
+def run_workload(args):
+    import torch
+    from paper_2103_01380_gb300 import build, inputs, spid
+    torch.cuda.set_device(0)
+    build.build()
+    spid.load_library()
+    peak, peak_kind = load_peaks()
+    if args.workload == "spectrum256":
+        line = _run_spectrum(args, torch, inputs, spid)
+    elif args.workload == "uneven4096":
+        line = _run_uneven(args, torch, inputs, spid)
+    else:
+        line = _run_insitu(args, torch, inputs, spid)
+    line.update({"metric": METRIC, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+                 "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                 "vs_baseline": None, "data": "synthetic", "gpu_launches": None})
+    sk = line.pop("_sketch_gbs", None)
+    if sk is not None:
+        line["roofline"] = {"bound": "hbm", "kernel": "sketch", "achieved": sk, "peak": peak,
+                            "unit": "GB/s", "frac": sk / peak, "peak_kind": peak_kind,
+                            "traffic": None}
+    print(json.dumps(line))
+    return 0
+
+
+def _run_spectrum(args, torch, inputs, spid):
+    """256 subdomains, A = U diag(sigma) V^T with sigma_i = 10^{-i/4}, m = 16384,
+    n = 256, adaptive rank to 1e-3 (k_max 32, p 10), every sketch precision."""
+    S, m, n, r = 256, 16384, 256, 32
+    sig = torch.tensor(10.0 ** (-np.arange(1, r + 1) / 4.0), device="cuda", dtype=torch.float32)
+    window = torch.empty(S * m * n, device="cuda", dtype=torch.float32)
+    g = torch.Generator(device="cuda")
+    for s in range(S):
+        g.manual_seed(3 + s)
+        U, _ = torch.linalg.qr(torch.randn(m, r, device="cuda", generator=g))
+        V, _ = torch.linalg.qr(torch.randn(n, r, device="cuda", generator=g))
+        window[s * m * n:(s + 1) * m * n].view(n, m).copy_(((U * sig) @ V.T).T)
+    nbytes = 4.0 * S * m * n
+    err = torch.zeros(2 * S, dtype=torch.float64, device="cuda")
+    tot = torch.zeros(4, dtype=torch.float64, device="cuda")
+    study = {}
+    for prec in ("tf32", "bf16x3", "bf16", "fp32"):
+        plan = spid.Plan([m] * S, [n] * S, np.arange(S) * m * n, [m] * S, k_max=32, p=10,
+                         tol=1e-3, precision=prec, seed=0x5EED0003)
+        sk, fi, er = _stage_times(torch, plan, window, args.steps, args.warmup, err, tot,
+                                  [(0, n)])
+        study[prec] = dict(value=nbytes / ((sk + fi + er) / 1e3) / 1e9,
+                           sketch_gbs=nbytes / (sk / 1e3) / 1e9, finalize_ms=fi,
+                           error_gbs=nbytes / (er / 1e3) / 1e9, **_summary(plan, tot))
+        plan.close()
+    line = {"value": study["tf32"]["value"], "ms_per_step": nbytes / study["tf32"]["value"] / 1e6,
+            "dtype": "f32 (tf32 sketch)",
+            "config": {"workload": "spectrum: 256 subdomains, A = U diag(10^{-i/4}) V^T "
+                                   "(Haar U, V; components beyond 32 sit below FP32 rounding), "
+                                   "m=16384, n=256, adaptive tol 1e-3, k_max=32, p=10",
+                       "l2": "inputs (4.29 GB) larger than L2; no flush"},
+            "precision_study": study, "_sketch_gbs": study["tf32"]["sketch_gbs"]}
+    if not args.no_cpu_baseline:
+        # the oracle on two sampled subdomains: its own error at the same tolerance
+        import oracle
+        host = window.view(S, n, m)[[0, S - 1]].cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        errs = []
+        for blk in host:
+            o = oracle.spid(blk.T, 42, 32, 1e-3, 2.0 ** -53, 0x5EED0003)
+            errs.append(float(np.sqrt(o["e2"] / o["a2"])))
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 2 * 4.0 * m * n / dt / 1e9, "unit": "GB/s",
+                                "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": "subdomains 0 and 255 (FP64 oracle, adaptive 1e-3)",
+                                "oracle_rel_err": errs}
+    return line
+
+
+def _run_uneven(args, torch, inputs, spid):
+    """4096 cubic boxes, edges {8,12,16,24,32} x 5 QoIs, windows 64..1024 snapshots,
+    of the TGV+Fourier field on a 256^3 grid; adaptive 1e-3 (k_max 32, p 10);
+    processed in waves that fit HBM, one plan per wave."""
+    boxes = inputs.uneven_boxes(4096, seed=4)
+    modes = inputs.fourier_modes(seed=2)
+    waves, cur, cur_b = [], [], 0.0
+    for b in boxes:
+        nb = 4.0 * 5 * b[1] ** 3 * b[2]
+        if cur and cur_b + nb > args.wave_gb * 1e9:
+            waves.append(cur)
+            cur, cur_b = [], 0.0
+        cur.append(b)
+        cur_b += nb
+    waves.append(cur)
+    tot_bytes, tot_ms, sk_ms_all, ks, e2, a2, mn, kd = 0.0, 0.0, 0.0, [], 0.0, 0.0, 0.0, 0.0
+    for wv in waves:
+        m = np.array([5 * e ** 3 for _, e, _ in wv], dtype=np.int64)
+        n = np.array([nn for _, _, nn in wv], dtype=np.int64)
+        off = np.concatenate([[0], np.cumsum(m * n)[:-1]])
+        window = torch.empty(int((m * n).sum()), device="cuda", dtype=torch.float32)
+        for s, (org, e, nn) in enumerate(wv):
+            f = inputs.DeviceField([org], e, 256, modes)
+            t = 10.0 * np.arange(nn) / max(nn - 1, 1)
+            blk = f.snapshots(t).reshape(5 * e ** 3, nn)                  # [m, n]
+            window[int(off[s]):int(off[s] + m[s] * nn)].view(nn, int(m[s])).copy_(blk.T)
+        S = len(wv)
+        err = torch.zeros(2 * S, dtype=torch.float64, device="cuda")
+        tot = torch.zeros(4, dtype=torch.float64, device="cuda")
+        plan = spid.Plan(m, n, off, m, k_max=32, p=10, tol=1e-3, precision="tf32",
+                         seed=0x5EED0004)
+        sk, fi, er = _stage_times(torch, plan, window, max(1, args.steps // 4), 1, err, tot,
+                                  [(0, int(n.max()))])
+        t = tot.detach().cpu().numpy()
+        e2, a2, mn, kd = e2 + t[0], a2 + t[1], mn + t[2], kd + t[3]
+        ks.extend(plan.factors()[0].tolist())
+        tot_bytes += 4.0 * float((m * n).sum())
+        tot_ms += sk + fi + er
+        sk_ms_all += sk
+        plan.close()
+        del window
+        torch.cuda.empty_cache()
+    return {"value": tot_bytes / (tot_ms / 1e3) / 1e9, "ms_per_step": tot_ms,
+            "dtype": "f32 (tf32 sketch)",
+            "config": {"workload": f"uneven: 4096 cubic boxes (edges 8..32) x 5 QoIs of a 256^3 "
+                                   f"TGV+Fourier field, n in 64..1024, adaptive 1e-3, "
+                                   f"{len(waves)} waves of <= {args.wave_gb:g} GB",
+                       "total_gb": tot_bytes / 1e9, "l2": "inputs larger than L2"},
+            "rel_err": float(np.sqrt(e2 / a2)), "compression_factor": float(mn / kd),
+            "k_mean": float(np.mean(ks)), "k_max": int(np.max(ks)),
+            "_sketch_gbs": tot_bytes / (sk_ms_all / 1e3) / 1e9}
+
+
+def _run_insitu(args, torch, inputs, spid):
+    """512 boxes of 32^3 x 5 QoIs of a 256^3 field, n = 256, snapshot-major window
+    (86 GB); the sketch runs per micro-batch of snapshots as they arrive; k 30,
+    p 10 (TF32).  Also: a producer stream writes each batch while the sketch
+    consumes the previous one."""
+    S, edge, grid, n, b = 512, 32, 256, 256, args.microbatch
+    origins = [(bx * edge, by * edge, bz * edge) for bz in range(8) for by in range(8)
+               for bx in range(8)]
+    field = inputs.DeviceField(origins, edge, grid, inputs.fourier_modes(seed=2))
+    m = 5 * edge ** 3
+    window = torch.empty(n * S * m, device="cuda", dtype=torch.float32)
+    t_all = 10.0 * np.arange(n) / (n - 1)
+    calls = [(j0, min(b, n - j0)) for j0 in range(0, n, b)]
+    for j0, nc in calls:
+        field.fill_snapshot_major(window, t_all[j0:j0 + nc], j0, n)
+    torch.cuda.synchronize()
+    nbytes = 4.0 * S * m * n
+    err = torch.zeros(2 * S, dtype=torch.float64, device="cuda")
+    tot = torch.zeros(4, dtype=torch.float64, device="cuda")
+    plan = spid.Plan([m] * S, [n] * S, np.arange(S) * m, [S * m] * S, k_max=30, p=10,
+                     precision="tf32", seed=0x5EED0005)
+    sk, fi, er = _stage_times(torch, plan, window, args.steps, args.warmup, err, tot, calls)
+    summ = _summary(plan, tot)
+    # in-situ overlap: producer writes batch i+1 while the sketch consumes batch i
+    prod = torch.cuda.Stream()
+    cons = torch.cuda.current_stream()
+    ready = [torch.cuda.Event() for _ in calls]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(cons)
+    prod.wait_event(e0)
+    with torch.cuda.stream(prod):
+        for i, (j0, nc) in enumerate(calls):
+            field.fill_snapshot_major(window, t_all[j0:j0 + nc], j0, n)
+            ready[i].record(prod)
+    for i, (j0, nc) in enumerate(calls):
+        cons.wait_event(ready[i])
+        plan.sketch(window, j0, nc)
+    plan.finalize()
+    plan.error(window, err, tot)
+    e1.record(cons)
+    torch.cuda.synchronize()
+    overlapped = e0.elapsed_time(e1)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(cons)
+    for j0, nc in calls:
+        field.fill_snapshot_major(window, t_all[j0:j0 + nc], j0, n)
+    p1.record(cons)
+    torch.cuda.synchronize()
+    produce = p0.elapsed_time(p1)
+    plan.close()
+    step = sk + fi + er
+    return {"value": nbytes / (step / 1e3) / 1e9, "ms_per_step": step,
+            "dtype": "f32 (tf32 sketch)",
+            "config": {"workload": f"in-situ: 512 boxes of 32^3 x 5 QoIs of a 256^3 TGV+Fourier "
+                                   f"field, n=256, snapshot-major window (85.9 GB), sketch per "
+                                   f"micro-batch of {b} snapshots, k=30, p=10",
+                       "l2": "inputs larger than L2"},
+            "stages_ms": {"sketch": sk, "finalize": fi, "error": er},
+            "sketch_gbs": nbytes / (sk / 1e3) / 1e9, "error_gbs": nbytes / (er / 1e3) / 1e9,
+            **summ,
+            "insitu_overlap": {"producer_ms": produce, "compress_ms": step,
+                               "overlapped_ms": overlapped,
+                               "hidden_fraction": max(0.0, (produce + step - overlapped) / step)},
+            "_sketch_gbs": nbytes / (sk / 1e3) / 1e9}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,9 +451,16 @@ def main():
                     help="first N boxes only (small profiling case; not the bench workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--workload", default="tgv3d64",
+                    choices=["tgv3d64", "spectrum256", "uneven4096", "insitu256"],
+                    help="tgv3d64 is the bench workload; the others print their own line")
+    ap.add_argument("--microbatch", type=int, default=64, help="insitu256: columns per call")
+    ap.add_argument("--wave-gb", type=float, default=48.0, help="uneven4096: GB per wave")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "tgv3d64":
+        return run_workload(args)
 
     import torch
     import torch.distributed as dist

@@ -239,6 +239,73 @@ def uneven_window(boxes, grid: int = 256, t_end: float = 10.0, nu: float = 0.01,
 
 
 # --------------------------------------------------------------------------
+# The same 3D field generated on the GPU (torch), for windows too large to
+# build on the host.  FP32 arithmetic; every Fourier phase k . x is reduced
+# exactly in integers (k and the grid indices are integers) before the
+# trigonometric call, so values agree with the FP64 host generator to ~1e-6.
+# --------------------------------------------------------------------------
+class DeviceField:
+    """Spatial basis of the TGV + Fourier field over a set of cubic boxes of a
+    grid^3 periodic grid, held on the GPU; `snapshots` evaluates it at any
+    batch of times.  Point order: box-major, then (z, y, x) inside the box."""
+
+    def __init__(self, origins, edge: int, grid: int, modes: FourierModes, nu: float = 0.01,
+                 device="cuda"):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.edge, self.grid, self.nu, self.modes = edge, grid, nu, modes
+        self.S = len(origins)
+        self.npts = edge ** 3
+        e = torch.arange(edge, device=device, dtype=torch.int64)
+        zl, yl, xl = torch.meshgrid(e, e, e, indexing="ij")
+        org = torch.tensor(origins, device=device, dtype=torch.int64)            # [S, 3] (x, y, z)
+        ix = (org[:, 0, None] + xl.reshape(1, -1)) % grid                          # [S, npts]
+        iy = (org[:, 1, None] + yl.reshape(1, -1)) % grid
+        iz = (org[:, 2, None] + zl.reshape(1, -1)) % grid
+        h = 2.0 * np.pi / grid
+        x, y, z = (ix.reshape(-1).float() * h, iy.reshape(-1).float() * h, iz.reshape(-1).float() * h)
+        self.tgv = torch.stack([torch.sin(x) * torch.cos(y) * torch.cos(z),
+                                -torch.cos(x) * torch.sin(y) * torch.cos(z),
+                                torch.zeros_like(x)], dim=1)                      # [P, 3]
+        kv = torch.tensor(modes.kvec, device=device, dtype=torch.int64)            # [K, 3]
+        ph = (ix.reshape(-1, 1) * kv[None, :, 0] + iy.reshape(-1, 1) * kv[None, :, 1]
+              + iz.reshape(-1, 1) * kv[None, :, 2]) % grid                         # exact, [P, K]
+        theta = ph.float() * h + torch.tensor(modes.phase, device=device, dtype=torch.float32)
+        self.cos = torch.cos(theta)
+        self.sin = torch.sin(theta)
+        self.dirn = torch.tensor(modes.dirn, device=device, dtype=torch.float32)   # [K, 3]
+
+    def snapshots(self, t: np.ndarray, p0: float = 100.0, gamma: float = 1.4):
+        """Field at times t: [5, P, len(t)] (QoIs rho, u, v, w, p), FP32."""
+        torch = self.torch
+        md = self.modes
+        decay = np.exp(-self.nu * (md.kvec ** 2).sum(1)[:, None] * t[None, :])
+        tc = torch.tensor(md.amp[:, None] * decay * np.cos(np.outer(md.omega, t)),
+                          device=self.device, dtype=torch.float32)                 # [K, b]
+        ts = torch.tensor(md.amp[:, None] * decay * np.sin(np.outer(md.omega, t)),
+                          device=self.device, dtype=torch.float32)
+        g = torch.tensor(np.exp(-3.0 * self.nu * t), device=self.device, dtype=torch.float32)
+        out = torch.empty((5, self.S * self.npts, len(t)), device=self.device, dtype=torch.float32)
+        for c in range(3):
+            d = self.dirn[:, c:c + 1]
+            out[1 + c] = (self.tgv[:, c:c + 1] * g[None, :] + self.cos @ (d * tc)
+                          - self.sin @ (d * ts))
+        speed2 = out[1] ** 2 + out[2] ** 2 + out[3] ** 2
+        out[0] = 1.0 + 0.01 * speed2
+        out[4] = p0 * out[0] ** gamma
+        return out
+
+    def fill_snapshot_major(self, window, t: np.ndarray, j0: int, n_total: int):
+        """Write snapshots j0 .. j0 + len(t) of every box into a snapshot-major
+        window [n_total][S][5 * npts] (rows of a box in (q, z, y, x) order)."""
+        b = len(t)
+        f = self.snapshots(t)                                           # [5, S*P, b]
+        w = window.view(n_total, self.S, 5, self.npts)
+        w[j0:j0 + b] = f.view(5, self.S, self.npts, b).permute(3, 1, 0, 2)
+
+
+# --------------------------------------------------------------------------
 # Prescribed-spectrum matrices (Haar-orthonormal factors)
 # --------------------------------------------------------------------------
 def haar(rows: int, cols: int, rng: np.random.Generator) -> np.ndarray:
