@@ -1,9 +1,10 @@
 // sketch_bf16.cu -- Gaussian sketch Y = Omega A (Section 2, random projection
 // B = Omega A) on the tensor cores in BF16 with FP32 accumulation.
 //
-// Same decomposition as the TF32 kernel (Y^T = A^T Omega^T, M = 128 window
-// columns, N = l_pad, K = 32 rows of A per chunk, accumulators in TMEM), with
-// one more warp group: the FP32 tiles that TMA lands (128-byte swizzle) are
+// Same decomposition and packed schedule as the TF32 kernel (Y^T = A^T
+// Omega^T, M = 128 window columns = two 64-column slices, N = l_pad, K = 32
+// rows of A per chunk, up to 4 tiles per pack, accumulators in TMEM), with one
+// more warp group: the FP32 tiles that TMA lands (128-byte swizzle) are
 // converted IN PLACE into BF16 K-major tiles with a 64-byte swizzle -- the
 // 16 KB FP32 tile becomes an 8 KB BF16 tile, or, in the split form, an 8 KB
 // "hi" tile bf16(a) followed by an 8 KB "lo" tile bf16(a - hi).
@@ -13,14 +14,15 @@
 //             MMAs per K-step; the tensor pipe has the headroom (the sketch
 //             is HBM-bound at 2 l flop per 4 bytes).
 //
-// Warp roles (320 threads):
-//   warp 0      TMA producer            warp 1      TMEM allocator + MMA issuer
-//   warps 2..5  Omega generators, then the TMEM -> partial-slot epilogue
-//   warps 6..9  FP32 -> BF16 converters (thread c owns row c of each tile)
+// Warp roles (448 threads):
+//   warp 0       TMA producer            warp 1      TMEM allocator + MMA issuer
+//   warps 2..9   Omega generators, then the TMEM -> partial-slot epilogue
+//   warps 10..13 FP32 -> BF16 converters (thread c owns row c of each tile)
 // Every mbarrier wait is bounded; see the TF32 kernel for the abort protocol.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include "sketch_pack.cuh"
 #include "spid_internal.cuh"
 #include "tcgen05_ptx.cuh"
 
@@ -30,10 +32,14 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThreads = 320;
+constexpr int kGenWarps = 8;
+constexpr int kGenThreads = 32 * kGenWarps;
+constexpr int kConvBase = 64 + kGenThreads;       // first converter thread
+constexpr int kThreads = kConvBase + 128;
 constexpr int kTileCols = 128;
 constexpr int kTileBytes = kTileCols * 128;      // FP32 tile: 128 columns x 32 rows
 constexpr int kBf16TileBytes = kTileCols * 64;   // BF16 tile: 128 columns x 32 rows
+constexpr int kSliceBytes = kSliceCols * 128;    // FP32 slice: 64 columns x 32 rows (one TMA box)
 constexpr int kMaxStages = 8;
 
 struct Bf16Args {
@@ -58,7 +64,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
 template <bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1) sketch_bf16_kernel(const Bf16Args args) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ int epi_last;
+  __shared__ int epi_last[kPackSlices];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const SketchArgs& a = args.s;
@@ -86,7 +92,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_bf16_kernel(const Bf16Args
     for (int s = 0; s < S; ++s) {
       mbar_init(smem_addr(&full[s]), 1);
       mbar_init(smem_addr(&empty[s]), 1);
-      mbar_init(smem_addr(&ofull[s]), 128);
+      mbar_init(smem_addr(&ofull[s]), kGenThreads);
       mbar_init(smem_addr(&cfull[s]), 128);
     }
     mbar_init(smem_addr(accum), 1);
@@ -113,19 +119,20 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_bf16_kernel(const Bf16Args
       bool ok = true;
       const CUtensorMap* tmaps = static_cast<const CUtensorMap*>(a.tmaps);
       for (int si = seg0; si < seg1 && ok; ++si) {
-        const Segment seg = a.segs[si];
-        const Problem pb = a.probs[seg.prob];
-        const int nt = (pb.ncols + kTileCols - 1) / kTileCols;
-        const CUtensorMap* tm = tmaps + pb.sub;
-        for (int ch = seg.chunk0; ch < seg.chunk1; ++ch, ++it) {
+        const PackSegment sg = a.psegs[si];
+        const Pack pk = a.packs[sg.pack];
+        for (int ch = sg.chunk0; ch < sg.chunk1; ++ch, ++it) {
           const int st = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
           if (!mbar_wait(smem_addr(&empty[st]), ph ^ 1u, abort_flag, a.status)) { ok = false; break; }
           const uint32_t fb = smem_addr(&full[st]);
-          mbar_arrive_expect_tx(fb, (uint32_t)(nt * kTileBytes));
-          for (int t = 0; t < nt; ++t)
-            tma_load_2d(smem_addr(smem_A + ((size_t)st * args.max_tiles + t) * kTileBytes), tm,
-                        ch * kChunkRows, pb.col0 + t * kTileCols, fb);
+          mbar_arrive_expect_tx(fb, (uint32_t)(pk.nslices * kSliceBytes));
+          unsigned char* dst = smem_A + (size_t)st * args.max_tiles * kTileBytes;
+          for (int h = 0; h < pk.nslices; ++h) {
+            const Slice sl = a.slices[pk.slice0 + h];
+            tma_load_2d(smem_addr(dst + h * kSliceBytes), tmaps + sl.sub, ch * kChunkRows,
+                        sl.col0, fb);
+          }
         }
       }
       const int first = it - S > 0 ? it - S : 0;
@@ -139,9 +146,8 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_bf16_kernel(const Bf16Args
       bool ok = true, issued = false;
       const uint32_t idesc = bf16_idesc(kTileCols, l_pad);
       for (int si = seg0; si < seg1 && ok; ++si) {
-        const Segment seg = a.segs[si];
-        const Problem pb = a.probs[seg.prob];
-        const int nt = (pb.ncols + kTileCols - 1) / kTileCols;
+        const PackSegment seg = a.psegs[si];
+        const int nt = (a.packs[seg.pack].nslices + 1) / 2;
         for (int ch = seg.chunk0; ch < seg.chunk1; ++ch, ++it) {
           const int st = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
@@ -175,15 +181,14 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_bf16_kernel(const Bf16Args
         mbar_wait(smem_addr(drain), 0u, abort_flag, a.status, false);
       }
     }
-  } else if (warp >= 6) {
+  } else if (threadIdx.x >= kConvBase) {
     // ------------------------------------------------ FP32 -> BF16 converters
-    const int row = threadIdx.x - 192;             // 0..127: row (window column) of the tile
+    const int row = threadIdx.x - kConvBase;       // 0..127: row (window column) of the tile
     int it = 0;
     bool ok = true;
     for (int si = seg0; si < seg1 && ok; ++si) {
-      const Segment seg = a.segs[si];
-      const Problem pb = a.probs[seg.prob];
-      const int nt = (pb.ncols + kTileCols - 1) / kTileCols;
+      const PackSegment seg = a.psegs[si];
+      const int nt = (a.packs[seg.pack].nslices + 1) / 2;
       for (int ch = seg.chunk0; ch < seg.chunk1; ++ch, ++it) {
         const int st = it % S;
         const uint32_t ph = (uint32_t)(it / S) & 1u;
@@ -226,64 +231,33 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_bf16_kernel(const Bf16Args
     }
   } else {
     // ------------------------------------------------ Omega generators + epilogue
-    const int gtid = threadIdx.x - 64;            // 0..127
+    const int gtid = threadIdx.x - 64;            // 0 .. kGenThreads-1
+    const int part = (warp - 2) / 4;              // warps sharing a quadrant split the columns
+    constexpr int kParts = kGenWarps / 4;
     const int quad = warp & 3;
     const uint2 key = philox_key(a.seed);
     const int groups = l_pad / 4;
-    float* partial = static_cast<float*>(a.partial);
     int it = 0, segi = 0;
     bool ok = true;
-    auto epilogue = [&](const Segment& seg, int seg_index) -> bool {
+    auto epilogue = [&](int si_done, int seg_index) -> bool {
       if (!mbar_wait(smem_addr(accum), (uint32_t)seg_index & 1u, abort_flag, a.status))
         return false;
       tc_fence_after();
-      const Problem pb = a.probs[seg.prob];
-      const int nt = (pb.ncols + kTileCols - 1) / kTileCols;
-      float* out = partial + a.slot_off[seg.slot];
-      for (int t = 0; t < nt; ++t) {
-        const int j = t * kTileCols + quad * 32 + lane;
-        for (int c = 0; c < l_pad; c += 16) {
-          uint32_t r[16];
-          __syncwarp();
-          tmem_ld16(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(t * args.acc_stride + c),
-                    r);
-          tmem_ld_wait();
-          if (j < pb.ncols) {
-            float4* dst = reinterpret_cast<float4*>(out + (int64_t)j * l_pad + c);
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                                   __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
-          }
-        }
-      }
-      tc_fence_before();
-      __threadfence();
-      named_bar_sync(1, 128);
-      if (gtid == 0) {
-        const int nslots = a.pslot_ptr[seg.prob + 1] - a.pslot_ptr[seg.prob];
-        epi_last = (atomicAdd(&a.prob_cnt[seg.prob], 1) == nslots - 1);
-      }
-      named_bar_sync(1, 128);
-      if (epi_last) {
-        __threadfence();
-        reduce_problem_slots<float>(a, seg.prob, gtid, 128);
-        if (gtid == 0) a.prob_cnt[seg.prob] = 0;
-      }
-      named_bar_sync(1, 128);
+      pack_epilogue(a, a.psegs[si_done], tmem_base, args.acc_stride, quad, part, kParts, lane,
+                    gtid, kGenThreads, epi_last, 1);
       return true;
     };
     for (int si = seg0; si < seg1 && ok; ++si, ++segi) {
-      const Segment seg = a.segs[si];
-      if (si > seg0 && !epilogue(a.segs[si - 1], segi - 1)) { ok = false; break; }
-      const Problem pb = a.probs[seg.prob];
+      const PackSegment seg = a.psegs[si];
+      if (si > seg0 && !epilogue(si - 1, segi - 1)) { ok = false; break; }
+      const Pack pb = a.packs[seg.pack];
       for (int ch = seg.chunk0; ch < seg.chunk1; ++ch, ++it) {
         const int st = it % S;
         const uint32_t ph = (uint32_t)(it / S) & 1u;
         if (!mbar_wait(smem_addr(&empty[st]), ph ^ 1u, abort_flag, a.status)) { ok = false; break; }
         unsigned char* ob = smem_O + (size_t)st * omega_bytes;
         const int r0 = ch * kChunkRows;
-        for (int task = gtid; task < kChunkRows * groups; task += 128) {
+        for (int task = gtid; task < kChunkRows * groups; task += kGenThreads) {
           const int k = task % kChunkRows, g = task / kChunkRows;
           float w[4] = {0.f, 0.f, 0.f, 0.f};
           if (4 * g < a.l && r0 + k < pb.m) {
@@ -306,7 +280,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_bf16_kernel(const Bf16Args
         mbar_arrive(smem_addr(&ofull[st]));
       }
     }
-    if (ok && seg1 > seg0) epilogue(a.segs[seg1 - 1], segi - 1);
+    if (ok && seg1 > seg0) epilogue(seg1 - 1, segi - 1);
   }
 
   tc_fence_before();

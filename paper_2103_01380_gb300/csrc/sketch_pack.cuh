@@ -1,0 +1,74 @@
+// sketch_pack.cuh -- the part of the tensor-core sketch kernels that depends on
+// the packed schedule but not on the MMA format: draining a pack's
+// accumulators from TMEM into its problems' partial slots, and the fixed-order
+// fold done by the CTA that completes a problem.
+#pragma once
+
+#include "spid_internal.cuh"
+#include "tcgen05_ptx.cuh"
+
+namespace spid {
+namespace tc {
+
+// Accumulator layout: tile t (two slices) at TMEM columns t * acc_stride, row r
+// of the tile = TMEM lane r; slice 2t owns rows 0..63, slice 2t+1 rows 64..127.
+// Called by all `nthreads` epilogue threads (whole warps); warp w reads TMEM
+// lanes 32 (w % 4) .. +31 and the warps sharing a quadrant (`part` of
+// `nparts`) take alternate 16-column slices.
+__device__ __forceinline__ void pack_epilogue(const SketchArgs& a, const PackSegment& sg,
+                                              uint32_t tmem_base, int acc_stride, int quad,
+                                              int part, int nparts, int lane, int gtid,
+                                              int nthreads, int* last_flags, int barrier_id) {
+  const Pack pk = a.packs[sg.pack];
+  const int l_pad = a.l_pad;
+  const int nt = (pk.nslices + 1) / 2;
+  float* partial = static_cast<float*>(a.partial);
+  const int row = quad * 32 + lane;                 // TMEM lane = tile row
+  for (int t = 0; t < nt; ++t) {
+    const int h = 2 * t + (row >> 6);
+    const int jj = row & 63;
+    bool valid = false;
+    float* out = nullptr;
+    if (h < pk.nslices) {
+      const Slice sl = a.slices[pk.slice0 + h];
+      if (jj < sl.ncols) {
+        valid = true;
+        out = partial + a.slot_off[sg.slot0 + sl.member] + (int64_t)(sl.out_col + jj) * l_pad;
+      }
+    }
+    for (int c = 16 * part; c < l_pad; c += 16 * nparts) {
+      uint32_t r[16];
+      __syncwarp();
+      tmem_ld16(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(t * acc_stride + c), r);
+      tmem_ld_wait();
+      if (valid) {
+        float4* dst = reinterpret_cast<float4*>(out + c);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                               __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+      }
+    }
+  }
+  tc_fence_before();
+  // every member problem counts this segment; whoever completes it folds it
+  __threadfence();
+  named_bar_sync(barrier_id, nthreads);
+  if (gtid < pk.nprob) {
+    const int p = pk.prob0 + gtid;
+    const int nslots = a.pslot_ptr[p + 1] - a.pslot_ptr[p];
+    last_flags[gtid] = (atomicAdd(&a.prob_cnt[p], 1) == nslots - 1);
+  }
+  named_bar_sync(barrier_id, nthreads);
+  for (int q = 0; q < pk.nprob; ++q) {
+    if (last_flags[q]) {
+      __threadfence();
+      reduce_problem_slots<float>(a, pk.prob0 + q, gtid, nthreads);
+      if (gtid == 0) a.prob_cnt[pk.prob0 + q] = 0;
+    }
+  }
+  named_bar_sync(barrier_id, nthreads);   // last_flags is reused by the next segment
+}
+
+}  // namespace tc
+}  // namespace spid

@@ -4,22 +4,26 @@
 // The contraction is computed transposed, Y^T = A^T Omega^T:
 //   MMA M = 128 window columns (snapshots), N = l_pad (rows of Omega),
 //   K = rows of A, 32 rows (one 128-byte swizzle row of FP32) per chunk.
-// A's columns are contiguous in rows, so a [32 rows x 128 columns] box loaded
-// by TMA with 128-byte swizzling is exactly the K-major canonical layout the
-// MMA reads; Omega(:, rows) is regenerated from Philox each chunk by four
-// warps directly into the same swizzled K-major layout and reused for every
-// 128-column tile of the column group; the accumulators live in TMEM.
+// A's columns are contiguous in rows, so a [32 rows x 64 columns] box loaded
+// by TMA with 128-byte swizzling is half of the K-major canonical tile the MMA
+// reads.  Omega does not depend on the subdomain, so one chunk of rows serves
+// a whole pack: up to 8 such boxes (64-column slices of subdomains with equal
+// m) stacked into 4 MMA tiles.  Omega(:, rows) is regenerated from Philox each
+// chunk by the generator warps directly into the same swizzled K-major layout;
+// the accumulators live in TMEM.
 //
-// Warp roles (192 threads):
+// Warp roles (320 threads):
 //   warp 0      TMA producer (one elected lane)
 //   warp 1      TMEM allocator + MMA issuer (one elected lane)
-//   warps 2..5  Omega generators, then the TMEM -> partial-slot epilogue
-//               (warp w reads TMEM lanes 32 (w % 4) .. +31)
+//   warps 2..9  Omega generators, then the TMEM -> partial-slot epilogue
+//               (warp w reads TMEM lanes 32 (w % 4) .. +31; the two warps of a
+//               quadrant take alternate 16-column slices)
 // Every mbarrier wait is bounded (kWaitLimitNs); on timeout the CTA records
 // kStatusTimeout, drains its own copies and MMAs (again bounded), frees TMEM
 // and returns.
 #include <cuda.h>
 
+#include "sketch_pack.cuh"
 #include "spid_internal.cuh"
 #include "tcgen05_ptx.cuh"
 
@@ -29,22 +33,27 @@ namespace {
 
 using namespace tc;
 
-constexpr int kTcThreads = 192;
+// Omega generation is a chain of Philox rounds and MUFU calls; two generator
+// warps per SM sub-partition keep it ahead of HBM even at l = 42.
+constexpr int kGenWarps = 8;
+constexpr int kGenThreads = 32 * kGenWarps;
+constexpr int kTcThreads = 64 + kGenThreads;
 constexpr int kTileCols = 128;                 // MMA M
 constexpr int kTileBytes = kTileCols * 128;    // 128 columns x 32 FP32 rows
+constexpr int kSliceBytes = kSliceCols * 128;  // one TMA box: 64 columns x 32 rows
 constexpr int kMaxStages = 8;
 
 struct TcArgs {
   SketchArgs s;
   int32_t stages;      // pipeline depth
-  int32_t max_tiles;   // 128-column tiles per column group (<= 4)
+  int32_t max_tiles;   // MMA tiles per pack (<= 4)
   int32_t acc_stride;  // TMEM columns per tile accumulator (multiple of 32 >= l_pad)
   int32_t tmem_cols;   // power of two >= max_tiles * acc_stride
 };
 
 __global__ void __launch_bounds__(kTcThreads, 1) sketch_tf32_kernel(const TcArgs args) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ int epi_last;
+  __shared__ int epi_last[kPackSlices];
   // 1024-byte alignment for the 128-byte swizzle atoms
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -57,9 +66,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) sketch_tf32_kernel(const TcArgs
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_O + (size_t)S * omega_bytes);
   uint64_t* full = bars;                       // [S] TMA bytes landed
   uint64_t* empty = bars + kMaxStages;         // [S] MMAs that read the stage completed
-  uint64_t* ofull = bars + 2 * kMaxStages;     // [S] Omega written (128 arrivals)
+  uint64_t* ofull = bars + 2 * kMaxStages;     // [S] Omega written (kGenThreads arrivals)
   uint64_t* accum = bars + 3 * kMaxStages;     // accumulators of a segment complete
-  uint64_t* drain = bars + 3 * kMaxStages + 1; // abort path: every issued MMA complete
+  uint64_t* drain = bars + 3 * kMaxStages + 1; // every issued MMA complete
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kMaxStages + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -72,7 +81,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sketch_tf32_kernel(const TcArgs
     for (int s = 0; s < S; ++s) {
       mbar_init(smem_addr(&full[s]), 1);
       mbar_init(smem_addr(&empty[s]), 1);
-      mbar_init(smem_addr(&ofull[s]), 128);
+      mbar_init(smem_addr(&ofull[s]), kGenThreads);
     }
     mbar_init(smem_addr(accum), 1);
     mbar_init(smem_addr(drain), 1);
@@ -98,19 +107,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) sketch_tf32_kernel(const TcArgs
       bool ok = true;
       const CUtensorMap* tmaps = static_cast<const CUtensorMap*>(a.tmaps);
       for (int si = seg0; si < seg1 && ok; ++si) {
-        const Segment seg = a.segs[si];
-        const Problem pb = a.probs[seg.prob];
-        const int nt = (pb.ncols + kTileCols - 1) / kTileCols;
-        const CUtensorMap* tm = tmaps + pb.sub;
-        for (int ch = seg.chunk0; ch < seg.chunk1; ++ch, ++it) {
+        const PackSegment sg = a.psegs[si];
+        const Pack pk = a.packs[sg.pack];
+        for (int ch = sg.chunk0; ch < sg.chunk1; ++ch, ++it) {
           const int st = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
           if (!mbar_wait(smem_addr(&empty[st]), ph ^ 1u, abort_flag, a.status)) { ok = false; break; }
           const uint32_t fb = smem_addr(&full[st]);
-          mbar_arrive_expect_tx(fb, (uint32_t)(nt * kTileBytes));
-          for (int t = 0; t < nt; ++t)
-            tma_load_2d(smem_addr(smem_A + ((size_t)st * args.max_tiles + t) * kTileBytes), tm,
-                        ch * kChunkRows, pb.col0 + t * kTileCols, fb);
+          mbar_arrive_expect_tx(fb, (uint32_t)(pk.nslices * kSliceBytes));
+          unsigned char* dst = smem_A + (size_t)st * args.max_tiles * kTileBytes;
+          for (int h = 0; h < pk.nslices; ++h) {
+            const Slice sl = a.slices[pk.slice0 + h];
+            tma_load_2d(smem_addr(dst + h * kSliceBytes), tmaps + sl.sub, ch * kChunkRows,
+                        sl.col0, fb);
+          }
         }
       }
       // Drain: every issued stage's bytes must have landed before the CTA exits.
@@ -125,10 +135,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) sketch_tf32_kernel(const TcArgs
       bool ok = true, issued = false;
       const uint32_t idesc = tf32_idesc(kTileCols, l_pad);
       for (int si = seg0; si < seg1 && ok; ++si) {
-        const Segment seg = a.segs[si];
-        const Problem pb = a.probs[seg.prob];
-        const int nt = (pb.ncols + kTileCols - 1) / kTileCols;
-        for (int ch = seg.chunk0; ch < seg.chunk1; ++ch, ++it) {
+        const PackSegment sg = a.psegs[si];
+        const int nt = (a.packs[sg.pack].nslices + 1) / 2;
+        for (int ch = sg.chunk0; ch < sg.chunk1; ++ch, ++it) {
           const int st = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
           if (!mbar_wait(smem_addr(&full[st]), ph, abort_flag, a.status)) { ok = false; break; }
@@ -142,11 +151,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) sketch_tf32_kernel(const TcArgs
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)   // K = 8 TF32 (32 bytes) per MMA
               umma_tf32(tmem_base + (uint32_t)(t * args.acc_stride), ad + 2 * kk, bd + 2 * kk,
-                        idesc, (ch > seg.chunk0 || kk > 0) ? 1u : 0u);
+                        idesc, (ch > sg.chunk0 || kk > 0) ? 1u : 0u);
           }
           issued = true;
           umma_commit(smem_addr(&empty[st]));
-          if (ch == seg.chunk1 - 1) umma_commit(smem_addr(accum));
+          if (ch == sg.chunk1 - 1) umma_commit(smem_addr(accum));
         }
       }
       // Every issued MMA must be complete before TMEM is released.
@@ -157,68 +166,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) sketch_tf32_kernel(const TcArgs
     }
   } else {
     // ------------------------------------------------ Omega generators + epilogue
-    const int gtid = threadIdx.x - 64;            // 0..127
+    const int gtid = threadIdx.x - 64;            // 0 .. kGenThreads-1
     const int quad = warp & 3;                    // TMEM lane quadrant of this warp
+    const int part = (warp - 2) / 4;              // warps sharing a quadrant split the columns
     const uint2 key = philox_key(a.seed);
     const int groups = l_pad / 4;
-    float* partial = static_cast<float*>(a.partial);
     int it = 0, segi = 0;
     bool ok = true;
-    auto epilogue = [&](const Segment& seg, int seg_index) -> bool {
+    auto epilogue = [&](int si_done, int seg_index) -> bool {
       if (!mbar_wait(smem_addr(accum), (uint32_t)seg_index & 1u, abort_flag, a.status))
         return false;
       tc_fence_after();
-      const Problem pb = a.probs[seg.prob];
-      const int nt = (pb.ncols + kTileCols - 1) / kTileCols;
-      float* out = partial + a.slot_off[seg.slot];
-      for (int t = 0; t < nt; ++t) {
-        const int j = t * kTileCols + quad * 32 + lane;
-        for (int c = 0; c < l_pad; c += 16) {
-          uint32_t r[16];
-          __syncwarp();
-          tmem_ld16(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(t * args.acc_stride + c),
-                    r);
-          tmem_ld_wait();
-          if (j < pb.ncols) {
-            float4* dst = reinterpret_cast<float4*>(out + (int64_t)j * l_pad + c);
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                                   __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
-          }
-        }
-      }
-      tc_fence_before();
-      // the CTA that completes a problem sums its slots in schedule order
-      __threadfence();
-      named_bar_sync(1, 128);
-      if (gtid == 0) {
-        const int nslots = a.pslot_ptr[seg.prob + 1] - a.pslot_ptr[seg.prob];
-        epi_last = (atomicAdd(&a.prob_cnt[seg.prob], 1) == nslots - 1);
-      }
-      named_bar_sync(1, 128);
-      if (epi_last) {
-        __threadfence();
-        reduce_problem_slots<float>(a, seg.prob, gtid, 128);
-        if (gtid == 0) a.prob_cnt[seg.prob] = 0;
-      }
-      named_bar_sync(1, 128);   // epi_last is reused by the next segment
+      pack_epilogue(a, a.psegs[si_done], tmem_base, args.acc_stride, quad, part, kGenWarps / 4,
+                    lane, gtid, kGenThreads, epi_last, 1);
       return true;
     };
     for (int si = seg0; si < seg1 && ok; ++si, ++segi) {
-      const Segment seg = a.segs[si];
-      if (si > seg0 && !epilogue(a.segs[si - 1], segi - 1)) { ok = false; break; }
-      const Problem pb = a.probs[seg.prob];
-      for (int ch = seg.chunk0; ch < seg.chunk1; ++ch, ++it) {
+      const PackSegment sg = a.psegs[si];
+      if (si > seg0 && !epilogue(si - 1, segi - 1)) { ok = false; break; }
+      const int m = a.packs[sg.pack].m;
+      for (int ch = sg.chunk0; ch < sg.chunk1; ++ch, ++it) {
         const int st = it % S;
         const uint32_t ph = (uint32_t)(it / S) & 1u;
         if (!mbar_wait(smem_addr(&empty[st]), ph ^ 1u, abort_flag, a.status)) { ok = false; break; }
         unsigned char* ob = smem_O + (size_t)st * omega_bytes;
         const int r0 = ch * kChunkRows;
-        for (int task = gtid; task < kChunkRows * groups; task += 128) {
+        for (int task = gtid; task < kChunkRows * groups; task += kGenThreads) {
           const int k = task % kChunkRows, g = task / kChunkRows;
           float w[4] = {0.f, 0.f, 0.f, 0.f};
-          if (4 * g < a.l && r0 + k < pb.m) {
+          if (4 * g < a.l && r0 + k < m) {
             omega_group<float>(key, (uint32_t)(r0 + k), (uint32_t)g, w);
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -236,7 +212,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sketch_tf32_kernel(const TcArgs
         mbar_arrive(smem_addr(&ofull[st]));
       }
     }
-    if (ok && seg1 > seg0) epilogue(a.segs[seg1 - 1], segi - 1);
+    if (ok && seg1 > seg0) epilogue(seg1 - 1, segi - 1);
   }
 
   tc_fence_before();
@@ -252,7 +228,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sketch_tf32_kernel(const TcArgs
 
 }  // namespace
 
-int sketch_tc_group_cols() { return 4 * kTileCols; }
+int sketch_tc_group_cols() { return kPackSlices * kSliceCols; }
 
 // Dynamic shared memory the TF32 sketch needs for a pipeline of `stages`.
 size_t sketch_tc_smem_bytes(int stages, int max_tiles, int l_pad) {

@@ -52,6 +52,9 @@ struct Schedule {
   const int32_t* pslot_ptr = nullptr;
   const int32_t* pslots = nullptr;
   int* prob_cnt = nullptr;   // per-problem completed-segment counters
+  const Slice* slices = nullptr;
+  const Pack* packs = nullptr;
+  const PackSegment* psegs = nullptr;
   int64_t partial_elems = 0;
 };
 
@@ -140,12 +143,26 @@ struct spid_plan_s {
 namespace {
 
 // Build the sketch schedule for window columns [col0, col0 + ncols).
+//
+// Problems: every subdomain restricted to groups of up to group_cols()
+// columns of the range.  Work units: a problem (CUDA-core kernels) or a pack
+// of problems with equal m cut into 64-column slices (tensor-core kernels,
+// which regenerate Omega once per chunk for the whole pack).  The chunks of all
+// units are partitioned over the CTAs, balanced by bytes; consecutive chunks of
+// one unit on one CTA form a segment, which writes one partial slot per
+// problem it touches.
 spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   const int CG = P->group_cols();
   const int G = P->sketch_grid();
+  const bool tc = P->tensor_core();
+  // ---- problems, subdomain by subdomain; with packing, ordered by m
+  std::vector<int> subs(P->S);
+  for (int s = 0; s < P->S; ++s) subs[s] = s;
+  if (tc && !P->per_sub())
+    std::stable_sort(subs.begin(), subs.end(), [&](int x, int y) { return P->m[x] < P->m[y]; });
   std::vector<Problem> probs;
-  std::vector<int> prob_sub_first(P->S + 1, 0);
-  for (int s = 0; s < P->S; ++s) {
+  std::vector<int> prob_sub_first(P->S + 1, 0);   // per-subdomain mode: problems of s
+  for (int s : subs) {
     prob_sub_first[s] = (int)probs.size();
     const int end = std::min<int64_t>((int64_t)col0 + ncols, P->n[s]);
     for (int c = col0; c < end; c += CG) {
@@ -159,57 +176,94 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
       probs.push_back(pb);
     }
   }
-  prob_sub_first[P->S] = (int)probs.size();
+  std::vector<int> prob_sub_last(P->S, 0);
+  for (int s : subs) {
+    const int end = std::min<int64_t>((int64_t)col0 + ncols, P->n[s]);
+    prob_sub_last[s] = prob_sub_first[s] + (end > col0 ? (end - col0 + CG - 1) / CG : 0);
+  }
+  // ---- work units
+  struct Unit { int nch; double w; int prob0; int nprob; int pack; };
+  std::vector<Unit> units;
+  std::vector<Slice> slices;
+  std::vector<Pack> packs;
+  auto make_units = [&](int p0, int p1) {
+    if (!tc) {
+      for (int p = p0; p < p1; ++p)
+        units.push_back({(probs[p].m + kChunkRows - 1) / kChunkRows, (double)probs[p].ncols, p, 1, -1});
+      return;
+    }
+    int p = p0;
+    while (p < p1) {
+      Pack pk;
+      pk.slice0 = (int)slices.size();
+      pk.nslices = 0;
+      pk.m = probs[p].m;
+      pk.prob0 = p;
+      pk.nprob = 0;
+      int cols = 0;
+      while (p < p1 && probs[p].m == pk.m &&
+             pk.nslices + (probs[p].ncols + kSliceCols - 1) / kSliceCols <= kPackSlices) {
+        for (int c = 0; c < probs[p].ncols; c += kSliceCols) {
+          Slice sl;
+          sl.prob = p;
+          sl.sub = probs[p].sub;
+          sl.col0 = probs[p].col0 + c;
+          sl.ncols = std::min(kSliceCols, probs[p].ncols - c);
+          sl.out_col = c;
+          sl.member = pk.nprob;
+          slices.push_back(sl);
+          ++pk.nslices;
+        }
+        cols += probs[p].ncols;
+        ++pk.nprob;
+        ++p;
+      }
+      units.push_back({(pk.m + kChunkRows - 1) / kChunkRows, (double)cols, pk.prob0, pk.nprob,
+                       (int)packs.size()});
+      packs.push_back(pk);
+    }
+  };
   std::vector<Segment> segs;
+  std::vector<PackSegment> psegs;
   std::vector<int32_t> seg_ptr;
   std::vector<int64_t> slot_off;
   int64_t slot_total = 0;
   std::vector<std::vector<int32_t>> slots_of_prob(probs.size());
-  int max_tiles = 1;
-  for (const Problem& pb : probs) max_tiles = std::max(max_tiles, (pb.ncols + 127) / 128);
-
-  // Partition the chunk sequence of problems [p0, p1) over G CTAs, balanced by
-  // bytes (chunk weight = columns of its problem).
-  // Chunk i of the concatenated sequence goes to the CTA whose equal share of
-  // the total weight contains the chunk's midpoint; consecutive chunks of one
-  // problem on one CTA form a segment.  Appends G + 1 entries to seg_ptr.
-  auto partition = [&](int p0, int p1) {
+  // chunk i of the units [u0, u1) goes to the CTA whose equal share of the
+  // total weight contains the chunk's midpoint; appends G + 1 entries to seg_ptr
+  auto partition = [&](int u0, int u1) {
     double W = 0.0;
-    for (int p = p0; p < p1; ++p)
-      W += (double)((probs[p].m + kChunkRows - 1) / kChunkRows) * probs[p].ncols;
-    std::vector<std::vector<Segment>> per_cta(G);
+    for (int u = u0; u < u1; ++u) W += units[u].nch * units[u].w;
+    struct Run { int unit, chunk0, chunk1; };
+    std::vector<std::vector<Run>> per_cta(G);
     double acc = 0.0;
-    for (int p = p0; p < p1; ++p) {
-      const int nch = (probs[p].m + kChunkRows - 1) / kChunkRows;
-      const double w = probs[p].ncols;
-      for (int ch = 0; ch < nch; ++ch) {
-        int c = (int)((acc + 0.5 * w) * G / W);
+    for (int u = u0; u < u1; ++u) {
+      const double w = units[u].w;
+      for (int ch = 0; ch < units[u].nch; ++ch) {
+        int c = W > 0 ? (int)((acc + 0.5 * w) * G / W) : 0;
         c = std::min(std::max(c, 0), G - 1);
-        std::vector<Segment>& v = per_cta[c];
-        if (!v.empty() && v.back().prob == p && v.back().chunk1 == ch) {
-          v.back().chunk1 = ch + 1;
-        } else {
-          Segment sg;
-          sg.prob = p;
-          sg.chunk0 = ch;
-          sg.chunk1 = ch + 1;
-          sg.slot = -1;
-          v.push_back(sg);
-        }
+        std::vector<Run>& v = per_cta[c];
+        if (!v.empty() && v.back().unit == u && v.back().chunk1 == ch) v.back().chunk1 = ch + 1;
+        else v.push_back({u, ch, ch + 1});
         acc += w;
       }
     }
     for (int c = 0; c < G; ++c) {
-      seg_ptr.push_back((int32_t)segs.size());
-      for (Segment sg : per_cta[c]) {
-        sg.slot = (int32_t)slot_off.size();
-        slot_off.push_back(slot_total);
-        slot_total += (int64_t)probs[sg.prob].ncols * P->l_pad;
-        slots_of_prob[sg.prob].push_back(sg.slot);
-        segs.push_back(sg);
+      seg_ptr.push_back((int32_t)(tc ? psegs.size() : segs.size()));
+      for (const Run& r : per_cta[c]) {
+        const Unit& un = units[r.unit];
+        const int32_t first_slot = (int32_t)slot_off.size();
+        for (int q = 0; q < un.nprob; ++q) {
+          const int p = un.prob0 + q;
+          slots_of_prob[p].push_back((int32_t)slot_off.size());
+          slot_off.push_back(slot_total);
+          slot_total += (int64_t)probs[p].ncols * P->l_pad;
+        }
+        if (tc) psegs.push_back({un.pack, r.chunk0, r.chunk1, first_slot});
+        else segs.push_back({un.prob0, r.chunk0, r.chunk1, first_slot});
       }
     }
-    seg_ptr.push_back((int32_t)segs.size());
+    seg_ptr.push_back((int32_t)(tc ? psegs.size() : segs.size()));
   };
   sc.cta_base_of_sub.assign(P->S, 0);
   sc.prob_base_of_sub.assign(P->S, 0);
@@ -219,11 +273,14 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
     for (int s = 0; s < P->S; ++s) {
       sc.cta_base_of_sub[s] = (int)seg_ptr.size();
       sc.prob_base_of_sub[s] = prob_sub_first[s];
-      sc.nprob_of_sub[s] = prob_sub_first[s + 1] - prob_sub_first[s];
-      partition(prob_sub_first[s], prob_sub_first[s + 1]);
+      sc.nprob_of_sub[s] = prob_sub_last[s] - prob_sub_first[s];
+      const int u0 = (int)units.size();
+      make_units(prob_sub_first[s], prob_sub_last[s]);
+      partition(u0, (int)units.size());
     }
   } else {
-    partition(0, (int)probs.size());
+    make_units(0, (int)probs.size());
+    partition(0, (int)units.size());
   }
   std::vector<int32_t> pslot_ptr(probs.size() + 1, 0), pslots;
   for (size_t p = 0; p < probs.size(); ++p) {
@@ -231,57 +288,57 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
     for (int32_t q : slots_of_prob[p]) pslots.push_back(q);
   }
   pslot_ptr[probs.size()] = (int32_t)pslots.size();
+  int max_slices = 1;
+  for (const Pack& pk : packs) max_slices = std::max(max_slices, pk.nslices);
 
   sc.grid = G;
   sc.nprob = (int)probs.size();
-  sc.max_tiles = max_tiles;
+  sc.max_tiles = tc ? (max_slices + 1) / 2 : 1;
   sc.partial_elems = slot_total;
   if (slot_total > P->partial_cap)
     return fail(SPID_ERR_INVALID_ARG, "sketch schedule exceeds the partial workspace");
   // one device block for all tables (16-byte aligned pieces)
-  auto al = [](size_t b) { return (b + 15) / 16 * 16; };
-  const size_t b_probs = al(sizeof(Problem) * std::max<size_t>(probs.size(), 1));
-  const size_t b_segs = al(sizeof(Segment) * std::max<size_t>(segs.size(), 1));
-  const size_t b_segp = al(sizeof(int32_t) * seg_ptr.size());
-  const size_t b_slot = al(sizeof(int64_t) * std::max<size_t>(slot_off.size(), 1));
-  const size_t b_pptr = al(sizeof(int32_t) * pslot_ptr.size());
-  const size_t b_psl = al(sizeof(int32_t) * std::max<size_t>(pslots.size(), 1));
-  const size_t b_cnt = al(sizeof(int) * std::max<size_t>(probs.size(), 1));
-  const size_t total = b_probs + b_segs + b_segp + b_slot + b_pptr + b_psl + b_cnt;
-  std::vector<unsigned char> host(total, 0);
-  size_t o = 0;
-  auto put = [&](const void* src, size_t bytes, size_t span) {
-    if (bytes) std::memcpy(host.data() + o, src, bytes);
-    size_t at = o;
-    o += span;
-    return at;
+  std::vector<unsigned char> host;
+  std::vector<size_t> at;
+  auto put = [&](const void* src, size_t bytes) {
+    at.push_back(host.size());
+    const size_t span = (std::max<size_t>(bytes, 16) + 15) / 16 * 16;
+    host.resize(host.size() + span, 0);
+    if (bytes && src) std::memcpy(host.data() + at.back(), src, bytes);
   };
-  const size_t o_probs = put(probs.data(), sizeof(Problem) * probs.size(), b_probs);
-  const size_t o_segs = put(segs.data(), sizeof(Segment) * segs.size(), b_segs);
-  const size_t o_segp = put(seg_ptr.data(), sizeof(int32_t) * seg_ptr.size(), b_segp);
-  const size_t o_slot = put(slot_off.data(), sizeof(int64_t) * slot_off.size(), b_slot);
-  const size_t o_pptr = put(pslot_ptr.data(), sizeof(int32_t) * pslot_ptr.size(), b_pptr);
-  const size_t o_psl = put(pslots.data(), sizeof(int32_t) * pslots.size(), b_psl);
-  const size_t o_cnt = put(nullptr, 0, b_cnt);   // problem counters start at zero
-  SPID_CUDA(P->alloc(&sc.dev, total));
-  SPID_CUDA(cudaMemcpy(sc.dev, host.data(), total, cudaMemcpyHostToDevice));
+  put(probs.data(), sizeof(Problem) * probs.size());                 // 0
+  put(segs.data(), sizeof(Segment) * segs.size());                   // 1
+  put(seg_ptr.data(), sizeof(int32_t) * seg_ptr.size());             // 2
+  put(slot_off.data(), sizeof(int64_t) * slot_off.size());           // 3
+  put(pslot_ptr.data(), sizeof(int32_t) * pslot_ptr.size());         // 4
+  put(pslots.data(), sizeof(int32_t) * pslots.size());               // 5
+  put(nullptr, sizeof(int) * probs.size());                          // 6: counters start at zero
+  put(slices.data(), sizeof(Slice) * slices.size());                 // 7
+  put(packs.data(), sizeof(Pack) * packs.size());                    // 8
+  put(psegs.data(), sizeof(PackSegment) * psegs.size());             // 9
+  SPID_CUDA(P->alloc(&sc.dev, host.size()));
+  SPID_CUDA(cudaMemcpy(sc.dev, host.data(), host.size(), cudaMemcpyHostToDevice));
   unsigned char* d = static_cast<unsigned char*>(sc.dev);
-  sc.probs = reinterpret_cast<const Problem*>(d + o_probs);
-  sc.segs = reinterpret_cast<const Segment*>(d + o_segs);
-  sc.seg_ptr = reinterpret_cast<const int32_t*>(d + o_segp);
-  sc.slot_off = reinterpret_cast<const int64_t*>(d + o_slot);
-  sc.pslot_ptr = reinterpret_cast<const int32_t*>(d + o_pptr);
-  sc.pslots = reinterpret_cast<const int32_t*>(d + o_psl);
-  sc.prob_cnt = reinterpret_cast<int*>(d + o_cnt);
-  if (P->tensor_core()) {
+  sc.probs = reinterpret_cast<const Problem*>(d + at[0]);
+  sc.segs = reinterpret_cast<const Segment*>(d + at[1]);
+  sc.seg_ptr = reinterpret_cast<const int32_t*>(d + at[2]);
+  sc.slot_off = reinterpret_cast<const int64_t*>(d + at[3]);
+  sc.pslot_ptr = reinterpret_cast<const int32_t*>(d + at[4]);
+  sc.pslots = reinterpret_cast<const int32_t*>(d + at[5]);
+  sc.prob_cnt = reinterpret_cast<int*>(d + at[6]);
+  sc.slices = reinterpret_cast<const Slice*>(d + at[7]);
+  sc.packs = reinterpret_cast<const Pack*>(d + at[8]);
+  sc.psegs = reinterpret_cast<const PackSegment*>(d + at[9]);
+  if (tc) {
     const bool split = P->prec == SPID_PREC_BF16X3;
-    const size_t fixed = P->bf16() ? sketch_bf16_smem_bytes(0, max_tiles, P->l_pad, split)
-                                   : sketch_tc_smem_bytes(0, max_tiles, P->l_pad);
-    const size_t per_stage = (P->bf16() ? sketch_bf16_smem_bytes(1, max_tiles, P->l_pad, split)
-                                        : sketch_tc_smem_bytes(1, max_tiles, P->l_pad)) - fixed;
+    const int mt = sc.max_tiles;
+    const size_t fixed = P->bf16() ? sketch_bf16_smem_bytes(0, mt, P->l_pad, split)
+                                   : sketch_tc_smem_bytes(0, mt, P->l_pad);
+    const size_t per_stage = (P->bf16() ? sketch_bf16_smem_bytes(1, mt, P->l_pad, split)
+                                        : sketch_tc_smem_bytes(1, mt, P->l_pad)) - fixed;
     int stages = (int)((P->smem_optin - fixed) / per_stage);
     stages = std::min(stages, sketch_tc_max_stages());
-    if (stages < 2) return fail(SPID_ERR_UNSUPPORTED, "not enough shared memory for the TF32 pipeline");
+    if (stages < 2) return fail(SPID_ERR_UNSUPPORTED, "not enough shared memory for the sketch pipeline");
     sc.stages = stages;
   }
   return SPID_OK;
@@ -327,7 +384,7 @@ spid_status bind_window(spid_plan_t P, const void* window, cudaStream_t st) {
     void* base = const_cast<char*>(static_cast<const char*>(window)) + P->off[s] * P->esz;
     cuuint64_t dims[2] = {(cuuint64_t)P->m[s], (cuuint64_t)P->n[s]};
     cuuint64_t strides[1] = {(cuuint64_t)P->ld[s] * P->esz};
-    cuuint32_t box[2] = {32, 128};
+    cuuint32_t box[2] = {32, (cuuint32_t)kSliceCols};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(&maps[s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -606,6 +663,9 @@ spid_status spid_sketch(spid_plan_t P, const void* window, int32_t col0, int32_t
   a.prob_cnt = sc->prob_cnt;
   a.Y = P->d_Y;
   a.yoff = P->d_yoff;
+  a.slices = sc->slices;
+  a.packs = sc->packs;
+  a.psegs = sc->psegs;
   const int nlaunch = P->per_sub() ? P->S : 1;
   for (int q = 0; q < nlaunch; ++q) {
     a.cta_base = P->per_sub() ? sc->cta_base_of_sub[q] : 0;

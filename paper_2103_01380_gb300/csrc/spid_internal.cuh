@@ -40,6 +40,39 @@ struct Segment {
   int32_t slot;
 };
 
+// Tensor-core packing: Omega does not depend on the subdomain, so one chunk of
+// rows can serve several subdomains at once.  A slice is up to 64 columns of
+// one problem (one 8 KB TMA box); a pack is up to 8 slices of problems with
+// the same m, streamed together as 4 MMA tiles of 128 rows (two slices each).
+constexpr int kSliceCols = 64;
+constexpr int kPackSlices = 8;
+
+struct Slice {
+  int32_t prob;      // problem index (the fold unit)
+  int32_t sub;       // subdomain (tensor map)
+  int32_t col0;      // first window column of the slice
+  int32_t ncols;     // <= kSliceCols
+  int32_t out_col;   // column of the slice inside its problem's partial slot
+  int32_t member;    // index of its problem among the pack's problems
+};
+
+struct Pack {
+  int32_t slice0;    // first slice
+  int32_t nslices;   // 1 .. kPackSlices
+  int32_t m;         // rows of every member
+  int32_t prob0;     // first member problem (members are consecutive problems)
+  int32_t nprob;     // number of member problems
+};
+
+// A contiguous range of row chunks of one pack, processed by one CTA; member
+// problem q of the pack writes its partial to slot slot0 + q.
+struct PackSegment {
+  int32_t pack;
+  int32_t chunk0;
+  int32_t chunk1;
+  int32_t slot0;
+};
+
 // Sketch schedule arguments (both sketch kernels).
 struct SketchArgs {
   const Problem* probs;
@@ -61,6 +94,10 @@ struct SketchArgs {
   int* prob_cnt;              // [problems] completed-segment counters (zero between calls)
   void* Y;                    // stored sketches, Y_s at yoff[s], [n_s][l_pad]
   const int64_t* yoff;
+  // tensor-core schedule: CTA c owns psegs[seg_ptr[c] .. seg_ptr[c+1])
+  const Slice* slices;
+  const Pack* packs;
+  const PackSegment* psegs;
 };
 
 template <typename T> struct Vec16;   // 16-byte vector of T

@@ -104,7 +104,10 @@ def test_insitu_boxes_streamed_snapshot_major():
     g = run_gpu(win, "tf32", 30, p=10, batches=64, reconstruct=False)
     assert g["status"] == 0
     one = run_gpu(win, "tf32", 30, p=10, reconstruct=False)
+    # the two schedules cut the 5120 row chunks into different partial sums:
+    # the sketches agree up to FP32 re-association, about u sqrt(chunks)
+    chunks = -(-int(win.m[0]) // 32)
     for s in range(4):
-        assert rel_fro(g["Y"][s], one["Y"][s]) <= 1e-6
+        assert rel_fro(g["Y"][s], one["Y"][s]) <= 2 * 2.0**-24 * np.sqrt(chunks)
     check_sampled(win, g, "tf32", 30, 10, 0.0, samples=(2,), err_target=1e-3)
     assert np.sqrt(g["total"][0] / g["total"][1]) <= 1e-3
