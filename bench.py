@@ -38,11 +38,11 @@ WORKLOAD = ("TGV+Fourier 64^3 grid, 64 subdomains of 16^3 x 5 QoIs (m=20480), n=
 # (profiles/dram_traffic_tf32_tgv3d_64sub.md).  A figure is reported only while
 # the kernel's sources hash to the value they had when it was measured.
 MEASURED_TRAFFIC = {
-    "sketch": {"bytes": 2693607424 + 7129856,
-               "sources": ("sketch_tc.cu", "tcgen05_ptx.cuh", "spid_internal.cuh"),
-               "sha256_16": "ab4f1f584cc52fb7"},
-    "error": {"bytes": 2684970240 + 400640, "sources": ("error.cu", "spid_internal.cuh"),
-              "sha256_16": "d659a1baed82867a"},
+    "sketch": {"bytes": 2693808640 + 6736896,
+               "sources": ('sketch_tc.cu', 'sketch_pack.cuh', 'tcgen05_ptx.cuh', 'spid_internal.cuh'),
+               "sha256_16": "60212d7988fb91d5"},
+    "error": {"bytes": 2685110528 + 574720, "sources": ('error.cu', 'error_fold.cuh', 'spid_internal.cuh'),
+              "sha256_16": "453548979ca007ee"},
 }
 
 
@@ -285,12 +285,16 @@ def _run_spectrum(args, torch, inputs, spid):
     err = torch.zeros(2 * S, dtype=torch.float64, device="cuda")
     tot = torch.zeros(4, dtype=torch.float64, device="cuda")
     study = {}
-    for prec in ("tf32", "bf16x3", "bf16", "fp32"):
+    # "tf32_tensor_core_error": the same TF32 plan with the rank-k product of the
+    # error pass on the tensor cores
+    for label, prec, flags in (("tf32", "tf32", 0), ("bf16x3", "bf16x3", 0), ("bf16", "bf16", 0),
+                               ("fp32", "fp32", 0),
+                               ("tf32_tensor_core_error", "tf32", spid.FLAG_TC_ERROR)):
         plan = spid.Plan([m] * S, [n] * S, np.arange(S) * m * n, [m] * S, k_max=32, p=10,
-                         tol=1e-3, precision=prec, seed=0x5EED0003)
+                         tol=1e-3, precision=prec, seed=0x5EED0003, flags=flags)
         sk, fi, er = _stage_times(torch, plan, window, args.steps, args.warmup, err, tot,
                                   [(0, n)])
-        study[prec] = dict(value=nbytes / ((sk + fi + er) / 1e3) / 1e9,
+        study[label] = dict(value=nbytes / ((sk + fi + er) / 1e3) / 1e9,
                            sketch_gbs=nbytes / (sk / 1e3) / 1e9, finalize_ms=fi,
                            error_gbs=nbytes / (er / 1e3) / 1e9, **_summary(plan, tot))
         plan.close()
@@ -449,6 +453,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=64)
     ap.add_argument("--boxes", type=int, default=None,
                     help="first N boxes only (small profiling case; not the bench workload)")
+    ap.add_argument("--tc-error", action="store_true",
+                    help="error pass with the rank-k product on the tensor cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--workload", default="tgv3d64",
@@ -518,7 +524,7 @@ def main():
         er = [e[2].elapsed_time(e[3]) for e in ev]
         return total_ms, sk, fi, er
 
-    plan = make_plan(args.precision)
+    plan = make_plan(args.precision, flags=spid.FLAG_TC_ERROR if args.tc_error else 0)
     with ClockSampler(local) as clk:
         total_ms, sk, fi, er = timed(plan, args.steps, args.warmup)
     clocks = clk.summary()
@@ -607,6 +613,9 @@ def main():
             "config": {"workload": WORKLOAD if args.boxes is None else
                        f"first {args.boxes} boxes of: " + WORKLOAD, "precision": args.precision,
                        "subdomains_per_gpu": win.num_sub, "bytes_per_step_per_gpu": nbytes,
+                       "error_pass": "tensor-core (3xTF32)" if (args.tc_error and
+                                                                args.precision != "fp32")
+                       else "cuda-core",
                        "l2": "inputs (2.68 GB) larger than L2; no flush"},
             "stages_ms": {"sketch": sk_ms, "finalize": fi_ms, "error": er_ms},
             "sketch_gbs": nbytes / (sk_ms / 1e3) / 1e9,

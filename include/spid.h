@@ -80,6 +80,9 @@ typedef enum {
 
 /* Plain (unbatched) form: one kernel launch per subdomain per stage. */
 #define SPID_FLAG_PER_SUBDOMAIN 1u
+/* Error pass / reconstruction with the rank-k product on the tensor cores
+ * (TF32, BF16 and 3xBF16 plans, batched, k_max <= 32; ignored otherwise). */
+#define SPID_FLAG_TC_ERROR 2u
 
 typedef struct {
   int32_t num_sub;        /* number of subdomains S >= 1 */
@@ -123,10 +126,11 @@ spid_status spid_sketch(spid_plan_t plan, const void* window, int32_t col0, int3
 spid_status spid_reset(spid_plan_t plan, spid_stream_t stream);
 
 /* Finalize (steps a3-a5): batched Householder QR with column pivoting of
- * every Y_s (FP64 pivot norms, ties to the lowest column index), the rank
+ * every Y_s (pivot norms with FP64-class accuracy -- double-float pairs in
+ * FP32 modes, FP64 in FP64 mode -- ties to the lowest column index), the rank
  * decision (fixed k_max or adaptive tol, then the guard |R_jj| > 2 u |R_00|
- * with u the unit roundoff of the sketch arithmetic), the FP64
- * back-substitution T = R11^-1 R12 and C with C(:, J) = I exactly. */
+ * with u the unit roundoff of the sketch arithmetic), the back-substitution
+ * T = R11^-1 R12 with FP64-class accuracy and C with C(:, J) = I exactly. */
 spid_status spid_finalize(spid_plan_t plan, spid_stream_t stream);
 
 /* Relative Frobenius error (Section 5.1; step a6): for every subdomain,
@@ -135,6 +139,10 @@ spid_status spid_finalize(spid_plan_t plan, spid_stream_t stream);
  * {sum e2, sum a2, sum m_s n_s, sum k_s (m_s + n_s)}, so the global relative
  * error is sqrt(total[0] / total[1]) and the compression factor (Section 2,
  * Eq. for CF, aggregated over subdomains) is total[2] / total[3].
+ * A_hat is formed in FP32 on the CUDA cores (FP64 for FP64 plans), or, with
+ * SPID_FLAG_TC_ERROR on a batched TF32/BF16/3xBF16 plan with k_max <= 32, on
+ * the tensor cores as a three-term TF32 split product (about 2^-21 of
+ * |A(:,J)| |C| per entry).
  * err_dev may be NULL.  Requires spid_finalize. */
 spid_status spid_error(spid_plan_t plan, const void* window, double* err_dev, double* total_dev,
                        spid_stream_t stream);

@@ -18,6 +18,7 @@
 // order, and the last subdomain to finish sums the window totals; every
 // counter is reset by the CTA that completes it, so results are deterministic
 // and the plan is ready for the next call.
+#include "error_fold.cuh"
 #include "spid_internal.cuh"
 
 namespace spid {
@@ -173,49 +174,7 @@ __global__ void __launch_bounds__(256) error_kernel(ErrArgs a) {
   }
   __syncthreads();
   if (!last_sub || warp != 0) return;
-  // ---- this CTA completed subdomain s: fixed-order sum of its unit partials
-  __threadfence();
-  const int u0 = a.unit_ptr[s], u1 = a.unit_ptr[s + 1];
-  double es = 0.0, as = 0.0;
-  for (int q = u0 + lane; q < u1; q += 32) {
-    es += __ldcg(a.part + 2 * (int64_t)q);
-    as += __ldcg(a.part + 2 * (int64_t)q + 1);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    es += __shfl_xor_sync(0xffffffffu, es, o);
-    as += __shfl_xor_sync(0xffffffffu, as, o);
-  }
-  int last_all = 0;
-  if (lane == 0) {
-    a.sub_err[2 * s] = es;
-    a.sub_err[2 * s + 1] = as;
-    if (a.err) { a.err[2 * s] = es; a.err[2 * s + 1] = as; }
-    a.sub_cnt[s] = 0;
-    __threadfence();
-    last_all = (atomicAdd(a.all_cnt, 1) == a.S - 1);
-  }
-  last_all = __shfl_sync(0xffffffffu, last_all, 0);
-  if (!last_all) return;
-  // ---- last subdomain of the window: fixed-order window totals
-  __threadfence();
-  double te = 0.0, ta = 0.0, mn = 0.0, kd = 0.0;
-  for (int q = lane; q < a.S; q += 32) {
-    te += __ldcg(a.sub_err + 2 * (int64_t)q);
-    ta += __ldcg(a.sub_err + 2 * (int64_t)q + 1);
-    const double mq = (double)a.m[q], nq = (double)a.n[q];
-    mn += mq * nq;
-    kd += (double)a.k[q] * (mq + nq);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    te += __shfl_xor_sync(0xffffffffu, te, o);
-    ta += __shfl_xor_sync(0xffffffffu, ta, o);
-    mn += __shfl_xor_sync(0xffffffffu, mn, o);
-    kd += __shfl_xor_sync(0xffffffffu, kd, o);
-  }
-  if (lane == 0) {
-    if (a.total) { a.total[0] = te; a.total[1] = ta; a.total[2] = mn; a.total[3] = kd; }
-    *a.all_cnt = 0;
-  }
+  error_fold_subdomain(a, s, lane);
 }
 
 }  // namespace

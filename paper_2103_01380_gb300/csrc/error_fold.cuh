@@ -1,0 +1,61 @@
+// error_fold.cuh -- the deterministic end of both error passes (Section 5.1
+// relative Frobenius error, Section 2 compression-factor sums): once the last
+// work unit of subdomain s has stored its {e2, a2} partial, one warp sums the
+// subdomain's partials in unit order, and the last subdomain to finish sums
+// the window totals {sum e2, sum a2, sum m n, sum k (m + n)} in subdomain
+// order.  Every counter is reset by the warp that completes it.
+#pragma once
+
+#include "spid_internal.cuh"
+
+namespace spid {
+
+// Called by the 32 lanes of one warp after a device-wide fence, by the CTA
+// whose unit completed subdomain s (its atomic on sub_cnt[s] returned the
+// last count).  Units of s are a.unit_ptr[s] .. a.unit_ptr[s + 1] of a.part.
+__device__ __forceinline__ void error_fold_subdomain(const ErrArgs& a, int s, int lane) {
+  __threadfence();
+  const int u0 = a.unit_ptr[s], u1 = a.unit_ptr[s + 1];
+  double es = 0.0, as = 0.0;
+  for (int q = u0 + lane; q < u1; q += 32) {
+    es += __ldcg(a.part + 2 * (int64_t)q);
+    as += __ldcg(a.part + 2 * (int64_t)q + 1);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    es += __shfl_xor_sync(0xffffffffu, es, o);
+    as += __shfl_xor_sync(0xffffffffu, as, o);
+  }
+  int last_all = 0;
+  if (lane == 0) {
+    a.sub_err[2 * s] = es;
+    a.sub_err[2 * s + 1] = as;
+    if (a.err) { a.err[2 * s] = es; a.err[2 * s + 1] = as; }
+    a.sub_cnt[s] = 0;
+    __threadfence();
+    last_all = (atomicAdd(a.all_cnt, 1) == a.S - 1);
+  }
+  last_all = __shfl_sync(0xffffffffu, last_all, 0);
+  if (!last_all) return;
+  // ---- last subdomain of the window: fixed-order window totals
+  __threadfence();
+  double te = 0.0, ta = 0.0, mn = 0.0, kd = 0.0;
+  for (int q = lane; q < a.S; q += 32) {
+    te += __ldcg(a.sub_err + 2 * (int64_t)q);
+    ta += __ldcg(a.sub_err + 2 * (int64_t)q + 1);
+    const double mq = (double)a.m[q], nq = (double)a.n[q];
+    mn += mq * nq;
+    kd += (double)a.k[q] * (mq + nq);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    te += __shfl_xor_sync(0xffffffffu, te, o);
+    ta += __shfl_xor_sync(0xffffffffu, ta, o);
+    mn += __shfl_xor_sync(0xffffffffu, mn, o);
+    kd += __shfl_xor_sync(0xffffffffu, kd, o);
+  }
+  if (lane == 0) {
+    if (a.total) { a.total[0] = te; a.total[1] = ta; a.total[2] = mn; a.total[3] = kd; }
+    *a.all_cnt = 0;
+  }
+}
+
+}  // namespace spid

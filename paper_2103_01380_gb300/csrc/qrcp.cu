@@ -18,8 +18,9 @@
 //     The argmax compares the (hi, lo) pairs exactly with integer redux.
 //   - adaptive stop: smallest k with sum of residual norms^2 <= tol^2 ||Y||_F^2;
 //   - rank guard: keep leading pivots with |R_jj| > 2 u |R_00|;
-//   - T = R11^-1 R12 by FP64 back-substitution, one thread per column, in
-//     place; C(:, J) = I exactly.
+//   - T = R11^-1 R12 by back-substitution with FP64-class accuracy (double-
+//     float on the FP32 pipe in FP32 modes, FP64 in FP64 mode), one thread per
+//     column, in place; C(:, J) = I exactly.
 #include "spid_internal.cuh"
 
 namespace spid {

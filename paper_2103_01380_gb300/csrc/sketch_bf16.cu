@@ -186,13 +186,15 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_bf16_kernel(const Bf16Args
     const int row = threadIdx.x - kConvBase;       // 0..127: row (window column) of the tile
     int it = 0;
     bool ok = true;
-    for (int si = seg0; si < seg1 && ok; ++si) {
+    // the converters share named barrier 2: uniform control flow, `ok` only
+    // switches off the work behind a wait that gave up
+    for (int si = seg0; si < seg1; ++si) {
       const PackSegment seg = a.psegs[si];
       const int nt = (a.packs[seg.pack].nslices + 1) / 2;
       for (int ch = seg.chunk0; ch < seg.chunk1; ++ch, ++it) {
         const int st = it % S;
         const uint32_t ph = (uint32_t)(it / S) & 1u;
-        if (!mbar_wait(smem_addr(&full[st]), ph, abort_flag, a.status)) { ok = false; break; }
+        if (ok) ok = mbar_wait(smem_addr(&full[st]), ph, abort_flag, a.status);
         for (int t = 0; t < nt; ++t) {
           unsigned char* tile = smem_A + ((size_t)st * args.max_tiles + t) * kTileBytes;
           // read this row's 32 FP32 values (128-byte swizzle) ...
@@ -200,10 +202,12 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_bf16_kernel(const Bf16Args
           const unsigned char* rowp = tile + (row >> 3) * 1024 + (row & 7) * 128;
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
-            const float4 v = *reinterpret_cast<const float4*>(rowp + ((c ^ (row & 7)) << 4));
+            const float4 v = ok ? *reinterpret_cast<const float4*>(rowp + ((c ^ (row & 7)) << 4))
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
             x[4 * c] = v.x; x[4 * c + 1] = v.y; x[4 * c + 2] = v.z; x[4 * c + 3] = v.w;
           }
           named_bar_sync(2, 128);   // every row read before any BF16 byte overwrites it
+          if (!ok) continue;
           // ... and write it back as BF16 (64-byte swizzle), hi tile then lo tile
           unsigned char* hrow = tile + (row >> 3) * 512 + (row & 7) * 64;
 #pragma unroll
@@ -225,6 +229,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_bf16_kernel(const Bf16Args
             if (SPLIT) *reinterpret_cast<uint4*>(hrow + kBf16TileBytes + off) = l;
           }
         }
+        if (!ok) continue;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(smem_addr(&cfull[st]));
       }
@@ -239,22 +244,23 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_bf16_kernel(const Bf16Args
     const int groups = l_pad / 4;
     int it = 0, segi = 0;
     bool ok = true;
-    auto epilogue = [&](int si_done, int seg_index) -> bool {
-      if (!mbar_wait(smem_addr(accum), (uint32_t)seg_index & 1u, abort_flag, a.status))
-        return false;
+    // uniform control flow across the group (named barrier 1), as in the TF32 kernel
+    auto epilogue = [&](int si_done, int seg_index) {
+      if (ok) ok = mbar_wait(smem_addr(accum), (uint32_t)seg_index & 1u, abort_flag, a.status);
+      ok = __all_sync(0xffffffffu, ok);
       tc_fence_after();
       pack_epilogue(a, a.psegs[si_done], tmem_base, args.acc_stride, quad, part, kParts, lane,
-                    gtid, kGenThreads, epi_last, 1);
-      return true;
+                    gtid, kGenThreads, epi_last, 1, ok);
     };
-    for (int si = seg0; si < seg1 && ok; ++si, ++segi) {
+    for (int si = seg0; si < seg1; ++si, ++segi) {
       const PackSegment seg = a.psegs[si];
-      if (si > seg0 && !epilogue(si - 1, segi - 1)) { ok = false; break; }
+      if (si > seg0) epilogue(si - 1, segi - 1);
       const Pack pb = a.packs[seg.pack];
       for (int ch = seg.chunk0; ch < seg.chunk1; ++ch, ++it) {
         const int st = it % S;
         const uint32_t ph = (uint32_t)(it / S) & 1u;
-        if (!mbar_wait(smem_addr(&empty[st]), ph ^ 1u, abort_flag, a.status)) { ok = false; break; }
+        if (ok) ok = mbar_wait(smem_addr(&empty[st]), ph ^ 1u, abort_flag, a.status);
+        if (!ok) continue;
         unsigned char* ob = smem_O + (size_t)st * omega_bytes;
         const int r0 = ch * kChunkRows;
         for (int task = gtid; task < kChunkRows * groups; task += kGenThreads) {
@@ -280,7 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_bf16_kernel(const Bf16Args
         mbar_arrive(smem_addr(&ofull[st]));
       }
     }
-    if (ok && seg1 > seg0) epilogue(seg1 - 1, segi - 1);
+    if (seg1 > seg0) epilogue(seg1 - 1, segi - 1);
   }
 
   tc_fence_before();

@@ -14,17 +14,20 @@ namespace tc {
 // of the tile = TMEM lane r; slice 2t owns rows 0..63, slice 2t+1 rows 64..127.
 // Called by all `nthreads` epilogue threads (whole warps); warp w reads TMEM
 // lanes 32 (w % 4) .. +31 and the warps sharing a quadrant (`part` of
-// `nparts`) take alternate 16-column slices.
+// `nparts`) take alternate 16-column slices.  `ok` (uniform per warp) false:
+// an earlier bounded wait gave up -- the thread still takes every barrier but
+// reads, writes and counts nothing.
 __device__ __forceinline__ void pack_epilogue(const SketchArgs& a, const PackSegment& sg,
                                               uint32_t tmem_base, int acc_stride, int quad,
                                               int part, int nparts, int lane, int gtid,
-                                              int nthreads, int* last_flags, int barrier_id) {
+                                              int nthreads, int* last_flags, int barrier_id,
+                                              bool ok) {
   const Pack pk = a.packs[sg.pack];
   const int l_pad = a.l_pad;
   const int nt = (pk.nslices + 1) / 2;
   float* partial = static_cast<float*>(a.partial);
   const int row = quad * 32 + lane;                 // TMEM lane = tile row
-  for (int t = 0; t < nt; ++t) {
+  for (int t = 0; t < nt && ok; ++t) {
     const int h = 2 * t + (row >> 6);
     const int jj = row & 63;
     bool valid = false;
@@ -57,7 +60,7 @@ __device__ __forceinline__ void pack_epilogue(const SketchArgs& a, const PackSeg
   if (gtid < pk.nprob) {
     const int p = pk.prob0 + gtid;
     const int nslots = a.pslot_ptr[p + 1] - a.pslot_ptr[p];
-    last_flags[gtid] = (atomicAdd(&a.prob_cnt[p], 1) == nslots - 1);
+    last_flags[gtid] = ok && (atomicAdd(&a.prob_cnt[p], 1) == nslots - 1);
   }
   named_bar_sync(barrier_id, nthreads);
   for (int q = 0; q < pk.nprob; ++q) {

@@ -173,22 +173,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) sketch_tf32_kernel(const TcArgs
     const int groups = l_pad / 4;
     int it = 0, segi = 0;
     bool ok = true;
-    auto epilogue = [&](int si_done, int seg_index) -> bool {
-      if (!mbar_wait(smem_addr(accum), (uint32_t)seg_index & 1u, abort_flag, a.status))
-        return false;
+    // The generator/epilogue warps share named barriers, so their control flow
+    // stays uniform for the whole schedule: a wait that gives up only clears
+    // `ok`, which switches off the work (and further waits) behind it.
+    auto epilogue = [&](int si_done, int seg_index) {
+      if (ok) ok = mbar_wait(smem_addr(accum), (uint32_t)seg_index & 1u, abort_flag, a.status);
+      ok = __all_sync(0xffffffffu, ok);
       tc_fence_after();
       pack_epilogue(a, a.psegs[si_done], tmem_base, args.acc_stride, quad, part, kGenWarps / 4,
-                    lane, gtid, kGenThreads, epi_last, 1);
-      return true;
+                    lane, gtid, kGenThreads, epi_last, 1, ok);
     };
-    for (int si = seg0; si < seg1 && ok; ++si, ++segi) {
+    for (int si = seg0; si < seg1; ++si, ++segi) {
       const PackSegment sg = a.psegs[si];
-      if (si > seg0 && !epilogue(si - 1, segi - 1)) { ok = false; break; }
+      if (si > seg0) epilogue(si - 1, segi - 1);
       const int m = a.packs[sg.pack].m;
       for (int ch = sg.chunk0; ch < sg.chunk1; ++ch, ++it) {
         const int st = it % S;
         const uint32_t ph = (uint32_t)(it / S) & 1u;
-        if (!mbar_wait(smem_addr(&empty[st]), ph ^ 1u, abort_flag, a.status)) { ok = false; break; }
+        if (ok) ok = mbar_wait(smem_addr(&empty[st]), ph ^ 1u, abort_flag, a.status);
+        if (!ok) continue;
         unsigned char* ob = smem_O + (size_t)st * omega_bytes;
         const int r0 = ch * kChunkRows;
         for (int task = gtid; task < kChunkRows * groups; task += kGenThreads) {
@@ -212,7 +215,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sketch_tf32_kernel(const TcArgs
         mbar_arrive(smem_addr(&ofull[st]));
       }
     }
-    if (ok && seg1 > seg0) epilogue(seg1 - 1, segi - 1);
+    if (seg1 > seg0) epilogue(seg1 - 1, segi - 1);
   }
 
   tc_fence_before();

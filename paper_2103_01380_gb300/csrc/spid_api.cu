@@ -80,6 +80,10 @@ struct spid_plan_s {
   bool per_sub() const { return (flags & SPID_FLAG_PER_SUBDOMAIN) != 0; }
   bool tensor_core() const { return prec >= SPID_PREC_TF32; }
   bool bf16() const { return prec == SPID_PREC_BF16 || prec == SPID_PREC_BF16X3; }
+  bool err_tc_eligible() const {
+    return tensor_core() && !per_sub() && (flags & SPID_FLAG_TC_ERROR) &&
+           k_max <= kErrTcKMax && smem_optin >= error_tc_smem_bytes();
+  }
   double u_mode() const {
     switch (prec) {
       case SPID_PREC_FP64: return std::ldexp(1.0, -53);
@@ -109,6 +113,13 @@ struct spid_plan_s {
   double* d_err_part = nullptr;
   double* d_sub_err = nullptr;
   int* d_err_cnt = nullptr;     // [S + 1] error-pass completion counters
+  // tensor-core error pass: segments of 128-row tiles over one CTA per SM
+  bool err_tc = false;
+  int err_tc_grid = 0;
+  ErrSeg* d_err_segs = nullptr;
+  int32_t* d_err_seg_ptr = nullptr;   // [grid + 1]
+  int32_t* d_err_tc_ptr = nullptr;    // [S + 1] segments of each subdomain
+  double* d_err_tc_part = nullptr;    // [segments][2]
   void* d_tmaps = nullptr;
   void* d_partial = nullptr;
   int64_t partial_cap = 0;
@@ -344,6 +355,50 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   return SPID_OK;
 }
 
+// Tensor-core error schedule: the 128-row tiles of every (subdomain, column
+// block of <= 256 columns), in that order, cut into G contiguous ranges of
+// equal bytes (a tile goes to the CTA whose share holds its midpoint); a run of
+// one (subdomain, block) on one CTA is a segment.  Segments come out grouped
+// by subdomain, so each subdomain's partials are a contiguous range.
+void build_error_tc_schedule(spid_plan_t P, int G, std::vector<ErrSeg>& segs,
+                             std::vector<int32_t>& seg_ptr, std::vector<int32_t>& sub_ptr) {
+  double W = 0.0;
+  for (int s = 0; s < P->S; ++s) W += (double)P->m[s] * P->n[s];
+  segs.clear();
+  seg_ptr.assign(G + 1, 0);
+  sub_ptr.assign(P->S + 1, 0);
+  std::vector<std::vector<ErrSeg>> per_cta(G);
+  double acc = 0.0;
+  for (int s = 0; s < P->S; ++s) {
+    const int tiles = (P->m[s] + kErrTcRows - 1) / kErrTcRows;
+    for (int c0 = 0; c0 < P->n[s]; c0 += kErrTcCols) {
+      const int nc = std::min(kErrTcCols, P->n[s] - c0);
+      for (int t = 0; t < tiles; ++t) {
+        const double w = (double)std::min(kErrTcRows, P->m[s] - t * kErrTcRows) * nc;
+        int c = W > 0 ? (int)((acc + 0.5 * w) * G / W) : 0;
+        c = std::min(std::max(c, 0), G - 1);
+        std::vector<ErrSeg>& v = per_cta[c];
+        if (!v.empty() && v.back().sub == s && v.back().col0 == c0 && v.back().tile1 == t)
+          v.back().tile1 = t + 1;
+        else
+          v.push_back({s, c0, nc, t, t + 1});
+        acc += w;
+      }
+    }
+  }
+  for (int c = 0; c < G; ++c) {
+    seg_ptr[c] = (int32_t)segs.size();
+    segs.insert(segs.end(), per_cta[c].begin(), per_cta[c].end());
+  }
+  seg_ptr[G] = (int32_t)segs.size();
+  // subdomain ranges (CTA ranges are consecutive, so s is non-decreasing)
+  int q = 0;
+  for (int s = 0; s <= P->S; ++s) {
+    while (q < (int)segs.size() && segs[q].sub < s) ++q;
+    sub_ptr[s] = q;
+  }
+}
+
 spid_status get_schedule(spid_plan_t P, int col0, int ncols, Schedule** out) {
   std::lock_guard<std::mutex> g(P->mu);
   auto key = std::make_pair(col0, ncols);
@@ -568,6 +623,17 @@ spid_status spid_plan_create(const spid_plan_desc* d, spid_plan_t* out) {
   SPID_ALLOC(P->d_err_cnt, sizeof(int) * (P->S + 1));
   SPID_ALLOC(P->d_partial, esz * P->partial_cap);
   if (P->tensor_core()) SPID_ALLOC(P->d_tmaps, sizeof(CUtensorMap) * P->S);
+  std::vector<ErrSeg> esegs;
+  std::vector<int32_t> eseg_ptr, esub_ptr;
+  if (P->err_tc_eligible()) {
+    P->err_tc = true;
+    P->err_tc_grid = P->num_sms;
+    build_error_tc_schedule(P, P->err_tc_grid, esegs, eseg_ptr, esub_ptr);
+    SPID_ALLOC(P->d_err_segs, sizeof(ErrSeg) * esegs.size());
+    SPID_ALLOC(P->d_err_seg_ptr, sizeof(int32_t) * eseg_ptr.size());
+    SPID_ALLOC(P->d_err_tc_ptr, sizeof(int32_t) * esub_ptr.size());
+    SPID_ALLOC(P->d_err_tc_part, sizeof(double) * 2 * esegs.size());
+  }
 #undef SPID_ALLOC
 #define SPID_H2D(dst, src, bytes)                                                          \
   do {                                                                                     \
@@ -587,6 +653,11 @@ spid_status spid_plan_create(const spid_plan_desc* d, spid_plan_t* out) {
   SPID_H2D(P->d_unit_row0, urow.data(), sizeof(int32_t) * P->units);
   SPID_H2D(P->d_unit_col0, ucol.data(), sizeof(int32_t) * P->units);
   SPID_H2D(P->d_unit_ptr, P->unit_ptr.data(), sizeof(int32_t) * (P->S + 1));
+  if (P->err_tc) {
+    SPID_H2D(P->d_err_segs, esegs.data(), sizeof(ErrSeg) * esegs.size());
+    SPID_H2D(P->d_err_seg_ptr, eseg_ptr.data(), sizeof(int32_t) * eseg_ptr.size());
+    SPID_H2D(P->d_err_tc_ptr, esub_ptr.data(), sizeof(int32_t) * esub_ptr.size());
+  }
 #undef SPID_H2D
   if (cudaMemset(P->d_Y, 0, esz * P->y_elems) != cudaSuccess ||
       cudaMemset(P->d_status, 0, sizeof(int)) != cudaSuccess ||
@@ -739,6 +810,18 @@ static spid_status run_error(spid_plan_t P, const void* window, void* out, doubl
   a.sub_err = P->d_sub_err;
   a.total = total_dev;
   a.S = P->S;
+  if (P->err_tc) {
+    ErrTcArgs t;
+    t.e = a;
+    t.e.part = P->d_err_tc_part;
+    t.e.unit_ptr = P->d_err_tc_ptr;
+    t.segs = P->d_err_segs;
+    t.seg_ptr = P->d_err_seg_ptr;
+    t.status = P->d_status;
+    cudaError_t e = launch_error_tc(t, P->err_tc_grid, cs);
+    if (e != cudaSuccess) return fail(SPID_ERR_CUDA, std::string("error launch: ") + cudaGetErrorString(e));
+    return SPID_OK;
+  }
   if (P->per_sub()) {
     for (int s = 0; s < P->S; ++s) {
       a.unit_base = P->unit_ptr[s];

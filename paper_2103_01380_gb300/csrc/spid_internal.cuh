@@ -197,6 +197,28 @@ struct ErrArgs {
   int32_t S;
 };
 
+// Tensor-core error pass (FP32 windows, k_max <= 32): a segment is a run of
+// 128-row tiles of one (subdomain, column block of <= 256 columns) processed by
+// one CTA; the segments of subdomain s are unit_ptr[s] .. unit_ptr[s + 1].
+constexpr int kErrTcRows = 128;
+constexpr int kErrTcCols = 256;
+constexpr int kErrTcKMax = 32;
+
+struct ErrSeg {
+  int32_t sub;
+  int32_t col0;
+  int32_t ncols;   // <= kErrTcCols
+  int32_t tile0;   // first 128-row tile
+  int32_t tile1;   // one past the last tile
+};
+
+struct ErrTcArgs {
+  ErrArgs e;               // unit_* fields unused; part/unit_ptr index segments
+  const ErrSeg* segs;
+  const int32_t* seg_ptr;  // CTA c owns segs[seg_ptr[c] .. seg_ptr[c + 1])
+  int* status;
+};
+
 // Detail message returned by spid_last_error() on the calling thread.
 void set_last_error(const char* msg);
 
@@ -215,6 +237,8 @@ int qrcp_cols_per_thread(int n_max, int l_pad, bool fp64);
 cudaError_t launch_qrcp(const QrcpArgs& a, int grid, int n_max, int l_pad, bool fp64,
                         cudaStream_t st);
 size_t error_smem_bytes(int k_max, bool fp64);
+size_t error_tc_smem_bytes();
+cudaError_t launch_error_tc(const ErrTcArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_error(const ErrArgs& a, int units, bool fp64, cudaStream_t st);
 
 // ---------------------------------------------------------------------------

@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "SPID_OK", 1: "SPID_ERR_INVALID_ARG", 2: "SPID_ERR_CUDA", 3: 
                 7: "SPID_ERR_UNSUPPORTED"}
 PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "bf16x3": 4}
 FLAG_PER_SUBDOMAIN = 1
+FLAG_TC_ERROR = 2
 
 # every symbol include/spid.h declares
 EXPORTS = ["spid_plan_create", "spid_plan_destroy", "spid_plan_info", "spid_sketch", "spid_reset",
