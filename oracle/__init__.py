@@ -86,6 +86,18 @@ def _load():
                                        c.c_int32, c.c_int32, c.c_double, c.c_double, c.c_uint64,
                                        c.c_void_p, _i32p, _i32p, _f64p, _f64p, _f64p]
         lib.orc_spid_batch.restype = c.c_int
+        lib.orc_coarse_axis.argtypes = [c.c_int32, c.c_int32, c.c_void_p]
+        lib.orc_coarse_axis.restype = c.c_int
+        lib.orc_coarse_rows.argtypes = [_i32p, _i32p]
+        lib.orc_coarse_rows.restype = c.c_int64
+        lib.orc_subsample.argtypes = [_f64p, c.c_int64, c.c_int64, _i32p, _i32p, _f64p]
+        lib.orc_subsample.restype = None
+        lib.orc_trilinear.argtypes = [_f64p, c.c_int64, _i32p, _i32p, _f64p, c.c_int64]
+        lib.orc_trilinear.restype = None
+        lib.orc_subid.argtypes = [_f64p, c.c_int64, c.c_int64, _i32p, _i32p, c.c_int32,
+                                  c.c_double, c.c_double, _i32p, _f64p, c.c_void_p, _f64p,
+                                  c.c_void_p]
+        lib.orc_subid.restype = c.c_int
         lib.orc_num_threads.argtypes = []
         lib.orc_num_threads.restype = c.c_int
         _lib = lib
@@ -244,3 +256,75 @@ def spid(A: np.ndarray, l: int, kmax: int, tol: float, u_mode: float, seed: int,
     if want_y:
         res["Y"] = out["Y"][0]
     return res
+
+
+# ---------------------------------------------------------------------------
+# Subsampled ID / single-pass ID on a coarse grid (Section 2, Algorithms 2-3).
+# box = (nq, ez, ey, ex), stride = (sz, sy, sx); rows r = ((q ez + z) ey + y) ex + x.
+# ---------------------------------------------------------------------------
+def _box(box, stride):
+    return (np.ascontiguousarray(box, dtype=np.int32).reshape(4),
+            np.ascontiguousarray(stride, dtype=np.int32).reshape(3))
+
+
+def coarse_axis(e: int, s: int) -> np.ndarray:
+    """Coarse indices of an axis of e points with interval s (end point kept)."""
+    lib = _load()
+    cnt = int(lib.orc_coarse_axis(int(e), int(s), None))
+    out = np.zeros(max(cnt, 1), dtype=np.int32)
+    lib.orc_coarse_axis(int(e), int(s), out.ctypes.data)
+    return out[:cnt]
+
+
+def coarse_rows(box, stride) -> int:
+    b, st = _box(box, stride)
+    return int(_load().orc_coarse_rows(b, st))
+
+
+def subsample(A: np.ndarray, box, stride) -> np.ndarray:
+    """B = A(J, :) (mc x n) for an m x n matrix of one box."""
+    b, st = _box(box, stride)
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    mc = coarse_rows(b, st)
+    Af = np.ascontiguousarray(A.T).reshape(-1)
+    out = np.zeros(mc * max(n, 1), dtype=np.float64)
+    _load().orc_subsample(Af, m, n, b, st, out)
+    return out[:mc * n].reshape(n, mc).T.copy()
+
+
+def trilinear(G: np.ndarray, box, stride) -> np.ndarray:
+    """F = M G: trilinear interpolation of a coarse mc x n matrix onto the box."""
+    b, st = _box(box, stride)
+    G = np.asarray(G, dtype=np.float64)
+    mc, n = G.shape
+    m = int(np.prod(b))
+    Gf = np.ascontiguousarray(G.T).reshape(-1)
+    F = np.zeros(m * max(n, 1), dtype=np.float64)
+    _load().orc_trilinear(Gf, n, b, st, F, m)
+    return F[:m * n].reshape(n, m).T.copy()
+
+
+def subid(A: np.ndarray, box, stride, kmax: int, tol: float = 0.0, u_mode: float = 2.0 ** -53,
+          want_ahat: bool = False) -> dict:
+    """SubID / SPID on one box: J, k, C (k x n), Bskel (mc x k), and the squared
+    errors of A(:,I_B) C_B (SubID) and M B(:,I_B) C_B (SPID)."""
+    b, st = _box(box, stride)
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    assert m == int(np.prod(b))
+    mc = coarse_rows(b, st)
+    Af = np.ascontiguousarray(A.T).reshape(-1)
+    J = np.zeros(kmax, dtype=np.int32)
+    C = np.zeros(kmax * max(n, 1), dtype=np.float64)
+    Bs = np.zeros(mc * kmax, dtype=np.float64)
+    err = np.zeros(4, dtype=np.float64)
+    H = np.zeros(m * max(n, 1), dtype=np.float64) if want_ahat else None
+    k = int(_load().orc_subid(Af, m, n, b, st, kmax, float(tol), float(u_mode), J, C,
+                              Bs.ctypes.data, err, H.ctypes.data if want_ahat else None))
+    out = {"k": k, "J": J[:k].copy(), "J_full": J, "C": C[:kmax * n].reshape(kmax, n)[:k].copy(),
+           "Bskel": Bs.reshape(kmax, mc).T[:, :k].copy(), "e2_subid": float(err[0]),
+           "e2_spid": float(err[1]), "a2": float(err[2]), "mc": int(err[3])}
+    if want_ahat:
+        out["Ahat_spid"] = H[:m * n].reshape(n, m).T.copy()
+    return out

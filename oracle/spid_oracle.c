@@ -381,6 +381,184 @@ int orc_spid_batch(const double* window, int32_t num, const int64_t* m, const in
   return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Subsampled ID and single-pass ID on a coarse grid (Section 2, SubID and  */
+/* SPID paragraphs, Algorithms 2 and 3; Section 5.2 subsampling study).     */
+/* A subdomain is a box of nq QoIs x ez x ey x ex points whose rows are     */
+/* ordered r = ((q ez + z) ey + y) ex + x.  B = A(J,:) keeps the points of a */
+/* coarse grid with interval s along each axis; M interpolates the coarse   */
+/* grid back onto the box (trilinear, Section 5.2).                         */
+/* ------------------------------------------------------------------------ */
+
+/* Coarse indices along one axis of e points with interval s >= 1:
+ * 0, s, 2s, ... < e, and e - 1 appended when it is not one of them (reading:
+ * the 64-point runs of Section 5.2 with intervals 3, 7 and 9 keep both ends
+ * because 63 is a multiple of each; appending the end keeps that property for
+ * every size, so M never extrapolates).  Returns the count; idx may be NULL. */
+int orc_coarse_axis(int32_t e, int32_t s, int32_t* idx) {
+  int32_t c = 0;
+  for (int32_t x = 0; x < e; x += s) {
+    if (idx) idx[c] = x;
+    ++c;
+  }
+  if (e > 0 && (e - 1) % s != 0) {
+    if (idx) idx[c] = e - 1;
+    ++c;
+  }
+  return c;
+}
+
+/* Rows of the coarse matrix: nq * cz * cy * cx. */
+int64_t orc_coarse_rows(const int32_t box[4], const int32_t stride[3]) {
+  return (int64_t)box[0] * orc_coarse_axis(box[1], stride[0], NULL) *
+         orc_coarse_axis(box[2], stride[1], NULL) * orc_coarse_axis(box[3], stride[2], NULL);
+}
+
+/* B = A(J, :): B is mc x n column-major (leading dimension mc), its rows in
+ * (q, cz, cy, cx) order with cx fastest.  box = (nq, ez, ey, ex),
+ * stride = (sz, sy, sx). */
+void orc_subsample(const double* A, int64_t ld, int64_t n, const int32_t box[4],
+                   const int32_t stride[3], double* B) {
+  const int32_t nq = box[0], ez = box[1], ey = box[2], ex = box[3];
+  int32_t* iz = (int32_t*)malloc(sizeof(int32_t) * (size_t)ez);
+  int32_t* iy = (int32_t*)malloc(sizeof(int32_t) * (size_t)ey);
+  int32_t* ix = (int32_t*)malloc(sizeof(int32_t) * (size_t)ex);
+  const int32_t cz = orc_coarse_axis(ez, stride[0], iz);
+  const int32_t cy = orc_coarse_axis(ey, stride[1], iy);
+  const int32_t cx = orc_coarse_axis(ex, stride[2], ix);
+  const int64_t mc = (int64_t)nq * cz * cy * cx;
+  for (int64_t j = 0; j < n; ++j) {
+    int64_t cr = 0;
+    for (int32_t q = 0; q < nq; ++q)
+      for (int32_t a = 0; a < cz; ++a)
+        for (int32_t b = 0; b < cy; ++b)
+          for (int32_t c = 0; c < cx; ++c, ++cr) {
+            const int64_t r = (((int64_t)q * ez + iz[a]) * ey + iy[b]) * ex + ix[c];
+            B[cr + mc * j] = A[r + ld * j];
+          }
+  }
+  free(iz);
+  free(iy);
+  free(ix);
+}
+
+/* Coarse cell of fine coordinate x on one axis: lower coarse index position
+ * a (idx[a] <= x, and a + 1 < count unless count == 1) and the weight of the
+ * upper node, w = (x - idx[a]) / (idx[a+1] - idx[a]). */
+static void coarse_cell(const int32_t* idx, int32_t count, int32_t x, int32_t* a, double* w) {
+  if (count == 1) { *a = 0; *w = 0.0; return; }
+  int32_t lo = 0;
+  while (lo + 2 < count && idx[lo + 1] <= x) ++lo;
+  *a = lo;
+  *w = (double)(x - idx[lo]) / (double)(idx[lo + 1] - idx[lo]);
+}
+
+/* F = M G: trilinear interpolation of the coarse matrix G (mc x n, leading
+ * dimension mc, rows as orc_subsample) onto the box (F m x n, leading
+ * dimension ldf).  Per axis the fine point lies in coarse cell [X_a, X_a+1]
+ * with upper weight w; the value is the sum over the 8 cell corners of
+ * prod((1 - w) or w) times the corner value.  A fine point on a coarse node
+ * gets that node's value. */
+void orc_trilinear(const double* G, int64_t n, const int32_t box[4], const int32_t stride[3],
+                   double* F, int64_t ldf) {
+  const int32_t nq = box[0], ez = box[1], ey = box[2], ex = box[3];
+  int32_t* iz = (int32_t*)malloc(sizeof(int32_t) * (size_t)ez);
+  int32_t* iy = (int32_t*)malloc(sizeof(int32_t) * (size_t)ey);
+  int32_t* ix = (int32_t*)malloc(sizeof(int32_t) * (size_t)ex);
+  const int32_t cz = orc_coarse_axis(ez, stride[0], iz);
+  const int32_t cy = orc_coarse_axis(ey, stride[1], iy);
+  const int32_t cx = orc_coarse_axis(ex, stride[2], ix);
+  const int64_t mc = (int64_t)nq * cz * cy * cx;
+  for (int64_t j = 0; j < n; ++j) {
+    const double* g = G + mc * j;
+    for (int32_t q = 0; q < nq; ++q)
+      for (int32_t z = 0; z < ez; ++z)
+        for (int32_t y = 0; y < ey; ++y)
+          for (int32_t x = 0; x < ex; ++x) {
+            int32_t a, b, c;
+            double wz, wy, wx;
+            coarse_cell(iz, cz, z, &a, &wz);
+            coarse_cell(iy, cy, y, &b, &wy);
+            coarse_cell(ix, cx, x, &c, &wx);
+            double v = 0.0;
+            for (int32_t dz = 0; dz < 2; ++dz)
+              for (int32_t dy = 0; dy < 2; ++dy)
+                for (int32_t dx = 0; dx < 2; ++dx) {
+                  const double w = (dz ? wz : 1.0 - wz) * (dy ? wy : 1.0 - wy) *
+                                   (dx ? wx : 1.0 - wx);
+                  if (w == 0.0) continue;   /* also keeps single-node axes in range */
+                  const int64_t cr = (((int64_t)q * cz + a + dz) * cy + b + dy) * cx + c + dx;
+                  v += w * g[cr];
+                }
+            const int64_t r = (((int64_t)q * ez + z) * ey + y) * ex + x;
+            F[r + ldf * j] = v;
+          }
+  }
+  free(iz);
+  free(iy);
+  free(ix);
+}
+
+/* SubID and SPID on one box (Algorithms 2 and 3): B = A(J,:); pivoted MGS QR
+ * of B (orc_qrcp_mgs: norms from scratch, ties to the lowest index, adaptive
+ * stop when tol > 0), rank guard with u_mode, C_B = [I | R11^-1 R12] Z^T.
+ * Outputs: J (kmax, -1 past k), C (kmax x n row-major, zero rows past k),
+ * Bskel = B(:, I_B) (mc x kmax column-major, may be NULL), and
+ * err[0] = ||A - A(:,I_B) C_B||_F^2 (SubID), err[1] = ||A - M B(:,I_B) C_B||_F^2
+ * (SPID), err[2] = ||A||_F^2, err[3] = mc.  Ahat (m x n, ld m, may be NULL)
+ * receives the SPID reconstruction.  Returns k. */
+int orc_subid(const double* A, int64_t ld, int64_t n, const int32_t box[4],
+              const int32_t stride[3], int32_t kmax, double tol, double u_mode, int32_t* J,
+              double* C, double* Bskel, double* err, double* Ahat) {
+  const int64_t m = (int64_t)box[0] * box[1] * box[2] * box[3];
+  const int64_t mc = orc_coarse_rows(box, stride);
+  const int64_t nn = n > 0 ? n : 1;
+  double* B = (double*)malloc(sizeof(double) * (size_t)(mc * nn));
+  double* W = (double*)malloc(sizeof(double) * (size_t)(mc * nn));
+  double* R = (double*)malloc(sizeof(double) * (size_t)kmax * (size_t)nn);
+  orc_subsample(A, ld, n, box, stride, B);
+  memcpy(W, B, sizeof(double) * (size_t)(mc * n));
+  for (int32_t p = 0; p < kmax; ++p) J[p] = -1;
+  double normB2 = 0.0;
+  const int32_t k0 = orc_qrcp_mgs(W, (int32_t)mc, n, kmax, tol, J, R, &normB2);
+  const int32_t k = orc_rank_guard(R, n, J, k0, u_mode);
+  for (int32_t p = k; p < kmax; ++p) J[p] = -1;
+  for (int64_t x = 0; x < (int64_t)kmax * n; ++x) C[x] = 0.0;
+  orc_coefficients(R, n, J, k, C);
+  if (Bskel)
+    for (int32_t p = 0; p < kmax; ++p)
+      for (int64_t cr = 0; cr < mc; ++cr) Bskel[cr + mc * p] = (p < k) ? B[cr + mc * J[p]] : 0.0;
+  /* SubID: A(:, I_B) C_B */
+  double e2s = 0.0, a2 = 0.0;
+  orc_reconstruct_error(A, m, n, ld, J, k, C, NULL, 0, &e2s, &a2);
+  /* SPID: M (B(:, I_B) C_B) -- interpolate the coarse reconstruction */
+  double* G = (double*)malloc(sizeof(double) * (size_t)(mc * nn));
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t cr = 0; cr < mc; ++cr) {
+      double v = 0.0;
+      for (int32_t p = 0; p < k; ++p) v += B[cr + mc * J[p]] * C[(int64_t)p * n + j];
+      G[cr + mc * j] = v;
+    }
+  double* F = Ahat ? Ahat : (double*)malloc(sizeof(double) * (size_t)(m * nn));
+  orc_trilinear(G, n, box, stride, F, m);
+  double se = 0.0, ce = 0.0;
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t r = 0; r < m; ++r) {
+      const double e = A[r + ld * j] - F[r + m * j];
+      neu_add(&se, &ce, e * e);
+    }
+  err[0] = e2s;
+  err[1] = se + ce;
+  err[2] = a2;
+  err[3] = (double)mc;
+  if (!Ahat) free(F);
+  free(G);
+  free(B);
+  free(W);
+  free(R);
+  return k;
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
   extern int omp_get_max_threads(void);

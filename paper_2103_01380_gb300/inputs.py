@@ -340,3 +340,40 @@ def separated_lowrank(m: int, n: int, r: int, seed: int, decay: float = 0.5,
     if noise > 0:
         A = A + noise * np.random.default_rng(seed + 7919).standard_normal((m, n))
     return A
+
+
+def smooth_box_field(box, n: int, seed: int, modes: int = 6, kmax: int = 2,
+                     noise: float = 0.0) -> np.ndarray:
+    """m x n field of one box (nq, ez, ey, ex), rows in (q, z, y, x) order:
+    per QoI a sum of `modes` separable sine/cosine products of wavenumbers
+    1..kmax over the box, mode i with amplitude 2^-i and its own time signal,
+    plus optional i.i.d. noise.  Smooth in space, so a coarse grid sees it."""
+    nq, ez, ey, ex = (int(v) for v in box)
+    rng = np.random.default_rng(seed)
+    z, y, x = np.meshgrid(np.arange(ez) / ez, np.arange(ey) / ey, np.arange(ex) / ex,
+                          indexing="ij")
+    t = np.linspace(0.0, 1.0, n)
+    A = np.zeros((nq, ez, ey, ex, n))
+    for q in range(nq):
+        for i in range(modes):
+            kx, ky, kz = rng.integers(1, kmax + 1, size=3)
+            ph = rng.uniform(0.0, 2.0 * np.pi, 3)
+            sp = (np.sin(2 * np.pi * kx * x + ph[0]) * np.cos(2 * np.pi * ky * y + ph[1]) *
+                  np.sin(2 * np.pi * kz * z + ph[2]))
+            amp = 0.5 ** i * np.cos(2 * np.pi * (i + 1) * t + rng.uniform(0.0, 6.0))
+            A[q] += sp[..., None] * amp
+    A = A.reshape(-1, n)
+    if noise > 0:
+        A = A + noise * rng.standard_normal(A.shape)
+    return A
+
+
+def box_window(boxes, n, seed: int, dtype=np.float32, noise: float = 0.0, **kw) -> "Window":
+    """Window of smooth_box_field blocks, one per box (nq, ez, ey, ex); n is a
+    common length or one per box."""
+    ns = np.broadcast_to(np.atleast_1d(n), (len(boxes),))
+    blocks = [smooth_box_field(b, int(ns[i]), seed + i, noise=noise, **kw)
+              for i, b in enumerate(boxes)]
+    w = pack_blocks(blocks, dtype=dtype)
+    w.meta["boxes"] = np.asarray(boxes, dtype=np.int32).reshape(-1, 4)
+    return w
