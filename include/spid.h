@@ -223,6 +223,92 @@ const char* spid_status_string(spid_status status);
 /* Detail of the last error raised on the calling thread ("" if none). */
 const char* spid_last_error(void);
 
+/* ==========================================================================
+ * Subsampled ID and single-pass ID on a coarse grid (Section 2, SubID and SPID
+ * paragraphs; Algorithms 2 and 3; Section 5.2 subsampling study).
+ *
+ * The sketch is deterministic: B = A(J,:) keeps the rows of a coarse grid of
+ * each subdomain box (interval s along each axis: indices 0, s, 2s, ... and
+ * the last point of the axis, which is appended when it is not a multiple of
+ * s).  A pivoted modified Gram-Schmidt QR of B (the paper's mgsqr: residual
+ * norms from the updated columns at every step, ties to the lowest column,
+ * adaptive stop as Remark 2.1 when tol > 0, rank guard |R_jj| > 2^-23 |R_00|)
+ * gives I_B and C_B = [I | R11^-1 R12] Z^T.  Two reconstructions:
+ *   SubID  A ~ A(:, I_B) C_B                (needs the window again)
+ *   SPID   A ~ M B(:, I_B) C_B              (M = trilinear interpolation from
+ *                                            the coarse grid; needs only the
+ *                                            stored coarse skeleton)
+ * FP32 windows only.  Subdomain s is a box of nq x ez x ey x ex (QoIs x
+ * points), stored as an m_s x n_s column-major block of the window
+ * (m_s = nq ez ey ex; rows r = ((q ez + z) ey + y) ex + x; off/ld as for
+ * spid_plan_desc).  The coarse matrix B_s is m_c(s) x n_s with rows in
+ * (q, cz, cy, cx) order.
+ * ========================================================================== */
+typedef struct spid_sub_plan_s* spid_sub_plan_t;
+
+/* Reconstruction forms of spid_sub_error / spid_sub_reconstruct. */
+#define SPID_FORM_SPID 0
+#define SPID_FORM_SUBID 1
+
+typedef struct {
+  int32_t num_sub;        /* S >= 1 */
+  const int32_t* box;     /* host [4 S]: (nq, ez, ey, ex) of subdomain s, all >= 1 */
+  const int32_t* n;       /* host [S]: window length n_s, 1 <= n_s <= 1024 */
+  const int64_t* off;     /* host [S]: element offset of A_s(0,0) (multiple of 4) */
+  const int64_t* ld;      /* host [S]: leading dimension >= m_s (multiple of 4) */
+  int32_t stride[3];      /* coarse interval along z, y, x; each >= 1 */
+  int32_t k_max;          /* 1 <= k_max <= 64; k_s <= min(k_max, n_s, m_c(s)) */
+  double tol;             /* 0: fixed rank k_max; > 0: smallest k with
+                             ||R22||_F <= tol ||B||_F (Remark 2.1 reading) */
+  uint32_t flags;         /* 0 */
+} spid_sub_desc;
+
+/* Create a plan: validates, allocates all workspace (later calls allocate
+ * nothing).  m_c(s) <= 40960 coarse rows (the QR keeps one column of B in
+ * shared memory); SPID_ERR_UNSUPPORTED beyond. */
+spid_status spid_sub_plan_create(const spid_sub_desc* desc, spid_sub_plan_t* plan);
+spid_status spid_sub_plan_destroy(spid_sub_plan_t plan);
+
+/* mc_host (may be NULL): [S] coarse rows m_c(s).  workspace (may be NULL):
+ * device bytes owned by the plan. */
+spid_status spid_sub_plan_info(spid_sub_plan_t plan, int64_t* mc_host, int64_t* workspace);
+
+/* Gather B_s(:, col0 .. col0 + ncols) = A_s(J, cols) for every subdomain with
+ * n_s > col0 (columns past n_s are skipped).  Single pass: the window columns
+ * may be overwritten once the call's stream has passed it. */
+spid_status spid_sub_sample(spid_sub_plan_t plan, const float* window, int32_t col0,
+                            int32_t ncols, spid_stream_t stream);
+
+/* Pivoted MGS QR of every B_s, rank decision, C_B and the coarse skeleton
+ * B_s(:, I_B).  A subdomain whose B holds a non-finite value gets k = 0 and
+ * sets SPID_ERR_NONFINITE in the sticky status. */
+spid_status spid_sub_finalize(spid_sub_plan_t plan, spid_stream_t stream);
+
+/* Errors of the chosen form, as spid_error: err_dev[2 s] = ||A_s - A_hat_s||^2,
+ * err_dev[2 s + 1] = ||A_s||^2 (may be NULL), total_dev[0..3] = {sum e2,
+ * sum a2, sum m_s n_s, sum k_s (r_s + n_s)} with r_s = m_c(s) for SPID (the
+ * coarse skeleton is what is stored) and r_s = m_s for SubID. */
+spid_status spid_sub_error(spid_sub_plan_t plan, const float* window, int32_t form,
+                           double* err_dev, double* total_dev, spid_stream_t stream);
+
+/* A_hat written to out (window layout).  SPID needs no window (NULL allowed). */
+spid_status spid_sub_reconstruct(spid_sub_plan_t plan, const float* window, int32_t form,
+                                 float* out, spid_stream_t stream);
+
+/* Copy factors to the host (synchronizes): k_host[S], J_host[S k_max] (-1 past
+ * k_s), C_host k_max x n_s row-major per subdomain at k_max sum_{s'<s} n_s',
+ * Bskel_host m_c(s) x k_max column-major per subdomain at
+ * k_max sum_{s'<s} m_c(s') (columns past k_s zero).  Any pointer may be NULL. */
+spid_status spid_sub_get_factors(spid_sub_plan_t plan, int32_t* k_host, int32_t* J_host,
+                                 float* C_host, float* Bskel_host, spid_stream_t stream);
+
+/* Copy the gathered coarse matrices to the host (synchronizes): B_s as
+ * m_c(s) x n_s column-major at sum_{s'<s} m_c(s') n_s'. */
+spid_status spid_sub_get_coarse(spid_sub_plan_t plan, float* B_host, spid_stream_t stream);
+
+/* Sticky device status of the plan (as spid_device_status), then cleared. */
+spid_status spid_sub_device_status(spid_sub_plan_t plan, spid_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -2,8 +2,9 @@
 // relative Frobenius error, Section 2 compression-factor sums): once the last
 // work unit of subdomain s has stored its {e2, a2} partial, one warp sums the
 // subdomain's partials in unit order, and the last subdomain to finish sums
-// the window totals {sum e2, sum a2, sum m n, sum k (m + n)} in subdomain
-// order.  Every counter is reset by the warp that completes it.
+// the window totals {sum e2, sum a2, sum m n, sum k (r + n)} in subdomain
+// order, r = the rows stored per skeleton column (m, or m_c for a coarse-grid
+// skeleton, Section 5.2).  Every counter is reset by the warp that completes it.
 #pragma once
 
 #include "spid_internal.cuh"
@@ -43,8 +44,9 @@ __device__ __forceinline__ void error_fold_subdomain(const ErrArgs& a, int s, in
     te += __ldcg(a.sub_err + 2 * (int64_t)q);
     ta += __ldcg(a.sub_err + 2 * (int64_t)q + 1);
     const double mq = (double)a.m[q], nq = (double)a.n[q];
+    const double sq = a.srows ? (double)a.srows[q] : mq;   // coarse skeleton: m_c rows
     mn += mq * nq;
-    kd += (double)a.k[q] * (mq + nq);
+    kd += (double)a.k[q] * (sq + nq);
   }
   for (int o = 16; o > 0; o >>= 1) {
     te += __shfl_xor_sync(0xffffffffu, te, o);

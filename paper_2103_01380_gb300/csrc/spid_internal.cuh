@@ -195,6 +195,7 @@ struct ErrArgs {
   double* sub_err;            // plan copy [S][2]
   double* total;              // [4] or nullptr
   int32_t S;
+  const int32_t* srows = nullptr;   // rows stored per subdomain for the CF sums (nullptr: m)
 };
 
 // Tensor-core error pass (FP32 windows, k_max <= 32): a segment is a run of

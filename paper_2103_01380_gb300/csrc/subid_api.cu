@@ -1,0 +1,447 @@
+// subid_api.cu -- C ABI of the coarse-grid column ID (include/spid.h,
+// spid_sub_*): plan creation with all workspace, the subsample gather, the
+// finalize (pivoted MGS QR + coefficients + coarse skeleton), and the SPID
+// (trilinear) and SubID error / reconstruction passes.  Section 2 SubID and
+// SPID paragraphs, Algorithms 2 and 3, Section 5.2.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/spid.h"
+#include "subid_internal.cuh"
+
+using namespace spid;
+
+struct spid_sub_plan_s {
+  int device = 0;
+  int S = 0;
+  std::vector<SubBox> box;
+  std::vector<int32_t> m, n, mc;
+  std::vector<int64_t> off, ld, boff, coff, sklo;
+  int k_max = 0;
+  double tol = 0.0;
+  int mc_max = 0, n_max = 0, e_max = 0;
+  int64_t b_elems = 0, c_elems = 0, sk_elems = 0;
+  // SPID error units (per subdomain: n_s columns x zblocks)
+  std::vector<int32_t> uptr;
+  int64_t spid_units = 0;
+  // SubID error units (512-row x 256-column blocks, as the main error pass)
+  std::vector<int32_t> usub, urow, ucol, uptr_subid;
+  // device
+  SubBox* d_box = nullptr;
+  int32_t *d_m = nullptr, *d_n = nullptr, *d_mc = nullptr;
+  int64_t *d_off = nullptr, *d_ld = nullptr, *d_boff = nullptr, *d_coff = nullptr,
+          *d_sklo = nullptr, *d_ccoff = nullptr;   // d_ccoff = k_max * coff (C in elements)
+  float *d_B = nullptr, *d_W = nullptr, *d_R = nullptr, *d_C = nullptr, *d_Bsk = nullptr;
+  int32_t *d_J = nullptr, *d_k = nullptr;
+  int* d_status = nullptr;
+  int32_t* d_uptr = nullptr;
+  double* d_part_spid = nullptr;
+  int32_t *d_usub = nullptr, *d_urow = nullptr, *d_ucol = nullptr, *d_uptr_subid = nullptr;
+  double* d_part_subid = nullptr;
+  double* d_sub_err = nullptr;
+  int* d_cnt = nullptr;   // [S + 1]
+  std::vector<void*> allocs;
+  int64_t workspace = 0;
+
+  cudaError_t alloc(void** p, size_t bytes) {
+    bytes = std::max<size_t>(bytes, 16);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) {
+      allocs.push_back(*p);
+      workspace += (int64_t)bytes;
+    }
+    return e;
+  }
+  SubArgs args() const {
+    SubArgs a;
+    a.box = d_box;
+    a.m = d_m;
+    a.n = d_n;
+    a.mc = d_mc;
+    a.off = d_off;
+    a.ld = d_ld;
+    a.boff = d_boff;
+    a.coff = d_coff;
+    a.sklo = d_sklo;
+    a.B = d_B;
+    a.W = d_W;
+    a.R = d_R;
+    a.C = d_C;
+    a.Bskel = d_Bsk;
+    a.J = d_J;
+    a.k = d_k;
+    a.k_max = k_max;
+    a.S = S;
+    a.tol = tol;
+    a.status = d_status;
+    return a;
+  }
+  ErrArgs fold_args(const float* window, float* out, double* err, double* total) const {
+    ErrArgs e;
+    e.window = window;
+    e.out = out;
+    e.m = d_m;
+    e.n = d_n;
+    e.off = d_off;
+    e.ld = d_ld;
+    e.C = d_C;
+    e.coff = nullptr;
+    e.J = d_J;
+    e.k = d_k;
+    e.k_max = k_max;
+    e.unit_sub = nullptr;
+    e.unit_row0 = nullptr;
+    e.unit_col0 = nullptr;
+    e.part = nullptr;
+    e.unit_base = 0;
+    e.unit_ptr = nullptr;
+    e.sub_cnt = d_cnt;
+    e.all_cnt = d_cnt + S;
+    e.err = err;
+    e.sub_err = d_sub_err;
+    e.total = total;
+    e.S = S;
+    e.srows = nullptr;
+    return e;
+  }
+};
+
+namespace {
+
+spid_status sfail(spid_status st, const std::string& msg) {
+  set_last_error(msg.c_str());
+  return st;
+}
+
+#define SUB_CUDA(call)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return sfail(e_ == cudaErrorMemoryAllocation ? SPID_ERR_OOM : SPID_ERR_CUDA,         \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));                    \
+  } while (0)
+
+int coarse_count(int e, int s) { return (e - 1) / s + 1 + ((e - 1) % s != 0 ? 1 : 0); }
+
+spid_status check(spid_sub_plan_t P) {
+  if (!P) return sfail(SPID_ERR_INVALID_ARG, "plan is NULL");
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != P->device) SUB_CUDA(cudaSetDevice(P->device));
+  return SPID_OK;
+}
+
+spid_status check_window(const void* w, const char* what) {
+  if (!w) return sfail(SPID_ERR_INVALID_ARG, std::string(what) + " is NULL");
+  if (reinterpret_cast<uintptr_t>(w) % 16)
+    return sfail(SPID_ERR_INVALID_ARG, std::string(what) + " must be 16-byte aligned");
+  return SPID_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+spid_status spid_sub_plan_create(const spid_sub_desc* d, spid_sub_plan_t* out) {
+  if (!d || !out) return sfail(SPID_ERR_INVALID_ARG, "desc/out is NULL");
+  *out = nullptr;
+  if (d->num_sub < 1 || d->num_sub > 65535)
+    return sfail(SPID_ERR_INVALID_ARG, "num_sub must be in [1, 65535]");
+  if (!d->box || !d->n || !d->off || !d->ld) return sfail(SPID_ERR_INVALID_ARG, "NULL array");
+  if (d->k_max < 1 || d->k_max > kSubMaxK)
+    return sfail(SPID_ERR_INVALID_ARG, "k_max must be in [1, 64]");
+  if (!(d->tol >= 0.0)) return sfail(SPID_ERR_INVALID_ARG, "tol must be >= 0");
+  for (int i = 0; i < 3; ++i)
+    if (d->stride[i] < 1) return sfail(SPID_ERR_INVALID_ARG, "stride must be >= 1");
+  if (d->flags != 0) return sfail(SPID_ERR_INVALID_ARG, "flags must be 0");
+  spid_sub_plan_s* P = new spid_sub_plan_s();
+  auto bail = [&](spid_status st) {
+    spid_sub_plan_destroy(P);
+    return st;
+  };
+  P->S = d->num_sub;
+  P->k_max = d->k_max;
+  P->tol = d->tol;
+  int64_t bsum = 0, csum = 0, ssum = 0, units = 0;
+  P->uptr.assign(P->S + 1, 0);
+  P->uptr_subid.assign(P->S + 1, 0);
+  for (int s = 0; s < P->S; ++s) {
+    SubBox b;
+    b.nq = d->box[4 * s];
+    b.ez = d->box[4 * s + 1];
+    b.ey = d->box[4 * s + 2];
+    b.ex = d->box[4 * s + 3];
+    if (b.nq < 1 || b.ez < 1 || b.ey < 1 || b.ex < 1) {
+      delete P;
+      return sfail(SPID_ERR_INVALID_ARG, "box extents must be >= 1 (subdomain " +
+                                             std::to_string(s) + ")");
+    }
+    b.sz = d->stride[0];
+    b.sy = d->stride[1];
+    b.sx = d->stride[2];
+    b.cz = coarse_count(b.ez, b.sz);
+    b.cy = coarse_count(b.ey, b.sy);
+    b.cx = coarse_count(b.ex, b.sx);
+    const int64_t m = (int64_t)b.nq * b.ez * b.ey * b.ex;
+    const int64_t mc = (int64_t)b.nq * b.cz * b.cy * b.cx;
+    const int ns = d->n[s];
+    if (m > INT32_MAX || ns < 1 || ns > kSubMaxN || d->ld[s] < m || d->off[s] < 0 ||
+        d->off[s] % 4 || d->ld[s] % 4) {
+      delete P;
+      return sfail(SPID_ERR_INVALID_ARG, "bad n/off/ld for subdomain " + std::to_string(s));
+    }
+    if (mc > kSubMaxCoarse) {
+      delete P;
+      return sfail(SPID_ERR_UNSUPPORTED, "coarse grid of subdomain " + std::to_string(s) +
+                                             " exceeds 40960 rows");
+    }
+    // SPID error units: columns x z blocks of about kSubUnitElems fine elements
+    const int64_t per_col = std::max<int64_t>(1, (m + kSubUnitElems - 1) / kSubUnitElems);
+    b.zc = (int)std::max<int64_t>(1, (b.ez + per_col - 1) / per_col);
+    b.zblocks = (b.ez + b.zc - 1) / b.zc;
+    P->box.push_back(b);
+    P->m.push_back((int32_t)m);
+    P->n.push_back(ns);
+    P->mc.push_back((int32_t)mc);
+    P->off.push_back(d->off[s]);
+    P->ld.push_back(d->ld[s]);
+    P->boff.push_back(bsum);
+    P->coff.push_back(csum);
+    P->sklo.push_back(ssum);
+    bsum += mc * ns;
+    csum += ns;
+    ssum += mc;
+    P->uptr[s] = (int32_t)units;
+    units += (int64_t)ns * b.zblocks;
+    P->mc_max = std::max<int>(P->mc_max, (int)mc);
+    P->n_max = std::max(P->n_max, ns);
+    P->e_max = std::max({P->e_max, b.ez, b.ey, b.ex});
+    P->uptr_subid[s] = (int32_t)P->usub.size();
+    for (int64_t r = 0; r < m; r += kErrRowBlock)
+      for (int c = 0; c < ns; c += kErrColBlock) {
+        P->usub.push_back(s);
+        P->urow.push_back((int32_t)r);
+        P->ucol.push_back(c);
+      }
+  }
+  if (units > INT32_MAX) {
+    delete P;
+    return sfail(SPID_ERR_UNSUPPORTED, "too many error units");
+  }
+  P->uptr[P->S] = (int32_t)units;
+  P->uptr_subid[P->S] = (int32_t)P->usub.size();
+  P->spid_units = units;
+  P->b_elems = bsum;
+  P->c_elems = csum * P->k_max;
+  P->sk_elems = ssum * P->k_max;
+  if (cudaGetDevice(&P->device) != cudaSuccess) {
+    delete P;
+    return sfail(SPID_ERR_CUDA, "cudaGetDevice failed");
+  }
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
+  if (subid_qr_smem_bytes(P->mc_max, P->n_max, P->k_max) + 1024 > (size_t)optin ||
+      spid_interp_smem_bytes(P->mc_max, P->e_max) + 1024 > (size_t)optin) {
+    delete P;
+    return sfail(SPID_ERR_UNSUPPORTED, "coarse grid too large for shared memory");
+  }
+#define SUB_ALLOC(ptr, bytes)                                                              \
+  do {                                                                                     \
+    cudaError_t e_ = P->alloc(reinterpret_cast<void**>(&(ptr)), (bytes));                  \
+    if (e_ != cudaSuccess)                                                                 \
+      return bail(sfail(e_ == cudaErrorMemoryAllocation ? SPID_ERR_OOM : SPID_ERR_CUDA,    \
+                        std::string("cudaMalloc: ") + cudaGetErrorString(e_)));            \
+  } while (0)
+  const size_t S = (size_t)P->S;
+  SUB_ALLOC(P->d_box, sizeof(SubBox) * S);
+  SUB_ALLOC(P->d_m, sizeof(int32_t) * S);
+  SUB_ALLOC(P->d_n, sizeof(int32_t) * S);
+  SUB_ALLOC(P->d_mc, sizeof(int32_t) * S);
+  SUB_ALLOC(P->d_off, sizeof(int64_t) * S);
+  SUB_ALLOC(P->d_ld, sizeof(int64_t) * S);
+  SUB_ALLOC(P->d_boff, sizeof(int64_t) * S);
+  SUB_ALLOC(P->d_coff, sizeof(int64_t) * S);
+  SUB_ALLOC(P->d_sklo, sizeof(int64_t) * S);
+  SUB_ALLOC(P->d_ccoff, sizeof(int64_t) * S);
+  SUB_ALLOC(P->d_B, sizeof(float) * P->b_elems);
+  SUB_ALLOC(P->d_W, sizeof(float) * P->b_elems);
+  SUB_ALLOC(P->d_R, sizeof(float) * P->c_elems);
+  SUB_ALLOC(P->d_C, sizeof(float) * P->c_elems);
+  SUB_ALLOC(P->d_Bsk, sizeof(float) * P->sk_elems);
+  SUB_ALLOC(P->d_J, sizeof(int32_t) * S * P->k_max);
+  SUB_ALLOC(P->d_k, sizeof(int32_t) * S);
+  SUB_ALLOC(P->d_status, sizeof(int));
+  SUB_ALLOC(P->d_uptr, sizeof(int32_t) * (S + 1));
+  SUB_ALLOC(P->d_part_spid, sizeof(double) * 2 * (size_t)P->spid_units);
+  SUB_ALLOC(P->d_usub, sizeof(int32_t) * P->usub.size());
+  SUB_ALLOC(P->d_urow, sizeof(int32_t) * P->usub.size());
+  SUB_ALLOC(P->d_ucol, sizeof(int32_t) * P->usub.size());
+  SUB_ALLOC(P->d_uptr_subid, sizeof(int32_t) * (S + 1));
+  SUB_ALLOC(P->d_part_subid, sizeof(double) * 2 * P->usub.size());
+  SUB_ALLOC(P->d_sub_err, sizeof(double) * 2 * S);
+  SUB_ALLOC(P->d_cnt, sizeof(int) * (S + 1));
+#undef SUB_ALLOC
+  std::vector<int64_t> ccoff(S);
+  for (size_t i = 0; i < S; ++i) ccoff[i] = (int64_t)P->k_max * P->coff[i];
+  struct Up { void* dst; const void* src; size_t bytes; };
+  const Up ups[] = {
+      {P->d_box, P->box.data(), sizeof(SubBox) * S},
+      {P->d_m, P->m.data(), sizeof(int32_t) * S},
+      {P->d_n, P->n.data(), sizeof(int32_t) * S},
+      {P->d_mc, P->mc.data(), sizeof(int32_t) * S},
+      {P->d_off, P->off.data(), sizeof(int64_t) * S},
+      {P->d_ld, P->ld.data(), sizeof(int64_t) * S},
+      {P->d_boff, P->boff.data(), sizeof(int64_t) * S},
+      {P->d_coff, P->coff.data(), sizeof(int64_t) * S},
+      {P->d_sklo, P->sklo.data(), sizeof(int64_t) * S},
+      {P->d_ccoff, ccoff.data(), sizeof(int64_t) * S},
+      {P->d_uptr, P->uptr.data(), sizeof(int32_t) * (S + 1)},
+      {P->d_usub, P->usub.data(), sizeof(int32_t) * P->usub.size()},
+      {P->d_urow, P->urow.data(), sizeof(int32_t) * P->usub.size()},
+      {P->d_ucol, P->ucol.data(), sizeof(int32_t) * P->usub.size()},
+      {P->d_uptr_subid, P->uptr_subid.data(), sizeof(int32_t) * (S + 1)},
+  };
+  for (const Up& u : ups)
+    if (cudaMemcpy(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(sfail(SPID_ERR_CUDA, "cudaMemcpy failed"));
+  if (cudaMemset(P->d_B, 0, sizeof(float) * P->b_elems) != cudaSuccess ||
+      cudaMemset(P->d_k, 0, sizeof(int32_t) * S) != cudaSuccess ||
+      cudaMemset(P->d_status, 0, sizeof(int)) != cudaSuccess ||
+      cudaMemset(P->d_cnt, 0, sizeof(int) * (S + 1)) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess)
+    return bail(sfail(SPID_ERR_CUDA, "cudaMemset failed"));
+  *out = P;
+  return SPID_OK;
+}
+
+spid_status spid_sub_plan_destroy(spid_sub_plan_t P) {
+  if (!P) return SPID_OK;
+  cudaSetDevice(P->device);
+  cudaDeviceSynchronize();
+  for (void* p : P->allocs) cudaFree(p);
+  delete P;
+  return SPID_OK;
+}
+
+spid_status spid_sub_plan_info(spid_sub_plan_t P, int64_t* mc_host, int64_t* workspace) {
+  if (!P) return sfail(SPID_ERR_INVALID_ARG, "plan is NULL");
+  if (mc_host)
+    for (int s = 0; s < P->S; ++s) mc_host[s] = P->mc[s];
+  if (workspace) *workspace = P->workspace;
+  return SPID_OK;
+}
+
+spid_status spid_sub_sample(spid_sub_plan_t P, const float* window, int32_t col0, int32_t ncols,
+                            spid_stream_t stream) {
+  spid_status st = check(P);
+  if (st != SPID_OK) return st;
+  st = check_window(window, "window");
+  if (st != SPID_OK) return st;
+  if (col0 < 0 || ncols < 0) return sfail(SPID_ERR_INVALID_ARG, "negative column range");
+  if (ncols == 0 || col0 >= P->n_max) return SPID_OK;
+  ncols = std::min(ncols, P->n_max - col0);
+  const int64_t max_work = (int64_t)P->mc_max * ncols;
+  SUB_CUDA(launch_subsample(P->args(), window, col0, ncols, max_work, (cudaStream_t)stream));
+  return SPID_OK;
+}
+
+spid_status spid_sub_finalize(spid_sub_plan_t P, spid_stream_t stream) {
+  spid_status st = check(P);
+  if (st != SPID_OK) return st;
+  SUB_CUDA(launch_subid_qr(P->args(), P->mc_max, P->n_max, (cudaStream_t)stream));
+  return SPID_OK;
+}
+
+static spid_status run_sub_error(spid_sub_plan_t P, const float* window, int32_t form,
+                                 float* out, double* err_dev, double* total_dev,
+                                 cudaStream_t cs) {
+  if (form == SPID_FORM_SPID) {
+    SUB_CUDA(launch_coarse_recon(P->args(), (int64_t)P->mc_max * P->n_max, cs));
+    SubErrArgs a;
+    a.a = P->args();
+    a.e = P->fold_args(window, out, err_dev, total_dev);
+    a.e.part = P->d_part_spid;
+    a.e.unit_ptr = P->d_uptr;
+    a.e.srows = P->d_mc;
+    a.window = window;
+    a.out = out;
+    SUB_CUDA(launch_spid_interp(a, P->spid_units, P->mc_max, P->e_max, cs));
+    return SPID_OK;
+  }
+  if (form == SPID_FORM_SUBID) {
+    // A(:, I_B) C_B: the CUDA-core error pass of the sketched ID on these factors
+    ErrArgs e = P->fold_args(window, out, err_dev, total_dev);
+    e.coff = P->d_ccoff;
+    e.unit_sub = P->d_usub;
+    e.unit_row0 = P->d_urow;
+    e.unit_col0 = P->d_ucol;
+    e.part = P->d_part_subid;
+    e.unit_ptr = P->d_uptr_subid;
+    SUB_CUDA(launch_error(e, (int)P->usub.size(), false, cs));
+    return SPID_OK;
+  }
+  return sfail(SPID_ERR_INVALID_ARG, "form must be SPID_FORM_SPID or SPID_FORM_SUBID");
+}
+
+spid_status spid_sub_error(spid_sub_plan_t P, const float* window, int32_t form,
+                           double* err_dev, double* total_dev, spid_stream_t stream) {
+  spid_status st = check(P);
+  if (st != SPID_OK) return st;
+  st = check_window(window, "window");
+  if (st != SPID_OK) return st;
+  return run_sub_error(P, window, form, nullptr, err_dev, total_dev, (cudaStream_t)stream);
+}
+
+spid_status spid_sub_reconstruct(spid_sub_plan_t P, const float* window, int32_t form, float* out,
+                                 spid_stream_t stream) {
+  spid_status st = check(P);
+  if (st != SPID_OK) return st;
+  st = check_window(out, "out");
+  if (st != SPID_OK) return st;
+  if (form == SPID_FORM_SUBID) {
+    st = check_window(window, "window");
+    if (st != SPID_OK) return st;
+  } else if (window) {
+    st = check_window(window, "window");
+    if (st != SPID_OK) return st;
+  }
+  return run_sub_error(P, window, form, out, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+spid_status spid_sub_get_factors(spid_sub_plan_t P, int32_t* k_host, int32_t* J_host,
+                                 float* C_host, float* Bskel_host, spid_stream_t stream) {
+  spid_status st = check(P);
+  if (st != SPID_OK) return st;
+  SUB_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  if (k_host) SUB_CUDA(cudaMemcpy(k_host, P->d_k, sizeof(int32_t) * P->S, cudaMemcpyDeviceToHost));
+  if (J_host)
+    SUB_CUDA(cudaMemcpy(J_host, P->d_J, sizeof(int32_t) * P->S * P->k_max, cudaMemcpyDeviceToHost));
+  if (C_host) SUB_CUDA(cudaMemcpy(C_host, P->d_C, sizeof(float) * P->c_elems, cudaMemcpyDeviceToHost));
+  if (Bskel_host)
+    SUB_CUDA(cudaMemcpy(Bskel_host, P->d_Bsk, sizeof(float) * P->sk_elems, cudaMemcpyDeviceToHost));
+  return SPID_OK;
+}
+
+spid_status spid_sub_get_coarse(spid_sub_plan_t P, float* B_host, spid_stream_t stream) {
+  spid_status st = check(P);
+  if (st != SPID_OK) return st;
+  if (!B_host) return sfail(SPID_ERR_INVALID_ARG, "B_host is NULL");
+  SUB_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  SUB_CUDA(cudaMemcpy(B_host, P->d_B, sizeof(float) * P->b_elems, cudaMemcpyDeviceToHost));
+  return SPID_OK;
+}
+
+spid_status spid_sub_device_status(spid_sub_plan_t P, spid_stream_t stream) {
+  spid_status st = check(P);
+  if (st != SPID_OK) return st;
+  SUB_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  int v = 0;
+  SUB_CUDA(cudaMemcpy(&v, P->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  SUB_CUDA(cudaMemset(P->d_status, 0, sizeof(int)));
+  if (v & kStatusNonfinite) return sfail(SPID_ERR_NONFINITE, "non-finite value in a coarse matrix");
+  return SPID_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+// subid_internal.cuh -- types shared by the host side and the kernels of the
+// coarse-grid (subsampled / single-pass) ID: Section 2 SubID and SPID,
+// Algorithms 2 and 3, Section 5.2.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spid_internal.cuh"
+
+namespace spid {
+
+constexpr int kSubMaxK = 64;          // k_max bound (coefficient solve keeps k values per column)
+constexpr int kSubMaxN = 1024;        // window length bound (one residual norm per column in smem)
+constexpr int kSubMaxCoarse = 40960;  // coarse rows bound (one column of B in shared memory)
+constexpr int kSubUnitElems = 32768;  // target fine elements per SPID error unit
+
+// One subdomain box and its coarse grid.  Coarse index a of an axis with e
+// points and interval s is min(a s, e - 1); count c = (e - 1) / s + 1, plus one
+// when (e - 1) % s != 0 (the end point is kept).
+struct SubBox {
+  int32_t nq, ez, ey, ex;     // QoIs, points along z, y, x
+  int32_t cz, cy, cx;         // coarse points along z, y, x
+  int32_t sz, sy, sx;         // intervals
+  int32_t zc;                 // z planes per SPID error unit
+  int32_t zblocks;            // SPID error units per column = ceil(ez / zc)
+};
+
+struct SubArgs {
+  const SubBox* box;          // [S]
+  const int32_t* m;           // [S] fine rows
+  const int32_t* n;           // [S]
+  const int32_t* mc;          // [S] coarse rows
+  const int64_t* off;         // [S] window offsets
+  const int64_t* ld;          // [S]
+  const int64_t* boff;        // [S] B_s / W_s at boff[s], mc x n column-major
+  const int64_t* coff;        // [S] sum of n before s (R, C at k_max * coff[s])
+  const int64_t* sklo;        // [S] sum of mc before s (Bskel at k_max * sklo[s])
+  float* B;                   // gathered coarse matrices
+  float* W;                   // MGS working copy; after finalize, the coarse reconstruction
+  float* R;                   // k_max x n_s row-major per subdomain
+  float* C;                   // k_max x n_s row-major per subdomain
+  float* Bskel;               // mc x k_max column-major per subdomain
+  int32_t* J;                 // [S][k_max]
+  int32_t* k;                 // [S]
+  int32_t k_max;
+  int32_t S;
+  double tol;
+  int* status;
+};
+
+// SPID error units: subdomain s owns units [uptr[s], uptr[s+1]), unit
+// uptr[s] + j * zblocks + b covers column j and z planes [b zc, b zc + zc).
+struct SubErrArgs {
+  SubArgs a;
+  ErrArgs e;                  // fold: m, n, k, part, unit_ptr(= uptr), counters, totals, srows
+  const float* window;
+  float* out;                 // SPID reconstruction or nullptr
+};
+
+cudaError_t launch_subsample(const SubArgs& a, const float* window, int col0, int ncols,
+                             int64_t max_work, cudaStream_t st);
+size_t subid_qr_smem_bytes(int mc_max, int n_max, int k_max);
+cudaError_t launch_subid_qr(const SubArgs& a, int mc_max, int n_max, cudaStream_t st);
+cudaError_t launch_coarse_recon(const SubArgs& a, int64_t max_work, cudaStream_t st);
+size_t spid_interp_smem_bytes(int mc_max, int e_max);
+cudaError_t launch_spid_interp(const SubErrArgs& a, int64_t units, int mc_max, int e_max,
+                               cudaStream_t st);
+
+}  // namespace spid

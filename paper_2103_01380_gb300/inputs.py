@@ -377,3 +377,13 @@ def box_window(boxes, n, seed: int, dtype=np.float32, noise: float = 0.0, **kw) 
     w = pack_blocks(blocks, dtype=dtype)
     w.meta["boxes"] = np.asarray(boxes, dtype=np.int32).reshape(-1, 4)
     return w
+
+
+def tgv3d_u1(grid: int, t: np.ndarray, nu: float = 0.01, dtype=np.float32) -> np.ndarray:
+    """u1 of the 3D TGV alone (Section 5.2 initial condition, no Fourier modes)
+    on the whole grid^3 box: sin x cos y cos z exp(-3 nu t), rows (z, y, x)."""
+    h = 2.0 * np.pi / grid
+    c = np.arange(grid) * h
+    Z, Yg, X = np.meshgrid(c, c, c, indexing="ij")
+    space = (np.sin(X) * np.cos(Yg) * np.cos(Z)).reshape(-1)
+    return np.outer(space, np.exp(-3.0 * nu * np.asarray(t))).astype(dtype)

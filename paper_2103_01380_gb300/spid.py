@@ -30,7 +30,12 @@ EXPORTS = ["spid_plan_create", "spid_plan_destroy", "spid_plan_info", "spid_sket
            "spid_finalize", "spid_error", "spid_reconstruct", "spid_get_factors",
            "spid_get_sketch", "spid_device_status", "spid_omega", "spid_philox",
            "spid_compression_factor", "spid_status_string", "spid_last_error",
-           "spid_sketch_fp32_noalloc"]
+           "spid_sketch_fp32_noalloc",
+           "spid_sub_plan_create", "spid_sub_plan_destroy", "spid_sub_plan_info",
+           "spid_sub_sample", "spid_sub_finalize", "spid_sub_error", "spid_sub_reconstruct",
+           "spid_sub_get_factors", "spid_sub_get_coarse", "spid_sub_device_status"]
+FORM_SPID = 0
+FORM_SUBID = 1
 
 
 class SpidError(RuntimeError):
@@ -51,6 +56,18 @@ class _Desc(ctypes.Structure):
                 ("precision", ctypes.c_int32),
                 ("flags", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64)]
+
+
+class _SubDesc(ctypes.Structure):
+    _fields_ = [("num_sub", ctypes.c_int32),
+                ("box", ctypes.POINTER(ctypes.c_int32)),
+                ("n", ctypes.POINTER(ctypes.c_int32)),
+                ("off", ctypes.POINTER(ctypes.c_int64)),
+                ("ld", ctypes.POINTER(ctypes.c_int64)),
+                ("stride", ctypes.c_int32 * 3),
+                ("k_max", ctypes.c_int32),
+                ("tol", ctypes.c_double),
+                ("flags", ctypes.c_uint32)]
 
 
 _lib = None
@@ -87,6 +104,16 @@ def load_library(path: str = LIB_PATH):
             "spid_status_string": ([c.c_int], c.c_char_p),
             "spid_last_error": ([], c.c_char_p),
             "spid_sketch_fp32_noalloc": ([vp, i32, i32, i64, i32, u64, vp, i32, vp], c.c_int),
+            "spid_sub_plan_create": ([c.POINTER(_SubDesc), c.POINTER(vp)], c.c_int),
+            "spid_sub_plan_destroy": ([vp], c.c_int),
+            "spid_sub_plan_info": ([vp, vp, c.POINTER(i64)], c.c_int),
+            "spid_sub_sample": ([vp, vp, i32, i32, vp], c.c_int),
+            "spid_sub_finalize": ([vp, vp], c.c_int),
+            "spid_sub_error": ([vp, vp, i32, vp, vp, vp], c.c_int),
+            "spid_sub_reconstruct": ([vp, vp, i32, vp, vp], c.c_int),
+            "spid_sub_get_factors": ([vp, vp, vp, vp, vp, vp], c.c_int),
+            "spid_sub_get_coarse": ([vp, vp, vp], c.c_int),
+            "spid_sub_device_status": ([vp, vp], c.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -221,6 +248,103 @@ class Plan:
 
     def device_status(self, stream=None) -> int:
         return int(load_library().spid_device_status(self._h, _stream_handle(stream)))
+
+
+class SubPlan:
+    """Coarse-grid column ID (Section 2 SubID / SPID, Algorithms 2-3) over a
+    window of boxes.  box: [S, 4] (nq, ez, ey, ex) per subdomain (rows of a box
+    in (q, z, y, x) order, x fastest); stride: coarse interval (sz, sy, sx)."""
+
+    def __init__(self, box, n, off, ld, stride, k_max: int, tol: float = 0.0):
+        lib = load_library()
+        self.box = np.ascontiguousarray(box, dtype=np.int32).reshape(-1, 4)
+        self.S = int(self.box.shape[0])
+        self.n = np.ascontiguousarray(np.broadcast_to(n, (self.S,)), dtype=np.int32)
+        self.off = np.ascontiguousarray(off, dtype=np.int64)
+        self.ld = np.ascontiguousarray(ld, dtype=np.int64)
+        self.m = self.box.prod(axis=1).astype(np.int64)
+        self.k_max = int(k_max)
+        d = _SubDesc()
+        d.num_sub = self.S
+        d.box = self.box.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        d.n = self.n.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        d.off = self.off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        d.ld = self.ld.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        for i in range(3):
+            d.stride[i] = int(stride[i])
+        d.k_max = self.k_max
+        d.tol = float(tol)
+        d.flags = 0
+        h = ctypes.c_void_p()
+        _check(lib.spid_sub_plan_create(ctypes.byref(d), ctypes.byref(h)), "spid_sub_plan_create")
+        self._h = h
+        mc = np.zeros(self.S, dtype=np.int64)
+        ws = ctypes.c_int64()
+        _check(lib.spid_sub_plan_info(h, mc.ctypes.data, ctypes.byref(ws)), "spid_sub_plan_info")
+        self.mc, self.workspace_bytes = mc, int(ws.value)
+
+    @classmethod
+    def for_window(cls, win, stride, **kw) -> "SubPlan":
+        return cls(win.meta["boxes"], win.n, win.off, win.ld, stride, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().spid_sub_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sample(self, window, col0: int = 0, ncols: int | None = None, stream=None):
+        if ncols is None:
+            ncols = int(self.n.max()) - col0
+        _check(load_library().spid_sub_sample(self._h, _ptr(window), int(col0), int(ncols),
+                                              _stream_handle(stream)), "spid_sub_sample")
+
+    def finalize(self, stream=None):
+        _check(load_library().spid_sub_finalize(self._h, _stream_handle(stream)),
+               "spid_sub_finalize")
+
+    def error(self, window, form: int = FORM_SPID, err=None, total=None, stream=None):
+        _check(load_library().spid_sub_error(self._h, _ptr(window), int(form), _ptr(err),
+                                             _ptr(total), _stream_handle(stream)),
+               "spid_sub_error")
+
+    def reconstruct(self, window, out, form: int = FORM_SPID, stream=None):
+        _check(load_library().spid_sub_reconstruct(self._h, _ptr(window), int(form), _ptr(out),
+                                                   _stream_handle(stream)),
+               "spid_sub_reconstruct")
+
+    def factors(self, stream=None):
+        """(k [S], J [S, k_max], C list of k_max x n_s, Bskel list of mc_s x k_max)."""
+        k = np.zeros(self.S, dtype=np.int32)
+        J = np.zeros((self.S, self.k_max), dtype=np.int32)
+        C = np.zeros(self.k_max * int(self.n.sum()), dtype=np.float32)
+        Bs = np.zeros(self.k_max * int(self.mc.sum()), dtype=np.float32)
+        _check(load_library().spid_sub_get_factors(self._h, k.ctypes.data, J.ctypes.data,
+                                                   C.ctypes.data, Bs.ctypes.data,
+                                                   _stream_handle(stream)), "spid_sub_get_factors")
+        coff = np.concatenate([[0], np.cumsum(self.n)]) * self.k_max
+        soff = np.concatenate([[0], np.cumsum(self.mc)]) * self.k_max
+        Cs = [C[coff[s]:coff[s + 1]].reshape(self.k_max, int(self.n[s])) for s in range(self.S)]
+        Bk = [Bs[soff[s]:soff[s + 1]].reshape(self.k_max, int(self.mc[s])).T
+              for s in range(self.S)]
+        return k, J, Cs, Bk
+
+    def coarse(self, stream=None):
+        """List of the gathered B_s (mc_s x n_s)."""
+        B = np.zeros(int((self.mc * self.n).sum()), dtype=np.float32)
+        _check(load_library().spid_sub_get_coarse(self._h, B.ctypes.data, _stream_handle(stream)),
+               "spid_sub_get_coarse")
+        boff = np.concatenate([[0], np.cumsum(self.mc * self.n)])
+        return [B[boff[s]:boff[s + 1]].reshape(int(self.n[s]), int(self.mc[s])).T
+                for s in range(self.S)]
+
+    def device_status(self, stream=None) -> int:
+        return int(load_library().spid_sub_device_status(self._h, _stream_handle(stream)))
 
 
 def omega(seed: int, r0: int, nrows: int, l: int, precision: str, out, stream=None):
