@@ -255,6 +255,8 @@ def run_workload(args):
         line = _run_spectrum(args, torch, inputs, spid)
     elif args.workload == "uneven4096":
         line = _run_uneven(args, torch, inputs, spid)
+    elif args.workload == "coarse_tgv3d64":
+        line = _run_coarse(args, torch, inputs, spid)
     else:
         line = _run_insitu(args, torch, inputs, spid)
     line.update({"metric": METRIC, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
@@ -267,6 +269,96 @@ def run_workload(args):
                             "traffic": None}
     print(json.dumps(line))
     return 0
+
+
+def _coarse_stage_times(torch, plan, window, steps, warmup, err, tot, form):
+    """Mean sample / finalize / error times (ms) of the coarse-grid ID."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        plan.sample(window)
+        plan.finalize()
+        plan.error(window, form, err, tot)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for i in range(steps):
+        ev[i][0].record(stream)
+        plan.sample(window)
+        ev[i][1].record(stream)
+        plan.finalize()
+        ev[i][2].record(stream)
+        plan.error(window, form, err, tot)
+        ev[i][3].record(stream)
+    torch.cuda.synchronize()
+    return tuple(statistics.mean(e[a].elapsed_time(e[a + 1]) for e in ev) for a in range(3))
+
+
+def _run_coarse(args, torch, inputs, spid):
+    """Coarse-grid column ID (Section 2 SubID / SPID, Algorithms 2-3; Section
+    5.2): the bench window (64 boxes of 16^3 x 5 QoIs, n = 512) at coarse
+    intervals 3 and 5, adaptive tol 1e-3 on B, and the paper's E3 case (64^3
+    TGV u1, 100 snapshots, interval 3)."""
+    win = make_window(0, None)
+    w = torch.from_numpy(win.data).cuda()
+    nbytes = float(win.nbytes_payload())
+    boxes = np.tile(np.array([5, 16, 16, 16], dtype=np.int32), (win.num_sub, 1))
+    err = torch.zeros(2 * win.num_sub, dtype=torch.float64, device="cuda")
+    tot = torch.zeros(4, dtype=torch.float64, device="cuda")
+    study = {}
+    for stride in (3, 5):
+        plan = spid.SubPlan(boxes, win.n, win.off, win.ld, (stride,) * 3, k_max=20, tol=1e-3)
+        res = {"coarse_rows": int(plan.mc[0]), "fine_rows": int(win.m[0])}
+        for form, tag in ((spid.FORM_SPID, "spid"), (spid.FORM_SUBID, "subid")):
+            sa, fi, er = _coarse_stage_times(torch, plan, w, args.steps, args.warmup, err, tot,
+                                             form)
+            t = tot.cpu().numpy()
+            res[tag] = {"value": nbytes / ((sa + fi + er) / 1e3) / 1e9,
+                        "single_pass_gbs": nbytes / ((sa + fi) / 1e3) / 1e9,
+                        "stages_ms": {"sample": sa, "finalize": fi, "error": er},
+                        "error_gbs": nbytes / (er / 1e3) / 1e9,
+                        "rel_err": float(np.sqrt(t[0] / t[1])),
+                        "compression_factor": float(t[2] / t[3])}
+        k, _, _, _ = plan.factors()
+        res["k_mean"], res["k_max"] = float(np.mean(k)), int(np.max(k))
+        study[f"interval{stride}"] = res
+        plan.close()
+    # E3 (Section 5.2): 64^3 TGV u1, n = 100, interval 3, rank decided at tol 1e-3
+    t = np.linspace(0.0, 10.0, 100)
+    u1 = inputs.tgv3d_u1(64, t)
+    e3 = inputs.pack_blocks([u1])
+    we = torch.from_numpy(e3.data).cuda()
+    plan = spid.SubPlan([[1, 64, 64, 64]], e3.n, e3.off, e3.ld, (3, 3, 3), k_max=4, tol=1e-3)
+    err1 = torch.zeros(2, dtype=torch.float64, device="cuda")
+    sa, fi, er = _coarse_stage_times(torch, plan, we, args.steps, args.warmup, err1, tot,
+                                     spid.FORM_SPID)
+    tt = tot.cpu().numpy()
+    k, _, _, _ = plan.factors()
+    e3b = float(e3.nbytes_payload())
+    study["e3_tgv64_u1_interval3"] = {
+        "k": int(k[0]), "rel_err": float(np.sqrt(tt[0] / tt[1])),
+        "compression_factor": float(tt[2] / tt[3]),
+        "paper": "interval 3: ~2% error, compression ~2400",
+        "stages_ms": {"sample": sa, "finalize": fi, "error": er},
+        "single_pass_gbs": e3b / ((sa + fi) / 1e3) / 1e9}
+    plan.close()
+    main = study["interval3"]["spid"]
+    line = {"value": main["value"], "ms_per_step": nbytes / main["value"] / 1e6,
+            "dtype": "f32", "config": {
+                "workload": "coarse-grid SPID (trilinear M) of the TGV+Fourier 64^3 window: "
+                            "64 boxes of 16^3 x 5 QoIs, n=512, coarse interval 3 "
+                            "(m_c = 6^3 x 5 = 1080), adaptive tol 1e-3 on B, k_max=20",
+                "l2": "inputs (2.68 GB) larger than L2; no flush"},
+            "study": study}
+    if not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        for s in (0, win.num_sub - 1):
+            oracle.subid(win.block(s).astype(np.float64), (5, 16, 16, 16), (3, 3, 3), 20, 1e-3,
+                         2.0 ** -24)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 2 * 4.0 * int(win.m[0]) * int(win.n[0]) / dt / 1e9,
+                                "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                "sample": "subdomains 0 and 63, interval 3 (FP64 oracle)"}
+    return line
 
 
 def _run_spectrum(args, torch, inputs, spid):
@@ -458,7 +550,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--workload", default="tgv3d64",
-                    choices=["tgv3d64", "spectrum256", "uneven4096", "insitu256"],
+                    choices=["tgv3d64", "spectrum256", "uneven4096", "insitu256",
+                             "coarse_tgv3d64"],
                     help="tgv3d64 is the bench workload; the others print their own line")
     ap.add_argument("--microbatch", type=int, default=64, help="insitu256: columns per call")
     ap.add_argument("--wave-gb", type=float, default=48.0, help="uneven4096: GB per wave")

@@ -21,7 +21,7 @@ namespace spid {
 
 namespace {
 
-constexpr int kQrThreads = 512;
+constexpr int kQrThreads = 1024;
 constexpr int kQrWarps = kQrThreads / 32;
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -39,24 +39,38 @@ __global__ void __launch_bounds__(256) subsample_kernel(const SubArgs a, const f
   if (c1 <= col0) return;
   const SubBox b = a.box[s];
   const int mc = a.mc[s];
-  const int64_t work = (int64_t)mc * (c1 - col0);
+  const int work = mc * (c1 - col0);   // < 2^31: m_c <= 40960, n <= 1024
   const float* A = window + a.off[s];
   const int64_t ld = a.ld[s];
   float* B = a.B + a.boff[s];
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < work;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int j = col0 + (int)(e / mc);
-    const int cr = (int)(e % mc);
-    int t = cr;
-    const int cx = t % b.cx;
-    t /= b.cx;
-    const int cy = t % b.cy;
-    t /= b.cy;
-    const int cz = t % b.cz;
-    const int q = t / b.cz;
-    const int64_t r = (((int64_t)q * b.ez + coarse_index(cz, b.sz, b.ez)) * b.ey +
-                       coarse_index(cy, b.sy, b.ey)) * b.ex + coarse_index(cx, b.sx, b.ex);
-    B[(int64_t)j * mc + cr] = A[(int64_t)j * ld + r];
+  // four independent gathers in flight per thread
+  const int stride = gridDim.x * blockDim.x;
+  for (int e0 = blockIdx.x * blockDim.x + threadIdx.x; e0 < work; e0 += 4 * stride) {
+    float v[4];
+    int64_t dst[4];
+#pragma unroll
+    for (int uu = 0; uu < 4; ++uu) {
+      const int e = e0 + uu * stride;
+      dst[uu] = -1;
+      if (e < work) {
+        const int jj = (int)fdiv((uint32_t)e, b.div_mc);
+        const int j = col0 + jj;
+        const int cr = e - jj * mc;
+        const int t1 = (int)fdiv((uint32_t)cr, b.div_cx);
+        const int cx = cr - t1 * b.cx;
+        const int t2 = (int)fdiv((uint32_t)t1, b.div_cy);
+        const int cy = t1 - t2 * b.cy;
+        const int q = (int)fdiv((uint32_t)t2, b.div_cz);
+        const int cz = t2 - q * b.cz;
+        const int64_t r = (((int64_t)q * b.ez + coarse_index(cz, b.sz, b.ez)) * b.ey +
+                           coarse_index(cy, b.sy, b.ey)) * b.ex + coarse_index(cx, b.sx, b.ex);
+        v[uu] = __ldg(A + (int64_t)j * ld + r);
+        dst[uu] = (int64_t)j * mc + cr;
+      }
+    }
+#pragma unroll
+    for (int uu = 0; uu < 4; ++uu)
+      if (dst[uu] >= 0) B[dst[uu]] = v[uu];
   }
 }
 
@@ -111,17 +125,27 @@ __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a
   int32_t* J = a.J + (int64_t)s * k_max;
 
   for (int64_t e = tid; e < (int64_t)k_max * n; e += kQrThreads) R[e] = 0.f;
-  // W = B and the initial column norms; non-finite check
+  // initial column norms (B stays untouched: step 0 reads it and writes the
+  // working copy W); non-finite check
   bool bad = false;
   for (int c = warp; c < n; c += kQrWarps) {
-    float acc = 0.f;
-    for (int i = lane; i < mc; i += 32) {
-      const float x = B[(int64_t)c * mc + i];
-      W[(int64_t)c * mc + i] = x;
-      acc = fmaf(x, x, acc);
+    const float* col = B + (int64_t)c * mc;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int i = lane;
+    for (; i + 96 < mc; i += 128) {
+      const float x0 = col[i], x1 = col[i + 32], x2 = col[i + 64], x3 = col[i + 96];
+      a0 = fmaf(x0, x0, a0);
+      a1 = fmaf(x1, x1, a1);
+      a2 = fmaf(x2, x2, a2);
+      a3 = fmaf(x3, x3, a3);
+      bad |= !isfinite(x0) || !isfinite(x1) || !isfinite(x2) || !isfinite(x3);
+    }
+    for (; i < mc; i += 32) {
+      const float x = col[i];
+      a0 = fmaf(x, x, a0);
       bad |= !isfinite(x);
     }
-    acc = warp_sum(acc);
+    const float acc = warp_sum((a0 + a1) + (a2 + a3));
     if (lane == 0) {
       nu[c] = acc;
       step[c] = -1;
@@ -184,8 +208,9 @@ __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a
     const float rjj = sqrtf(nu_p);
     if (j == 0) r00 = rjj;
     else if (!(rjj > 0x1p-23f * r00)) break;   // rank guard |R_jj| > 2 u |R_00|, u = 2^-24
-    // ---- q_j = w_p / R_jj
-    for (int i = tid; i < mc; i += kQrThreads) qv[i] = W[(int64_t)p * mc + i] / rjj;
+    // ---- q_j = w_p / R_jj  (step 0 reads B itself)
+    const float* src = (j == 0) ? B : W;
+    for (int i = tid; i < mc; i += kQrThreads) qv[i] = src[(int64_t)p * mc + i] / rjj;
     if (tid == 0) {
       J[j] = p;
       Js[j] = p;
@@ -196,17 +221,38 @@ __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a
     // ---- modified Gram-Schmidt against q_j, norms from the updated columns
     for (int c = warp; c < n; c += kQrWarps) {
       if (step[c] != -1) continue;   // warp-uniform
+      const float* x = src + (int64_t)c * mc;
       float* w = W + (int64_t)c * mc;
-      float d = 0.f;
-      for (int i = lane; i < mc; i += 32) d = fmaf(qv[i], w[i], d);
-      d = warp_sum(d);
-      float acc = 0.f;
-      for (int i = lane; i < mc; i += 32) {
-        const float v = fmaf(-d, qv[i], w[i]);
-        w[i] = v;
-        acc = fmaf(v, v, acc);
+      float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+      int i = lane;
+      for (; i + 96 < mc; i += 128) {
+        d0 = fmaf(qv[i], x[i], d0);
+        d1 = fmaf(qv[i + 32], x[i + 32], d1);
+        d2 = fmaf(qv[i + 64], x[i + 64], d2);
+        d3 = fmaf(qv[i + 96], x[i + 96], d3);
       }
-      acc = warp_sum(acc);
+      for (; i < mc; i += 32) d0 = fmaf(qv[i], x[i], d0);
+      const float d = warp_sum((d0 + d1) + (d2 + d3));
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      i = lane;
+      for (; i + 96 < mc; i += 128) {
+        const float v0 = fmaf(-d, qv[i], x[i]), v1 = fmaf(-d, qv[i + 32], x[i + 32]);
+        const float v2 = fmaf(-d, qv[i + 64], x[i + 64]), v3 = fmaf(-d, qv[i + 96], x[i + 96]);
+        w[i] = v0;
+        w[i + 32] = v1;
+        w[i + 64] = v2;
+        w[i + 96] = v3;
+        a0 = fmaf(v0, v0, a0);
+        a1 = fmaf(v1, v1, a1);
+        a2 = fmaf(v2, v2, a2);
+        a3 = fmaf(v3, v3, a3);
+      }
+      for (; i < mc; i += 32) {
+        const float v = fmaf(-d, qv[i], x[i]);
+        w[i] = v;
+        a0 = fmaf(v, v, a0);
+      }
+      const float acc = warp_sum((a0 + a1) + (a2 + a3));
       if (lane == 0) {
         R[(int64_t)j * n + c] = d;
         nu[c] = acc;
@@ -277,93 +323,182 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
   s = t;
 }
 
+// A_hat = M G per unit (subdomain, column, z block), without intermediate
+// stages: a task is one (y, x) position -- four consecutive x of one row when
+// ex is a multiple of four, read as one 16-byte vector -- and a run of up to
+// kZRun consecutive fine z planes.  The thread computes the position's
+// bilinear (y, x) weights and corner offsets once, evaluates the bilinear
+// value on each coarse z plane its run crosses (the upper plane of one cell
+// is the lower plane of the next), and each fine element is then one lerp in
+// z.  All of a task's A loads for one QoI are issued before any is used.
+// One CTA walks a contiguous range of units; the subdomain lookup and its
+// per-axis cell tables are refreshed only when the range crosses into the
+// next subdomain, and the only barriers are around staging G(:, j).
+constexpr int kZRun = 4;
+
 template <bool WRITE>
-__global__ void __launch_bounds__(256) spid_interp_kernel(const SubErrArgs args, int mc_max,
-                                                          int e_max) {
+__global__ void __launch_bounds__(256, 3) spid_interp_kernel(const SubErrArgs args, int mc_max,
+                                                          int e_max, int units_per_cta,
+                                                          int total_units) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[2][8];
   __shared__ int last_sub;
   const SubArgs& a = args.a;
   const ErrArgs& e = args.e;
   float* g = reinterpret_cast<float*>(smem_raw);                  // G(:, j) [mc]
-  int32_t* tab_a = reinterpret_cast<int32_t*>(g + mc_max);        // [3][e_max] cells z, y, x
-  float* tab_w = reinterpret_cast<float*>(tab_a + 3 * e_max);     // [3][e_max] weights
+  int32_t* tab_a = reinterpret_cast<int32_t*>(g + ((mc_max + 3) & ~3));   // [3][e_max]
+  float* tab_w = reinterpret_cast<float*>(tab_a + 3 * e_max);             // [3][e_max]
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int u = blockIdx.x;
-  // subdomain of unit u (binary search over the unit prefix)
-  int lo = 0, hi = a.S;
+  const int nthr = blockDim.x;
+  const int u0 = blockIdx.x * units_per_cta;
+  const int u1 = min(u0 + units_per_cta, total_units);
+  if (u0 >= u1) return;
+  int lo = 0, hi = a.S;                   // subdomain of the first unit
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
-    if (e.unit_ptr[mid] <= u) lo = mid; else hi = mid;
+    if (e.unit_ptr[mid] <= u0) lo = mid; else hi = mid;
   }
-  const int s = lo;
-  const SubBox b = a.box[s];
-  const int mc = a.mc[s];
-  const int rel = u - e.unit_ptr[s];
-  const int j = rel / b.zblocks;
-  const int z0 = (rel % b.zblocks) * b.zc, z1 = min(b.ez, z0 + b.zc);
-  const float* G = a.W + a.boff[s] + (int64_t)j * mc;
-  for (int i = tid; i < mc; i += blockDim.x) g[i] = G[i];
-  for (int x = tid; x < b.ez; x += blockDim.x) axis_cell(x, b.ez, b.sz, b.cz, tab_a[x], tab_w[x]);
-  for (int x = tid; x < b.ey; x += blockDim.x)
-    axis_cell(x, b.ey, b.sy, b.cy, tab_a[e_max + x], tab_w[e_max + x]);
-  for (int x = tid; x < b.ex; x += blockDim.x)
-    axis_cell(x, b.ex, b.sx, b.cx, tab_a[2 * e_max + x], tab_w[2 * e_max + x]);
-  __syncthreads();
-  const int64_t colbase = a.off[s] + (int64_t)j * a.ld[s];
+  int s = lo;
+  int s_tab = -1;
+  int s_end = e.unit_ptr[s + 1];
   const bool have_a = args.window != nullptr;
-  const float* A = have_a ? args.window + colbase : nullptr;
-  const int plane = b.ey * b.ex;
-  float se = 0.f, ce = 0.f, sa = 0.f, ca = 0.f;
-  for (int pxy = tid; pxy < plane; pxy += blockDim.x) {
-    const int y = pxy / b.ex, x = pxy - (pxy / b.ex) * b.ex;
-    const int ay = tab_a[e_max + y], ax = tab_a[2 * e_max + x];
-    const float wy = tab_w[e_max + y], wx = tab_w[2 * e_max + x];
-    const int ay1 = min(ay + 1, b.cy - 1), ax1 = min(ax + 1, b.cx - 1);
-    const float w00 = (1.f - wy) * (1.f - wx), w01 = (1.f - wy) * wx;
-    const float w10 = wy * (1.f - wx), w11 = wy * wx;
-    float le = 0.f, la = 0.f;
-    for (int q = 0; q < b.nq; ++q) {
-      for (int z = z0; z < z1; ++z) {
-        const int az = tab_a[z], az1 = min(az + 1, b.cz - 1);
-        const float wz = tab_w[z];
-        const int p0 = (q * b.cz + az) * b.cy, p1 = (q * b.cz + az1) * b.cy;
-        const float lo_z = w00 * g[(p0 + ay) * b.cx + ax] + w01 * g[(p0 + ay) * b.cx + ax1] +
-                           w10 * g[(p0 + ay1) * b.cx + ax] + w11 * g[(p0 + ay1) * b.cx + ax1];
-        const float hi_z = w00 * g[(p1 + ay) * b.cx + ax] + w01 * g[(p1 + ay) * b.cx + ax1] +
-                           w10 * g[(p1 + ay1) * b.cx + ax] + w11 * g[(p1 + ay1) * b.cx + ax1];
-        const float v = fmaf(wz, hi_z - lo_z, lo_z);
-        const int64_t r = ((int64_t)q * b.ez + z) * plane + pxy;
-        const float av = have_a ? __ldg(A + r) : 0.f;   // reconstruction alone needs no A
-        const float d = av - v;
-        le = fmaf(d, d, le);
-        la = fmaf(av, av, la);
-        if (WRITE) args.out[colbase + r] = v;
+  for (int u = u0; u < u1; ++u) {
+    while (u >= s_end) s_end = e.unit_ptr[++s + 1];
+    const SubBox b = a.box[s];
+    const int mc = a.mc[s];
+    const int rel = u - e.unit_ptr[s];
+    const int j = rel / b.zblocks;
+    const int z0 = (rel - j * b.zblocks) * b.zc, z1 = min(b.ez, z0 + b.zc);
+    const int plane = b.ey * b.ex;
+    const int cplane = b.cy * b.cx;
+    __syncthreads();   // the previous unit is done with g and the tables
+    const float* G = a.W + a.boff[s] + (int64_t)j * mc;
+    for (int i = tid; i < mc; i += nthr) g[i] = G[i];
+    if (s != s_tab) {
+      for (int x = tid; x < b.ez; x += nthr) axis_cell(x, b.ez, b.sz, b.cz, tab_a[x], tab_w[x]);
+      for (int x = tid; x < b.ey; x += nthr)
+        axis_cell(x, b.ey, b.sy, b.cy, tab_a[e_max + x], tab_w[e_max + x]);
+      for (int x = tid; x < b.ex; x += nthr)
+        axis_cell(x, b.ex, b.sx, b.cx, tab_a[2 * e_max + x], tab_w[2 * e_max + x]);
+      s_tab = s;
+    }
+    __syncthreads();
+    const int64_t colbase = a.off[s] + (int64_t)j * a.ld[s];
+    const bool vec = (b.ex & 3) == 0;               // four x of one row per 16-byte vector
+    const int W = vec ? 4 : 1;                       // fine x points per task
+    const int npos = plane / W;
+    const int nzr = (z1 - z0 + kZRun - 1) / kZRun;   // z runs
+    float se = 0.f, ce = 0.f, sa = 0.f, ca = 0.f;
+    for (int task = tid; task < npos * nzr; task += nthr) {
+      const int zr = task / npos, pos = task - zr * npos;
+      const int yx = pos * W;
+      const int y = (int)fdiv((uint32_t)yx, b.div_ex), x0 = yx - y * b.ex;
+      const int ay = tab_a[e_max + y], ay1 = min(ay + 1, b.cy - 1);
+      const float wy = tab_w[e_max + y];
+      // per fine x of the task: the four (y, x) corners and their weights
+      int o00[4], o01[4];
+      float c00[4], c01[4], c10[4], c11[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int xx = min(x0 + t, b.ex - 1);
+        const int ax = tab_a[2 * e_max + xx], ax1 = min(ax + 1, b.cx - 1);
+        const float wx = tab_w[2 * e_max + xx];
+        o00[t] = ay * b.cx + ax;
+        o01[t] = ay * b.cx + ax1;
+        c00[t] = (1.f - wy) * (1.f - wx);
+        c01[t] = (1.f - wy) * wx;
+        c10[t] = wy * (1.f - wx);
+        c11[t] = wy * wx;
+      }
+      const int dy = (ay1 - ay) * b.cx;              // row offset to the y + 1 corners
+      const int zs = z0 + zr * kZRun, ze = min(z1, zs + kZRun);
+      for (int q = 0; q < b.nq; ++q) {
+        // this task's A for QoI q: up to kZRun vectors, all in flight first
+        float4 av[kZRun];
+        const float* Aq = have_a ? args.window + colbase + ((int64_t)q * b.ez) * plane + yx
+                                 : nullptr;
+#pragma unroll
+        for (int r = 0; r < kZRun; ++r) {
+          const int z = zs + r;
+          if (have_a && z < ze) {
+            av[r] = vec ? __ldg(reinterpret_cast<const float4*>(Aq + (int64_t)z * plane))
+                        : make_float4(__ldg(Aq + (int64_t)z * plane), 0.f, 0.f, 0.f);
+          } else {
+            av[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
+        const float* gq = g + q * b.cz * cplane;
+        float lo4[4], hi4[4];
+        int cur = -1;
+        float le = 0.f, la = 0.f;
+#pragma unroll
+        for (int r = 0; r < kZRun; ++r) {
+          const int z = zs + r;
+          if (z >= ze) break;
+          const int az = tab_a[z];
+          const float wz = tab_w[z];
+          if (az != cur) {
+            const int az1 = min(az + 1, b.cz - 1);
+            const float* p1 = gq + az1 * cplane;
+            if (az == cur + 1 && cur >= 0) {
+#pragma unroll
+              for (int t = 0; t < 4; ++t) lo4[t] = hi4[t];
+            } else {
+              const float* p0 = gq + az * cplane;
+#pragma unroll
+              for (int t = 0; t < 4; ++t)
+                lo4[t] = c00[t] * p0[o00[t]] + c01[t] * p0[o01[t]] + c10[t] * p0[o00[t] + dy] +
+                         c11[t] * p0[o01[t] + dy];
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              hi4[t] = c00[t] * p1[o00[t]] + c01[t] * p1[o01[t]] + c10[t] * p1[o00[t] + dy] +
+                       c11[t] * p1[o01[t] + dy];
+            cur = az;
+          }
+          const float v0 = fmaf(wz, hi4[0] - lo4[0], lo4[0]);
+          const float v1 = fmaf(wz, hi4[1] - lo4[1], lo4[1]);
+          const float v2 = fmaf(wz, hi4[2] - lo4[2], lo4[2]);
+          const float v3 = fmaf(wz, hi4[3] - lo4[3], lo4[3]);
+          const float4 x = av[r];
+          const float d0 = x.x - v0;
+          le = fmaf(d0, d0, le);
+          la = fmaf(x.x, x.x, la);
+          if (vec) {
+            const float d1 = x.y - v1, d2 = x.z - v2, d3 = x.w - v3;
+            le = fmaf(d1, d1, fmaf(d2, d2, fmaf(d3, d3, le)));
+            la = fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, la)));
+          }
+          if (WRITE) {
+            float* o = args.out + colbase + ((int64_t)q * b.ez + z) * plane + yx;
+            if (vec) *reinterpret_cast<float4*>(o) = make_float4(v0, v1, v2, v3);
+            else *o = v0;
+          }
+        }
+        kahan_add(se, ce, le);
+        kahan_add(sa, ca, la);
       }
     }
-    kahan_add(se, ce, le);
-    kahan_add(sa, ca, la);
+    // unit partial: warp tree in FP32, FP64 across warps, then the fixed-order fold
+    float we = se - ce, wa = sa - ca;
+    for (int o = 16; o > 0; o >>= 1) {
+      we += __shfl_xor_sync(0xffffffffu, we, o);
+      wa += __shfl_xor_sync(0xffffffffu, wa, o);
+    }
+    if (lane == 0) { red[0][warp] = (double)we; red[1][warp] = (double)wa; }
+    __syncthreads();
+    if (tid == 0) {
+      double te = 0.0, ta = 0.0;
+      for (int w = 0; w < (int)(nthr / 32); ++w) { te += red[0][w]; ta += red[1][w]; }
+      e.part[2 * (int64_t)u] = te;
+      e.part[2 * (int64_t)u + 1] = ta;
+      __threadfence();
+      const int units_s = e.unit_ptr[s + 1] - e.unit_ptr[s];
+      last_sub = (atomicAdd(&e.sub_cnt[s], 1) == units_s - 1);
+    }
+    __syncthreads();
+    if (last_sub && warp == 0) error_fold_subdomain(e, s, lane);
   }
-  // CTA partial: warp tree in FP32, FP64 across warps, then the fixed-order fold
-  float we = se - ce, wa = sa - ca;
-  for (int o = 16; o > 0; o >>= 1) {
-    we += __shfl_xor_sync(0xffffffffu, we, o);
-    wa += __shfl_xor_sync(0xffffffffu, wa, o);
-  }
-  if (lane == 0) { red[0][warp] = (double)we; red[1][warp] = (double)wa; }
-  __syncthreads();
-  if (tid == 0) {
-    double te = 0.0, ta = 0.0;
-    for (int w = 0; w < (int)(blockDim.x / 32); ++w) { te += red[0][w]; ta += red[1][w]; }
-    e.part[2 * (int64_t)u] = te;
-    e.part[2 * (int64_t)u + 1] = ta;
-    __threadfence();
-    const int units_s = e.unit_ptr[s + 1] - e.unit_ptr[s];
-    last_sub = (atomicAdd(&e.sub_cnt[s], 1) == units_s - 1);
-  }
-  __syncthreads();
-  if (!last_sub || warp != 0) return;
-  error_fold_subdomain(e, s, lane);
 }
 
 int grid_for(int64_t work) {
@@ -402,24 +537,33 @@ cudaError_t launch_coarse_recon(const SubArgs& a, int64_t max_work, cudaStream_t
 }
 
 size_t spid_interp_smem_bytes(int mc_max, int e_max) {
-  return sizeof(float) * (size_t)mc_max + 3 * (sizeof(int32_t) + sizeof(float)) * (size_t)e_max;
+  return sizeof(float) * (size_t)((mc_max + 3) & ~3) +
+         3 * (sizeof(int32_t) + sizeof(float)) * (size_t)e_max;
 }
 
 cudaError_t launch_spid_interp(const SubErrArgs& a, int64_t units, int mc_max, int e_max,
                                cudaStream_t st) {
   if (units <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  // three resident CTAs per SM (register-bound), a few waves; each CTA walks a
+  // contiguous range of units
+  const int64_t target = (int64_t)sms * 6;
+  const int per = (int)((units + target - 1) / target);
+  const int grid = (int)((units + per - 1) / per);
   const size_t smem = spid_interp_smem_bytes(mc_max, e_max);
-  cudaError_t e;
   if (a.out) {
     e = cudaFuncSetAttribute(spid_interp_kernel<true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    spid_interp_kernel<true><<<(unsigned)units, 256, smem, st>>>(a, mc_max, e_max);
+    spid_interp_kernel<true><<<grid, 256, smem, st>>>(a, mc_max, e_max, per, (int)units);
   } else {
     e = cudaFuncSetAttribute(spid_interp_kernel<false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    spid_interp_kernel<false><<<(unsigned)units, 256, smem, st>>>(a, mc_max, e_max);
+    spid_interp_kernel<false><<<grid, 256, smem, st>>>(a, mc_max, e_max, per, (int)units);
   }
   return cudaGetLastError();
 }

@@ -126,6 +126,8 @@ spid_status sfail(spid_status st, const std::string& msg) {
 
 int coarse_count(int e, int s) { return (e - 1) / s + 1 + ((e - 1) % s != 0 ? 1 : 0); }
 
+
+
 spid_status check(spid_sub_plan_t P) {
   if (!P) return sfail(SPID_ERR_INVALID_ARG, "plan is NULL");
   int cur = -1;
@@ -201,6 +203,12 @@ spid_status spid_sub_plan_create(const spid_sub_desc* d, spid_sub_plan_t* out) {
     const int64_t per_col = std::max<int64_t>(1, (m + kSubUnitElems - 1) / kSubUnitElems);
     b.zc = (int)std::max<int64_t>(1, (b.ez + per_col - 1) / per_col);
     b.zblocks = (b.ez + b.zc - 1) / b.zc;
+    b.div_ex = make_fastdiv((uint32_t)b.ex);
+    b.div_plane = make_fastdiv((uint32_t)((int64_t)b.ey * b.ex));
+    b.div_cx = make_fastdiv((uint32_t)b.cx);
+    b.div_cy = make_fastdiv((uint32_t)b.cy);
+    b.div_cz = make_fastdiv((uint32_t)b.cz);
+    b.div_mc = make_fastdiv((uint32_t)mc);
     P->box.push_back(b);
     P->m.push_back((int32_t)m);
     P->n.push_back(ns);

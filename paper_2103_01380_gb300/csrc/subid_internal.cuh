@@ -15,6 +15,25 @@ constexpr int kSubMaxN = 1024;        // window length bound (one residual norm 
 constexpr int kSubMaxCoarse = 40960;  // coarse rows bound (one column of B in shared memory)
 constexpr int kSubUnitElems = 32768;  // target fine elements per SPID error unit
 
+// Division by a fixed divisor d >= 1 as a multiply-high and a shift
+// (Granlund and Montgomery, PLDI'94, Section 4): for 0 <= x < 2^31,
+// x / d = (umulhi(x, mul) + x) >> shift with shift = ceil(log2 d) and
+// mul = floor(2^32 (2^shift - d) / d) + 1.
+struct FastDiv {
+  uint32_t d, mul, shift;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  uint32_t sh = 0;
+  while ((1ull << sh) < d) ++sh;
+  const uint64_t m = ((1ull << 32) * ((1ull << sh) - d)) / d + 1;
+  return FastDiv{d, (uint32_t)m, sh};
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv& f) {
+  return (__umulhi(x, f.mul) + x) >> f.shift;
+}
+
 // One subdomain box and its coarse grid.  Coarse index a of an axis with e
 // points and interval s is min(a s, e - 1); count c = (e - 1) / s + 1, plus one
 // when (e - 1) % s != 0 (the end point is kept).
@@ -24,6 +43,8 @@ struct SubBox {
   int32_t sz, sy, sx;         // intervals
   int32_t zc;                 // z planes per SPID error unit
   int32_t zblocks;            // SPID error units per column = ceil(ez / zc)
+  FastDiv div_ex, div_plane;  // fine x and (y, x)-plane decodes
+  FastDiv div_cx, div_cy, div_cz, div_mc;   // coarse-row decodes
 };
 
 struct SubArgs {
