@@ -98,6 +98,11 @@ def _load():
                                   c.c_double, c.c_double, _i32p, _f64p, c.c_void_p, _f64p,
                                   c.c_void_p]
         lib.orc_subid.restype = c.c_int
+        lib.orc_two_stage.argtypes = [_f64p, c.c_int64, c.c_int64, c.c_int64, c.c_int32,
+                                      c.c_int32, c.c_int32, c.c_int32, c.c_double, c.c_double,
+                                      c.c_uint64, _i32p, _f64p, _i32p, _i32p, _f64p, _i32p,
+                                      _f64p, _f64p]
+        lib.orc_two_stage.restype = c.c_int
         lib.orc_num_threads.argtypes = []
         lib.orc_num_threads.restype = c.c_int
         _lib = lib
@@ -328,3 +333,30 @@ def subid(A: np.ndarray, box, stride, kmax: int, tol: float = 0.0, u_mode: float
     if want_ahat:
         out["Ahat_spid"] = H[:m * n].reshape(n, m).T.copy()
     return out
+
+
+# ---------------------------------------------------------------------------
+# Modified (two-stage) SPID, Section 3.3.2 / Algorithm 6.
+# ---------------------------------------------------------------------------
+def two_stage(A: np.ndarray, N: int, k: int, p: int, k2max: int, tol2: float, u_mode: float,
+              seed: int) -> dict:
+    """Stage-1 IDs of N column blocks (rank k), stage-2 ID of their skeletons
+    (tolerance tol2), composed into A ~ A(:, J) C."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    assert n % N == 0
+    nb = n // N
+    Af = np.ascontiguousarray(A.T).reshape(-1)
+    J = np.zeros(k2max, dtype=np.int32)
+    C = np.zeros(k2max * n, dtype=np.float64)
+    Jb = np.zeros(N * k, dtype=np.int32)
+    kb = np.zeros(N, dtype=np.int32)
+    Cb = np.zeros(N * k * nb, dtype=np.float64)
+    J2 = np.zeros(k2max, dtype=np.int32)
+    C1 = np.zeros(k2max * N * k, dtype=np.float64)
+    err = np.zeros(2, dtype=np.float64)
+    k2 = int(_load().orc_two_stage(Af, m, n, m, N, k, p, k2max, float(tol2), float(u_mode),
+                                   int(seed), J, C, Jb, kb, Cb, J2, C1, err))
+    return {"k": k2, "J": J[:k2].copy(), "C": C.reshape(k2max, n)[:k2].copy(),
+            "Jb": Jb.reshape(N, k), "kb": kb, "Cb": Cb.reshape(N, k, nb), "J2": J2[:k2].copy(),
+            "C1": C1.reshape(k2max, N * k)[:k2].copy(), "e2": float(err[0]), "a2": float(err[1])}

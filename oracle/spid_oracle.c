@@ -559,6 +559,85 @@ int orc_subid(const double* A, int64_t ld, int64_t n, const int32_t box[4],
   return k;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Modified (two-stage) SPID, Section 3.3.2 and Algorithm 6.                */
+/* Stage 1: the n columns are cut into N blocks of nb = n / N; block b gets */
+/* the sketched ID with target rank k (orc_spid, tol = 0): A_b ~ A_b(:,I_b) */
+/* C_b.  Stage 2: A0' = [A_0(:,I_0) .. A_{N-1}(:,I_{N-1})] gets the         */
+/* sketched ID with tolerance tol2 (rank cap k2max): A0' ~ A0'(:,J2) C1.    */
+/* Final: C1' = C1 C0', C0' = blockdiag(C_0, .., C_{N-1}) (kN x n; the      */
+/* printed size k(N-1) x N is read as kN x n, the size the product needs),  */
+/* and J = I_U(J2), the window column of A0' column q = b k + p being       */
+/* b nb + I_b(p).  A0' keeps k slots per block; a block whose rank guard    */
+/* kept k_b < k pads with zero columns (never picked, C rows zero).         */
+/* Outputs: J (k2max, -1 past k2), C (k2max x n row-major, zero rows past   */
+/* k2), optional stage-1 Jb (N x k) / kb (N) / Cb (N x k x nb), stage-2 J2   */
+/* (k2max) / C1 (k2max x N k); err = {e2, a2}.  Returns k2.                 */
+/* ------------------------------------------------------------------------ */
+int orc_two_stage(const double* A, int64_t m, int64_t n, int64_t ld, int32_t N, int32_t k,
+                  int32_t p, int32_t k2max, double tol2, double u_mode, uint64_t seed,
+                  int32_t* J, double* C, int32_t* Jb, int32_t* kb, double* Cb, int32_t* J2,
+                  double* C1, double* err) {
+  const int64_t nb = n / N;
+  const int64_t n2 = (int64_t)N * k;
+  int32_t* Jbw = (int32_t*)malloc(sizeof(int32_t) * (size_t)n2);
+  int32_t* kbw = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+  double* Cbw = (double*)malloc(sizeof(double) * (size_t)n2 * (size_t)nb);
+  double* A0 = (double*)malloc(sizeof(double) * (size_t)m * (size_t)n2);
+  int32_t* J2w = (int32_t*)malloc(sizeof(int32_t) * (size_t)k2max);
+  double* C1w = (double*)malloc(sizeof(double) * (size_t)k2max * (size_t)n2);
+  /* stage 1, block by block */
+  for (int32_t b = 0; b < N; ++b) {
+    orc_spid(A + ld * (b * nb), m, nb, ld, k + p, k, 0.0, u_mode, seed, NULL, Jbw + (int64_t)b * k,
+             kbw + b, NULL, Cbw + (int64_t)b * k * nb, NULL, NULL);
+  }
+  /* A0': k slots per block, zero past k_b */
+  for (int32_t b = 0; b < N; ++b)
+    for (int32_t q = 0; q < k; ++q) {
+      double* dst = A0 + m * ((int64_t)b * k + q);
+      if (q < kbw[b]) {
+        const double* src = A + ld * (b * nb + Jbw[(int64_t)b * k + q]);
+        for (int64_t r = 0; r < m; ++r) dst[r] = src[r];
+      } else {
+        for (int64_t r = 0; r < m; ++r) dst[r] = 0.0;
+      }
+    }
+  /* stage 2 with the tolerance */
+  int32_t k2 = 0;
+  orc_spid(A0, m, n2, m, k2max + p, k2max, tol2, u_mode, seed, NULL, J2w, &k2, NULL, C1w, NULL,
+           NULL);
+  /* composition C1' = C1 C0' and J = I_U(J2) */
+  for (int32_t i = 0; i < k2max; ++i) {
+    for (int64_t t = 0; t < n; ++t) {
+      const int64_t b = t / nb, tt = t - b * nb;
+      double acc = 0.0;
+      if (i < k2)
+        for (int32_t q = 0; q < k; ++q)
+          acc += C1w[(int64_t)i * n2 + b * k + q] * Cbw[((int64_t)b * k + q) * nb + tt];
+      C[(int64_t)i * n + t] = acc;
+    }
+    if (i < k2) {
+      const int32_t q = J2w[i];
+      J[i] = (int32_t)((q / k) * nb + Jbw[q]);
+    } else {
+      J[i] = -1;
+    }
+  }
+  if (err) orc_reconstruct_error(A, m, n, ld, J, k2, C, NULL, 0, err, err + 1);
+  if (Jb) memcpy(Jb, Jbw, sizeof(int32_t) * (size_t)n2);
+  if (kb) memcpy(kb, kbw, sizeof(int32_t) * (size_t)N);
+  if (Cb) memcpy(Cb, Cbw, sizeof(double) * (size_t)n2 * (size_t)nb);
+  if (J2) memcpy(J2, J2w, sizeof(int32_t) * (size_t)k2max);
+  if (C1) memcpy(C1, C1w, sizeof(double) * (size_t)k2max * (size_t)n2);
+  free(Jbw);
+  free(kbw);
+  free(Cbw);
+  free(A0);
+  free(J2w);
+  free(C1w);
+  return k2;
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
   extern int omp_get_max_threads(void);
