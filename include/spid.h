@@ -309,6 +309,66 @@ spid_status spid_sub_get_coarse(spid_sub_plan_t plan, float* B_host, spid_stream
 /* Sticky device status of the plan (as spid_device_status), then cleared. */
 spid_status spid_sub_device_status(spid_sub_plan_t plan, spid_stream_t stream);
 
+/* ==========================================================================
+ * Modified (two-stage) SPID (Section 3.3.2, Algorithm 6).
+ *
+ * Stage 1: the window of every subdomain is cut into N time blocks of n_s / N
+ * snapshots and each block gets its own sketched column ID with target rank k
+ * (A_b ~ A_b(:, I_b) C_b), computed block by block as the snapshots arrive.
+ * Stage 2: the skeleton columns of all blocks, A0' = [A_0(:, I_0) .. A_{N-1}(:,
+ * I_{N-1})] (m_s x N k), get a sketched column ID with a tolerance,
+ * A0' ~ A1' C1, and the final factors are A1' = A(:, J) with J the union
+ * indices I_U picked by stage 2, and C1' = C1 C0' (C0' = blockdiag(C_b)),
+ * so A ~ A(:, J) C1'.  C1'(:, J) = I exactly.
+ * ========================================================================== */
+typedef struct spid_ts_plan_s* spid_ts_plan_t;
+
+typedef struct {
+  spid_plan_desc base;   /* the S subdomains over the whole window: m, n (each n_s a
+                            multiple of blocks), off, ld; k_max = the stage-1 target
+                            rank k; p, precision, seed as spid_plan_desc (both stages);
+                            base.tol and base.flags must be 0 */
+  int32_t blocks;        /* N >= 1 */
+  int32_t k2_max;        /* stage-2 rank cap, 1 <= k2_max <= N k_max, k2_max + p <= 64 */
+  double tol2;           /* stage-2 tolerance (> 0; Remark 2.1 reading as spid_plan_desc) */
+} spid_ts_desc;
+
+/* Create: allocates every workspace (N stage-1 plans, the skeleton buffer
+ * holding A0' (m_s x N k per subdomain, element type of the window), the
+ * stage-2 plan and the final factors).  Later calls allocate nothing. */
+spid_status spid_ts_plan_create(const spid_ts_desc* desc, spid_ts_plan_t* plan);
+spid_status spid_ts_plan_destroy(spid_ts_plan_t plan);
+
+/* Stage 1 for time block b (0 <= b < N): sketch of columns b n_s / N ..
+ * (b + 1) n_s / N - 1 of every subdomain, QR, rank k, C_b.  Blocks may be run
+ * in any order, each once per window. */
+spid_status spid_ts_block(spid_ts_plan_t plan, const void* window, int32_t block,
+                          spid_stream_t stream);
+
+/* Stage 2 (after every block): gathers A0' from the window, its sketched ID
+ * with tol2, and the composition C1' = C1 C0', J = I_U(J2). */
+spid_status spid_ts_finalize(spid_ts_plan_t plan, const void* window, spid_stream_t stream);
+
+/* Error / reconstruction of the final factors, as spid_error / spid_reconstruct. */
+spid_status spid_ts_error(spid_ts_plan_t plan, const void* window, double* err_dev,
+                          double* total_dev, spid_stream_t stream);
+spid_status spid_ts_reconstruct(spid_ts_plan_t plan, const void* window, void* out,
+                                spid_stream_t stream);
+
+/* Final factors as spid_get_factors (synchronizes): k_host[S],
+ * J_host[S k2_max] (window column indices, -1 past k_s), C_host k2_max x n_s
+ * row-major per subdomain at k2_max sum_{s'<s} n_s'. */
+spid_status spid_ts_get_factors(spid_ts_plan_t plan, int32_t* k_host, int32_t* J_host,
+                                void* C_host, spid_stream_t stream);
+
+/* Stage-1 factors of block b, as spid_get_factors of a plan over the block
+ * (J local to the block, C k_max x n_s / N per subdomain). */
+spid_status spid_ts_get_block_factors(spid_ts_plan_t plan, int32_t block, int32_t* k_host,
+                                      int32_t* J_host, void* C_host, spid_stream_t stream);
+
+/* Sticky status of every plan the two-stage plan owns, then cleared. */
+spid_status spid_ts_device_status(spid_ts_plan_t plan, spid_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

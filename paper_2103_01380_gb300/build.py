@@ -15,7 +15,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libspid.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-UNITS = ["sketch_simt", "sketch_tc", "sketch_bf16", "qrcp", "error", "error_tc", "subid", "subid_api", "spid_api",
+UNITS = ["sketch_simt", "sketch_tc", "sketch_bf16", "qrcp", "error", "error_tc", "subid", "subid_api", "spid_ts", "spid_api",
          "sketch_noalloc"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + INCLUDE]

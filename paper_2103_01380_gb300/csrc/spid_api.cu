@@ -62,6 +62,10 @@ struct Schedule {
 
 void spid::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 
+namespace spid {
+PlanView plan_view(spid_plan_t P);
+}
+
 struct spid_plan_s {
   int device = 0;
   int num_sms = 0;
@@ -476,6 +480,21 @@ spid_status check_plan(spid_plan_t P) {
 }
 
 }  // namespace
+
+spid::PlanView spid::plan_view(spid_plan_t P) {
+  PlanView v;
+  v.S = P->S;
+  v.k_max = P->k_max;
+  v.esz = P->esz;
+  v.m = P->d_m;
+  v.n = P->d_n;
+  v.k = P->d_k;
+  v.J = P->d_J;
+  v.C = P->d_C;
+  v.coff = P->d_coff;
+  v.status = P->d_status;
+  return v;
+}
 
 extern "C" {
 

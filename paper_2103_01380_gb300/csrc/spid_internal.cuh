@@ -223,6 +223,21 @@ struct ErrTcArgs {
 // Detail message returned by spid_last_error() on the calling thread.
 void set_last_error(const char* msg);
 
+// Device view of a plan's factors and status (used by the two-stage driver,
+// which composes plans).  C_s starts at element coff[s] (k_max x n_s row-major).
+struct PlanView {
+  int32_t S;
+  int32_t k_max;
+  size_t esz;
+  const int32_t* m;       // device [S]
+  const int32_t* n;       // device [S]
+  int32_t* k;             // device [S]
+  int32_t* J;             // device [S][k_max]
+  void* C;
+  const int64_t* coff;    // device [S]
+  int* status;
+};
+
 // Launchers (one translation unit each).
 int sketch_simt_group_cols(bool fp64);
 cudaError_t launch_sketch_simt(const SketchArgs& a, int grid, bool fp64, cudaStream_t st);

@@ -33,7 +33,10 @@ EXPORTS = ["spid_plan_create", "spid_plan_destroy", "spid_plan_info", "spid_sket
            "spid_sketch_fp32_noalloc",
            "spid_sub_plan_create", "spid_sub_plan_destroy", "spid_sub_plan_info",
            "spid_sub_sample", "spid_sub_finalize", "spid_sub_error", "spid_sub_reconstruct",
-           "spid_sub_get_factors", "spid_sub_get_coarse", "spid_sub_device_status"]
+           "spid_sub_get_factors", "spid_sub_get_coarse", "spid_sub_device_status",
+           "spid_ts_plan_create", "spid_ts_plan_destroy", "spid_ts_block", "spid_ts_finalize",
+           "spid_ts_error", "spid_ts_reconstruct", "spid_ts_get_factors",
+           "spid_ts_get_block_factors", "spid_ts_device_status"]
 FORM_SPID = 0
 FORM_SUBID = 1
 
@@ -68,6 +71,13 @@ class _SubDesc(ctypes.Structure):
                 ("k_max", ctypes.c_int32),
                 ("tol", ctypes.c_double),
                 ("flags", ctypes.c_uint32)]
+
+
+class _TsDesc(ctypes.Structure):
+    _fields_ = [("base", _Desc),
+                ("blocks", ctypes.c_int32),
+                ("k2_max", ctypes.c_int32),
+                ("tol2", ctypes.c_double)]
 
 
 _lib = None
@@ -114,6 +124,15 @@ def load_library(path: str = LIB_PATH):
             "spid_sub_get_factors": ([vp, vp, vp, vp, vp, vp], c.c_int),
             "spid_sub_get_coarse": ([vp, vp, vp], c.c_int),
             "spid_sub_device_status": ([vp, vp], c.c_int),
+            "spid_ts_plan_create": ([c.POINTER(_TsDesc), c.POINTER(vp)], c.c_int),
+            "spid_ts_plan_destroy": ([vp], c.c_int),
+            "spid_ts_block": ([vp, vp, i32, vp], c.c_int),
+            "spid_ts_finalize": ([vp, vp, vp], c.c_int),
+            "spid_ts_error": ([vp, vp, vp, vp, vp], c.c_int),
+            "spid_ts_reconstruct": ([vp, vp, vp, vp], c.c_int),
+            "spid_ts_get_factors": ([vp, vp, vp, vp, vp], c.c_int),
+            "spid_ts_get_block_factors": ([vp, i32, vp, vp, vp, vp], c.c_int),
+            "spid_ts_device_status": ([vp, vp], c.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -345,6 +364,94 @@ class SubPlan:
 
     def device_status(self, stream=None) -> int:
         return int(load_library().spid_sub_device_status(self._h, _stream_handle(stream)))
+
+
+class TsPlan:
+    """Modified (two-stage) SPID (Section 3.3.2, Algorithm 6): N time blocks with
+    a target-rank-k sketched ID each, then a sketched ID with tolerance tol2 of
+    the concatenated skeletons, composed into A ~ A(:, J) C."""
+
+    def __init__(self, m, n, off, ld, blocks: int, k: int, k2_max: int, tol2: float,
+                 p: int = 10, precision: str = "tf32", seed: int = 0x5EED0001):
+        lib = load_library()
+        self.m = np.ascontiguousarray(m, dtype=np.int32)
+        self.n = np.ascontiguousarray(n, dtype=np.int32)
+        self.off = np.ascontiguousarray(off, dtype=np.int64)
+        self.ld = np.ascontiguousarray(ld, dtype=np.int64)
+        self.S = int(len(self.m))
+        self.N, self.k, self.k2_max = int(blocks), int(k), int(k2_max)
+        self.dtype = np.float64 if precision == "fp64" else np.float32
+        d = _TsDesc()
+        b = d.base
+        b.num_sub = self.S
+        b.m = self.m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        b.n = self.n.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        b.off = self.off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        b.ld = self.ld.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        b.k_max = self.k
+        b.p = int(p)
+        b.tol = 0.0
+        b.precision = PREC[precision]
+        b.flags = 0
+        b.seed = int(seed)
+        d.blocks = self.N
+        d.k2_max = self.k2_max
+        d.tol2 = float(tol2)
+        h = ctypes.c_void_p()
+        _check(lib.spid_ts_plan_create(ctypes.byref(d), ctypes.byref(h)), "spid_ts_plan_create")
+        self._h = h
+
+    @classmethod
+    def for_window(cls, win, **kw) -> "TsPlan":
+        return cls(win.m, win.n, win.off, win.ld, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().spid_ts_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def block(self, window, b: int, stream=None):
+        _check(load_library().spid_ts_block(self._h, _ptr(window), int(b), _stream_handle(stream)),
+               "spid_ts_block")
+
+    def finalize(self, window, stream=None):
+        _check(load_library().spid_ts_finalize(self._h, _ptr(window), _stream_handle(stream)),
+               "spid_ts_finalize")
+
+    def error(self, window, err=None, total=None, stream=None):
+        _check(load_library().spid_ts_error(self._h, _ptr(window), _ptr(err), _ptr(total),
+                                            _stream_handle(stream)), "spid_ts_error")
+
+    def reconstruct(self, window, out, stream=None):
+        _check(load_library().spid_ts_reconstruct(self._h, _ptr(window), _ptr(out),
+                                                  _stream_handle(stream)), "spid_ts_reconstruct")
+
+    def _factors(self, fn, kmax, ncols, *pre):
+        k = np.zeros(self.S, dtype=np.int32)
+        J = np.zeros((self.S, kmax), dtype=np.int32)
+        C = np.zeros(kmax * int(ncols.sum()), dtype=self.dtype)
+        _check(fn(self._h, *pre, k.ctypes.data, J.ctypes.data, C.ctypes.data,
+                  _stream_handle(None)), "spid_ts factors")
+        coff = np.concatenate([[0], np.cumsum(ncols)]) * kmax
+        return k, J, [C[coff[s]:coff[s + 1]].reshape(kmax, int(ncols[s])) for s in range(self.S)]
+
+    def factors(self):
+        """Final (k, J [S, k2_max] window columns, C list of k2_max x n_s)."""
+        return self._factors(load_library().spid_ts_get_factors, self.k2_max, self.n)
+
+    def block_factors(self, b: int):
+        """Stage-1 (k, J local to block b, C list of k x n_s / N)."""
+        return self._factors(load_library().spid_ts_get_block_factors, self.k, self.n // self.N,
+                             int(b))
+
+    def device_status(self, stream=None) -> int:
+        return int(load_library().spid_ts_device_status(self._h, _stream_handle(stream)))
 
 
 def omega(seed: int, r0: int, nrows: int, l: int, precision: str, out, stream=None):
