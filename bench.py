@@ -490,6 +490,7 @@ def _run_uneven(args, torch, inputs, spid):
         cur_b += nb
     waves.append(cur)
     tot_bytes, tot_ms, sk_ms_all, ks, e2, a2, mn, kd = 0.0, 0.0, 0.0, [], 0.0, 0.0, 0.0, 0.0
+    tuning = None
     for wv in waves:
         m = np.array([5 * e ** 3 for _, e, _ in wv], dtype=np.int64)
         n = np.array([nn for _, _, nn in wv], dtype=np.int64)
@@ -505,6 +506,12 @@ def _run_uneven(args, torch, inputs, spid):
         tot = torch.zeros(4, dtype=torch.float64, device="cuda")
         plan = spid.Plan(m, n, off, m, k_max=32, p=10, tol=1e-3, precision="tf32",
                          seed=0x5EED0004)
+        # the waves share one size distribution: tune on the first, reuse after
+        if not args.no_autotune:
+            if tuning is None:
+                tuning = plan.autotune(window)
+            else:
+                plan.set_tuning(tuning)
         sk, fi, er = _stage_times(torch, plan, window, max(1, args.steps // 4), 1, err, tot,
                                   [(0, int(n.max()))])
         t = tot.detach().cpu().numpy()
@@ -521,7 +528,8 @@ def _run_uneven(args, torch, inputs, spid):
             "config": {"workload": f"uneven: 4096 cubic boxes (edges 8..32) x 5 QoIs of a 256^3 "
                                    f"TGV+Fourier field, n in 64..1024, adaptive 1e-3, "
                                    f"{len(waves)} waves of <= {args.wave_gb:g} GB",
-                       "total_gb": tot_bytes / 1e9, "l2": "inputs larger than L2"},
+                       "total_gb": tot_bytes / 1e9, "l2": "inputs larger than L2",
+                       "tuning": tuning},
             "rel_err": float(np.sqrt(e2 / a2)), "compression_factor": float(mn / kd),
             "k_mean": float(np.mean(ks)), "k_max": int(np.max(ks)),
             "_sketch_gbs": tot_bytes / (sk_ms_all / 1e3) / 1e9}
@@ -548,6 +556,7 @@ def _run_insitu(args, torch, inputs, spid):
     tot = torch.zeros(4, dtype=torch.float64, device="cuda")
     plan = spid.Plan([m] * S, [n] * S, np.arange(S) * m, [S * m] * S, k_max=30, p=10,
                      precision="tf32", seed=0x5EED0005)
+    tuning = None if args.no_autotune else plan.autotune(window)
     sk, fi, er = _stage_times(torch, plan, window, args.steps, args.warmup, err, tot, calls)
     summ = _summary(plan, tot)
     # in-situ overlap: producer writes batch i+1 while the sketch consumes batch i
@@ -584,7 +593,7 @@ def _run_insitu(args, torch, inputs, spid):
             "config": {"workload": f"in-situ: 512 boxes of 32^3 x 5 QoIs of a 256^3 TGV+Fourier "
                                    f"field, n=256, snapshot-major window (85.9 GB), sketch per "
                                    f"micro-batch of {b} snapshots, k=30, p=10",
-                       "l2": "inputs larger than L2"},
+                       "l2": "inputs larger than L2", "tuning": tuning},
             "stages_ms": {"sketch": sk, "finalize": fi, "error": er},
             "sketch_gbs": nbytes / (sk / 1e3) / 1e9, "error_gbs": nbytes / (er / 1e3) / 1e9,
             **summ,
@@ -609,6 +618,8 @@ def main():
                     help="error pass with the rank-k product on the tensor cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default tile shapes (no measurement)")
     ap.add_argument("--workload", default="tgv3d64",
                     choices=["tgv3d64", "spectrum256", "uneven4096", "insitu256",
                              "coarse_tgv3d64", "two_stage_tgv3d64"],
@@ -678,8 +689,35 @@ def main():
         return total_ms, sk, fi, er
 
     plan = make_plan(args.precision, flags=spid.FLAG_TC_ERROR if args.tc_error else 0)
+    # tile shapes and schedules: measured on this window by the library's autotuner
+    if args.no_autotune:
+        tuning = dict(plan.tuning(), cached=None)
+    else:
+        tuning = plan.autotune(dev)
+    # one step = one CUDA-graph launch (sketch, finalize, error kernels)
+    graph = plan.graph(dev, err=err, total=tot)
+
+    def timed_graph(steps, warmup):
+        for _ in range(warmup):
+            graph.launch()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(steps):
+            graph.launch()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return g0.elapsed_time(g1)
+
     with ClockSampler(local) as clk:
-        total_ms, sk, fi, er = timed(plan, args.steps, args.warmup)
+        # per-stage durations (eager launches, events between the stages), then
+        # the headline: the same steps replayed as one graph launch each
+        _, sk, fi, er = timed(plan, args.steps, args.warmup)
+        total_ms = timed_graph(args.steps, args.warmup)
     clocks = clk.summary()
     t = torch.tensor([total_ms], dtype=torch.float64)
     if world > 1:
@@ -688,23 +726,21 @@ def main():
     ms_per_step = total_ms / args.steps
     value = world * nbytes * args.steps / (total_ms / 1e3) / 1e9
 
-    # global error / CF across ranks: a host-side sum of four doubles
     # global error / CF across ranks: one host-side sum of four doubles
     from paper_2103_01380_gb300 import shard
     rel_err, cf, _ = shard.combine_totals(tot.detach().cpu().numpy())
     k, J, C = plan.factors()
 
-    # end to end through the public API: pinned host window -> device, full
-    # path, device -> host read of the error sums, every step
+    # end to end through the public API: pinned host window -> device, the
+    # graph-launched step, device -> host read of the error sums, every step
     host_tot = torch.zeros(4, dtype=torch.float64).pin_memory()
     for _ in range(max(args.warmup, 1)):
         dev.copy_(host, non_blocking=True)
-        plan.sketch(dev); plan.finalize(); plan.error(dev, err, tot)
+        graph.launch()
         host_tot.copy_(tot, non_blocking=True)
     torch.cuda.synchronize()
     barrier()
     e2e_steps = max(3, args.steps // 4)
-    t0 = time.perf_counter()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     hc = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -714,7 +750,7 @@ def main():
         hc[i][0].record(stream)
         dev.copy_(host, non_blocking=True)
         hc[i][1].record(stream)
-        plan.sketch(dev); plan.finalize(); plan.error(dev, err, tot)
+        graph.launch()
         host_tot.copy_(tot, non_blocking=True)
         stream.synchronize()
     e1.record(stream)
@@ -725,6 +761,7 @@ def main():
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_value = world * nbytes / (float(te.item()) / 1e3) / 1e9
+    graph.close()
 
     # comparator: plain FP32 (SIMT sketch, one launch per subdomain per stage, no graph)
     comparator = None
@@ -769,7 +806,9 @@ def main():
                        "error_pass": "tensor-core (3xTF32)" if (args.tc_error and
                                                                 args.precision != "fp32")
                        else "cuda-core",
-                       "l2": "inputs (2.68 GB) larger than L2; no flush"},
+                       "l2": "inputs (2.68 GB) larger than L2; no flush",
+                       "launch": "one CUDA graph per step (sketch, finalize, error kernels)",
+                       "tuning": tuning},
             "stages_ms": {"sketch": sk_ms, "finalize": fi_ms, "error": er_ms},
             "sketch_gbs": nbytes / (sk_ms / 1e3) / 1e9,
             "error_gbs": nbytes / (er_ms / 1e3) / 1e9,

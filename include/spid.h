@@ -187,6 +187,89 @@ spid_status spid_philox(const uint32_t* ctr_dev, uint32_t key0, uint32_t key1, u
 double spid_compression_factor(int32_t num_sub, const int32_t* m, const int32_t* n,
                                const int32_t* k);
 
+/* ---- Tuning ------------------------------------------------------------
+ * Tile shapes and schedules of a plan's kernels.  The defaults are fixed;
+ * spid_plan_autotune measures the candidates below on the caller's own window
+ * (CUDA events on the plan's stream, median of 5 timed runs after one warm-up)
+ * and keeps the fastest; a candidate replaces the best one so far only when it
+ * is at least 2% faster, so the defaults stay unless a shape clearly wins.  No paper passage corresponds: the paper's
+ * subdomains run as independent Legion tasks (Section 3.2) with no kernel of
+ * their own.  Results depend on the tuning only through the order of FP32
+ * partial sums (sketch slots, error-pass units); each tuning is deterministic. */
+typedef struct {
+  int32_t sketch_pack_slices;  /* tensor-core sketch: 64-column slices of equal-m subdomains
+                                  sharing one generated Omega chunk: 1, 2, 4 or 8 (default 8) */
+  int32_t sketch_stages;       /* tensor-core sketch pipeline depth: 0 = as many as fit in
+                                  shared memory (default), else 2..8 (capped by what fits) */
+  int32_t sketch_ctas_per_sm;  /* CUDA-core (FP32/FP64) sketch: persistent CTAs per SM, 1 or 2;
+                                  0 = by the kernel's register budget (default) */
+  int32_t error_path;          /* 0 = CUDA-core error pass (default); 1 = tensor-core pass
+                                  (batched TF32/BF16/3xBF16 plans with k_max <= 32 only) */
+  int32_t error_rows;          /* CUDA-core error pass: rows per work unit, 256, 512 (default)
+                                  or 1024 */
+  int32_t error_cols;          /* CUDA-core error pass: columns per work unit, 128 or 256
+                                  (default) */
+  float sketch_ms;             /* spid_plan_autotune: measured whole-window sketch time of the
+                                  chosen shape (0 if the tuning was set, not measured) */
+  float error_ms;              /* spid_plan_autotune: measured error-pass time */
+} spid_tuning;
+
+/* Current tuning of the plan.  Host-only. */
+spid_status spid_plan_get_tuning(spid_plan_t plan, spid_tuning* out);
+
+/* Apply a tuning (for example one saved from an earlier spid_plan_autotune of
+ * a plan with the same spid_plan_tuning_key).  Synchronizes the device and
+ * rebuilds the cached sketch schedules; may allocate (schedule tables, the
+ * tensor-core error schedule on first use), so call it outside stream capture.
+ * SPID_ERR_INVALID_ARG for a value outside the lists above,
+ * SPID_ERR_UNSUPPORTED for error_path 1 on a plan that cannot use it,
+ * SPID_ERR_STATE while graphs captured from the plan exist.  sketch_ms and
+ * error_ms are ignored. */
+spid_status spid_plan_set_tuning(spid_plan_t plan, const spid_tuning* tuning);
+
+/* Measure every candidate shape on `window` (device, the plan's layout) and
+ * apply the fastest: the sketch candidates on the whole window, then, after a
+ * finalize, the error-pass candidates.  Leaves the plan as after
+ * spid_sketch(whole window) + spid_finalize with the chosen tuning.
+ * Synchronizes; may allocate (as spid_plan_set_tuning); best (may be NULL)
+ * receives the chosen tuning and its times.  SPID_ERR_STATE while graphs
+ * captured from the plan exist. */
+spid_status spid_plan_autotune(spid_plan_t plan, const void* window, spid_stream_t stream,
+                               spid_tuning* best);
+
+/* A text key for caching tunings across runs: the device (compute capability,
+ * SM count), precision, flags, l_pad, k_max and log2 buckets of the subdomain
+ * count and of the mean m and n.  Writes at most len bytes including the
+ * terminating NUL; SPID_ERR_INVALID_ARG if it does not fit. */
+spid_status spid_plan_tuning_key(spid_plan_t plan, char* buf, int32_t len);
+
+/* ---- CUDA graphs -------------------------------------------------------
+ * One step of the hot path captured once and replayed with one launch:
+ * the sketch of window columns [col0, col0 + ncols) (in calls of `microbatch`
+ * columns each, 0 = one call), the finalize and the error pass, or any subset
+ * (`what`, an OR of the SPID_GRAPH_* bits, kept in that order).  The graph
+ * owns its own tensor maps of `window`, so other calls on the plan with other
+ * windows do not disturb it; it uses the plan's workspace (sketch, partial
+ * sums, factors, counters), so a graph launch and any other call on the same
+ * plan must not overlap on the GPU.  err_dev / total_dev as spid_error (used
+ * with SPID_GRAPH_ERROR; both may be NULL).  Creation synchronizes and may
+ * allocate (schedules of new column ranges, the graph's tensor maps); launches
+ * allocate nothing.  Graphs must be destroyed before their plan (the plan's
+ * destroy and set_tuning return SPID_ERR_STATE while any exists). */
+typedef struct spid_graph_s* spid_graph_t;
+#define SPID_GRAPH_SKETCH 1u
+#define SPID_GRAPH_FINALIZE 2u
+#define SPID_GRAPH_ERROR 4u
+spid_status spid_graph_create(spid_plan_t plan, const void* window, int32_t col0, int32_t ncols,
+                              int32_t microbatch, uint32_t what, double* err_dev,
+                              double* total_dev, spid_graph_t* graph_out);
+
+/* Replay the captured step on `stream` (asynchronous). */
+spid_status spid_graph_launch(spid_graph_t graph, spid_stream_t stream);
+
+/* Release the graph (synchronizes the device first). */
+spid_status spid_graph_destroy(spid_graph_t graph);
+
 /* ---- Allocation-free sketch -------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory when they need a sketch: an in-situ

@@ -3,7 +3,8 @@
 // ||A - A_hat||_F^2 and ||A||_F^2 per subdomain and over the window, plus the
 // compression-factor sums (Section 2, Eq. for CF).
 //
-// A unit is (subdomain, 512-row block, 256-column block).  The CTA stages the
+// A unit is (subdomain, row block, column block): 512 x 256 by default, or the
+// shape the plan's autotuner measured fastest.  The CTA stages the
 // coefficient block C(:, cols) and, per 128-row tile, the skeleton rows
 // A(rows, J) in shared memory, then streams A once: lane l of warp w owns rows
 // 4l..4l+3 of the tile and 4 columns at a time, so each k-step is two shared
@@ -75,18 +76,19 @@ __global__ void __launch_bounds__(256) error_kernel(ErrArgs a) {
   const int row0 = a.unit_row0[u], col0 = a.unit_col0[u];
   const int m = a.m[s], n = a.n[s];
   const int kk = a.k[s];
-  const int ncb = min(kErrColBlock, n - col0);
-  const int nrb = min(kErrRowBlock, m - row0);
-  T* Cs = reinterpret_cast<T*>(smem_raw);                 // [kk][kErrColBlock]
-  T* AJ = Cs + (size_t)a.k_max * kErrColBlock;             // [kk][kErrTile]
+  const int cb = a.col_block;
+  const int ncb = min(cb, n - col0);
+  const int nrb = min(a.row_block, m - row0);
+  T* Cs = reinterpret_cast<T*>(smem_raw);                 // [kk][cb]
+  T* AJ = Cs + (size_t)a.k_max * cb;                       // [kk][kErrTile]
   const T* A = static_cast<const T*>(a.window) + a.off[s];
   const int64_t ld = a.ld[s];
   const T* Cg = static_cast<const T*>(a.C) + a.coff[s];
   const int32_t* Jg = a.J + (int64_t)s * a.k_max;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
 
-  for (int e = tid; e < kk * kErrColBlock; e += 256) {
-    const int p = e / kErrColBlock, jj = e % kErrColBlock;
+  for (int e = tid; e < kk * cb; e += 256) {
+    const int p = e / cb, jj = e % cb;
     Cs[e] = (jj < ncb) ? Cg[(int64_t)p * n + col0 + jj] : T(0);
   }
   T se = T(0), ce = T(0), sa = T(0), ca = T(0);   // Kahan sums of e^2 and a^2
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(256) error_kernel(ErrArgs a) {
       for (int p = 0; p < kk; ++p) {
         T aj[4], cc[4];
         V4<T>::lds(AJ + p * kErrTile + 4 * lane, aj);
-        V4<T>::lds(Cs + p * kErrColBlock + cg, cc);
+        V4<T>::lds(Cs + p * cb + cg, cc);
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -179,13 +181,16 @@ __global__ void __launch_bounds__(256) error_kernel(ErrArgs a) {
 
 }  // namespace
 
-size_t error_smem_bytes(int k_max, bool fp64) {
-  return (fp64 ? 8 : 4) * (size_t)k_max * (kErrColBlock + kErrTile) + 16;
+size_t error_smem_bytes(int k_max, int col_block, bool fp64) {
+  return (fp64 ? 8 : 4) * (size_t)k_max * (col_block + kErrTile) + 16;
 }
 
 cudaError_t launch_error(const ErrArgs& a, int units, bool fp64, cudaStream_t st) {
   if (units <= 0) return cudaSuccess;
-  const size_t smem = error_smem_bytes(a.k_max, fp64);
+  if (a.row_block < kErrTile || a.row_block % kErrTile || a.col_block < 32 || a.col_block % 32 ||
+      a.col_block > kErrColBlockMax)
+    return cudaErrorInvalidValue;
+  const size_t smem = error_smem_bytes(a.k_max, a.col_block, fp64);
   cudaError_t e = cudaSuccess;
 #define SPID_LAUNCH_ERR(T, W)                                                               \
   do {                                                                                      \

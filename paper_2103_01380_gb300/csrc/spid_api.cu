@@ -66,6 +66,16 @@ namespace spid {
 PlanView plan_view(spid_plan_t P);
 }
 
+// Tile shapes and schedules of one plan (spid_tuning without the timings).
+struct TuneCfg {
+  int pack_slices = kPackSlices;   // tensor-core sketch: 64-column slices per Omega chunk
+  int stages = 0;                  // tensor-core sketch pipeline depth, 0 = as many as fit
+  int ctas_per_sm = 0;             // CUDA-core sketch CTAs per SM, 0 = by register budget
+  int err_path = 0;                // 0 CUDA cores, 1 tensor cores
+  int err_rows = kErrRowBlock;     // error-pass unit rows
+  int err_cols = kErrColBlock;     // error-pass unit columns
+};
+
 struct spid_plan_s {
   int device = 0;
   int num_sms = 0;
@@ -84,9 +94,9 @@ struct spid_plan_s {
   bool per_sub() const { return (flags & SPID_FLAG_PER_SUBDOMAIN) != 0; }
   bool tensor_core() const { return prec >= SPID_PREC_TF32; }
   bool bf16() const { return prec == SPID_PREC_BF16 || prec == SPID_PREC_BF16X3; }
-  bool err_tc_eligible() const {
-    return tensor_core() && !per_sub() && (flags & SPID_FLAG_TC_ERROR) &&
-           k_max <= kErrTcKMax && smem_optin >= error_tc_smem_bytes();
+  bool err_tc_possible() const {
+    return tensor_core() && !per_sub() && k_max <= kErrTcKMax &&
+           smem_optin >= error_tc_smem_bytes();
   }
   double u_mode() const {
     switch (prec) {
@@ -118,8 +128,7 @@ struct spid_plan_s {
   double* d_sub_err = nullptr;
   int* d_err_cnt = nullptr;     // [S + 1] error-pass completion counters
   // tensor-core error pass: segments of 128-row tiles over one CTA per SM
-  bool err_tc = false;
-  int err_tc_grid = 0;
+  int err_tc_grid = 0;          // > 0 once the tensor-core error schedule exists
   ErrSeg* d_err_segs = nullptr;
   int32_t* d_err_seg_ptr = nullptr;   // [grid + 1]
   int32_t* d_err_tc_ptr = nullptr;    // [S + 1] segments of each subdomain
@@ -128,14 +137,19 @@ struct spid_plan_s {
   void* d_partial = nullptr;
   int64_t partial_cap = 0;
   int units = 0;
+  int units_cap = 0;            // unit arrays are sized for the smallest unit shape
   std::vector<int32_t> unit_ptr;
+  TuneCfg tune;
+  float tuned_sketch_ms = 0.f, tuned_error_ms = 0.f;
   int64_t y_elems = 0, c_elems = 0;
   int64_t workspace = 0;
 
   const void* bound_window = nullptr;
+  int live_graphs = 0;          // graphs captured from this plan and not yet destroyed
   std::map<std::pair<int, int>, Schedule> schedules;
   std::vector<void*> allocs;
-  std::mutex mu;
+  std::mutex mu;                // schedule cache
+  std::mutex tune_mu;           // set_tuning / autotune
 
   cudaError_t alloc(void** p, size_t bytes) {
     bytes = std::max<size_t>(bytes, 16);
@@ -147,10 +161,14 @@ struct spid_plan_s {
     return e;
   }
   int group_cols() const {
-    return tensor_core() ? sketch_tc_group_cols() : sketch_simt_group_cols(fp64());
+    return tensor_core() ? tune.pack_slices * kSliceCols : sketch_simt_group_cols(fp64());
+  }
+  int group_cols_max() const {
+    return tensor_core() ? kPackSlices * kSliceCols : sketch_simt_group_cols(fp64());
   }
   int sketch_grid() const {
     if (tensor_core()) return num_sms;
+    if (tune.ctas_per_sm > 0) return tune.ctas_per_sm * num_sms;
     return (!fp64() && l_pad <= 32) || (fp64() && l_pad <= 16) ? 2 * num_sms : num_sms;
   }
 };
@@ -217,7 +235,7 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
       pk.nprob = 0;
       int cols = 0;
       while (p < p1 && probs[p].m == pk.m &&
-             pk.nslices + (probs[p].ncols + kSliceCols - 1) / kSliceCols <= kPackSlices) {
+             pk.nslices + (probs[p].ncols + kSliceCols - 1) / kSliceCols <= P->tune.pack_slices) {
         for (int c = 0; c < probs[p].ncols; c += kSliceCols) {
           Slice sl;
           sl.prob = p;
@@ -312,6 +330,19 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   sc.partial_elems = slot_total;
   if (slot_total > P->partial_cap)
     return fail(SPID_ERR_INVALID_ARG, "sketch schedule exceeds the partial workspace");
+  if (tc) {
+    const bool split = P->prec == SPID_PREC_BF16X3;
+    const int mt = sc.max_tiles;
+    const size_t fixed = P->bf16() ? sketch_bf16_smem_bytes(0, mt, P->l_pad, split)
+                                   : sketch_tc_smem_bytes(0, mt, P->l_pad);
+    const size_t per_stage = (P->bf16() ? sketch_bf16_smem_bytes(1, mt, P->l_pad, split)
+                                        : sketch_tc_smem_bytes(1, mt, P->l_pad)) - fixed;
+    int stages = (int)((P->smem_optin - fixed) / per_stage);
+    stages = std::min(stages, sketch_tc_max_stages());
+    if (P->tune.stages > 0) stages = std::min(stages, P->tune.stages);
+    if (stages < 2) return fail(SPID_ERR_UNSUPPORTED, "not enough shared memory for the sketch pipeline");
+    sc.stages = stages;
+  }
   // one device block for all tables (16-byte aligned pieces)
   std::vector<unsigned char> host;
   std::vector<size_t> at;
@@ -344,18 +375,6 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   sc.slices = reinterpret_cast<const Slice*>(d + at[7]);
   sc.packs = reinterpret_cast<const Pack*>(d + at[8]);
   sc.psegs = reinterpret_cast<const PackSegment*>(d + at[9]);
-  if (tc) {
-    const bool split = P->prec == SPID_PREC_BF16X3;
-    const int mt = sc.max_tiles;
-    const size_t fixed = P->bf16() ? sketch_bf16_smem_bytes(0, mt, P->l_pad, split)
-                                   : sketch_tc_smem_bytes(0, mt, P->l_pad);
-    const size_t per_stage = (P->bf16() ? sketch_bf16_smem_bytes(1, mt, P->l_pad, split)
-                                        : sketch_tc_smem_bytes(1, mt, P->l_pad)) - fixed;
-    int stages = (int)((P->smem_optin - fixed) / per_stage);
-    stages = std::min(stages, sketch_tc_max_stages());
-    if (stages < 2) return fail(SPID_ERR_UNSUPPORTED, "not enough shared memory for the sketch pipeline");
-    sc.stages = stages;
-  }
   return SPID_OK;
 }
 
@@ -417,6 +436,73 @@ spid_status get_schedule(spid_plan_t P, int col0, int ncols, Schedule** out) {
   return SPID_OK;
 }
 
+// Unit shapes the tuner may choose for the CUDA-core error pass.
+constexpr int kTuneErrRows[] = {256, 512, 1024};
+constexpr int kTuneErrCols[] = {128, 256};
+constexpr int kTuneMaxCtasPerSm = 2;
+
+int count_error_units(spid_plan_t P, int rows, int cols) {
+  int64_t u = 0;
+  for (int s = 0; s < P->S; ++s)
+    u += (int64_t)((P->m[s] + rows - 1) / rows) * ((P->n[s] + cols - 1) / cols);
+  return (int)std::min<int64_t>(u, INT32_MAX);
+}
+
+// Error-pass units (subdomain, row block, column block) for the plan's unit
+// shape, copied into the arrays sized at plan creation (synchronous).
+spid_status upload_error_units(spid_plan_t P) {
+  const int rows = P->tune.err_rows, cols = P->tune.err_cols;
+  std::vector<int32_t> usub, urow, ucol, uptr(P->S + 1, 0);
+  for (int s = 0; s < P->S; ++s) {
+    uptr[s] = (int32_t)usub.size();
+    for (int r = 0; r < P->m[s]; r += rows)
+      for (int c = 0; c < P->n[s]; c += cols) {
+        usub.push_back(s);
+        urow.push_back(r);
+        ucol.push_back(c);
+      }
+  }
+  uptr[P->S] = (int32_t)usub.size();
+  if ((int64_t)usub.size() > P->units_cap)
+    return fail(SPID_ERR_INVALID_ARG, "error-pass unit shape below the smallest supported one");
+  SPID_CUDA(cudaMemcpy(P->d_unit_sub, usub.data(), sizeof(int32_t) * usub.size(),
+                       cudaMemcpyHostToDevice));
+  SPID_CUDA(cudaMemcpy(P->d_unit_row0, urow.data(), sizeof(int32_t) * urow.size(),
+                       cudaMemcpyHostToDevice));
+  SPID_CUDA(cudaMemcpy(P->d_unit_col0, ucol.data(), sizeof(int32_t) * ucol.size(),
+                       cudaMemcpyHostToDevice));
+  SPID_CUDA(cudaMemcpy(P->d_unit_ptr, uptr.data(), sizeof(int32_t) * uptr.size(),
+                       cudaMemcpyHostToDevice));
+  P->unit_ptr = uptr;
+  P->units = (int)usub.size();
+  return SPID_OK;
+}
+
+// The tensor-core error schedule, built (and its tables allocated) the first
+// time a tuning selects that path.
+spid_status ensure_error_tc(spid_plan_t P) {
+  if (P->err_tc_grid > 0) return SPID_OK;
+  if (!P->err_tc_possible())
+    return fail(SPID_ERR_UNSUPPORTED, "the tensor-core error pass needs a batched TF32/BF16/3xBF16 "
+                                      "plan with k_max <= 32");
+  std::vector<ErrSeg> esegs;
+  std::vector<int32_t> eseg_ptr, esub_ptr;
+  const int G = P->num_sms;
+  build_error_tc_schedule(P, G, esegs, eseg_ptr, esub_ptr);
+  SPID_CUDA(P->alloc(reinterpret_cast<void**>(&P->d_err_segs), sizeof(ErrSeg) * esegs.size()));
+  SPID_CUDA(P->alloc(reinterpret_cast<void**>(&P->d_err_seg_ptr), sizeof(int32_t) * eseg_ptr.size()));
+  SPID_CUDA(P->alloc(reinterpret_cast<void**>(&P->d_err_tc_ptr), sizeof(int32_t) * esub_ptr.size()));
+  SPID_CUDA(P->alloc(reinterpret_cast<void**>(&P->d_err_tc_part), sizeof(double) * 2 * esegs.size()));
+  SPID_CUDA(cudaMemcpy(P->d_err_segs, esegs.data(), sizeof(ErrSeg) * esegs.size(),
+                       cudaMemcpyHostToDevice));
+  SPID_CUDA(cudaMemcpy(P->d_err_seg_ptr, eseg_ptr.data(), sizeof(int32_t) * eseg_ptr.size(),
+                       cudaMemcpyHostToDevice));
+  SPID_CUDA(cudaMemcpy(P->d_err_tc_ptr, esub_ptr.data(), sizeof(int32_t) * esub_ptr.size(),
+                       cudaMemcpyHostToDevice));
+  P->err_tc_grid = G;
+  return SPID_OK;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
@@ -431,14 +517,13 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// Encode one 2-D tensor map per subdomain over the window: dim0 = rows
-// (contiguous), dim1 = window columns, box = 32 rows x 128 columns, 128-byte
-// swizzle, zero fill outside [0, m) x [0, n).
-spid_status bind_window(spid_plan_t P, const void* window, cudaStream_t st) {
-  if (P->bound_window == window) return SPID_OK;
+// One 2-D tensor map per subdomain over the window: dim0 = rows (contiguous),
+// dim1 = window columns, box = 32 rows x 64 columns, 128-byte swizzle, zero
+// fill outside [0, m) x [0, n).
+spid_status encode_window_maps(spid_plan_t P, const void* window, std::vector<CUtensorMap>& maps) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return fail(SPID_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
-  std::vector<CUtensorMap> maps(P->S);
+  maps.resize(P->S);
   for (int s = 0; s < P->S; ++s) {
     void* base = const_cast<char*>(static_cast<const char*>(window)) + P->off[s] * P->esz;
     cuuint64_t dims[2] = {(cuuint64_t)P->m[s], (cuuint64_t)P->n[s]};
@@ -452,11 +537,69 @@ spid_status bind_window(spid_plan_t P, const void* window, cudaStream_t st) {
       return fail(SPID_ERR_INVALID_ARG, "cuTensorMapEncodeTiled failed for subdomain " +
                                             std::to_string(s) + " (code " + std::to_string((int)r) + ")");
   }
-  // previous maps may still be read by work in flight on this stream
+  return SPID_OK;
+}
+
+// Point the plan's own tensor maps at `window` (synchronizes the stream when
+// the window changes: work in flight may still read the previous maps).
+spid_status bind_window(spid_plan_t P, const void* window, cudaStream_t st) {
+  if (P->bound_window == window) return SPID_OK;
+  std::vector<CUtensorMap> maps;
+  spid_status rc = encode_window_maps(P, window, maps);
+  if (rc != SPID_OK) return rc;
   SPID_CUDA(cudaStreamSynchronize(st));
   SPID_CUDA(cudaMemcpy(P->d_tmaps, maps.data(), sizeof(CUtensorMap) * P->S, cudaMemcpyHostToDevice));
   P->bound_window = window;
   return SPID_OK;
+}
+
+// Launch the sketch of window columns [col0, col0 + ncols) with a schedule
+// already built; tmaps: device tensor maps of `window` (tensor-core plans).
+spid_status launch_sketch_range(spid_plan_t P, const Schedule* sc, const void* window,
+                                const void* tmaps, cudaStream_t cs) {
+  SketchArgs a;
+  a.probs = sc->probs;
+  a.segs = sc->segs;
+  a.seg_ptr = sc->seg_ptr;
+  a.slot_off = sc->slot_off;
+  a.partial = P->d_partial;
+  a.window = window;
+  a.tmaps = tmaps;
+  a.cta_base = 0;
+  a.l = P->l;
+  a.l_pad = P->l_pad;
+  a.seed = P->seed;
+  a.status = P->d_status;
+  a.pslot_ptr = sc->pslot_ptr;
+  a.pslots = sc->pslots;
+  a.prob_cnt = sc->prob_cnt;
+  a.Y = P->d_Y;
+  a.yoff = P->d_yoff;
+  a.slices = sc->slices;
+  a.packs = sc->packs;
+  a.psegs = sc->psegs;
+  const int nlaunch = P->per_sub() ? P->S : 1;
+  for (int q = 0; q < nlaunch; ++q) {
+    a.cta_base = P->per_sub() ? sc->cta_base_of_sub[q] : 0;
+    cudaError_t e =
+        P->bf16() ? launch_sketch_bf16(a, sc->grid, sc->stages, sc->max_tiles,
+                                       P->prec == SPID_PREC_BF16X3, cs)
+        : P->tensor_core() ? launch_sketch_tc(a, sc->grid, sc->stages, sc->max_tiles, cs)
+                           : launch_sketch_simt(a, sc->grid, P->fp64(), cs);
+    if (e != cudaSuccess) return fail(SPID_ERR_CUDA, std::string("sketch launch: ") + cudaGetErrorString(e));
+  }
+  return SPID_OK;
+}
+
+// Free every cached sketch schedule (their tables encode the tuning).
+// The caller has synchronized the device.
+void drop_schedules(spid_plan_t P) {
+  for (auto& kv : P->schedules) {
+    void* d = kv.second.dev;
+    cudaFree(d);
+    P->allocs.erase(std::remove(P->allocs.begin(), P->allocs.end(), d), P->allocs.end());
+  }
+  P->schedules.clear();
 }
 
 // Zero every completion counter (schedules and error pass).  Needed only after
@@ -593,26 +736,19 @@ spid_status spid_plan_create(const spid_plan_desc* d, spid_plan_t* out) {
   }
   P->y_elems = ysum;
   P->c_elems = csum;
-  // error units: (subdomain, 512-row block, 256-column block)
-  std::vector<int32_t> usub, urow, ucol;
-  P->unit_ptr.assign(P->S + 1, 0);
-  for (int s = 0; s < P->S; ++s) {
-    P->unit_ptr[s] = (int32_t)usub.size();
-    for (int r = 0; r < P->m[s]; r += kErrRowBlock)
-      for (int c = 0; c < P->n[s]; c += kErrColBlock) {
-        usub.push_back(s);
-        urow.push_back(r);
-        ucol.push_back(c);
-      }
-  }
-  P->unit_ptr[P->S] = (int32_t)usub.size();
-  P->units = (int)usub.size();
-  // partial workspace bound: (CTAs + problems) slots of one column group each
-  const int CG = P->group_cols();
+  // error units: the arrays hold the unit list of the smallest unit shape the
+  // tuner may pick (kTuneErrRows[0] x kTuneErrCols[0])
+  P->units_cap = count_error_units(P, kTuneErrRows[0], kTuneErrCols[0]);
+  // partial workspace bound: (CTAs + problems) slots of one column group each,
+  // for the widest column group and the largest grid any tuning may use
+  // (narrower groups divide the widest, so they need no more)
+  const int CG = P->group_cols_max();
   int64_t nprob_full = 0;
   for (int s = 0; s < P->S; ++s) nprob_full += (P->n[s] + CG - 1) / CG;
-  const int64_t ctas = (int64_t)P->sketch_grid() * (P->per_sub() ? P->S : 1);
+  const int64_t ctas = (int64_t)std::max(P->sketch_grid(), kTuneMaxCtasPerSm * P->num_sms) *
+                       (P->per_sub() ? P->S : 1);
   P->partial_cap = (ctas + nprob_full) * (int64_t)CG * P->l_pad;
+  if (P->flags & SPID_FLAG_TC_ERROR) P->tune.err_path = P->err_tc_possible() ? 1 : 0;
 
 #define SPID_ALLOC(ptr, bytes)                                                            \
   do {                                                                                    \
@@ -633,26 +769,15 @@ spid_status spid_plan_create(const spid_plan_desc* d, spid_plan_t* out) {
   SPID_ALLOC(P->d_J, sizeof(int32_t) * P->S * P->k_max);
   SPID_ALLOC(P->d_k, sizeof(int32_t) * P->S);
   SPID_ALLOC(P->d_status, sizeof(int));
-  SPID_ALLOC(P->d_unit_sub, sizeof(int32_t) * P->units);
-  SPID_ALLOC(P->d_unit_row0, sizeof(int32_t) * P->units);
-  SPID_ALLOC(P->d_unit_col0, sizeof(int32_t) * P->units);
+  SPID_ALLOC(P->d_unit_sub, sizeof(int32_t) * P->units_cap);
+  SPID_ALLOC(P->d_unit_row0, sizeof(int32_t) * P->units_cap);
+  SPID_ALLOC(P->d_unit_col0, sizeof(int32_t) * P->units_cap);
   SPID_ALLOC(P->d_unit_ptr, sizeof(int32_t) * (P->S + 1));
-  SPID_ALLOC(P->d_err_part, sizeof(double) * 2 * P->units);
+  SPID_ALLOC(P->d_err_part, sizeof(double) * 2 * P->units_cap);
   SPID_ALLOC(P->d_sub_err, sizeof(double) * 2 * P->S);
   SPID_ALLOC(P->d_err_cnt, sizeof(int) * (P->S + 1));
   SPID_ALLOC(P->d_partial, esz * P->partial_cap);
   if (P->tensor_core()) SPID_ALLOC(P->d_tmaps, sizeof(CUtensorMap) * P->S);
-  std::vector<ErrSeg> esegs;
-  std::vector<int32_t> eseg_ptr, esub_ptr;
-  if (P->err_tc_eligible()) {
-    P->err_tc = true;
-    P->err_tc_grid = P->num_sms;
-    build_error_tc_schedule(P, P->err_tc_grid, esegs, eseg_ptr, esub_ptr);
-    SPID_ALLOC(P->d_err_segs, sizeof(ErrSeg) * esegs.size());
-    SPID_ALLOC(P->d_err_seg_ptr, sizeof(int32_t) * eseg_ptr.size());
-    SPID_ALLOC(P->d_err_tc_ptr, sizeof(int32_t) * esub_ptr.size());
-    SPID_ALLOC(P->d_err_tc_part, sizeof(double) * 2 * esegs.size());
-  }
 #undef SPID_ALLOC
 #define SPID_H2D(dst, src, bytes)                                                          \
   do {                                                                                     \
@@ -668,16 +793,12 @@ spid_status spid_plan_create(const spid_plan_desc* d, spid_plan_t* out) {
   SPID_H2D(P->d_ld, P->ld.data(), sizeof(int64_t) * P->S);
   SPID_H2D(P->d_yoff, yoff.data(), sizeof(int64_t) * P->S);
   SPID_H2D(P->d_coff, coff.data(), sizeof(int64_t) * P->S);
-  SPID_H2D(P->d_unit_sub, usub.data(), sizeof(int32_t) * P->units);
-  SPID_H2D(P->d_unit_row0, urow.data(), sizeof(int32_t) * P->units);
-  SPID_H2D(P->d_unit_col0, ucol.data(), sizeof(int32_t) * P->units);
-  SPID_H2D(P->d_unit_ptr, P->unit_ptr.data(), sizeof(int32_t) * (P->S + 1));
-  if (P->err_tc) {
-    SPID_H2D(P->d_err_segs, esegs.data(), sizeof(ErrSeg) * esegs.size());
-    SPID_H2D(P->d_err_seg_ptr, eseg_ptr.data(), sizeof(int32_t) * eseg_ptr.size());
-    SPID_H2D(P->d_err_tc_ptr, esub_ptr.data(), sizeof(int32_t) * esub_ptr.size());
-  }
 #undef SPID_H2D
+  {
+    spid_status st = upload_error_units(P);
+    if (st == SPID_OK && P->tune.err_path == 1) st = ensure_error_tc(P);
+    if (st != SPID_OK) return bail(st);
+  }
   if (cudaMemset(P->d_Y, 0, esz * P->y_elems) != cudaSuccess ||
       cudaMemset(P->d_status, 0, sizeof(int)) != cudaSuccess ||
       cudaMemset(P->d_err_cnt, 0, sizeof(int) * (P->S + 1)) != cudaSuccess ||
@@ -694,6 +815,8 @@ spid_status spid_plan_create(const spid_plan_desc* d, spid_plan_t* out) {
 
 spid_status spid_plan_destroy(spid_plan_t P) {
   if (!P) return SPID_OK;
+  if (P->live_graphs > 0)
+    return fail(SPID_ERR_STATE, "destroy the plan's graphs (spid_graph_destroy) first");
   cudaSetDevice(P->device);
   cudaDeviceSynchronize();
   for (void* p : P->allocs) cudaFree(p);
@@ -735,43 +858,10 @@ spid_status spid_sketch(spid_plan_t P, const void* window, int32_t col0, int32_t
     st = bind_window(P, window, cs);
     if (st != SPID_OK) return st;
   }
-  SketchArgs a;
-  a.probs = sc->probs;
-  a.segs = sc->segs;
-  a.seg_ptr = sc->seg_ptr;
-  a.slot_off = sc->slot_off;
-  a.partial = P->d_partial;
-  a.window = window;
-  a.tmaps = P->d_tmaps;
-  a.cta_base = 0;
-  a.l = P->l;
-  a.l_pad = P->l_pad;
-  a.seed = P->seed;
-  a.status = P->d_status;
-  a.pslot_ptr = sc->pslot_ptr;
-  a.pslots = sc->pslots;
-  a.prob_cnt = sc->prob_cnt;
-  a.Y = P->d_Y;
-  a.yoff = P->d_yoff;
-  a.slices = sc->slices;
-  a.packs = sc->packs;
-  a.psegs = sc->psegs;
-  const int nlaunch = P->per_sub() ? P->S : 1;
-  for (int q = 0; q < nlaunch; ++q) {
-    a.cta_base = P->per_sub() ? sc->cta_base_of_sub[q] : 0;
-    cudaError_t e =
-        P->bf16() ? launch_sketch_bf16(a, sc->grid, sc->stages, sc->max_tiles,
-                                       P->prec == SPID_PREC_BF16X3, cs)
-        : P->tensor_core() ? launch_sketch_tc(a, sc->grid, sc->stages, sc->max_tiles, cs)
-                           : launch_sketch_simt(a, sc->grid, P->fp64(), cs);
-    if (e != cudaSuccess) return fail(SPID_ERR_CUDA, std::string("sketch launch: ") + cudaGetErrorString(e));
-  }
-  return SPID_OK;
+  return launch_sketch_range(P, sc, window, P->d_tmaps, cs);
 }
 
-spid_status spid_finalize(spid_plan_t P, spid_stream_t stream) {
-  spid_status st = check_plan(P);
-  if (st != SPID_OK) return st;
+static spid_status run_finalize(spid_plan_t P, cudaStream_t cs) {
   QrcpArgs a;
   a.Y = P->d_Y;
   a.yoff = P->d_yoff;
@@ -786,7 +876,6 @@ spid_status spid_finalize(spid_plan_t P, spid_stream_t stream) {
   a.u_mode = P->u_mode();
   a.sub_base = 0;
   a.status = P->d_status;
-  cudaStream_t cs = (cudaStream_t)stream;
   if (P->per_sub()) {
     for (int s = 0; s < P->S; ++s) {
       a.sub_base = s;
@@ -798,6 +887,12 @@ spid_status spid_finalize(spid_plan_t P, spid_stream_t stream) {
     if (e != cudaSuccess) return fail(SPID_ERR_CUDA, std::string("qrcp launch: ") + cudaGetErrorString(e));
   }
   return SPID_OK;
+}
+
+spid_status spid_finalize(spid_plan_t P, spid_stream_t stream) {
+  spid_status st = check_plan(P);
+  if (st != SPID_OK) return st;
+  return run_finalize(P, (cudaStream_t)stream);
 }
 
 static spid_status run_error(spid_plan_t P, const void* window, void* out, double* err_dev,
@@ -829,7 +924,9 @@ static spid_status run_error(spid_plan_t P, const void* window, void* out, doubl
   a.sub_err = P->d_sub_err;
   a.total = total_dev;
   a.S = P->S;
-  if (P->err_tc) {
+  a.row_block = P->tune.err_rows;
+  a.col_block = P->tune.err_cols;
+  if (P->tune.err_path == 1 && P->err_tc_grid > 0) {
     ErrTcArgs t;
     t.e = a;
     t.e.part = P->d_err_tc_part;
@@ -965,5 +1062,358 @@ extern "C" spid_status spid_philox(const uint32_t* ctr_dev, uint32_t key0, uint3
   const int grid = (int)std::min<int64_t>((count + 255) / 256, 4096);
   philox_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(ctr_dev, key0, key1, out_dev, count);
   SPID_CUDA(cudaGetLastError());
+  return SPID_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tuning: candidate tile shapes and schedules, measured on the caller's window
+// ---------------------------------------------------------------------------
+namespace {
+
+bool valid_tuning(const spid_tuning& t) {
+  auto in = [](int v, std::initializer_list<int> set) {
+    return std::find(set.begin(), set.end(), v) != set.end();
+  };
+  return in(t.sketch_pack_slices, {1, 2, 4, 8}) && (t.sketch_stages == 0 ||
+         (t.sketch_stages >= 2 && t.sketch_stages <= 8)) &&
+         in(t.sketch_ctas_per_sm, {0, 1, 2}) && in(t.error_path, {0, 1}) &&
+         in(t.error_rows, {256, 512, 1024}) && in(t.error_cols, {128, 256});
+}
+
+TuneCfg cfg_of(const spid_tuning& t) {
+  TuneCfg c;
+  c.pack_slices = t.sketch_pack_slices;
+  c.stages = t.sketch_stages;
+  c.ctas_per_sm = t.sketch_ctas_per_sm;
+  c.err_path = t.error_path;
+  c.err_rows = t.error_rows;
+  c.err_cols = t.error_cols;
+  return c;
+}
+
+spid_tuning tuning_of(const TuneCfg& c, float sk, float er) {
+  spid_tuning t;
+  t.sketch_pack_slices = c.pack_slices;
+  t.sketch_stages = c.stages;
+  t.sketch_ctas_per_sm = c.ctas_per_sm;
+  t.error_path = c.err_path;
+  t.error_rows = c.err_rows;
+  t.error_cols = c.err_cols;
+  t.sketch_ms = sk;
+  t.error_ms = er;
+  return t;
+}
+
+// Install a sketch configuration: drop the cached schedules and rebuild the
+// whole-window one.  The device is idle.
+spid_status apply_sketch_cfg(spid_plan_t P, const TuneCfg& c) {
+  P->tune.pack_slices = c.pack_slices;
+  P->tune.stages = c.stages;
+  P->tune.ctas_per_sm = c.ctas_per_sm;
+  drop_schedules(P);
+  Schedule* sc = nullptr;
+  return get_schedule(P, 0, P->n_max, &sc);
+}
+
+spid_status apply_error_cfg(spid_plan_t P, const TuneCfg& c) {
+  if (c.err_path == 1) {
+    spid_status st = ensure_error_tc(P);
+    if (st != SPID_OK) return st;
+  }
+  P->tune.err_path = c.err_path;
+  P->tune.err_rows = c.err_rows;
+  P->tune.err_cols = c.err_cols;
+  return upload_error_units(P);
+}
+
+// Median of `reps` timed runs of fn after one warm-up, CUDA events on cs.
+template <typename F>
+spid_status time_median(cudaStream_t cs, int reps, F fn, float* ms) {
+  spid_status st = fn();
+  if (st != SPID_OK) return st;
+  std::vector<float> t;
+  cudaEvent_t e0, e1;
+  SPID_CUDA(cudaEventCreate(&e0));
+  SPID_CUDA(cudaEventCreate(&e1));
+  for (int r = 0; r < reps && st == SPID_OK; ++r) {
+    cudaEventRecord(e0, cs);
+    st = fn();
+    cudaEventRecord(e1, cs);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float x = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&x, e0, e1);
+    if (e != cudaSuccess && st == SPID_OK)
+      st = fail(SPID_ERR_CUDA, std::string("tuning timer: ") + cudaGetErrorString(e));
+    t.push_back(x);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != SPID_OK) return st;
+  std::sort(t.begin(), t.end());
+  *ms = t[t.size() / 2];
+  return SPID_OK;
+}
+
+}  // namespace
+
+extern "C" spid_status spid_plan_get_tuning(spid_plan_t P, spid_tuning* out) {
+  if (!P || !out) return fail(SPID_ERR_INVALID_ARG, "plan/out is NULL");
+  *out = tuning_of(P->tune, P->tuned_sketch_ms, P->tuned_error_ms);
+  return SPID_OK;
+}
+
+extern "C" spid_status spid_plan_set_tuning(spid_plan_t P, const spid_tuning* t) {
+  spid_status st = check_plan(P);
+  if (st != SPID_OK) return st;
+  if (!t || !valid_tuning(*t)) return fail(SPID_ERR_INVALID_ARG, "tuning value out of range");
+  if (P->live_graphs > 0) return fail(SPID_ERR_STATE, "graphs captured from the plan exist");
+  if (t->error_path == 1 && !P->err_tc_possible())
+    return fail(SPID_ERR_UNSUPPORTED, "the tensor-core error pass needs a batched TF32/BF16/3xBF16 "
+                                      "plan with k_max <= 32");
+  std::lock_guard<std::mutex> g(P->tune_mu);
+  SPID_CUDA(cudaDeviceSynchronize());
+  const TuneCfg c = cfg_of(*t);
+  st = apply_sketch_cfg(P, c);
+  if (st == SPID_OK) st = apply_error_cfg(P, c);
+  P->tuned_sketch_ms = P->tuned_error_ms = 0.f;
+  return st;
+}
+
+extern "C" spid_status spid_plan_autotune(spid_plan_t P, const void* window, spid_stream_t stream,
+                                          spid_tuning* best) {
+  spid_status st = check_plan(P);
+  if (st != SPID_OK) return st;
+  if (!window || reinterpret_cast<uintptr_t>(window) % 16)
+    return fail(SPID_ERR_INVALID_ARG, "window is NULL or not 16-byte aligned");
+  if (P->live_graphs > 0) return fail(SPID_ERR_STATE, "graphs captured from the plan exist");
+  std::lock_guard<std::mutex> g(P->tune_mu);
+  cudaStream_t cs = (cudaStream_t)stream;
+  SPID_CUDA(cudaDeviceSynchronize());
+  if (P->tensor_core()) {
+    st = bind_window(P, window, cs);
+    if (st != SPID_OK) return st;
+  }
+  constexpr int kReps = 5;
+  constexpr float kTuneMargin = 0.02f;
+  // ---- sketch candidates
+  std::vector<TuneCfg> cands;
+  if (P->tensor_core()) {
+    for (int ps : {8, 4, 2, 1})
+      for (int stg : {0, 4, 2}) {
+        TuneCfg c = P->tune;
+        c.pack_slices = ps;
+        c.stages = stg;
+        cands.push_back(c);
+      }
+  } else {
+    for (int cps : {1, 2}) {
+      TuneCfg c = P->tune;
+      c.ctas_per_sm = cps;
+      cands.push_back(c);
+    }
+  }
+  TuneCfg best_cfg = P->tune;
+  float best_sk = 0.f;
+  int seen_stages = -1, seen_pack = -1;
+  for (const TuneCfg& c : cands) {
+    st = apply_sketch_cfg(P, c);
+    if (st == SPID_ERR_UNSUPPORTED) continue;   // e.g. too few stages fit
+    if (st != SPID_OK) return st;
+    Schedule* sc = nullptr;
+    st = get_schedule(P, 0, P->n_max, &sc);
+    if (st != SPID_OK) return st;
+    // stage counts above what fits collapse onto the same launch: skip repeats
+    if (P->tensor_core() && sc->stages == seen_stages && c.pack_slices == seen_pack) continue;
+    seen_stages = sc->stages;
+    seen_pack = c.pack_slices;
+    float ms = 0.f;
+    st = time_median(cs, kReps, [&] { return launch_sketch_range(P, sc, window, P->d_tmaps, cs); },
+                     &ms);
+    if (st != SPID_OK) return st;
+    // the first candidate is the default; another must beat the best so far
+    // by kTuneMargin to replace it (run-to-run noise is a few percent)
+    if (best_sk == 0.f || ms < best_sk * (1.f - kTuneMargin)) {
+      best_sk = ms;
+      best_cfg.pack_slices = c.pack_slices;
+      best_cfg.stages = c.stages;
+      best_cfg.ctas_per_sm = c.ctas_per_sm;
+    }
+  }
+  st = apply_sketch_cfg(P, best_cfg);
+  if (st != SPID_OK) return st;
+  {
+    Schedule* sc = nullptr;
+    st = get_schedule(P, 0, P->n_max, &sc);
+    if (st == SPID_OK) st = launch_sketch_range(P, sc, window, P->d_tmaps, cs);
+    if (st == SPID_OK) st = run_finalize(P, cs);
+    if (st != SPID_OK) return st;
+  }
+  // ---- error-pass candidates
+  std::vector<TuneCfg> ecands;
+  {
+    TuneCfg t = best_cfg;   // the default shape first
+    t.err_path = 0;
+    t.err_rows = kErrRowBlock;
+    t.err_cols = kErrColBlock;
+    ecands.push_back(t);
+  }
+  for (int r : kTuneErrRows)
+    for (int c : kTuneErrCols) {
+      if (r == kErrRowBlock && c == kErrColBlock) continue;
+      TuneCfg t = best_cfg;
+      t.err_path = 0;
+      t.err_rows = r;
+      t.err_cols = c;
+      ecands.push_back(t);
+    }
+  if (P->err_tc_possible()) {
+    TuneCfg t = best_cfg;
+    t.err_path = 1;
+    t.err_rows = kErrRowBlock;
+    t.err_cols = kErrColBlock;
+    ecands.push_back(t);
+  }
+  float best_er = 0.f;
+  TuneCfg best_e = best_cfg;
+  for (const TuneCfg& c : ecands) {
+    st = apply_error_cfg(P, c);
+    if (st != SPID_OK) return st;
+    float ms = 0.f;
+    st = time_median(cs, kReps, [&] { return run_error(P, window, nullptr, nullptr, nullptr, cs); },
+                     &ms);
+    if (st != SPID_OK) return st;
+    if (best_er == 0.f || ms < best_er * (1.f - kTuneMargin)) {
+      best_er = ms;
+      best_e = c;
+    }
+  }
+  st = apply_error_cfg(P, best_e);
+  if (st != SPID_OK) return st;
+  SPID_CUDA(cudaStreamSynchronize(cs));
+  P->tuned_sketch_ms = best_sk;
+  P->tuned_error_ms = best_er;
+  if (best) *best = tuning_of(P->tune, best_sk, best_er);
+  return SPID_OK;
+}
+
+extern "C" spid_status spid_plan_tuning_key(spid_plan_t P, char* buf, int32_t len) {
+  spid_status st = check_plan(P);
+  if (st != SPID_OK) return st;
+  if (!buf || len <= 0) return fail(SPID_ERR_INVALID_ARG, "buf is NULL or len <= 0");
+  cudaDeviceProp prop;
+  SPID_CUDA(cudaGetDeviceProperties(&prop, P->device));
+  double msum = 0.0, nsum = 0.0;
+  for (int s = 0; s < P->S; ++s) {
+    msum += P->m[s];
+    nsum += P->n[s];
+  }
+  auto lg = [](double x) { return x >= 1.0 ? (int)std::floor(std::log2(x)) : 0; };
+  const int w = std::snprintf(buf, (size_t)len,
+                              "spid-tune-1;cc=%d.%d;sms=%d;prec=%d;flags=%u;l_pad=%d;k_max=%d;"
+                              "log2S=%d;log2m=%d;log2n=%d",
+                              prop.major, prop.minor, P->num_sms, P->prec, P->flags, P->l_pad,
+                              P->k_max, lg(P->S), lg(msum / P->S), lg(nsum / P->S));
+  if (w < 0 || w >= len) return fail(SPID_ERR_INVALID_ARG, "key buffer too small");
+  return SPID_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graphs of one step
+// ---------------------------------------------------------------------------
+struct spid_graph_s {
+  spid_plan_t plan = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  void* d_tmaps = nullptr;
+};
+
+extern "C" spid_status spid_graph_destroy(spid_graph_t G) {
+  if (!G) return SPID_OK;
+  if (G->plan) cudaSetDevice(G->plan->device);
+  cudaDeviceSynchronize();
+  if (G->exec) cudaGraphExecDestroy(G->exec);
+  if (G->graph) cudaGraphDestroy(G->graph);
+  if (G->d_tmaps) cudaFree(G->d_tmaps);
+  if (G->plan) G->plan->live_graphs--;
+  delete G;
+  return SPID_OK;
+}
+
+extern "C" spid_status spid_graph_create(spid_plan_t P, const void* window, int32_t col0,
+                                         int32_t ncols, int32_t microbatch, uint32_t what,
+                                         double* err_dev, double* total_dev,
+                                         spid_graph_t* out) {
+  spid_status st = check_plan(P);
+  if (st != SPID_OK) return st;
+  if (!out) return fail(SPID_ERR_INVALID_ARG, "graph_out is NULL");
+  *out = nullptr;
+  if (what == 0 || (what & ~7u)) return fail(SPID_ERR_INVALID_ARG, "what must be a non-empty OR of SPID_GRAPH_*");
+  const bool sketch = what & SPID_GRAPH_SKETCH, finalize = what & SPID_GRAPH_FINALIZE,
+             error = what & SPID_GRAPH_ERROR;
+  if ((sketch || error) && (!window || reinterpret_cast<uintptr_t>(window) % 16))
+    return fail(SPID_ERR_INVALID_ARG, "window is NULL or not 16-byte aligned");
+  if (col0 < 0 || ncols < 0 || microbatch < 0)
+    return fail(SPID_ERR_INVALID_ARG, "negative column range or micro-batch");
+  // schedules of every sketch call, built before capture (they may allocate)
+  std::vector<Schedule*> scheds;
+  if (sketch && ncols > 0 && col0 < P->n_max) {
+    ncols = std::min(ncols, P->n_max - col0);
+    const int mb = microbatch > 0 ? microbatch : ncols;
+    for (int c = col0; c < col0 + ncols; c += mb) {
+      Schedule* sc = nullptr;
+      st = get_schedule(P, c, std::min(mb, col0 + ncols - c), &sc);
+      if (st != SPID_OK) return st;
+      scheds.push_back(sc);
+    }
+  }
+  spid_graph_s* G = new spid_graph_s();
+  G->plan = P;
+  P->live_graphs++;
+  auto bail = [&](spid_status s2) {
+    spid_graph_destroy(G);
+    return s2;
+  };
+  if (!scheds.empty() && P->tensor_core()) {
+    std::vector<CUtensorMap> maps;
+    st = encode_window_maps(P, window, maps);
+    if (st != SPID_OK) return bail(st);
+    cudaError_t e = cudaMalloc(&G->d_tmaps, sizeof(CUtensorMap) * P->S);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(G->d_tmaps, maps.data(), sizeof(CUtensorMap) * P->S, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess)
+      return bail(fail(e == cudaErrorMemoryAllocation ? SPID_ERR_OOM : SPID_ERR_CUDA,
+                       std::string("graph tensor maps: ") + cudaGetErrorString(e)));
+  }
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return bail(fail(SPID_ERR_CUDA, cudaGetErrorString(e)));
+  e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return bail(fail(SPID_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e)));
+  }
+  spid_status cap = SPID_OK;
+  for (Schedule* sc : scheds)
+    if (cap == SPID_OK) cap = launch_sketch_range(P, sc, window, G->d_tmaps, cs);
+  if (cap == SPID_OK && finalize) cap = run_finalize(P, cs);
+  if (cap == SPID_OK && error) cap = run_error(P, window, nullptr, err_dev, total_dev, cs);
+  e = cudaStreamEndCapture(cs, &G->graph);
+  cudaStreamDestroy(cs);
+  if (cap != SPID_OK) return bail(cap);
+  if (e != cudaSuccess)
+    return bail(fail(SPID_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e)));
+  e = cudaGraphInstantiate(&G->exec, G->graph, 0);
+  if (e != cudaSuccess)
+    return bail(fail(SPID_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e)));
+  *out = G;
+  return SPID_OK;
+}
+
+extern "C" spid_status spid_graph_launch(spid_graph_t G, spid_stream_t stream) {
+  if (!G || !G->exec) return fail(SPID_ERR_INVALID_ARG, "graph is NULL");
+  spid_status st = check_plan(G->plan);
+  if (st != SPID_OK) return st;
+  SPID_CUDA(cudaGraphLaunch(G->exec, (cudaStream_t)stream));
   return SPID_OK;
 }

@@ -166,9 +166,13 @@ struct QrcpArgs {
   int* status;
 };
 
-// Fused reconstruction / error pass.
+// Fused reconstruction / error pass.  A work unit is (subdomain, block of
+// row_block rows, block of col_block columns); the defaults below, or a shape
+// chosen by the plan's autotuner (row_block a multiple of kErrTile, col_block
+// a multiple of 32, at most kErrColBlockMax).
 constexpr int kErrRowBlock = 512;
 constexpr int kErrColBlock = 256;
+constexpr int kErrColBlockMax = 256;
 constexpr int kErrTile = 128;
 
 struct ErrArgs {
@@ -196,6 +200,8 @@ struct ErrArgs {
   double* total;              // [4] or nullptr
   int32_t S;
   const int32_t* srows = nullptr;   // rows stored per subdomain for the CF sums (nullptr: m)
+  int32_t row_block = kErrRowBlock; // rows of a unit
+  int32_t col_block = kErrColBlock; // columns of a unit (C block staged in shared memory)
 };
 
 // Tensor-core error pass (FP32 windows, k_max <= 32): a segment is a run of
@@ -252,7 +258,7 @@ cudaError_t launch_sketch_tc(const SketchArgs& s, int grid, int stages, int max_
 int qrcp_cols_per_thread(int n_max, int l_pad, bool fp64);
 cudaError_t launch_qrcp(const QrcpArgs& a, int grid, int n_max, int l_pad, bool fp64,
                         cudaStream_t st);
-size_t error_smem_bytes(int k_max, bool fp64);
+size_t error_smem_bytes(int k_max, int col_block, bool fp64);
 size_t error_tc_smem_bytes();
 cudaError_t launch_error_tc(const ErrTcArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_error(const ErrArgs& a, int units, bool fp64, cudaStream_t st);

@@ -36,7 +36,12 @@ EXPORTS = ["spid_plan_create", "spid_plan_destroy", "spid_plan_info", "spid_sket
            "spid_sub_get_factors", "spid_sub_get_coarse", "spid_sub_device_status",
            "spid_ts_plan_create", "spid_ts_plan_destroy", "spid_ts_block", "spid_ts_finalize",
            "spid_ts_error", "spid_ts_reconstruct", "spid_ts_get_factors",
-           "spid_ts_get_block_factors", "spid_ts_device_status"]
+           "spid_ts_get_block_factors", "spid_ts_device_status",
+           "spid_plan_get_tuning", "spid_plan_set_tuning", "spid_plan_autotune",
+           "spid_plan_tuning_key", "spid_graph_create", "spid_graph_launch", "spid_graph_destroy"]
+GRAPH_SKETCH = 1
+GRAPH_FINALIZE = 2
+GRAPH_ERROR = 4
 FORM_SPID = 0
 FORM_SUBID = 1
 
@@ -71,6 +76,27 @@ class _SubDesc(ctypes.Structure):
                 ("k_max", ctypes.c_int32),
                 ("tol", ctypes.c_double),
                 ("flags", ctypes.c_uint32)]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("sketch_pack_slices", ctypes.c_int32),
+                ("sketch_stages", ctypes.c_int32),
+                ("sketch_ctas_per_sm", ctypes.c_int32),
+                ("error_path", ctypes.c_int32),
+                ("error_rows", ctypes.c_int32),
+                ("error_cols", ctypes.c_int32),
+                ("sketch_ms", ctypes.c_float),
+                ("error_ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "_Tuning":
+        t = cls()
+        for name, _ in cls._fields_:
+            setattr(t, name, d.get(name, 0))
+        return t
 
 
 class _TsDesc(ctypes.Structure):
@@ -133,6 +159,13 @@ def load_library(path: str = LIB_PATH):
             "spid_ts_get_factors": ([vp, vp, vp, vp, vp], c.c_int),
             "spid_ts_get_block_factors": ([vp, i32, vp, vp, vp, vp], c.c_int),
             "spid_ts_device_status": ([vp, vp], c.c_int),
+            "spid_plan_get_tuning": ([vp, c.POINTER(_Tuning)], c.c_int),
+            "spid_plan_set_tuning": ([vp, c.POINTER(_Tuning)], c.c_int),
+            "spid_plan_autotune": ([vp, vp, vp, c.POINTER(_Tuning)], c.c_int),
+            "spid_plan_tuning_key": ([vp, c.c_char_p, i32], c.c_int),
+            "spid_graph_create": ([vp, vp, i32, i32, i32, u32, vp, vp, c.POINTER(vp)], c.c_int),
+            "spid_graph_launch": ([vp, vp], c.c_int),
+            "spid_graph_destroy": ([vp], c.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -213,6 +246,8 @@ class Plan:
 
     def close(self):
         if getattr(self, "_h", None):
+            for g in list(getattr(self, "_graphs", [])):
+                g.close()
             load_library().spid_plan_destroy(self._h)
             self._h = None
 
@@ -221,6 +256,65 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    # ---------------------------------------------------------------- tuning
+    def tuning(self) -> dict:
+        t = _Tuning()
+        _check(load_library().spid_plan_get_tuning(self._h, ctypes.byref(t)),
+               "spid_plan_get_tuning")
+        return t.as_dict()
+
+    def set_tuning(self, tuning: dict):
+        t = _Tuning.from_dict(tuning)
+        _check(load_library().spid_plan_set_tuning(self._h, ctypes.byref(t)),
+               "spid_plan_set_tuning")
+
+    def tuning_key(self) -> str:
+        buf = ctypes.create_string_buffer(512)
+        _check(load_library().spid_plan_tuning_key(self._h, buf, 512), "spid_plan_tuning_key")
+        return buf.value.decode()
+
+    def autotune(self, window, stream=None, cache: str | None = None) -> dict:
+        """Measure the candidate tile shapes on `window` and keep the fastest.
+        With `cache` (a JSON file path), a tuning stored under this plan's
+        tuning key is applied instead of measuring, and a new measurement is
+        stored there."""
+        import json
+        key = self.tuning_key()
+        store = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                store = json.load(f)
+            if key in store:
+                self.set_tuning(store[key])
+                return dict(store[key], cached=True)
+        t = _Tuning()
+        _check(load_library().spid_plan_autotune(self._h, _ptr(window), _stream_handle(stream),
+                                                 ctypes.byref(t)), "spid_plan_autotune")
+        d = t.as_dict()
+        if cache:
+            store[key] = d
+            tmp = f"{cache}.tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(store, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return dict(d, cached=False)
+
+    def graph(self, window, what: int = GRAPH_SKETCH | GRAPH_FINALIZE | GRAPH_ERROR, err=None,
+              total=None, col0: int = 0, ncols: int | None = None,
+              microbatch: int = 0) -> "Graph":
+        """Capture one step (the SPID_GRAPH_* stages in `what`) as a CUDA graph."""
+        if ncols is None:
+            ncols = int(self.n.max()) - col0
+        h = ctypes.c_void_p()
+        _check(load_library().spid_graph_create(self._h, _ptr(window), int(col0), int(ncols),
+                                                int(microbatch), int(what), _ptr(err), _ptr(total),
+                                                ctypes.byref(h)), "spid_graph_create")
+        g = Graph(self, h)
+        if not hasattr(self, "_graphs"):
+            self._graphs = []
+        self._graphs.append(g)
+        return g
 
     # ---------------------------------------------------------------- hot path
     def sketch(self, window, col0: int = 0, ncols: int | None = None, stream=None):
@@ -267,6 +361,32 @@ class Plan:
 
     def device_status(self, stream=None) -> int:
         return int(load_library().spid_device_status(self._h, _stream_handle(stream)))
+
+
+class Graph:
+    """A captured step of a Plan (spid_graph_*); replay with launch()."""
+
+    def __init__(self, plan: Plan, handle):
+        self._plan = plan
+        self._h = handle
+
+    def launch(self, stream=None):
+        _check(load_library().spid_graph_launch(self._h, _stream_handle(stream)),
+               "spid_graph_launch")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().spid_graph_destroy(self._h)
+            self._h = None
+            graphs = getattr(self._plan, "_graphs", [])
+            if self in graphs:
+                graphs.remove(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class SubPlan:

@@ -1,0 +1,205 @@
+"""CUDA graphs and the autotuner, through the C ABI.
+
+* A captured step (sketch, finalize, error) replays the eager calls
+  bit for bit: the same kernels run on the same schedules, and every cross-CTA
+  sum is folded in a fixed order.
+* The graph keeps its own tensor maps: eager calls that rebind the plan to
+  another window do not change what the graph reads.
+* Every tuning (pack width, pipeline depth, error-pass unit shape and path)
+  changes only the order of FP32 partial sums, so the sketch moves by rounding
+  alone (relative FP32 sum reordering bound, far below the TF32 product
+  rounding), the separated pivots stay identical, and the result still meets
+  the oracle parity bars of the default tuning.
+"""
+import json
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2103_01380_gb300 import inputs, spid
+from _helpers import oracle_window, rel_fro, separated_prefix, U_MODE
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_01380_gb300 import build
+    build.build()
+    spid.load_library()
+    torch.cuda.init()
+
+
+def _window(seed=40, dtype=np.float32, m=(33, 200, 1000, 4099, 4099), n=(40, 300, 130, 600, 512)):
+    blocks = [inputs.separated_lowrank(mm, nn, 6, seed + s, noise=1e-3)
+              for s, (mm, nn) in enumerate(zip(m, n))]
+    return inputs.pack_blocks(blocks, dtype=dtype)
+
+
+def _state(plan, err, tot):
+    torch.cuda.synchronize()
+    k, J, C = plan.factors()
+    Y = plan.sketches()
+    return {"k": k, "J": J, "C": [c.copy() for c in C], "Y": [y.copy() for y in Y],
+            "err": err.cpu().numpy().copy(), "tot": tot.cpu().numpy().copy()}
+
+
+def _same(a, b):
+    assert np.array_equal(a["k"], b["k"])
+    assert np.array_equal(a["J"], b["J"])
+    for x, y in zip(a["Y"], b["Y"]):
+        assert np.array_equal(x, y)
+    for x, y in zip(a["C"], b["C"]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a["err"], b["err"])
+    assert np.array_equal(a["tot"], b["tot"])
+
+
+@pytest.mark.parametrize("precision,flags", [("tf32", 0), ("bf16x3", 0), ("fp32", 0),
+                                             ("fp64", 0), ("fp32", spid.FLAG_PER_SUBDOMAIN),
+                                             ("tf32", spid.FLAG_TC_ERROR)])
+def test_graph_replays_eager_step_bitwise(precision, flags):
+    win = _window(dtype=np.float64 if precision == "fp64" else np.float32)
+    w = torch.from_numpy(win.data).cuda()
+    plan = spid.Plan.for_window(win, k_max=5, p=8, precision=precision, seed=7, flags=flags)
+    err = torch.zeros(2 * win.num_sub, dtype=torch.float64, device="cuda")
+    tot = torch.zeros(4, dtype=torch.float64, device="cuda")
+    plan.sketch(w); plan.finalize(); plan.error(w, err, tot)
+    eager = _state(plan, err, tot)
+    g = plan.graph(w, err=err, total=tot)
+    plan.reset()
+    err.zero_(); tot.zero_()
+    for _ in range(3):
+        g.launch()
+    graphed = _state(plan, err, tot)
+    assert plan.device_status() == 0
+    _same(eager, graphed)
+    g.close()
+    plan.close()
+
+
+def test_graph_microbatches_and_own_tensor_maps():
+    win = _window(seed=50)
+    win2 = _window(seed=60)
+    w = torch.from_numpy(win.data).cuda()
+    w2 = torch.from_numpy(win2.data).cuda()
+    plan = spid.Plan.for_window(win, k_max=5, p=8, precision="tf32", seed=9)
+    err = torch.zeros(2 * win.num_sub, dtype=torch.float64, device="cuda")
+    tot = torch.zeros(4, dtype=torch.float64, device="cuda")
+    for c0 in range(0, int(win.n.max()), 64):
+        plan.sketch(w, c0, 64)
+    plan.finalize(); plan.error(w, err, tot)
+    eager = _state(plan, err, tot)
+    g = plan.graph(w, err=err, total=tot, microbatch=64)
+    # rebind the plan's own maps to another window, then replay the graph
+    plan.sketch(w2)
+    plan.reset()
+    g.launch()
+    _same(eager, _state(plan, err, tot))
+    # a graph of the stages alone composes with eager calls
+    gs = plan.graph(w, what=spid.GRAPH_SKETCH, microbatch=64)
+    gf = plan.graph(None, what=spid.GRAPH_FINALIZE)
+    plan.reset()
+    gs.launch(); gf.launch(); plan.error(w, err, tot)
+    _same(eager, _state(plan, err, tot))
+    # the plan refuses to go away or be retuned while graphs exist
+    assert spid.load_library().spid_plan_destroy(plan._h) == 4   # SPID_ERR_STATE
+    with pytest.raises(spid.SpidError) as ei:
+        plan.set_tuning(plan.tuning())
+    assert ei.value.status == 4
+    for x in (g, gs, gf):
+        x.close()
+    plan.set_tuning(plan.tuning())
+    plan.close()
+
+
+def test_set_tuning_rejects_out_of_range_values():
+    win = _window(seed=70, m=(100,), n=(50,))
+    plan = spid.Plan.for_window(win, k_max=5, p=8, precision="fp32", seed=1)
+    base = plan.tuning()
+    assert base["sketch_pack_slices"] == 8 and base["error_rows"] == 512
+    for key, bad in [("sketch_pack_slices", 3), ("sketch_stages", 1), ("sketch_stages", 9),
+                     ("sketch_ctas_per_sm", 3), ("error_rows", 300), ("error_cols", 64),
+                     ("error_path", 2)]:
+        with pytest.raises(spid.SpidError) as ei:
+            plan.set_tuning(dict(base, **{key: bad}))
+        assert ei.value.status == 1, key
+    with pytest.raises(spid.SpidError) as ei:
+        plan.set_tuning(dict(base, error_path=1))   # FP32 plans have no tensor-core pass
+    assert ei.value.status == 7
+    plan.close()
+
+
+TUNINGS = [dict(sketch_pack_slices=ps, sketch_stages=st, error_path=0, error_rows=r, error_cols=c)
+           for ps, st, r, c in [(8, 0, 512, 256), (4, 2, 256, 128), (2, 4, 1024, 256),
+                                (1, 0, 256, 256)]] + \
+          [dict(sketch_pack_slices=8, sketch_stages=3, error_path=1, error_rows=512, error_cols=256)]
+
+
+@pytest.mark.parametrize("tuning", TUNINGS)
+def test_every_tuning_meets_parity(tuning):
+    win = _window(seed=80)
+    w = torch.from_numpy(win.data).cuda()
+    k_max, p, prec, seed = 5, 8, "tf32", 11
+    ref = spid.Plan.for_window(win, k_max=k_max, p=p, precision=prec, seed=seed)
+    plan = spid.Plan.for_window(win, k_max=k_max, p=p, precision=prec, seed=seed)
+    plan.set_tuning(dict(plan.tuning(), **tuning))
+    got = plan.tuning()
+    for key, v in tuning.items():
+        assert got[key] == v
+    res = []
+    for pl in (ref, plan):
+        err = torch.zeros(2 * win.num_sub, dtype=torch.float64, device="cuda")
+        tot = torch.zeros(4, dtype=torch.float64, device="cuda")
+        pl.sketch(w); pl.finalize(); pl.error(w, err, tot)
+        res.append(_state(pl, err, tot))
+        assert pl.device_status() == 0
+    o = oracle_window(win, k_max + p, k_max, 0.0, prec, seed)
+    for s in range(win.num_sub):
+        # FP32 reordering of the same TF32 products: far below the 3e-3 TF32 bar
+        assert rel_fro(res[1]["Y"][s], res[0]["Y"][s]) <= 1e-5
+        pre = min(separated_prefix(o["Y"][s], 5, 2e-2, U_MODE[prec]), int(o["k"][s]))
+        assert list(res[1]["J"][s][:pre]) == list(o["J"][s][:pre])
+        eg = np.sqrt(res[1]["err"][2 * s] / res[1]["err"][2 * s + 1])
+        eo = np.sqrt(o["e2"][s] / o["a2"][s])
+        assert eg <= max(1e-3, 2 * eo)
+    # a2 sums: the same FP32 inputs, FP64-class totals in another order
+    assert res[1]["tot"][1] == pytest.approx(res[0]["tot"][1], rel=1e-6)
+    assert res[1]["tot"][2] == res[0]["tot"][2]
+    ref.close()
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", ["tf32", "fp32"])
+def test_autotune_and_cache(precision, tmp_path):
+    win = _window(seed=90)
+    w = torch.from_numpy(win.data).cuda()
+    plan = spid.Plan.for_window(win, k_max=5, p=8, precision=precision, seed=13)
+    cache = str(tmp_path / "tune.json")
+    t = plan.autotune(w, cache=cache)
+    assert t["cached"] is False and t["sketch_ms"] > 0 and t["error_ms"] > 0
+    assert plan.tuning()["sketch_pack_slices"] == t["sketch_pack_slices"]
+    # the plan is left as after sketch + finalize: the error pass can follow
+    err = torch.zeros(2 * win.num_sub, dtype=torch.float64, device="cuda")
+    tot = torch.zeros(4, dtype=torch.float64, device="cuda")
+    plan.error(w, err, tot)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    o = oracle_window(win, 13, 5, 0.0, precision, 13)
+    rel = float(np.sqrt(tot[0].item() / tot[1].item()))
+    rel_o = float(np.sqrt(o["e2"].sum() / o["a2"].sum()))
+    assert rel <= max(2 * rel_o, 1e-3)
+    # a second plan of the same shape takes the stored tuning without measuring
+    plan2 = spid.Plan.for_window(win, k_max=5, p=8, precision=precision, seed=13)
+    t2 = plan2.autotune(w, cache=cache)
+    assert t2["cached"] is True
+    assert {k: v for k, v in plan2.tuning().items() if not k.endswith("_ms")} == \
+        {k: v for k, v in t.items() if not k.endswith("_ms") and k != "cached"}
+    with open(cache) as f:
+        assert plan.tuning_key() in json.load(f)
+    plan.close()
+    plan2.close()
