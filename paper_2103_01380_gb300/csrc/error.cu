@@ -95,9 +95,17 @@ __global__ void __launch_bounds__(256) error_kernel(ErrArgs a) {
   for (int t0 = 0; t0 < nrb; t0 += kErrTile) {
     const int rt = row0 + t0;                       // first row of the tile
     __syncthreads();
-    for (int e = tid; e < kk * kErrTile; e += 256) {
-      const int p = e / kErrTile, r = e % kErrTile;
-      AJ[e] = (rt + r < m) ? A[(int64_t)Jg[p] * ld + rt + r] : T(0);
+    if (a.skel) {
+      const float* F = a.skel + a.skel_off[s];
+      for (int e = tid; e < kk * kErrTile; e += 256) {
+        const int p = e / kErrTile, r = e % kErrTile;
+        AJ[e] = (rt + r < m) ? T(F[(int64_t)p * m + rt + r]) : T(0);
+      }
+    } else {
+      for (int e = tid; e < kk * kErrTile; e += 256) {
+        const int p = e / kErrTile, r = e % kErrTile;
+        AJ[e] = (rt + r < m) ? A[(int64_t)Jg[p] * ld + rt + r] : T(0);
+      }
     }
     __syncthreads();
     const int r = rt + 4 * lane;                    // this lane's 4 rows

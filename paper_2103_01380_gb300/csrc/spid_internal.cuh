@@ -202,6 +202,11 @@ struct ErrArgs {
   const int32_t* srows = nullptr;   // rows stored per subdomain for the CF sums (nullptr: m)
   int32_t row_block = kErrRowBlock; // rows of a unit
   int32_t col_block = kErrColBlock; // columns of a unit (C block staged in shared memory)
+  // skeleton source: nullptr = the window's columns J (A_hat = A(:, J) C); else
+  // an m_s x k block per subdomain at skel_off[s], leading dimension m_s
+  // (A_hat = F C, e.g. F = M B(:, I_B) of the coarse-grid SPID)
+  const float* skel = nullptr;
+  const int64_t* skel_off = nullptr;
 };
 
 // Tensor-core error pass (FP32 windows, k_max <= 32): a segment is a run of

@@ -6,6 +6,8 @@
 //                rank decision, C_B = [I | R11^-1 R12] Z^T, skeleton B(:, I_B)
 //   coarse_recon G = B(:, I_B) C_B on the coarse grid
 //   spid_interp  A_hat = M G (trilinear) fused with ||A - A_hat||^2, ||A||^2
+//   fine_skeleton F = M B(:, I_B), the interpolated skeleton (m x k), so that
+//                the error pass is the rank-k product F C_B against A
 //
 // The QR runs one CTA per subdomain with B's working copy in global memory
 // (L2-resident at these sizes): every step picks the active column of largest
@@ -501,6 +503,47 @@ __global__ void __launch_bounds__(256, 3) spid_interp_kernel(const SubErrArgs ar
   }
 }
 
+// ---------------------------------------------------------------- fine skeleton
+// A_hat = M B(:, I_B) C_B is linear in both factors, so the interpolation can
+// be applied to the k skeleton columns once instead of to all n reconstructed
+// columns: F = M B(:, I_B) (m x k per subdomain, column p at p m_s of the
+// subdomain's block) is the trilinear interpolation of each coarse skeleton
+// column to the fine grid.  The error pass is then the rank-k product F C_B
+// against A -- the same HBM-rate kernel as the column ID's error pass.
+__global__ void __launch_bounds__(256) fine_skeleton_kernel(const SubArgs a, float* F,
+                                                            const int64_t* foff) {
+  const int s = blockIdx.y;
+  const SubBox b = a.box[s];
+  const int m = a.m[s], mc = a.mc[s], k = a.k[s];
+  const float* Bsk = a.Bskel + (int64_t)a.k_max * a.sklo[s];
+  float* Fs = F + foff[s];
+  const int plane = b.ey * b.ex;
+  const int cplane = b.cy * b.cx;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
+    const int qz = (int)fdiv((uint32_t)r, b.div_plane), yx = r - qz * plane;
+    const int q = qz / b.ez, z = qz - q * b.ez;
+    const int y = (int)fdiv((uint32_t)yx, b.div_ex), x = yx - y * b.ex;
+    int az, ay, ax;
+    float wz, wy, wx;
+    axis_cell(z, b.ez, b.sz, b.cz, az, wz);
+    axis_cell(y, b.ey, b.sy, b.cy, ay, wy);
+    axis_cell(x, b.ex, b.sx, b.cx, ax, wx);
+    const int az1 = min(az + 1, b.cz - 1), ay1 = min(ay + 1, b.cy - 1), ax1 = min(ax + 1, b.cx - 1);
+    const int base = q * b.cz * cplane;
+    const int i00 = base + az * cplane + ay * b.cx, i01 = base + az * cplane + ay1 * b.cx;
+    const int i10 = base + az1 * cplane + ay * b.cx, i11 = base + az1 * cplane + ay1 * b.cx;
+    for (int p = 0; p < k; ++p) {
+      const float* c = Bsk + (int64_t)p * mc;
+      const float v00 = fmaf(wx, c[i00 + ax1] - c[i00 + ax], c[i00 + ax]);
+      const float v01 = fmaf(wx, c[i01 + ax1] - c[i01 + ax], c[i01 + ax]);
+      const float v10 = fmaf(wx, c[i10 + ax1] - c[i10 + ax], c[i10 + ax]);
+      const float v11 = fmaf(wx, c[i11 + ax1] - c[i11 + ax], c[i11 + ax]);
+      const float v0 = fmaf(wy, v01 - v00, v00), v1 = fmaf(wy, v11 - v10, v10);
+      Fs[(int64_t)p * m + r] = fmaf(wz, v1 - v0, v0);
+    }
+  }
+}
+
 int grid_for(int64_t work) {
   const int64_t blocks = (work + 255) / 256;
   return (int)(blocks < 1 ? 1 : (blocks > 1024 ? 1024 : blocks));
@@ -565,6 +608,13 @@ cudaError_t launch_spid_interp(const SubErrArgs& a, int64_t units, int mc_max, i
     if (e != cudaSuccess) return e;
     spid_interp_kernel<false><<<grid, 256, smem, st>>>(a, mc_max, e_max, per, (int)units);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fine_skeleton(const SubArgs& a, float* F, const int64_t* foff, int m_max,
+                                 cudaStream_t st) {
+  if (m_max <= 0) return cudaSuccess;
+  fine_skeleton_kernel<<<dim3(grid_for(m_max), a.S), 256, 0, st>>>(a, F, foff);
   return cudaGetLastError();
 }
 

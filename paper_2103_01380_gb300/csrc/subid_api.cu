@@ -22,11 +22,13 @@ struct spid_sub_plan_s {
   std::vector<int64_t> off, ld, boff, coff, sklo;
   int k_max = 0;
   double tol = 0.0;
-  int mc_max = 0, n_max = 0, e_max = 0;
+  int mc_max = 0, n_max = 0, e_max = 0, m_max = 0;
+  std::vector<int64_t> foff;   // F_s at foff[s] = k_max sum_{s'<s} m_s'
   int64_t b_elems = 0, c_elems = 0, sk_elems = 0;
   // SPID error units (per subdomain: n_s columns x zblocks)
   std::vector<int32_t> uptr;
   int64_t spid_units = 0;
+  int64_t f_elems = 0;     // fine skeleton F = M B(:, I_B): sum m_s k_max
   // SubID error units (512-row x 256-column blocks, as the main error pass)
   std::vector<int32_t> usub, urow, ucol, uptr_subid;
   // device
@@ -35,6 +37,8 @@ struct spid_sub_plan_s {
   int64_t *d_off = nullptr, *d_ld = nullptr, *d_boff = nullptr, *d_coff = nullptr,
           *d_sklo = nullptr, *d_ccoff = nullptr;   // d_ccoff = k_max * coff (C in elements)
   float *d_B = nullptr, *d_W = nullptr, *d_R = nullptr, *d_C = nullptr, *d_Bsk = nullptr;
+  float* d_F = nullptr;         // fine skeleton M B(:, I_B)
+  int64_t* d_foff = nullptr;
   int32_t *d_J = nullptr, *d_k = nullptr;
   int* d_status = nullptr;
   int32_t* d_uptr = nullptr;
@@ -224,6 +228,9 @@ spid_status spid_sub_plan_create(const spid_sub_desc* d, spid_sub_plan_t* out) {
     P->uptr[s] = (int32_t)units;
     units += (int64_t)ns * b.zblocks;
     P->mc_max = std::max<int>(P->mc_max, (int)mc);
+    P->m_max = std::max<int>(P->m_max, (int)m);
+    P->foff.push_back(P->f_elems);
+    P->f_elems += m * d->k_max;
     P->n_max = std::max(P->n_max, ns);
     P->e_max = std::max({P->e_max, b.ez, b.ey, b.ex});
     P->uptr_subid[s] = (int32_t)P->usub.size();
@@ -278,6 +285,8 @@ spid_status spid_sub_plan_create(const spid_sub_desc* d, spid_sub_plan_t* out) {
   SUB_ALLOC(P->d_R, sizeof(float) * P->c_elems);
   SUB_ALLOC(P->d_C, sizeof(float) * P->c_elems);
   SUB_ALLOC(P->d_Bsk, sizeof(float) * P->sk_elems);
+  SUB_ALLOC(P->d_F, sizeof(float) * P->f_elems);
+  SUB_ALLOC(P->d_foff, sizeof(int64_t) * S);
   SUB_ALLOC(P->d_J, sizeof(int32_t) * S * P->k_max);
   SUB_ALLOC(P->d_k, sizeof(int32_t) * S);
   SUB_ALLOC(P->d_status, sizeof(int));
@@ -304,6 +313,7 @@ spid_status spid_sub_plan_create(const spid_sub_desc* d, spid_sub_plan_t* out) {
       {P->d_boff, P->boff.data(), sizeof(int64_t) * S},
       {P->d_coff, P->coff.data(), sizeof(int64_t) * S},
       {P->d_sklo, P->sklo.data(), sizeof(int64_t) * S},
+      {P->d_foff, P->foff.data(), sizeof(int64_t) * S},
       {P->d_ccoff, ccoff.data(), sizeof(int64_t) * S},
       {P->d_uptr, P->uptr.data(), sizeof(int32_t) * (S + 1)},
       {P->d_usub, P->usub.data(), sizeof(int32_t) * P->usub.size()},
@@ -366,7 +376,6 @@ static spid_status run_sub_error(spid_sub_plan_t P, const float* window, int32_t
                                  float* out, double* err_dev, double* total_dev,
                                  cudaStream_t cs) {
   if (form == SPID_FORM_SPID) {
-    SUB_CUDA(launch_coarse_recon(P->args(), (int64_t)P->mc_max * P->n_max, cs));
     SubErrArgs a;
     a.a = P->args();
     a.e = P->fold_args(window, out, err_dev, total_dev);
@@ -375,7 +384,25 @@ static spid_status run_sub_error(spid_sub_plan_t P, const float* window, int32_t
     a.e.srows = P->d_mc;
     a.window = window;
     a.out = out;
-    SUB_CUDA(launch_spid_interp(a, P->spid_units, P->mc_max, P->e_max, cs));
+    if (window) {
+      // F = M B(:, I_B) once, then the rank-k error pass F C_B against A
+      SUB_CUDA(launch_fine_skeleton(P->args(), P->d_F, P->d_foff, P->m_max, cs));
+      ErrArgs f = P->fold_args(window, out, err_dev, total_dev);
+      f.coff = P->d_ccoff;
+      f.unit_sub = P->d_usub;
+      f.unit_row0 = P->d_urow;
+      f.unit_col0 = P->d_ucol;
+      f.part = P->d_part_subid;
+      f.unit_ptr = P->d_uptr_subid;
+      f.srows = P->d_mc;
+      f.skel = P->d_F;
+      f.skel_off = P->d_foff;
+      SUB_CUDA(launch_error(f, (int)P->usub.size(), false, cs));
+    } else {
+      // reconstruction without the window: G = B(:, I_B) C_B, then M G
+      SUB_CUDA(launch_coarse_recon(P->args(), (int64_t)P->mc_max * P->n_max, cs));
+      SUB_CUDA(launch_spid_interp(a, P->spid_units, P->mc_max, P->e_max, cs));
+    }
     return SPID_OK;
   }
   if (form == SPID_FORM_SUBID) {

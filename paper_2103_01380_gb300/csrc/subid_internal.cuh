@@ -87,5 +87,9 @@ cudaError_t launch_coarse_recon(const SubArgs& a, int64_t max_work, cudaStream_t
 size_t spid_interp_smem_bytes(int mc_max, int e_max);
 cudaError_t launch_spid_interp(const SubErrArgs& a, int64_t units, int mc_max, int e_max,
                                cudaStream_t st);
+// F = M B(:, I_B): the trilinear interpolation of every coarse skeleton column
+// to the fine grid, m_s x k_s column-major at foff[s] (leading dimension m_s).
+cudaError_t launch_fine_skeleton(const SubArgs& a, float* F, const int64_t* foff, int m_max,
+                                 cudaStream_t st);
 
 }  // namespace spid

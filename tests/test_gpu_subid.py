@@ -177,3 +177,51 @@ def test_sample_then_repeat_is_bit_identical():
     assert all(np.array_equal(x, y) for x, y in zip(a["C"], b["C"]))
     assert np.array_equal(a["err_spid"], b["err_spid"])
     assert np.array_equal(a["total_spid"], b["total_spid"])
+
+
+def test_fine_skeleton_and_staged_spid_passes_agree():
+    # With the window, the SPID error pass and reconstruction interpolate the k
+    # skeleton columns once (F = M B(:, I_B), m x k) and form A_hat = F C_B in
+    # the rank-k error kernel; without it, the reconstruction forms G = B(:,
+    # I_B) C_B on the coarse grid first and then M G.  Both are exact
+    # rearrangements of M B(:, I_B) C_B (M is linear), so they differ by FP32
+    # rounding only: per element at most (k + 4) ulps of
+    # sum_p max|B(:, I_B)(:, p)| |C_B(p, j)| (trilinear weights are convex),
+    # x8 for the unknown contraction order.  The error sums follow from the
+    # A_hat difference (triangle inequality) and the compensated FP32 sums.
+    boxes = [(5, 16, 16, 16), (2, 20, 8, 12), (3, 32, 32, 32), (1, 8, 8, 8), (4, 9, 4, 4),
+             (2, 6, 2, 6), (1, 7, 5, 3)]
+    n = [70, 33, 40, 129, 64, 20, 31]
+    win = inputs.box_window(boxes, n, seed=71, noise=1e-4)
+    check_sub_parity(win, (3, 3, 3), 6)
+    plan = spid.SubPlan.for_window(win, (3, 3, 3), k_max=6)
+    w = torch.from_numpy(win.data).cuda()
+    plan.sample(w)
+    plan.finalize()
+    S = win.num_sub
+    err = torch.zeros(2 * S, dtype=torch.float64, device="cuda")
+    tot = torch.zeros(4, dtype=torch.float64, device="cuda")
+    plan.error(w, spid.FORM_SPID, err, tot)
+    fine = torch.zeros_like(w)
+    staged = torch.zeros_like(w)
+    plan.reconstruct(w, fine, spid.FORM_SPID)
+    plan.reconstruct(None, staged, spid.FORM_SPID)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    k, _, C, Bsk = plan.factors()
+    e = err.cpu().numpy().reshape(-1, 2)
+    wf = inputs.Window(fine.cpu().numpy(), win.m, win.n, win.off, win.ld)
+    wt = inputs.Window(staged.cpu().numpy(), win.m, win.n, win.off, win.ld)
+    for s in range(S):
+        kk = int(k[s])
+        a_f, a_t = wf.block(s).astype(np.float64), wt.block(s).astype(np.float64)
+        bmax = np.abs(Bsk[s][:, :kk].astype(np.float64)).max(axis=0) if kk else np.zeros(0)
+        scale = (np.abs(C[s][:kk].astype(np.float64)) * bmax[:, None]).sum(axis=0)   # per column
+        assert np.all(np.abs(a_f - a_t) <= 8 * (kk + 4) * U32 * scale[None, :] + 1e-30), s
+        A = win.block(s).astype(np.float64)
+        e2 = float(((A - a_t) ** 2).sum())
+        a2 = float((A ** 2).sum())
+        d = np.linalg.norm(a_f - a_t)
+        assert abs(e[s, 0] - e2) <= 2 * np.sqrt(e2) * d + d * d + 1e-5 * e2, s
+        assert e[s, 1] == pytest.approx(a2, rel=1e-6)
+    plan.close()
