@@ -66,17 +66,18 @@ __device__ __forceinline__ void kahan_add(T& s, T& c, T x) {
   s = t;
 }
 
-template <typename T, bool WRITE>
+template <typename T, bool WRITE, int CB>
 __global__ void __launch_bounds__(256) error_kernel(ErrArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[2][8];
   __shared__ int last_sub;
+  __shared__ const T* colp[kErrMaxK];
   const int u = blockIdx.x + a.unit_base;
   const int s = a.unit_sub[u];
   const int row0 = a.unit_row0[u], col0 = a.unit_col0[u];
   const int m = a.m[s], n = a.n[s];
   const int kk = a.k[s];
-  const int cb = a.col_block;
+  constexpr int cb = CB;                          // columns per unit (== a.col_block)
   const int ncb = min(cb, n - col0);
   const int nrb = min(a.row_block, m - row0);
   T* Cs = reinterpret_cast<T*>(smem_raw);                 // [kk][cb]
@@ -87,6 +88,11 @@ __global__ void __launch_bounds__(256) error_kernel(ErrArgs a) {
   const int32_t* Jg = a.J + (int64_t)s * a.k_max;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
 
+  // skeleton column p: A(:, J[p]) of the window, or column p of the m x k
+  // block the caller formed (floats; FP32 plans only)
+  if (tid < kk)
+    colp[tid] = a.skel ? reinterpret_cast<const T*>(a.skel + a.skel_off[s] + (int64_t)tid * m)
+                       : A + (int64_t)Jg[tid] * ld;
   for (int e = tid; e < kk * cb; e += 256) {
     const int p = e / cb, jj = e % cb;
     Cs[e] = (jj < ncb) ? Cg[(int64_t)p * n + col0 + jj] : T(0);
@@ -95,17 +101,9 @@ __global__ void __launch_bounds__(256) error_kernel(ErrArgs a) {
   for (int t0 = 0; t0 < nrb; t0 += kErrTile) {
     const int rt = row0 + t0;                       // first row of the tile
     __syncthreads();
-    if (a.skel) {
-      const float* F = a.skel + a.skel_off[s];
-      for (int e = tid; e < kk * kErrTile; e += 256) {
-        const int p = e / kErrTile, r = e % kErrTile;
-        AJ[e] = (rt + r < m) ? T(F[(int64_t)p * m + rt + r]) : T(0);
-      }
-    } else {
-      for (int e = tid; e < kk * kErrTile; e += 256) {
-        const int p = e / kErrTile, r = e % kErrTile;
-        AJ[e] = (rt + r < m) ? A[(int64_t)Jg[p] * ld + rt + r] : T(0);
-      }
+    for (int e = tid; e < kk * kErrTile; e += 256) {
+      const int p = e / kErrTile, r = e % kErrTile;
+      AJ[e] = (rt + r < m) ? colp[p][rt + r] : T(0);
     }
     __syncthreads();
     const int r = rt + 4 * lane;                    // this lane's 4 rows
@@ -195,23 +193,26 @@ size_t error_smem_bytes(int k_max, int col_block, bool fp64) {
 
 cudaError_t launch_error(const ErrArgs& a, int units, bool fp64, cudaStream_t st) {
   if (units <= 0) return cudaSuccess;
-  if (a.row_block < kErrTile || a.row_block % kErrTile || a.col_block < 32 || a.col_block % 32 ||
-      a.col_block > kErrColBlockMax)
+  if (a.row_block < kErrTile || a.row_block % kErrTile ||
+      (a.col_block != 128 && a.col_block != 256))
     return cudaErrorInvalidValue;
   const size_t smem = error_smem_bytes(a.k_max, a.col_block, fp64);
   cudaError_t e = cudaSuccess;
-#define SPID_LAUNCH_ERR(T, W)                                                               \
+#define SPID_LAUNCH_ERR(T, W, CB)                                                           \
   do {                                                                                      \
-    e = cudaFuncSetAttribute(error_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             (int)smem);                                                    \
+    e = cudaFuncSetAttribute(error_kernel<T, W, CB>,                                        \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
     if (e != cudaSuccess) return e;                                                         \
-    error_kernel<T, W><<<units, 256, smem, st>>>(a);                                        \
+    error_kernel<T, W, CB><<<units, 256, smem, st>>>(a);                                    \
   } while (0)
   const bool w = a.out != nullptr;
+  const bool wide = a.col_block == 256;
   if (fp64) {
-    if (w) SPID_LAUNCH_ERR(double, true); else SPID_LAUNCH_ERR(double, false);
+    if (w) { if (wide) SPID_LAUNCH_ERR(double, true, 256); else SPID_LAUNCH_ERR(double, true, 128); }
+    else { if (wide) SPID_LAUNCH_ERR(double, false, 256); else SPID_LAUNCH_ERR(double, false, 128); }
   } else {
-    if (w) SPID_LAUNCH_ERR(float, true); else SPID_LAUNCH_ERR(float, false);
+    if (w) { if (wide) SPID_LAUNCH_ERR(float, true, 256); else SPID_LAUNCH_ERR(float, true, 128); }
+    else { if (wide) SPID_LAUNCH_ERR(float, false, 256); else SPID_LAUNCH_ERR(float, false, 128); }
   }
 #undef SPID_LAUNCH_ERR
   return cudaGetLastError();

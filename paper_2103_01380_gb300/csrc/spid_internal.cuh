@@ -169,11 +169,11 @@ struct QrcpArgs {
 // Fused reconstruction / error pass.  A work unit is (subdomain, block of
 // row_block rows, block of col_block columns); the defaults below, or a shape
 // chosen by the plan's autotuner (row_block a multiple of kErrTile, col_block
-// a multiple of 32, at most kErrColBlockMax).
+// 128 or 256).
 constexpr int kErrRowBlock = 512;
 constexpr int kErrColBlock = 256;
-constexpr int kErrColBlockMax = 256;
 constexpr int kErrTile = 128;
+constexpr int kErrMaxK = 64;     // skeleton columns a unit can stage
 
 struct ErrArgs {
   const void* window;
