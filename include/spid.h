@@ -346,6 +346,37 @@ typedef struct {
   uint32_t flags;         /* 0 */
 } spid_sub_desc;
 
+/* Point-set form (unstructured grids; Section 2 allows the rows of A in any
+ * order, and Section 5.1 compresses a randomly generated point set): the
+ * caller gives, per subdomain, the rows of A_s kept in B_s and the
+ * interpolation operator M as a fixed-width stencil -- fine row r of
+ * subdomain s is sum_q w(r, q) B_s(idx(r, q), :) -- instead of a box and an
+ * interval.  Every spid_sub_* call accepts the plan; SPID reconstruction
+ * without the window forms M B(:, I_B) C_B directly.  The compression-factor
+ * sums count k (m_c + n) (M is not counted, as for boxes). */
+typedef struct {
+  int32_t num_sub;            /* S, 1..65535 */
+  const int32_t* m;           /* host [S]: rows m_s >= 1 */
+  const int32_t* n;           /* host [S]: window length, 1 <= n_s <= 1024 */
+  const int64_t* off;         /* host [S]: element offset of A_s(0,0) (multiple of 4) */
+  const int64_t* ld;          /* host [S]: leading dimension >= m_s (multiple of 4) */
+  const int32_t* mc;          /* host [S]: coarse rows, 1 <= m_c(s) <= min(m_s, 40960) */
+  const int32_t* coarse_rows; /* host [sum m_c]: subdomain s's rows of A_s (each in
+                                 [0, m_s)) at offset sum_{s'<s} m_c(s'); B_s row i is A_s
+                                 row coarse_rows[...+ i] */
+  int32_t stencil;            /* t, 1..16: coarse rows per fine row */
+  const int32_t* interp_idx;  /* host [t sum m]: fine row r of subdomain s at
+                                 t (sum_{s'<s} m_s' + r) .. + t - 1: coarse rows in [0, m_c(s)) */
+  const float* interp_w;      /* host, same layout: finite weights */
+  int32_t k_max;              /* 1..64 */
+  double tol;                 /* as spid_sub_desc */
+  uint32_t flags;             /* 0 */
+} spid_sub_points_desc;
+
+/* Create a point-set plan (the host tables are copied; later calls allocate
+ * nothing).  SPID_ERR_INVALID_ARG for a size, index or weight out of range. */
+spid_status spid_sub_plan_create_points(const spid_sub_points_desc* desc, spid_sub_plan_t* plan);
+
 /* Create a plan: validates, allocates all workspace (later calls allocate
  * nothing).  m_c(s) <= 40960 coarse rows (the QR keeps one column of B in
  * shared memory); SPID_ERR_UNSUPPORTED beyond. */

@@ -98,6 +98,11 @@ def _load():
                                   c.c_double, c.c_double, _i32p, _f64p, c.c_void_p, _f64p,
                                   c.c_void_p]
         lib.orc_subid.restype = c.c_int
+        lib.orc_subid_points.argtypes = [_f64p, c.c_int64, c.c_int64, c.c_int64, _i32p,
+                                         c.c_int64, c.c_int32, _i32p, _f64p, c.c_int32,
+                                         c.c_double, c.c_double, _i32p, _f64p, c.c_void_p,
+                                         _f64p, c.c_void_p]
+        lib.orc_subid_points.restype = c.c_int
         lib.orc_two_stage.argtypes = [_f64p, c.c_int64, c.c_int64, c.c_int64, c.c_int32,
                                       c.c_int32, c.c_int32, c.c_int32, c.c_double, c.c_double,
                                       c.c_uint64, _i32p, _f64p, _i32p, _i32p, _f64p, _i32p,
@@ -327,6 +332,34 @@ def subid(A: np.ndarray, box, stride, kmax: int, tol: float = 0.0, u_mode: float
     H = np.zeros(m * max(n, 1), dtype=np.float64) if want_ahat else None
     k = int(_load().orc_subid(Af, m, n, b, st, kmax, float(tol), float(u_mode), J, C,
                               Bs.ctypes.data, err, H.ctypes.data if want_ahat else None))
+    out = {"k": k, "J": J[:k].copy(), "J_full": J, "C": C[:kmax * n].reshape(kmax, n)[:k].copy(),
+           "Bskel": Bs.reshape(kmax, mc).T[:, :k].copy(), "e2_subid": float(err[0]),
+           "e2_spid": float(err[1]), "a2": float(err[2]), "mc": int(err[3])}
+    if want_ahat:
+        out["Ahat_spid"] = H[:m * n].reshape(n, m).T.copy()
+    return out
+
+
+def subid_points(A: np.ndarray, coarse_rows, interp_idx, interp_w, kmax: int, tol: float = 0.0,
+                 u_mode: float = 2.0 ** -53, want_ahat: bool = False) -> dict:
+    """SubID / SPID on a point set: B = A(coarse_rows, :); M given as a stencil
+    (interp_idx, interp_w: m x t).  Same outputs as subid()."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    crow = np.ascontiguousarray(coarse_rows, dtype=np.int32)
+    mc = int(crow.size)
+    idx = np.ascontiguousarray(interp_idx, dtype=np.int32).reshape(m, -1)
+    t = int(idx.shape[1])
+    w = np.ascontiguousarray(interp_w, dtype=np.float64).reshape(m, t)
+    Af = np.ascontiguousarray(A.T).reshape(-1)
+    J = np.zeros(kmax, dtype=np.int32)
+    C = np.zeros(kmax * max(n, 1), dtype=np.float64)
+    Bs = np.zeros(mc * kmax, dtype=np.float64)
+    err = np.zeros(4, dtype=np.float64)
+    H = np.zeros(m * max(n, 1), dtype=np.float64) if want_ahat else None
+    k = int(_load().orc_subid_points(Af, m, m, n, crow, mc, t, idx.reshape(-1), w.reshape(-1),
+                                     kmax, float(tol), float(u_mode), J, C, Bs.ctypes.data, err,
+                                     H.ctypes.data if want_ahat else None))
     out = {"k": k, "J": J[:k].copy(), "J_full": J, "C": C[:kmax * n].reshape(kmax, n)[:k].copy(),
            "Bskel": Bs.reshape(kmax, mc).T[:, :k].copy(), "e2_subid": float(err[0]),
            "e2_spid": float(err[1]), "a2": float(err[2]), "mc": int(err[3])}

@@ -559,6 +559,66 @@ int orc_subid(const double* A, int64_t ld, int64_t n, const int32_t box[4],
   return k;
 }
 
+/* SubID and SPID on an arbitrary point set (Section 2: rows of A in any
+ * order, e.g. a flattened unstructured grid; Section 5.1's random points).
+ * The coarse matrix keeps the listed rows, B = A(crow, :) (mc x n, row i =
+ * A row crow[i]); M is given as a stencil of t (index, weight) pairs per fine
+ * row: (M G)(r, j) = sum_q w[r t + q] G(idx[r t + q], j).  Otherwise as
+ * orc_subid: pivoted MGS of B, rank guard, C_B, Bskel = B(:, I_B), err[0] =
+ * ||A - A(:,I_B) C_B||^2, err[1] = ||A - M (B(:,I_B) C_B)||^2, err[2] =
+ * ||A||^2, err[3] = mc; Ahat (m x n, may be NULL) the SPID reconstruction.
+ * Returns k. */
+int orc_subid_points(const double* A, int64_t m, int64_t ld, int64_t n, const int32_t* crow,
+                     int64_t mc, int32_t t, const int32_t* idx, const double* w, int32_t kmax,
+                     double tol, double u_mode, int32_t* J, double* C, double* Bskel,
+                     double* err, double* Ahat) {
+  const int64_t nn = n > 0 ? n : 1;
+  double* B = (double*)malloc(sizeof(double) * (size_t)(mc * nn));
+  double* W = (double*)malloc(sizeof(double) * (size_t)(mc * nn));
+  double* R = (double*)malloc(sizeof(double) * (size_t)kmax * (size_t)nn);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < mc; ++i) B[i + mc * j] = A[crow[i] + ld * j];
+  memcpy(W, B, sizeof(double) * (size_t)(mc * n));
+  for (int32_t p = 0; p < kmax; ++p) J[p] = -1;
+  double normB2 = 0.0;
+  const int32_t k0 = orc_qrcp_mgs(W, (int32_t)mc, n, kmax, tol, J, R, &normB2);
+  const int32_t k = orc_rank_guard(R, n, J, k0, u_mode);
+  for (int32_t p = k; p < kmax; ++p) J[p] = -1;
+  for (int64_t x = 0; x < (int64_t)kmax * n; ++x) C[x] = 0.0;
+  orc_coefficients(R, n, J, k, C);
+  if (Bskel)
+    for (int32_t p = 0; p < kmax; ++p)
+      for (int64_t i = 0; i < mc; ++i) Bskel[i + mc * p] = (p < k) ? B[i + mc * J[p]] : 0.0;
+  double e2s = 0.0, a2 = 0.0;
+  orc_reconstruct_error(A, m, n, ld, J, k, C, NULL, 0, &e2s, &a2);
+  /* SPID: M (B(:, I_B) C_B) */
+  double* G = (double*)malloc(sizeof(double) * (size_t)(mc * nn));
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < mc; ++i) {
+      double v = 0.0;
+      for (int32_t p = 0; p < k; ++p) v += B[i + mc * J[p]] * C[(int64_t)p * n + j];
+      G[i + mc * j] = v;
+    }
+  double se = 0.0, ce = 0.0;
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t r = 0; r < m; ++r) {
+      double v = 0.0;
+      for (int32_t q = 0; q < t; ++q) v += w[r * t + q] * G[idx[r * t + q] + mc * j];
+      if (Ahat) Ahat[r + m * j] = v;
+      const double e = A[r + ld * j] - v;
+      neu_add(&se, &ce, e * e);
+    }
+  err[0] = e2s;
+  err[1] = se + ce;
+  err[2] = a2;
+  err[3] = (double)mc;
+  free(G);
+  free(B);
+  free(W);
+  free(R);
+  return k;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Modified (two-stage) SPID, Section 3.3.2 and Algorithm 6.                */
 /* Stage 1: the n columns are cut into N blocks of nb = n / N; block b gets */

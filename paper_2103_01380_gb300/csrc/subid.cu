@@ -16,6 +16,8 @@
 // updates w_c -= R(j, c) q_j and recomputes ||w_c||^2 from the updated
 // values -- the residual norms are therefore taken from the current columns
 // at every step, as in the oracle, with no downdating.
+#include <algorithm>
+
 #include "error_fold.cuh"
 #include "subid_internal.cuh"
 
@@ -544,6 +546,86 @@ __global__ void __launch_bounds__(256) fine_skeleton_kernel(const SubArgs a, flo
   }
 }
 
+// ---------------------------------------------------------------- point sets
+// Coarse-grid ID on an arbitrary point set (an unstructured grid, rows in any
+// order, Section 2): the coarse rows are an explicit list per subdomain and M
+// is a fixed-width stencil (t coarse rows and weights per fine row).
+
+// B_s(:, col0 + j) = A_s(crow_s, col0 + j).
+__global__ void __launch_bounds__(256) subsample_rows_kernel(const SubArgs a, const float* window,
+                                                             int col0, int ncols,
+                                                             const int32_t* crow,
+                                                             const int64_t* crow_off) {
+  const int s = blockIdx.y;
+  const int mc = a.mc[s], n = a.n[s];
+  const int nc = min(ncols, n - col0);
+  if (nc <= 0) return;
+  const int32_t* rows = crow + crow_off[s];
+  const float* A = window + a.off[s];
+  const int64_t ld = a.ld[s];
+  float* B = a.B + a.boff[s];
+  const int64_t work = (int64_t)mc * nc;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < work;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / mc), i = (int)(e - (int64_t)j * mc);
+    B[(int64_t)(col0 + j) * mc + i] = __ldg(A + (int64_t)(col0 + j) * ld + rows[i]);
+  }
+}
+
+// F_s(r, p) = sum_q w_s(r, q) B(:, I_B)(idx_s(r, q), p), p < k_s.
+__global__ void __launch_bounds__(256) fine_skeleton_points_kernel(
+    const SubArgs a, float* F, const int64_t* foff, const int32_t* iidx, const float* iw,
+    const int64_t* ioff, int t) {
+  const int s = blockIdx.y;
+  const int m = a.m[s], mc = a.mc[s], k = a.k[s];
+  const float* Bsk = a.Bskel + (int64_t)a.k_max * a.sklo[s];
+  const int32_t* idx = iidx + ioff[s];
+  const float* w = iw + ioff[s];
+  float* Fs = F + foff[s];
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
+    for (int p = 0; p < k; ++p) {
+      const float* c = Bsk + (int64_t)p * mc;
+      float v = 0.f;
+      for (int q = 0; q < t; ++q) v = fmaf(w[(int64_t)r * t + q], c[idx[(int64_t)r * t + q]], v);
+      Fs[(int64_t)p * m + r] = v;
+    }
+  }
+}
+
+// out_s(:, j) = F_s C_s(:, j) (reconstruction without the window): one thread
+// per (row, block of 32 columns), C's block staged in shared memory.
+__global__ void __launch_bounds__(256) skeleton_product_kernel(const SubArgs a, const float* F,
+                                                               const int64_t* foff, float* out) {
+  __shared__ float cs[kSubMaxK][32];
+  const int s = blockIdx.z;
+  const int m = a.m[s], n = a.n[s], k = a.k[s];
+  const int j0 = blockIdx.y * 32;
+  if (j0 >= n) return;
+  const int nc = min(32, n - j0);
+  const float* C = a.C + (int64_t)a.k_max * a.coff[s];
+  for (int e = threadIdx.x; e < k * 32; e += blockDim.x) {
+    const int p = e / 32, jj = e % 32;
+    cs[p][jj] = jj < nc ? C[(int64_t)p * n + j0 + jj] : 0.f;
+  }
+  __syncthreads();
+  const float* Fs = F + foff[s];
+  float* o = out + a.off[s];
+  const int64_t ld = a.ld[s];
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
+    float acc[32];
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) acc[jj] = 0.f;
+    for (int p = 0; p < k; ++p) {
+      const float f = Fs[(int64_t)p * m + r];
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) acc[jj] = fmaf(f, cs[p][jj], acc[jj]);
+    }
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj)
+      if (jj < nc) o[(int64_t)(j0 + jj) * ld + r] = acc[jj];
+  }
+}
+
 int grid_for(int64_t work) {
   const int64_t blocks = (work + 255) / 256;
   return (int)(blocks < 1 ? 1 : (blocks > 1024 ? 1024 : blocks));
@@ -615,6 +697,32 @@ cudaError_t launch_fine_skeleton(const SubArgs& a, float* F, const int64_t* foff
                                  cudaStream_t st) {
   if (m_max <= 0) return cudaSuccess;
   fine_skeleton_kernel<<<dim3(grid_for(m_max), a.S), 256, 0, st>>>(a, F, foff);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_subsample_rows(const SubArgs& a, const float* window, int col0, int ncols,
+                                  const int32_t* crow, const int64_t* crow_off, int64_t max_work,
+                                  cudaStream_t st) {
+  if (max_work <= 0) return cudaSuccess;
+  subsample_rows_kernel<<<dim3(grid_for(max_work), a.S), 256, 0, st>>>(a, window, col0, ncols,
+                                                                       crow, crow_off);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fine_skeleton_points(const SubArgs& a, float* F, const int64_t* foff,
+                                        const int32_t* iidx, const float* iw, const int64_t* ioff,
+                                        int t, int m_max, cudaStream_t st) {
+  if (m_max <= 0) return cudaSuccess;
+  fine_skeleton_points_kernel<<<dim3(grid_for(m_max), a.S), 256, 0, st>>>(a, F, foff, iidx, iw,
+                                                                          ioff, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_skeleton_product(const SubArgs& a, const float* F, const int64_t* foff,
+                                    float* out, int m_max, int n_max, cudaStream_t st) {
+  if (m_max <= 0 || n_max <= 0) return cudaSuccess;
+  const int gx = std::min((m_max + 255) / 256, 64);
+  skeleton_product_kernel<<<dim3(gx, (n_max + 31) / 32, a.S), 256, 0, st>>>(a, F, foff, out);
   return cudaGetLastError();
 }
 

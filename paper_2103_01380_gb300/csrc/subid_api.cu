@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -29,6 +30,17 @@ struct spid_sub_plan_s {
   std::vector<int32_t> uptr;
   int64_t spid_units = 0;
   int64_t f_elems = 0;     // fine skeleton F = M B(:, I_B): sum m_s k_max
+  // point-set plans (arbitrary grids): coarse rows and interpolation stencils
+  bool points = false;
+  int32_t t = 0;                              // stencil width
+  std::vector<int32_t> crow, iidx;            // concatenated coarse rows / stencil indices
+  std::vector<float> iw;                      // stencil weights
+  std::vector<int64_t> crow_off, ioff;        // per subdomain: sum m_c, sum m t
+  int32_t* d_crow = nullptr;
+  int64_t* d_crow_off = nullptr;
+  int32_t* d_iidx = nullptr;
+  float* d_iw = nullptr;
+  int64_t* d_ioff = nullptr;
   // SubID error units (512-row x 256-column blocks, as the main error pass)
   std::vector<int32_t> usub, urow, ucol, uptr_subid;
   // device
@@ -146,6 +158,115 @@ spid_status check_window(const void* w, const char* what) {
   return SPID_OK;
 }
 
+// Device workspace and uploads shared by both plan kinds (the host tables
+// of P are filled).  Takes ownership of P.
+spid_status finish_plan(spid_sub_plan_s* P, spid_sub_plan_t* out) {
+  if (cudaGetDevice(&P->device) != cudaSuccess) {
+    delete P;
+    return sfail(SPID_ERR_CUDA, "cudaGetDevice failed");
+  }
+  auto bail = [&](spid_status st) {
+    spid_sub_plan_destroy(P);
+    return st;
+  };
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
+  if (subid_qr_smem_bytes(P->mc_max, P->n_max, P->k_max) + 1024 > (size_t)optin ||
+      (!P->points && spid_interp_smem_bytes(P->mc_max, P->e_max) + 1024 > (size_t)optin)) {
+    delete P;
+    return sfail(SPID_ERR_UNSUPPORTED, "coarse grid too large for shared memory");
+  }
+#define SUB_ALLOC(ptr, bytes)                                                              \
+  do {                                                                                     \
+    cudaError_t e_ = P->alloc(reinterpret_cast<void**>(&(ptr)), (bytes));                  \
+    if (e_ != cudaSuccess)                                                                 \
+      return bail(sfail(e_ == cudaErrorMemoryAllocation ? SPID_ERR_OOM : SPID_ERR_CUDA,    \
+                        std::string("cudaMalloc: ") + cudaGetErrorString(e_)));            \
+  } while (0)
+  const size_t S = (size_t)P->S;
+  SUB_ALLOC(P->d_box, sizeof(SubBox) * S);
+  SUB_ALLOC(P->d_m, sizeof(int32_t) * S);
+  SUB_ALLOC(P->d_n, sizeof(int32_t) * S);
+  SUB_ALLOC(P->d_mc, sizeof(int32_t) * S);
+  SUB_ALLOC(P->d_off, sizeof(int64_t) * S);
+  SUB_ALLOC(P->d_ld, sizeof(int64_t) * S);
+  SUB_ALLOC(P->d_boff, sizeof(int64_t) * S);
+  SUB_ALLOC(P->d_coff, sizeof(int64_t) * S);
+  SUB_ALLOC(P->d_sklo, sizeof(int64_t) * S);
+  SUB_ALLOC(P->d_ccoff, sizeof(int64_t) * S);
+  SUB_ALLOC(P->d_B, sizeof(float) * P->b_elems);
+  SUB_ALLOC(P->d_W, sizeof(float) * P->b_elems);
+  SUB_ALLOC(P->d_R, sizeof(float) * P->c_elems);
+  SUB_ALLOC(P->d_C, sizeof(float) * P->c_elems);
+  SUB_ALLOC(P->d_Bsk, sizeof(float) * P->sk_elems);
+  SUB_ALLOC(P->d_F, sizeof(float) * P->f_elems);
+  SUB_ALLOC(P->d_foff, sizeof(int64_t) * S);
+  SUB_ALLOC(P->d_J, sizeof(int32_t) * S * P->k_max);
+  SUB_ALLOC(P->d_k, sizeof(int32_t) * S);
+  SUB_ALLOC(P->d_status, sizeof(int));
+  SUB_ALLOC(P->d_uptr, sizeof(int32_t) * (S + 1));
+  SUB_ALLOC(P->d_part_spid, sizeof(double) * 2 * (size_t)P->spid_units);
+  SUB_ALLOC(P->d_usub, sizeof(int32_t) * P->usub.size());
+  SUB_ALLOC(P->d_urow, sizeof(int32_t) * P->usub.size());
+  SUB_ALLOC(P->d_ucol, sizeof(int32_t) * P->usub.size());
+  SUB_ALLOC(P->d_uptr_subid, sizeof(int32_t) * (S + 1));
+  SUB_ALLOC(P->d_part_subid, sizeof(double) * 2 * P->usub.size());
+  SUB_ALLOC(P->d_sub_err, sizeof(double) * 2 * S);
+  SUB_ALLOC(P->d_cnt, sizeof(int) * (S + 1));
+  if (P->points) {
+    SUB_ALLOC(P->d_crow, sizeof(int32_t) * P->crow.size());
+    SUB_ALLOC(P->d_crow_off, sizeof(int64_t) * S);
+    SUB_ALLOC(P->d_iidx, sizeof(int32_t) * P->iidx.size());
+    SUB_ALLOC(P->d_iw, sizeof(float) * P->iw.size());
+    SUB_ALLOC(P->d_ioff, sizeof(int64_t) * S);
+  }
+#undef SUB_ALLOC
+  std::vector<int64_t> ccoff(S);
+  for (size_t i = 0; i < S; ++i) ccoff[i] = (int64_t)P->k_max * P->coff[i];
+  struct Up { void* dst; const void* src; size_t bytes; };
+  const Up ups[] = {
+      {P->d_box, P->box.data(), sizeof(SubBox) * P->box.size()},   // empty for point sets
+      {P->d_m, P->m.data(), sizeof(int32_t) * S},
+      {P->d_n, P->n.data(), sizeof(int32_t) * S},
+      {P->d_mc, P->mc.data(), sizeof(int32_t) * S},
+      {P->d_off, P->off.data(), sizeof(int64_t) * S},
+      {P->d_ld, P->ld.data(), sizeof(int64_t) * S},
+      {P->d_boff, P->boff.data(), sizeof(int64_t) * S},
+      {P->d_coff, P->coff.data(), sizeof(int64_t) * S},
+      {P->d_sklo, P->sklo.data(), sizeof(int64_t) * S},
+      {P->d_foff, P->foff.data(), sizeof(int64_t) * S},
+      {P->d_ccoff, ccoff.data(), sizeof(int64_t) * S},
+      {P->d_uptr, P->uptr.data(), sizeof(int32_t) * (S + 1)},
+      {P->d_usub, P->usub.data(), sizeof(int32_t) * P->usub.size()},
+      {P->d_urow, P->urow.data(), sizeof(int32_t) * P->usub.size()},
+      {P->d_ucol, P->ucol.data(), sizeof(int32_t) * P->usub.size()},
+      {P->d_uptr_subid, P->uptr_subid.data(), sizeof(int32_t) * (S + 1)},
+  };
+  for (const Up& u : ups)
+    if (u.bytes && cudaMemcpy(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(sfail(SPID_ERR_CUDA, "cudaMemcpy failed"));
+  if (P->points) {
+    const Up pts[] = {
+        {P->d_crow, P->crow.data(), sizeof(int32_t) * P->crow.size()},
+        {P->d_crow_off, P->crow_off.data(), sizeof(int64_t) * S},
+        {P->d_iidx, P->iidx.data(), sizeof(int32_t) * P->iidx.size()},
+        {P->d_iw, P->iw.data(), sizeof(float) * P->iw.size()},
+        {P->d_ioff, P->ioff.data(), sizeof(int64_t) * S},
+    };
+    for (const Up& u : pts)
+      if (cudaMemcpy(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(sfail(SPID_ERR_CUDA, "cudaMemcpy failed"));
+  }
+  if (cudaMemset(P->d_B, 0, sizeof(float) * P->b_elems) != cudaSuccess ||
+      cudaMemset(P->d_k, 0, sizeof(int32_t) * S) != cudaSuccess ||
+      cudaMemset(P->d_status, 0, sizeof(int)) != cudaSuccess ||
+      cudaMemset(P->d_cnt, 0, sizeof(int) * (S + 1)) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess)
+    return bail(sfail(SPID_ERR_CUDA, "cudaMemset failed"));
+  *out = P;
+  return SPID_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -251,87 +372,98 @@ spid_status spid_sub_plan_create(const spid_sub_desc* d, spid_sub_plan_t* out) {
   P->b_elems = bsum;
   P->c_elems = csum * P->k_max;
   P->sk_elems = ssum * P->k_max;
-  if (cudaGetDevice(&P->device) != cudaSuccess) {
-    delete P;
-    return sfail(SPID_ERR_CUDA, "cudaGetDevice failed");
+  return finish_plan(P, out);
+}
+
+spid_status spid_sub_plan_create_points(const spid_sub_points_desc* d, spid_sub_plan_t* out) {
+  if (!d || !out) return sfail(SPID_ERR_INVALID_ARG, "desc/out is NULL");
+  *out = nullptr;
+  if (d->num_sub < 1 || d->num_sub > 65535)
+    return sfail(SPID_ERR_INVALID_ARG, "num_sub must be in [1, 65535]");
+  if (!d->m || !d->n || !d->off || !d->ld || !d->mc || !d->coarse_rows || !d->interp_idx ||
+      !d->interp_w)
+    return sfail(SPID_ERR_INVALID_ARG, "NULL array");
+  if (d->k_max < 1 || d->k_max > kSubMaxK)
+    return sfail(SPID_ERR_INVALID_ARG, "k_max must be in [1, 64]");
+  if (!(d->tol >= 0.0)) return sfail(SPID_ERR_INVALID_ARG, "tol must be >= 0");
+  if (d->stencil < 1 || d->stencil > kSubMaxStencil)
+    return sfail(SPID_ERR_INVALID_ARG, "stencil must be in [1, 16]");
+  if (d->flags != 0) return sfail(SPID_ERR_INVALID_ARG, "flags must be 0");
+  spid_sub_plan_s* P = new spid_sub_plan_s();
+  P->S = d->num_sub;
+  P->k_max = d->k_max;
+  P->tol = d->tol;
+  P->points = true;
+  P->t = d->stencil;
+  const int t = d->stencil;
+  int64_t bsum = 0, csum = 0, ssum = 0, rsum = 0, isum = 0;
+  P->uptr.assign(P->S + 1, 0);
+  P->uptr_subid.assign(P->S + 1, 0);
+  for (int s = 0; s < P->S; ++s) {
+    const int32_t m = d->m[s], ns = d->n[s], mc = d->mc[s];
+    if (m < 1 || ns < 1 || ns > kSubMaxN || mc < 1 || mc > m || d->ld[s] < m || d->off[s] < 0 ||
+        d->off[s] % 4 || d->ld[s] % 4) {
+      delete P;
+      return sfail(SPID_ERR_INVALID_ARG, "bad m/n/mc/off/ld for subdomain " + std::to_string(s));
+    }
+    if (mc > kSubMaxCoarse) {
+      delete P;
+      return sfail(SPID_ERR_UNSUPPORTED, "coarse set of subdomain " + std::to_string(s) +
+                                             " exceeds 40960 rows");
+    }
+    for (int i = 0; i < mc; ++i) {
+      const int32_t r = d->coarse_rows[ssum + i];
+      if (r < 0 || r >= m) {
+        delete P;
+        return sfail(SPID_ERR_INVALID_ARG, "coarse row out of range in subdomain " + std::to_string(s));
+      }
+      P->crow.push_back(r);
+    }
+    for (int64_t e = 0; e < (int64_t)m * t; ++e) {
+      const int32_t q = d->interp_idx[isum + e];
+      const float w = d->interp_w[isum + e];
+      if (q < 0 || q >= mc || !std::isfinite(w)) {
+        delete P;
+        return sfail(SPID_ERR_INVALID_ARG, "stencil index/weight invalid in subdomain " +
+                                               std::to_string(s));
+      }
+      P->iidx.push_back(q);
+      P->iw.push_back(w);
+    }
+    P->m.push_back(m);
+    P->n.push_back(ns);
+    P->mc.push_back(mc);
+    P->off.push_back(d->off[s]);
+    P->ld.push_back(d->ld[s]);
+    P->boff.push_back(bsum);
+    P->coff.push_back(csum);
+    P->sklo.push_back(ssum);
+    P->crow_off.push_back(ssum);
+    P->ioff.push_back(isum);
+    P->foff.push_back(P->f_elems);
+    P->f_elems += (int64_t)m * d->k_max;
+    bsum += (int64_t)mc * ns;
+    csum += ns;
+    ssum += mc;
+    rsum += m;
+    isum += (int64_t)m * t;
+    P->mc_max = std::max<int>(P->mc_max, mc);
+    P->m_max = std::max<int>(P->m_max, m);
+    P->n_max = std::max(P->n_max, ns);
+    P->uptr_subid[s] = (int32_t)P->usub.size();
+    for (int64_t r = 0; r < m; r += kErrRowBlock)
+      for (int c = 0; c < ns; c += kErrColBlock) {
+        P->usub.push_back(s);
+        P->urow.push_back((int32_t)r);
+        P->ucol.push_back(c);
+      }
   }
-  int optin = 0;
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
-  if (subid_qr_smem_bytes(P->mc_max, P->n_max, P->k_max) + 1024 > (size_t)optin ||
-      spid_interp_smem_bytes(P->mc_max, P->e_max) + 1024 > (size_t)optin) {
-    delete P;
-    return sfail(SPID_ERR_UNSUPPORTED, "coarse grid too large for shared memory");
-  }
-#define SUB_ALLOC(ptr, bytes)                                                              \
-  do {                                                                                     \
-    cudaError_t e_ = P->alloc(reinterpret_cast<void**>(&(ptr)), (bytes));                  \
-    if (e_ != cudaSuccess)                                                                 \
-      return bail(sfail(e_ == cudaErrorMemoryAllocation ? SPID_ERR_OOM : SPID_ERR_CUDA,    \
-                        std::string("cudaMalloc: ") + cudaGetErrorString(e_)));            \
-  } while (0)
-  const size_t S = (size_t)P->S;
-  SUB_ALLOC(P->d_box, sizeof(SubBox) * S);
-  SUB_ALLOC(P->d_m, sizeof(int32_t) * S);
-  SUB_ALLOC(P->d_n, sizeof(int32_t) * S);
-  SUB_ALLOC(P->d_mc, sizeof(int32_t) * S);
-  SUB_ALLOC(P->d_off, sizeof(int64_t) * S);
-  SUB_ALLOC(P->d_ld, sizeof(int64_t) * S);
-  SUB_ALLOC(P->d_boff, sizeof(int64_t) * S);
-  SUB_ALLOC(P->d_coff, sizeof(int64_t) * S);
-  SUB_ALLOC(P->d_sklo, sizeof(int64_t) * S);
-  SUB_ALLOC(P->d_ccoff, sizeof(int64_t) * S);
-  SUB_ALLOC(P->d_B, sizeof(float) * P->b_elems);
-  SUB_ALLOC(P->d_W, sizeof(float) * P->b_elems);
-  SUB_ALLOC(P->d_R, sizeof(float) * P->c_elems);
-  SUB_ALLOC(P->d_C, sizeof(float) * P->c_elems);
-  SUB_ALLOC(P->d_Bsk, sizeof(float) * P->sk_elems);
-  SUB_ALLOC(P->d_F, sizeof(float) * P->f_elems);
-  SUB_ALLOC(P->d_foff, sizeof(int64_t) * S);
-  SUB_ALLOC(P->d_J, sizeof(int32_t) * S * P->k_max);
-  SUB_ALLOC(P->d_k, sizeof(int32_t) * S);
-  SUB_ALLOC(P->d_status, sizeof(int));
-  SUB_ALLOC(P->d_uptr, sizeof(int32_t) * (S + 1));
-  SUB_ALLOC(P->d_part_spid, sizeof(double) * 2 * (size_t)P->spid_units);
-  SUB_ALLOC(P->d_usub, sizeof(int32_t) * P->usub.size());
-  SUB_ALLOC(P->d_urow, sizeof(int32_t) * P->usub.size());
-  SUB_ALLOC(P->d_ucol, sizeof(int32_t) * P->usub.size());
-  SUB_ALLOC(P->d_uptr_subid, sizeof(int32_t) * (S + 1));
-  SUB_ALLOC(P->d_part_subid, sizeof(double) * 2 * P->usub.size());
-  SUB_ALLOC(P->d_sub_err, sizeof(double) * 2 * S);
-  SUB_ALLOC(P->d_cnt, sizeof(int) * (S + 1));
-#undef SUB_ALLOC
-  std::vector<int64_t> ccoff(S);
-  for (size_t i = 0; i < S; ++i) ccoff[i] = (int64_t)P->k_max * P->coff[i];
-  struct Up { void* dst; const void* src; size_t bytes; };
-  const Up ups[] = {
-      {P->d_box, P->box.data(), sizeof(SubBox) * S},
-      {P->d_m, P->m.data(), sizeof(int32_t) * S},
-      {P->d_n, P->n.data(), sizeof(int32_t) * S},
-      {P->d_mc, P->mc.data(), sizeof(int32_t) * S},
-      {P->d_off, P->off.data(), sizeof(int64_t) * S},
-      {P->d_ld, P->ld.data(), sizeof(int64_t) * S},
-      {P->d_boff, P->boff.data(), sizeof(int64_t) * S},
-      {P->d_coff, P->coff.data(), sizeof(int64_t) * S},
-      {P->d_sklo, P->sklo.data(), sizeof(int64_t) * S},
-      {P->d_foff, P->foff.data(), sizeof(int64_t) * S},
-      {P->d_ccoff, ccoff.data(), sizeof(int64_t) * S},
-      {P->d_uptr, P->uptr.data(), sizeof(int32_t) * (S + 1)},
-      {P->d_usub, P->usub.data(), sizeof(int32_t) * P->usub.size()},
-      {P->d_urow, P->urow.data(), sizeof(int32_t) * P->usub.size()},
-      {P->d_ucol, P->ucol.data(), sizeof(int32_t) * P->usub.size()},
-      {P->d_uptr_subid, P->uptr_subid.data(), sizeof(int32_t) * (S + 1)},
-  };
-  for (const Up& u : ups)
-    if (cudaMemcpy(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice) != cudaSuccess)
-      return bail(sfail(SPID_ERR_CUDA, "cudaMemcpy failed"));
-  if (cudaMemset(P->d_B, 0, sizeof(float) * P->b_elems) != cudaSuccess ||
-      cudaMemset(P->d_k, 0, sizeof(int32_t) * S) != cudaSuccess ||
-      cudaMemset(P->d_status, 0, sizeof(int)) != cudaSuccess ||
-      cudaMemset(P->d_cnt, 0, sizeof(int) * (S + 1)) != cudaSuccess ||
-      cudaDeviceSynchronize() != cudaSuccess)
-    return bail(sfail(SPID_ERR_CUDA, "cudaMemset failed"));
-  *out = P;
-  return SPID_OK;
+  P->uptr_subid[P->S] = (int32_t)P->usub.size();
+  P->spid_units = 0;
+  P->b_elems = bsum;
+  P->c_elems = csum * P->k_max;
+  P->sk_elems = ssum * P->k_max;
+  return finish_plan(P, out);
 }
 
 spid_status spid_sub_plan_destroy(spid_sub_plan_t P) {
@@ -361,7 +493,11 @@ spid_status spid_sub_sample(spid_sub_plan_t P, const float* window, int32_t col0
   if (ncols == 0 || col0 >= P->n_max) return SPID_OK;
   ncols = std::min(ncols, P->n_max - col0);
   const int64_t max_work = (int64_t)P->mc_max * ncols;
-  SUB_CUDA(launch_subsample(P->args(), window, col0, ncols, max_work, (cudaStream_t)stream));
+  if (P->points)
+    SUB_CUDA(launch_subsample_rows(P->args(), window, col0, ncols, P->d_crow, P->d_crow_off,
+                                   max_work, (cudaStream_t)stream));
+  else
+    SUB_CUDA(launch_subsample(P->args(), window, col0, ncols, max_work, (cudaStream_t)stream));
   return SPID_OK;
 }
 
@@ -384,9 +520,18 @@ static spid_status run_sub_error(spid_sub_plan_t P, const float* window, int32_t
     a.e.srows = P->d_mc;
     a.window = window;
     a.out = out;
+    if (P->points) {
+      SUB_CUDA(launch_fine_skeleton_points(P->args(), P->d_F, P->d_foff, P->d_iidx, P->d_iw,
+                                           P->d_ioff, P->t, P->m_max, cs));
+      if (!window) {   // reconstruction only: out = F C_B
+        SUB_CUDA(launch_skeleton_product(P->args(), P->d_F, P->d_foff, out, P->m_max, P->n_max, cs));
+        return SPID_OK;
+      }
+    } else if (window) {
+      SUB_CUDA(launch_fine_skeleton(P->args(), P->d_F, P->d_foff, P->m_max, cs));
+    }
     if (window) {
       // F = M B(:, I_B) once, then the rank-k error pass F C_B against A
-      SUB_CUDA(launch_fine_skeleton(P->args(), P->d_F, P->d_foff, P->m_max, cs));
       ErrArgs f = P->fold_args(window, out, err_dev, total_dev);
       f.coff = P->d_ccoff;
       f.unit_sub = P->d_usub;

@@ -14,6 +14,7 @@ constexpr int kSubMaxK = 64;          // k_max bound (coefficient solve keeps k 
 constexpr int kSubMaxN = 1024;        // window length bound (one residual norm per column in smem)
 constexpr int kSubMaxCoarse = 40960;  // coarse rows bound (one column of B in shared memory)
 constexpr int kSubUnitElems = 32768;  // target fine elements per SPID error unit
+constexpr int kSubMaxStencil = 16;   // coarse rows per fine row of a point-set interpolation
 
 // Division by a fixed divisor d >= 1 as a multiply-high and a shift
 // (Granlund and Montgomery, PLDI'94, Section 4): for 0 <= x < 2^31,
@@ -91,5 +92,16 @@ cudaError_t launch_spid_interp(const SubErrArgs& a, int64_t units, int mc_max, i
 // to the fine grid, m_s x k_s column-major at foff[s] (leading dimension m_s).
 cudaError_t launch_fine_skeleton(const SubArgs& a, float* F, const int64_t* foff, int m_max,
                                  cudaStream_t st);
+
+// Point-set plans: B = A(crow, :); F = M B(:, I_B) with a t-wide stencil
+// (iidx, iw: m_s x t per subdomain at ioff[s]); out = F C (no window).
+cudaError_t launch_subsample_rows(const SubArgs& a, const float* window, int col0, int ncols,
+                                  const int32_t* crow, const int64_t* crow_off, int64_t max_work,
+                                  cudaStream_t st);
+cudaError_t launch_fine_skeleton_points(const SubArgs& a, float* F, const int64_t* foff,
+                                        const int32_t* iidx, const float* iw, const int64_t* ioff,
+                                        int t, int m_max, cudaStream_t st);
+cudaError_t launch_skeleton_product(const SubArgs& a, const float* F, const int64_t* foff,
+                                    float* out, int m_max, int n_max, cudaStream_t st);
 
 }  // namespace spid

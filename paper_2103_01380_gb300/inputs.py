@@ -387,3 +387,91 @@ def tgv3d_u1(grid: int, t: np.ndarray, nu: float = 0.01, dtype=np.float32) -> np
     Z, Yg, X = np.meshgrid(c, c, c, indexing="ij")
     space = (np.sin(X) * np.cos(Yg) * np.cos(Z)).reshape(-1)
     return np.outer(space, np.exp(-3.0 * nu * np.asarray(t))).astype(dtype)
+
+
+# ---------------------------------------------------------------------------
+# Unstructured point sets (Section 5.1 runs the ID on randomly generated
+# points of the 2D TGV domain; rows of A follow the points in random order).
+# The coarse subset and the interpolation stencil are inputs of the coarse-grid
+# ID (the paper leaves the choice of M to the user).
+# ---------------------------------------------------------------------------
+def unstructured_tgv2d(npts: int, n: int, seed: int, nu: float = 0.01, t_end: float = 10.0,
+                       noise: float = 0.0, qois=("u1", "u2"), smooth_modes: int = 0):
+    """npts uniformly random points of [0, 2 pi)^2 (rows in random order) and
+    the 2D TGV fields at them over n snapshots on [0, t_end]: returns (pts
+    [npts, 2], A [len(qois) npts, n], rows QoI-major).  smooth_modes > 0 adds
+    that many smooth random space-time modes of amplitude 0.1 2^-i (rank
+    above one, still smooth for interpolation)."""
+    rng = np.random.default_rng(seed)
+    pts = rng.uniform(0.0, 2.0 * np.pi, size=(npts, 2))
+    t = t_end * np.arange(n) / max(n - 1, 1)
+    x1, x2 = pts[:, 0], pts[:, 1]
+    g = np.exp(-2.0 * nu * t)
+    fields = {"u1": np.outer(np.sin(x1) * np.cos(x2), g),
+              "u2": np.outer(-np.cos(x1) * np.sin(x2), g)}
+    A = np.concatenate([fields[q] for q in qois], axis=0)
+    for i in range(smooth_modes):
+        kx, ky = rng.integers(1, 3, size=2)
+        ph = rng.uniform(0.0, 2.0 * np.pi, 3)
+        sp = np.sin(kx * x1 + ph[0]) * np.cos(ky * x2 + ph[1])
+        tm = 0.1 * 0.5 ** i * np.cos((i + 1) * 2.0 * np.pi * t / t_end + ph[2])
+        A = A + np.outer(np.tile(sp, len(qois)), tm)
+    if noise > 0:
+        A = A + noise * rng.standard_normal(A.shape)
+    return pts, A
+
+
+def point_partitions(pts: np.ndarray, nbx: int, nby: int):
+    """Indices of the points in each of nbx x nby equal blocks of [0, 2 pi)^2
+    (block-row-major), each list in the points' own (random) order."""
+    bx = np.minimum((pts[:, 0] / (2.0 * np.pi) * nbx).astype(int), nbx - 1)
+    by = np.minimum((pts[:, 1] / (2.0 * np.pi) * nby).astype(int), nby - 1)
+    return [np.nonzero((by == j) & (bx == i))[0] for j in range(nby) for i in range(nbx)]
+
+
+def coarse_stencil(pts: np.ndarray, mc: int, t: int, seed: int, nq: int = 1,
+                   method: str = "linear"):
+    """Coarse subset and interpolation stencil of one subdomain's points (np
+    points, rows QoI-major over nq QoIs): mc random coarse points per QoI
+    (coarse rows listed QoI-major), and per fine row t coarse points of the same
+    QoI with weights summing to one.  method "linear": barycentric weights in
+    the Delaunay triangle of the coarse points that holds the point (t = 3;
+    exact for fields linear in space), falling back to "idw" outside their
+    hull; "idw": the t nearest coarse points with inverse-square-distance
+    weights.  A coarse point takes weight one on itself.  Returns (coarse_rows
+    [nq mc], idx [nq np, t], w [nq np, t])."""
+    from scipy.spatial import Delaunay, cKDTree
+    rng = np.random.default_rng(seed)
+    npt = pts.shape[0]
+    cpos = np.sort(rng.choice(npt, size=mc, replace=False))
+    cp = pts[cpos]
+    tree = cKDTree(cp)
+    tt = min(t, mc)
+    d, nb = tree.query(pts, k=tt)
+    d = np.asarray(d, dtype=np.float64).reshape(npt, tt)
+    nb = np.asarray(nb, dtype=np.int64).reshape(npt, tt)
+    w = np.zeros((npt, t))
+    idx = np.zeros((npt, t), dtype=np.int32)
+    inv = np.where(d > 0.0, 1.0 / np.where(d > 0.0, d, 1.0) ** 2, 0.0)
+    tot = inv.sum(axis=1, keepdims=True)
+    w[:, :tt] = inv / np.where(tot > 0.0, tot, 1.0)
+    idx[:, :tt] = nb
+    if method == "linear" and t >= 3 and mc >= 4:
+        tri = Delaunay(cp)
+        simp = tri.find_simplex(pts)
+        inside = simp >= 0
+        T = tri.transform[simp[inside]]                    # [k, 3, 2]
+        b = np.einsum("kij,kj->ki", T[:, :2, :], pts[inside] - T[:, 2, :])
+        bary = np.concatenate([b, 1.0 - b.sum(axis=1, keepdims=True)], axis=1)
+        w[inside] = 0.0
+        w[inside, :3] = bary
+        idx[inside] = 0
+        idx[inside, :3] = tri.simplices[simp[inside]]
+    exact = d[:, 0] == 0.0
+    w[exact] = 0.0
+    w[exact, 0] = 1.0
+    idx[exact, 0] = nb[exact, 0]
+    rows = np.concatenate([q * npt + cpos for q in range(nq)]).astype(np.int32)
+    idx_all = np.concatenate([idx + q * mc for q in range(nq)]).astype(np.int32)
+    w_all = np.concatenate([w] * nq)
+    return rows, idx_all, w_all

@@ -38,7 +38,8 @@ EXPORTS = ["spid_plan_create", "spid_plan_destroy", "spid_plan_info", "spid_sket
            "spid_ts_error", "spid_ts_reconstruct", "spid_ts_get_factors",
            "spid_ts_get_block_factors", "spid_ts_device_status",
            "spid_plan_get_tuning", "spid_plan_set_tuning", "spid_plan_autotune",
-           "spid_plan_tuning_key", "spid_graph_create", "spid_graph_launch", "spid_graph_destroy"]
+           "spid_plan_tuning_key", "spid_graph_create", "spid_graph_launch", "spid_graph_destroy",
+           "spid_sub_plan_create_points"]
 GRAPH_SKETCH = 1
 GRAPH_FINALIZE = 2
 GRAPH_ERROR = 4
@@ -97,6 +98,22 @@ class _Tuning(ctypes.Structure):
         for name, _ in cls._fields_:
             setattr(t, name, d.get(name, 0))
         return t
+
+
+class _SubPointsDesc(ctypes.Structure):
+    _fields_ = [("num_sub", ctypes.c_int32),
+                ("m", ctypes.POINTER(ctypes.c_int32)),
+                ("n", ctypes.POINTER(ctypes.c_int32)),
+                ("off", ctypes.POINTER(ctypes.c_int64)),
+                ("ld", ctypes.POINTER(ctypes.c_int64)),
+                ("mc", ctypes.POINTER(ctypes.c_int32)),
+                ("coarse_rows", ctypes.POINTER(ctypes.c_int32)),
+                ("stencil", ctypes.c_int32),
+                ("interp_idx", ctypes.POINTER(ctypes.c_int32)),
+                ("interp_w", ctypes.POINTER(ctypes.c_float)),
+                ("k_max", ctypes.c_int32),
+                ("tol", ctypes.c_double),
+                ("flags", ctypes.c_uint32)]
 
 
 class _TsDesc(ctypes.Structure):
@@ -166,6 +183,7 @@ def load_library(path: str = LIB_PATH):
             "spid_graph_create": ([vp, vp, i32, i32, i32, u32, vp, vp, c.POINTER(vp)], c.c_int),
             "spid_graph_launch": ([vp, vp], c.c_int),
             "spid_graph_destroy": ([vp], c.c_int),
+            "spid_sub_plan_create_points": ([c.POINTER(_SubPointsDesc), c.POINTER(vp)], c.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -421,6 +439,54 @@ class SubPlan:
         ws = ctypes.c_int64()
         _check(lib.spid_sub_plan_info(h, mc.ctypes.data, ctypes.byref(ws)), "spid_sub_plan_info")
         self.mc, self.workspace_bytes = mc, int(ws.value)
+
+    @classmethod
+    def from_points(cls, m, n, off, ld, coarse_rows, interp_idx, interp_w, k_max: int,
+                    tol: float = 0.0) -> "SubPlan":
+        """Point-set plan (spid_sub_plan_create_points): coarse_rows[s] lists the
+        rows of A_s kept in B_s; interp_idx[s] / interp_w[s] are m_s x t arrays,
+        fine row r = sum_q w[r, q] B_s(idx[r, q], :)."""
+        lib = load_library()
+        self = cls.__new__(cls)
+        self.m = np.ascontiguousarray(m, dtype=np.int32)
+        self.S = int(len(self.m))
+        self.n = np.ascontiguousarray(np.broadcast_to(n, (self.S,)), dtype=np.int32)
+        self.off = np.ascontiguousarray(off, dtype=np.int64)
+        self.ld = np.ascontiguousarray(ld, dtype=np.int64)
+        self.k_max = int(k_max)
+        t = int(np.asarray(interp_idx[0]).reshape(int(self.m[0]), -1).shape[1])
+        mc = np.array([len(c) for c in coarse_rows], dtype=np.int32)
+        crow = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.int32)
+                                                    for c in coarse_rows]))
+        iidx = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.int32).reshape(-1)
+                                                    for x in interp_idx]))
+        iw = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float32).reshape(-1)
+                                                  for x in interp_w]))
+        d = _SubPointsDesc()
+        d.num_sub = self.S
+        P32 = ctypes.POINTER(ctypes.c_int32)
+        P64 = ctypes.POINTER(ctypes.c_int64)
+        d.m = self.m.ctypes.data_as(P32)
+        d.n = self.n.ctypes.data_as(P32)
+        d.off = self.off.ctypes.data_as(P64)
+        d.ld = self.ld.ctypes.data_as(P64)
+        d.mc = mc.ctypes.data_as(P32)
+        d.coarse_rows = crow.ctypes.data_as(P32)
+        d.stencil = t
+        d.interp_idx = iidx.ctypes.data_as(P32)
+        d.interp_w = iw.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        d.k_max = self.k_max
+        d.tol = float(tol)
+        d.flags = 0
+        h = ctypes.c_void_p()
+        _check(lib.spid_sub_plan_create_points(ctypes.byref(d), ctypes.byref(h)),
+               "spid_sub_plan_create_points")
+        self._h = h
+        out_mc = np.zeros(self.S, dtype=np.int64)
+        ws = ctypes.c_int64()
+        _check(lib.spid_sub_plan_info(h, out_mc.ctypes.data, ctypes.byref(ws)), "spid_sub_plan_info")
+        self.mc, self.workspace_bytes = out_mc, int(ws.value)
+        return self
 
     @classmethod
     def for_window(cls, win, stride, **kw) -> "SubPlan":

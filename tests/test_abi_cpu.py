@@ -71,3 +71,18 @@ def test_compression_factor_matches_oracle_and_paper(lib):
         assert spid.compression_factor(m, n, k) == pytest.approx(oracle.compression_factor(m, n, k),
                                                                  rel=1e-15)
     assert spid.compression_factor([10], [10], [0]) == float("inf")
+
+
+def test_invalid_point_sets_are_rejected(lib):
+    # argument checks run before any device call
+    from paper_2103_01380_gb300 import inputs
+    win = inputs.pack_blocks([np.ones((20, 5))])
+    ok = dict(crows=[np.arange(5)], idxs=[np.zeros((20, 2), np.int32)], ws=[np.ones((20, 2))])
+    for bad in (dict(crows=[np.array([0, 1, 99])]),                       # row out of range
+                dict(idxs=[np.full((20, 2), 7, np.int32)]),               # coarse index out of range
+                dict(ws=[np.full((20, 2), np.nan)])):                    # non-finite weight
+        a = dict(ok, **bad)
+        with pytest.raises(spid.SpidError) as ei:
+            spid.SubPlan.from_points(win.m, win.n, win.off, win.ld, a["crows"], a["idxs"],
+                                     a["ws"], 3)
+        assert ei.value.status == 1
