@@ -257,6 +257,8 @@ def run_workload(args):
         line = _run_uneven(args, torch, inputs, spid)
     elif args.workload == "coarse_tgv3d64":
         line = _run_coarse(args, torch, inputs, spid)
+    elif args.workload == "points_tgv2d":
+        line = _run_points(args, torch, inputs, spid)
     elif args.workload == "two_stage_tgv3d64":
         line = _run_two_stage(args, torch, inputs, spid)
     else:
@@ -361,6 +363,56 @@ def _run_coarse(args, torch, inputs, spid):
                                 "unit": "GB/s", "cores": 1, "kind": "oracle",
                                 "sample": "subdomains 0 and 63, interval 3 (FP64 oracle)"}
     return line
+
+
+def _run_points(args, torch, inputs, spid):
+    """Coarse-grid ID on an unstructured point set (Section 2: rows in any order;
+    Section 5.1: random points): the 2D TGV (u1, u2) plus 4 smooth modes at 2^20
+    uniformly random points of [0, 2 pi)^2 in 16 x 16 spatial blocks (about
+    4096 points x 2 QoIs per block, rows in random order), n = 256 snapshots;
+    per block a random coarse subset of 1/8 of its points with barycentric
+    Delaunay stencils (t = 3); adaptive tol 1e-3 on B, k_max = 16."""
+    rng = np.random.default_rng(5)
+    npts, n = 1 << 20, 256
+    pts = rng.uniform(0.0, 2.0 * np.pi, size=(npts, 2))
+    parts = inputs.point_partitions(pts, 16, 16)
+    win, m, nn, off, ld = inputs.tgv2d_points_window_device(pts, parts, n, seed=5)
+    crows, idxs, ws = [], [], []
+    for b, part in enumerate(parts):
+        cr, ix, w = inputs.coarse_stencil(pts[part], max(4, len(part) // 8), 3, seed=500 + b,
+                                          nq=2)
+        crows.append(cr)
+        idxs.append(ix)
+        ws.append(w)
+    S = len(parts)
+    nbytes = 4.0 * float((m * nn).sum())
+    plan = spid.SubPlan.from_points(m, nn, off, ld, crows, idxs, ws, k_max=16, tol=1e-3)
+    err = torch.zeros(2 * S, dtype=torch.float64, device="cuda")
+    tot = torch.zeros(4, dtype=torch.float64, device="cuda")
+    res = {}
+    for form, tag in ((spid.FORM_SPID, "spid"), (spid.FORM_SUBID, "subid")):
+        sa, fi, er = _coarse_stage_times(torch, plan, win, args.steps, args.warmup, err, tot, form)
+        t = tot.cpu().numpy()
+        res[tag] = {"value": nbytes / ((sa + fi + er) / 1e3) / 1e9,
+                    "single_pass_gbs": nbytes / ((sa + fi) / 1e3) / 1e9,
+                    "stages_ms": {"sample": sa, "finalize": fi, "error": er},
+                    "error_gbs": nbytes / (er / 1e3) / 1e9,
+                    "rel_err": float(np.sqrt(t[0] / t[1])),
+                    "compression_factor": float(t[2] / t[3])}
+    k, _, _, _ = plan.factors()
+    status = plan.device_status()
+    plan.close()
+    main = res["spid"]
+    return {"value": main["value"], "ms_per_step": sum(main["stages_ms"].values()),
+            "dtype": "f32",
+            "config": {"workload": "coarse-grid SPID on an unstructured point set: 2D TGV "
+                                   "(u1, u2) + 4 smooth modes at 2^20 random points in 16 x 16 "
+                                   "blocks (~4096 points x 2 QoIs each, random row order), "
+                                   "n=256, coarse subsets of 1/8 of the points, Delaunay "
+                                   "barycentric stencils (t=3), adaptive tol 1e-3, k_max=16",
+                       "l2": f"inputs ({nbytes / 1e9:.2f} GB) larger than L2; no flush"},
+            "forms": res, "k_mean": float(np.mean(k)), "k_max": int(np.max(k)),
+            "status": status, "_sketch_gbs": main["single_pass_gbs"]}
 
 
 def _run_two_stage(args, torch, inputs, spid):
@@ -535,6 +587,86 @@ def _run_uneven(args, torch, inputs, spid):
             "_sketch_gbs": tot_bytes / (sk_ms_all / 1e3) / 1e9}
 
 
+def _insitu_solver(torch, spid, plan, window, field, t_all, calls, S, m, n, err, tot,
+                   substeps=4, dt=0.003, nu=0.01):
+    """Compression next to a running solver on the same GPU: the producer (an
+    advection-diffusion stand-in for the paper's flow solver, spid_producer_step)
+    advances the TGV+Fourier state `substeps` steps per snapshot and writes each
+    snapshot into the window; the sketch consumes each micro-batch of snapshots
+    on a second stream as soon as it lands, then finalize + error close the
+    window.  Times: solver alone, compression alone, and both overlapped."""
+    view = window.view(n, S * m)
+    scratch = [torch.empty(S * m, device="cuda"), torch.empty(S * m, device="cuda")]
+
+    def produce(j):
+        src = view[j - 1]
+        for i in range(substeps):
+            dst = view[j] if i == substeps - 1 else scratch[i % 2]
+            spid.producer_step(src, dst, 256, 32, 5, dt, nu)
+            src = dst
+
+    def initial():
+        field.fill_snapshot_major(window, t_all[:1], 0, n)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    cons = torch.cuda.current_stream()
+    prod = torch.cuda.Stream()
+    initial()
+    torch.cuda.synchronize()
+    a0, a1 = ev(), ev()
+    a0.record(cons)
+    for j in range(1, n):
+        produce(j)
+    a1.record(cons)
+    torch.cuda.synchronize()
+    solver_ms = a0.elapsed_time(a1)
+    # compression alone on the solver's window
+    b0, b1, b2 = ev(), ev(), ev()
+    b0.record(cons)
+    for j0, nc in calls:
+        plan.sketch(window, j0, nc)
+    b1.record(cons)
+    plan.finalize()
+    plan.error(window, err, tot)
+    b2.record(cons)
+    torch.cuda.synchronize()
+    sketch_ms, close_ms = b0.elapsed_time(b1), b1.elapsed_time(b2)
+    t = tot.cpu().numpy()
+    k, _, _ = plan.factors()
+    # both: the producer stream writes the window while the sketch consumes it
+    initial()
+    torch.cuda.synchronize()
+    ready = {}
+    c0, c1, c2 = ev(), ev(), ev()
+    c0.record(cons)
+    prod.wait_event(c0)
+    with torch.cuda.stream(prod):
+        for j0, nc in calls:
+            for j in range(max(j0, 1), j0 + nc):
+                produce(j)
+            ready[j0] = torch.cuda.Event()
+            ready[j0].record(prod)
+    for j0, nc in calls:
+        cons.wait_event(ready[j0])
+        plan.sketch(window, j0, nc)
+    c1.record(cons)
+    plan.finalize()
+    plan.error(window, err, tot)
+    c2.record(cons)
+    torch.cuda.synchronize()
+    both_ms = c0.elapsed_time(c2)
+    overlap_sketch_ms = c0.elapsed_time(c1)
+    return {"producer": "advection-diffusion stand-in (upwind + 7-point Laplacian), "
+                        f"{substeps} steps of dt={dt} per snapshot, nu={nu}",
+            "solver_ms": solver_ms, "sketch_ms": sketch_ms, "finalize_error_ms": close_ms,
+            "overlapped_ms": both_ms,
+            "sketch_hidden_fraction": max(0.0, (solver_ms + sketch_ms - overlap_sketch_ms) /
+                                          sketch_ms),
+            "overhead_vs_solver": both_ms / solver_ms - 1.0,
+            "rel_err": float(np.sqrt(t[0] / t[1])), "compression_factor": float(t[2] / t[3]),
+            "k_mean": float(np.mean(k)), "k_max": int(np.max(k))}
+
+
 def _run_insitu(args, torch, inputs, spid):
     """512 boxes of 32^3 x 5 QoIs of a 256^3 field, n = 256, snapshot-major window
     (86 GB); the sketch runs per micro-batch of snapshots as they arrive; k 30,
@@ -586,6 +718,7 @@ def _run_insitu(args, torch, inputs, spid):
     p1.record(cons)
     torch.cuda.synchronize()
     produce = p0.elapsed_time(p1)
+    solver = _insitu_solver(torch, spid, plan, window, field, t_all, calls, S, m, n, err, tot)
     plan.close()
     step = sk + fi + er
     return {"value": nbytes / (step / 1e3) / 1e9, "ms_per_step": step,
@@ -600,6 +733,7 @@ def _run_insitu(args, torch, inputs, spid):
             "insitu_overlap": {"producer_ms": produce, "compress_ms": step,
                                "overlapped_ms": overlapped,
                                "hidden_fraction": max(0.0, (produce + step - overlapped) / step)},
+            "insitu_solver": solver,
             "_sketch_gbs": nbytes / (sk / 1e3) / 1e9}
 
 
@@ -622,7 +756,7 @@ def main():
                     help="keep the library's default tile shapes (no measurement)")
     ap.add_argument("--workload", default="tgv3d64",
                     choices=["tgv3d64", "spectrum256", "uneven4096", "insitu256",
-                             "coarse_tgv3d64", "two_stage_tgv3d64"],
+                             "coarse_tgv3d64", "two_stage_tgv3d64", "points_tgv2d"],
                     help="tgv3d64 is the bench workload; the others print their own line")
     ap.add_argument("--microbatch", type=int, default=64, help="insitu256: columns per call")
     ap.add_argument("--wave-gb", type=float, default=48.0, help="uneven4096: GB per wave")

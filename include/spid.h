@@ -300,6 +300,23 @@ spid_status spid_graph_destroy(spid_graph_t graph);
 spid_status spid_sketch_fp32_noalloc(const float* A, int32_t m, int32_t n, int64_t ld, int32_t l,
                                      uint64_t seed, float* Y, int32_t ldy, spid_stream_t stream);
 
+/* ---- In-situ producer ---------------------------------------------------
+ * A snapshot producer for measuring compression next to a running solver
+ * (Section 5.2 and Algorithms 4-6: the solver updates the state every time
+ * step and the compression consumes its snapshots).  A stand-in for the
+ * paper's compressible Navier-Stokes solver, not part of the decomposition:
+ * one forward-Euler step of f_t + (u . grad) f = nu lap f for every QoI f,
+ * velocity u = QoIs 1..3, periodic grid^3 grid of spacing 2 pi / grid,
+ * first-order upwind advection and the 7-point Laplacian (stable for
+ * dt (3 max|u| / h + 6 nu / h^2) <= 1).  state_in / state_out: device, one
+ * snapshot of a box-major window, [box][q][z][y][x] with boxes of edge^3
+ * points and box index (bz nb + by) nb + bx, nb = grid / edge; distinct
+ * buffers of nq grid^3 floats.  SPID_ERR_INVALID_ARG unless grid % edge == 0,
+ * nq >= 4, dt > 0, nu >= 0.  Asynchronous on `stream`. */
+spid_status spid_producer_step(const float* state_in, float* state_out, int32_t grid,
+                               int32_t edge, int32_t nq, float dt, float nu,
+                               spid_stream_t stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* spid_status_string(spid_status status);
 

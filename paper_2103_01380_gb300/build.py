@@ -16,7 +16,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libspid.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 UNITS = ["sketch_simt", "sketch_tc", "sketch_bf16", "qrcp", "error", "error_tc", "subid", "subid_api", "spid_ts", "spid_api",
-         "sketch_noalloc"]
+         "sketch_noalloc", "producer"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

@@ -475,3 +475,37 @@ def coarse_stencil(pts: np.ndarray, mc: int, t: int, seed: int, nq: int = 1,
     idx_all = np.concatenate([idx + q * mc for q in range(nq)]).astype(np.int32)
     w_all = np.concatenate([w] * nq)
     return rows, idx_all, w_all
+
+
+def tgv2d_points_window_device(pts: np.ndarray, parts, n: int, seed: int, nu: float = 0.01,
+                               t_end: float = 10.0, smooth_modes: int = 4, device="cuda"):
+    """Subdomain-major FP32 window on the GPU of the 2D TGV (u1, u2) plus
+    `smooth_modes` smooth space-time modes (as unstructured_tgv2d) at the
+    points of each partition: block s holds rows (q, point of parts[s]), ld =
+    rows rounded up to 4.  Returns (window tensor, m, n, off, ld)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    t = t_end * np.arange(n) / max(n - 1, 1)
+    g = torch.tensor(np.exp(-2.0 * nu * t), device=device, dtype=torch.float32)
+    modes = []
+    for i in range(smooth_modes):
+        kx, ky = rng.integers(1, 3, size=2)
+        ph = rng.uniform(0.0, 2.0 * np.pi, 3)
+        tm = 0.1 * 0.5 ** i * np.cos((i + 1) * 2.0 * np.pi * t / t_end + ph[2])
+        modes.append((int(kx), int(ky), ph, torch.tensor(tm, device=device, dtype=torch.float32)))
+    m = np.array([2 * len(p) for p in parts], dtype=np.int64)
+    ld = (m + 3) // 4 * 4
+    off = np.concatenate([[0], np.cumsum(ld * n)[:-1]]).astype(np.int64)
+    win = torch.zeros(int((ld * n).sum()), device=device, dtype=torch.float32)
+    P = torch.tensor(pts, device=device, dtype=torch.float64)
+    for s, part in enumerate(parts):
+        idx = torch.tensor(part, device=device, dtype=torch.int64)
+        x1, x2 = P[idx, 0], P[idx, 1]
+        sp = torch.stack([torch.sin(x1) * torch.cos(x2), -torch.cos(x1) * torch.sin(x2)])   # [2, np]
+        blk = (sp.reshape(-1, 1).float() * g[None, :])
+        for kx, ky, ph, tm in modes:
+            mode = (torch.sin(kx * x1 + ph[0]) * torch.cos(ky * x2 + ph[1])).float()
+            blk = blk + torch.cat([mode, mode]).reshape(-1, 1) * tm[None, :]
+        view = win[int(off[s]):int(off[s] + ld[s] * n)].view(n, int(ld[s]))
+        view[:, :int(m[s])] = blk.T
+    return win, m, np.full(len(parts), n, dtype=np.int64), off, ld

@@ -39,7 +39,7 @@ EXPORTS = ["spid_plan_create", "spid_plan_destroy", "spid_plan_info", "spid_sket
            "spid_ts_get_block_factors", "spid_ts_device_status",
            "spid_plan_get_tuning", "spid_plan_set_tuning", "spid_plan_autotune",
            "spid_plan_tuning_key", "spid_graph_create", "spid_graph_launch", "spid_graph_destroy",
-           "spid_sub_plan_create_points"]
+           "spid_sub_plan_create_points", "spid_producer_step"]
 GRAPH_SKETCH = 1
 GRAPH_FINALIZE = 2
 GRAPH_ERROR = 4
@@ -184,6 +184,7 @@ def load_library(path: str = LIB_PATH):
             "spid_graph_launch": ([vp, vp], c.c_int),
             "spid_graph_destroy": ([vp], c.c_int),
             "spid_sub_plan_create_points": ([c.POINTER(_SubPointsDesc), c.POINTER(vp)], c.c_int),
+            "spid_producer_step": ([vp, vp, i32, i32, i32, c.c_float, c.c_float, vp], c.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -216,6 +217,14 @@ def _ptr(t) -> int:
             raise ValueError("expected a CUDA tensor")
         return t.data_ptr()
     return int(t)
+
+
+def producer_step(state_in, state_out, grid: int, edge: int, nq: int, dt: float, nu: float,
+                  stream=None):
+    """One step of the in-situ producer (spid_producer_step) on device tensors."""
+    _check(load_library().spid_producer_step(_ptr(state_in), _ptr(state_out), int(grid),
+                                             int(edge), int(nq), float(dt), float(nu),
+                                             _stream_handle(stream)), "spid_producer_step")
 
 
 class Plan:

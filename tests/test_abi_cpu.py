@@ -86,3 +86,14 @@ def test_invalid_point_sets_are_rejected(lib):
             spid.SubPlan.from_points(win.m, win.n, win.off, win.ld, a["crows"], a["idxs"],
                                      a["ws"], 3)
         assert ei.value.status == 1
+
+
+def test_producer_rejects_bad_arguments(lib):
+    import ctypes
+    buf = ctypes.create_string_buffer(64)
+    p = ctypes.addressof(buf)
+    for args in ((p, p, 16, 8, 5, 0.01, 0.01),        # in == out
+                 (p, p + 16, 16, 5, 5, 0.01, 0.01),   # grid % edge != 0
+                 (p, p + 16, 16, 8, 3, 0.01, 0.01),   # nq < 4
+                 (p, p + 16, 16, 8, 5, 0.0, 0.01)):   # dt <= 0
+        assert lib.spid_producer_step(*args, None) == 1
