@@ -195,7 +195,69 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
     std::stable_sort(subs.begin(), subs.end(), [&](int x, int y) { return P->m[x] < P->m[y]; });
   std::vector<Problem> probs;
   std::vector<int> prob_sub_first(P->S + 1, 0);   // per-subdomain mode: problems of s
+  struct Unit { int nch; double w; int prob0; int nprob; int pack; };
+  std::vector<Unit> units;
+  std::vector<Slice> slices;
+  std::vector<Pack> packs;
+  // Batched tensor-core plans: the 64-column slices of every subdomain of one m
+  // form a stream that is cut into packs of pack_slices slices, so every pack
+  // but the last of an m-class is full whatever the window lengths; a problem
+  // (the fold unit) is a subdomain's run of consecutive slices inside one pack.
+  // A chunk's weight counts its columns plus a fixed share for the Omega chunk
+  // it regenerates.
+  const bool streamed = tc && !P->per_sub();
+  if (streamed) {
+    Pack pk{};
+    int cols = 0;
+    auto close_pack = [&]() {
+      if (pk.nslices == 0) return;
+      units.push_back({(pk.m + kChunkRows - 1) / kChunkRows, (double)(cols + kSliceCols / 2),
+                       pk.prob0, pk.nprob, (int)packs.size()});
+      packs.push_back(pk);
+      pk = Pack{};
+      cols = 0;
+    };
+    for (size_t q = 0; q < subs.size(); ++q) {
+      const int s = subs[q];
+      if (pk.nslices > 0 && P->m[s] != pk.m) close_pack();
+      const int end = std::min<int64_t>((int64_t)col0 + ncols, P->n[s]);
+      for (int c = col0; c < end; c += kSliceCols) {
+        if (pk.nslices == P->tune.pack_slices) close_pack();
+        if (pk.nslices == 0) {
+          pk.slice0 = (int)slices.size();
+          pk.m = P->m[s];
+          pk.prob0 = (int)probs.size();
+          pk.nprob = 0;
+        }
+        const int nc = std::min(kSliceCols, end - c);
+        if (pk.nprob == 0 || probs.back().sub != s) {
+          Problem pb;
+          pb.sub = s;
+          pb.col0 = c;
+          pb.ncols = 0;
+          pb.m = P->m[s];
+          pb.off = P->off[s];
+          pb.ld = P->ld[s];
+          probs.push_back(pb);
+          ++pk.nprob;
+        }
+        Slice sl;
+        sl.prob = (int)probs.size() - 1;
+        sl.sub = s;
+        sl.col0 = c;
+        sl.ncols = nc;
+        sl.out_col = c - probs.back().col0;
+        sl.member = pk.nprob - 1;
+        slices.push_back(sl);
+        probs.back().ncols += nc;
+        ++pk.nslices;
+        cols += nc;
+      }
+    }
+    close_pack();
+  }
   for (int s : subs) {
+    if (streamed) break;
     prob_sub_first[s] = (int)probs.size();
     const int end = std::min<int64_t>((int64_t)col0 + ncols, P->n[s]);
     for (int c = col0; c < end; c += CG) {
@@ -215,10 +277,6 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
     prob_sub_last[s] = prob_sub_first[s] + (end > col0 ? (end - col0 + CG - 1) / CG : 0);
   }
   // ---- work units
-  struct Unit { int nch; double w; int prob0; int nprob; int pack; };
-  std::vector<Unit> units;
-  std::vector<Slice> slices;
-  std::vector<Pack> packs;
   auto make_units = [&](int p0, int p1) {
     if (!tc) {
       for (int p = p0; p < p1; ++p)
@@ -312,7 +370,7 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
       partition(u0, (int)units.size());
     }
   } else {
-    make_units(0, (int)probs.size());
+    if (!streamed) make_units(0, (int)probs.size());
     partition(0, (int)units.size());
   }
   std::vector<int32_t> pslot_ptr(probs.size() + 1, 0), pslots;
