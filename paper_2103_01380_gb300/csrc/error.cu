@@ -67,7 +67,7 @@ __device__ __forceinline__ void kahan_add(T& s, T& c, T x) {
 }
 
 template <typename T, bool WRITE, int CB>
-__global__ void __launch_bounds__(256) error_kernel(ErrArgs a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) error_kernel(ErrArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[2][8];
   __shared__ int last_sub;

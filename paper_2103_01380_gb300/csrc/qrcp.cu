@@ -108,58 +108,60 @@ __device__ __forceinline__ PivotKey warp_pivot(uint32_t k0, uint32_t k1, uint32_
 
 
 // T = R11^-1 r in place over r[0 .. keff), FP64-class accuracy.
-// FP32 data: every t_l is carried as an unevaluated pair (hi in r, lo in tl),
-// each product R_il t_l is split exactly with fma, and the running residual is
-// an error-free double-float sum; the division is corrected by one residual
+// FP32 data: every t_l is carried as an unevaluated pair (hi, lo), each product
+// R_il t_l is split exactly with fma, and the running residual is an
+// error-free double-float sum; the division is corrected by one residual
 // step.  All on the FP32 pipe.  FP64 data: plain FP64.
+// The loops run over keff only (usually a handful of pivots): the column is
+// copied to a per-thread array indexed at run time, so the code stays small
+// -- a fully unrolled LP x LP triangle is fetched almost entirely even when
+// only its first rows execute, and instruction fetch then dominates the QR.
 template <int LP>
-__device__ __forceinline__ void back_substitute(float (&r)[LP], const float (&R)[LP][LP],
-                                                int keff) {
-  float tl[LP];
+__device__ __noinline__ void back_substitute(float (&r)[LP], const float (&R)[LP][LP], int keff) {
+  float th[LP], tl[LP];
 #pragma unroll
-  for (int ii = LP - 1; ii >= 0; --ii) {
-    tl[ii] = 0.f;
-    if (ii < keff) {
-      float hi = r[ii], lo = 0.f;
-#pragma unroll
-      for (int ll = ii + 1; ll < LP; ++ll) {
-        if (ll < keff) {
-          const float Rv = R[ii][ll];
-          const float p = Rv * r[ll];
-          float pe = fmaf(Rv, r[ll], -p);
-          pe = fmaf(Rv, tl[ll], pe);
-          // (hi, lo) -= (p, pe)
-          const float s = hi - p;
-          const float bb = s - hi;
-          float e = (hi - (s - bb)) + (-p - bb);
-          e += lo - pe;
-          hi = s + e;
-          lo = e - (hi - s);
-        }
-      }
-      const float d = R[ii][ii];
-      const float q = hi / d;
-      const float res = fmaf(-q, d, hi) + lo;
-      const float ql = res / d;
-      r[ii] = q + ql;
-      tl[ii] = ql - (r[ii] - q);
-    }
+  for (int i = 0; i < LP; ++i) {
+    th[i] = r[i];
+    tl[i] = 0.f;
   }
+  for (int ii = keff - 1; ii >= 0; --ii) {
+    float hi = th[ii], lo = 0.f;
+    for (int ll = ii + 1; ll < keff; ++ll) {
+      const float Rv = R[ii][ll];
+      const float p = Rv * th[ll];
+      float pe = fmaf(Rv, th[ll], -p);
+      pe = fmaf(Rv, tl[ll], pe);
+      // (hi, lo) -= (p, pe)
+      const float s = hi - p;
+      const float bb = s - hi;
+      float e = (hi - (s - bb)) + (-p - bb);
+      e += lo - pe;
+      hi = s + e;
+      lo = e - (hi - s);
+    }
+    const float d = R[ii][ii];
+    const float q = hi / d;
+    const float res = fmaf(-q, d, hi) + lo;
+    const float ql = res / d;
+    th[ii] = q + ql;
+    tl[ii] = ql - (th[ii] - q);
+  }
+#pragma unroll
+  for (int i = 0; i < LP; ++i) r[i] = th[i];
 }
 
 template <int LP>
-__device__ __forceinline__ void back_substitute(double (&r)[LP], const double (&R)[LP][LP],
-                                                int keff) {
+__device__ __noinline__ void back_substitute(double (&r)[LP], const double (&R)[LP][LP], int keff) {
+  double t[LP];
 #pragma unroll
-  for (int ii = LP - 1; ii >= 0; --ii) {
-    if (ii < keff) {
-      double acc = r[ii];
-#pragma unroll
-      for (int ll = ii + 1; ll < LP; ++ll)
-        if (ll < keff) acc = fma(-R[ii][ll], r[ll], acc);
-      r[ii] = acc / R[ii][ii];
-    }
+  for (int i = 0; i < LP; ++i) t[i] = r[i];
+  for (int ii = keff - 1; ii >= 0; --ii) {
+    double acc = t[ii];
+    for (int ll = ii + 1; ll < keff; ++ll) acc = fma(-R[ii][ll], t[ll], acc);
+    t[ii] = acc / R[ii][ii];
   }
+#pragma unroll
+  for (int i = 0; i < LP; ++i) r[i] = t[i];
 }
 
 template <typename T, int LP, int CPT>
