@@ -309,13 +309,15 @@ spid_status spid_sketch_fp32_noalloc(const float* A, int32_t m, int32_t n, int64
  * velocity u = QoIs 1..3, periodic grid^3 grid of spacing 2 pi / grid,
  * first-order upwind advection and the 7-point Laplacian (stable for
  * dt (3 max|u| / h + 6 nu / h^2) <= 1).  state_in / state_out: device, one
- * snapshot of a box-major window, [box][q][z][y][x] with boxes of edge^3
- * points and box index (bz nb + by) nb + bx, nb = grid / edge; distinct
- * buffers of nq grid^3 floats.  SPID_ERR_INVALID_ARG unless grid % edge == 0,
- * nq >= 4, dt > 0, nu >= 0.  Asynchronous on `stream`. */
-spid_status spid_producer_step(const float* state_in, float* state_out, int32_t grid,
-                               int32_t edge, int32_t nq, float dt, float nu,
-                               spid_stream_t stream);
+ * snapshot each, boxes of edge^3 points with box index (bz nb + by) nb + bx,
+ * nb = grid / edge; box b's [q][z][y][x] block (nq edge^3 floats) starts at
+ * element b * box_stride -- nq edge^3 for a snapshot-major window, nq edge^3 n
+ * for a subdomain-major one (pointer at the snapshot's column).  Distinct
+ * buffers.  SPID_ERR_INVALID_ARG unless grid % edge == 0, nq >= 4, dt > 0,
+ * nu >= 0 and both strides >= nq edge^3.  Asynchronous on `stream`. */
+spid_status spid_producer_step(const float* state_in, int64_t in_box_stride, float* state_out,
+                               int64_t out_box_stride, int32_t grid, int32_t edge, int32_t nq,
+                               float dt, float nu, spid_stream_t stream);
 
 /* Human-readable name of a status code (static storage). */
 const char* spid_status_string(spid_status status);

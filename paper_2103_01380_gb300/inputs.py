@@ -296,6 +296,14 @@ class DeviceField:
         out[4] = p0 * out[0] ** gamma
         return out
 
+    def fill_subdomain_major(self, window, t: np.ndarray, j0: int, n_total: int):
+        """Write snapshots j0 .. j0 + len(t) of every box into a subdomain-major
+        window [S][n_total][5 * npts] (rows of a box in (q, z, y, x) order)."""
+        b = len(t)
+        f = self.snapshots(t)                                           # [5, S*P, b]
+        w = window.view(self.S, n_total, 5, self.npts)
+        w[:, j0:j0 + b] = f.view(5, self.S, self.npts, b).permute(1, 3, 0, 2)
+
     def fill_snapshot_major(self, window, t: np.ndarray, j0: int, n_total: int):
         """Write snapshots j0 .. j0 + len(t) of every box into a snapshot-major
         window [n_total][S][5 * npts] (rows of a box in (q, z, y, x) order)."""

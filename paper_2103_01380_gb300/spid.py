@@ -184,7 +184,8 @@ def load_library(path: str = LIB_PATH):
             "spid_graph_launch": ([vp, vp], c.c_int),
             "spid_graph_destroy": ([vp], c.c_int),
             "spid_sub_plan_create_points": ([c.POINTER(_SubPointsDesc), c.POINTER(vp)], c.c_int),
-            "spid_producer_step": ([vp, vp, i32, i32, i32, c.c_float, c.c_float, vp], c.c_int),
+            "spid_producer_step": ([vp, i64, vp, i64, i32, i32, i32, c.c_float, c.c_float, vp],
+                                   c.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -220,11 +221,15 @@ def _ptr(t) -> int:
 
 
 def producer_step(state_in, state_out, grid: int, edge: int, nq: int, dt: float, nu: float,
-                  stream=None):
-    """One step of the in-situ producer (spid_producer_step) on device tensors."""
-    _check(load_library().spid_producer_step(_ptr(state_in), _ptr(state_out), int(grid),
-                                             int(edge), int(nq), float(dt), float(nu),
-                                             _stream_handle(stream)), "spid_producer_step")
+                  stream=None, in_box_stride: int | None = None,
+                  out_box_stride: int | None = None):
+    """One step of the in-situ producer (spid_producer_step) on device tensors;
+    box strides default to a contiguous snapshot (nq edge^3)."""
+    be = int(nq) * int(edge) ** 3
+    _check(load_library().spid_producer_step(
+        _ptr(state_in), int(in_box_stride or be), _ptr(state_out), int(out_box_stride or be),
+        int(grid), int(edge), int(nq), float(dt), float(nu), _stream_handle(stream)),
+        "spid_producer_step")
 
 
 class Plan:

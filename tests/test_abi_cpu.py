@@ -92,8 +92,10 @@ def test_producer_rejects_bad_arguments(lib):
     import ctypes
     buf = ctypes.create_string_buffer(64)
     p = ctypes.addressof(buf)
-    for args in ((p, p, 16, 8, 5, 0.01, 0.01),        # in == out
-                 (p, p + 16, 16, 5, 5, 0.01, 0.01),   # grid % edge != 0
-                 (p, p + 16, 16, 8, 3, 0.01, 0.01),   # nq < 4
-                 (p, p + 16, 16, 8, 5, 0.0, 0.01)):   # dt <= 0
+    be = 5 * 8 ** 3
+    for args in ((p, be, p, be, 16, 8, 5, 0.01, 0.01),          # in == out
+                 (p, be, p + 16, be, 16, 5, 5, 0.01, 0.01),     # grid % edge != 0
+                 (p, be, p + 16, be, 16, 8, 3, 0.01, 0.01),     # nq < 4
+                 (p, be, p + 16, be, 16, 8, 5, 0.0, 0.01),      # dt <= 0
+                 (p, be - 1, p + 16, be, 16, 8, 5, 0.01, 0.01)):   # box stride too small
         assert lib.spid_producer_step(*args, None) == 1

@@ -52,6 +52,26 @@ def reference_step(F, dt, nu):
     return out
 
 
+def test_producer_step_between_window_layouts():
+    # the same step read from a snapshot-major state and written into column j
+    # of a subdomain-major window ([box][j][rows], box stride nq edge^3 n)
+    grid, edge, nq, n, j = 16, 8, 5, 3, 1
+    rng = np.random.default_rng(7)
+    F = rng.uniform(-1.0, 1.0, size=(nq, grid, grid, grid))
+    be = nq * edge ** 3
+    nbox = (grid // edge) ** 3
+    state = torch.tensor(to_boxes(F, grid, edge, nq), dtype=torch.float32, device="cuda")
+    win = torch.zeros(nbox * n * be, dtype=torch.float32, device="cuda")
+    spid.producer_step(state, win[j * be:], grid, edge, nq, 0.002, 0.01,
+                       out_box_stride=n * be)
+    ref = torch.empty_like(state)
+    spid.producer_step(state, ref, grid, edge, nq, 0.002, 0.01)
+    torch.cuda.synchronize()
+    got = win.view(nbox, n, be)[:, j, :].reshape(-1)
+    assert torch.equal(got, ref)
+    assert float(win.view(nbox, n, be)[:, 0, :].abs().max()) == 0.0   # other columns untouched
+
+
 @pytest.mark.parametrize("grid,edge,nq", [(16, 8, 5), (12, 4, 4), (8, 8, 5)])
 def test_producer_step_matches_the_stencil(grid, edge, nq):
     rng = np.random.default_rng(grid + edge)
