@@ -195,9 +195,19 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
     const int col = tid + c * NT;
     step_of[c] = (col < n) ? -1 : -2;   // -1 active, -2 no column, >= 0 pivot step
     nu[c].set_zero();
+    // the column is LP contiguous values (16-byte aligned: LP is a multiple of 16)
+    constexpr int VW = 16 / sizeof(T);
+#pragma unroll
+    for (int i4 = 0; i4 < LP; i4 += VW) {
+      typename Vec16<T>::type v = Vec16<T>::zero();
+      if (col < n)
+        v = __ldg(reinterpret_cast<const typename Vec16<T>::type*>(Y + (int64_t)col * LP + i4));
+      const T* vs_ = reinterpret_cast<const T*>(&v);
+#pragma unroll
+      for (int u = 0; u < VW; ++u) y[c][i4 + u] = vs_[u];
+    }
 #pragma unroll
     for (int i = 0; i < LP; ++i) {
-      y[c][i] = (col < n) ? Y[(int64_t)col * LP + i] : T(0);
       if (!isfinite(y[c][i])) bad = true;
       nu[c].add_square(y[c][i]);
     }
