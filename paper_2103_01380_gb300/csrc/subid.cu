@@ -9,17 +9,23 @@
 //   fine_skeleton F = M B(:, I_B), the interpolated skeleton (m x k), so that
 //                the error pass is the rank-k product F C_B against A
 //
-// The QR runs one CTA per subdomain with B's working copy in global memory
-// (L2-resident at these sizes): every step picks the active column of largest
-// residual norm (ties to the lowest index), turns it into q_j in shared
+// The QR runs one cluster of up to 8 CTAs per subdomain (the columns dealt
+// out to the CTAs' warps) with B's working copy in global memory: every step
+// picks the active column of largest residual norm (ties to the lowest
+// index; the CTAs exchange their candidates through distributed shared
+// memory and take the same decision), turns it into q_j in each CTA's shared
 // memory, and one warp per remaining column computes R(j, c) = q_j . w_c,
 // updates w_c -= R(j, c) q_j and recomputes ||w_c||^2 from the updated
 // values -- the residual norms are therefore taken from the current columns
 // at every step, as in the oracle, with no downdating.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "error_fold.cuh"
 #include "subid_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace spid {
 
@@ -107,20 +113,55 @@ __device__ void df_back_substitute(const float* R11, int k, float* th, float* tl
   }
 }
 
+// Error-free sum of two double-float values (h, l) += (bh, bl): the residual
+// norms are summed on the FP32 pipe (FP64 issue is a small fraction of it).
+__device__ __forceinline__ void df_add(float& h, float& l, float bh, float bl) {
+  const float s = h + bh;
+  const float bb = s - h;
+  const float e = ((h - (s - bb)) + (bh - bb)) + (l + bl);
+  h = s + e;
+  l = e - (h - s);
+}
+
+// One subdomain's QR runs on a cluster of G CTAs.  Column c belongs to rank
+// (c / kQrWarps) % G and, there, to warp c % kQrWarps; o-th column of a rank:
+__device__ __forceinline__ int owned_col(int o, int G, int rank) {
+  return ((o / kQrWarps) * G + rank) * kQrWarps + o % kQrWarps;
+}
+
+// What a CTA publishes to the other CTAs of its cluster (double-buffered by
+// pivot step: a slot is rewritten only after every rank has passed the
+// cluster barrier that follows its last read).
+struct QrXchg {
+  unsigned long long key;   // largest (||w_c||^2 bits, ~c) among own active columns
+  float rest_h, rest_l;     // sum of own active ||w_c||^2 (double-float)
+  double nb;                // sum of own ||b_c||^2 (initial exchange only)
+  int bad;                  // a non-finite entry in own columns (initial exchange only)
+};
+
 __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a, int n_max,
                                                                  int qv_floats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* qv = reinterpret_cast<float*>(smem_raw);          // q_j [mc], later R11 [k x k]
-  float* nu = qv + qv_floats;                              // residual norms^2 [n]
+  float* nu = qv + qv_floats;                              // residual norms^2 [n] (own columns)
   int32_t* step = reinterpret_cast<int32_t*>(nu + n_max);  // -1 active, >= 0 pivot step
   __shared__ unsigned long long wkey[kQrWarps];
-  __shared__ double wrest[kQrWarps];
+  __shared__ float wrest_h[kQrWarps], wrest_l[kQrWarps];
+  __shared__ double wnb[kQrWarps];
+  __shared__ QrXchg xs[2];
   __shared__ double normB2_s;
+  __shared__ int dec_p;     // pivot column of this step, -1: stop
+  __shared__ float dec_nu;  // its residual norm^2
   __shared__ int32_t Js[kSubMaxK];
 
-  const int s = blockIdx.x;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int G = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int s = blockIdx.x / G;
   const int n = a.n[s], mc = a.mc[s], k_max = a.k_max;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int cstride = G * kQrWarps;                 // a warp's column stride
+  const int c_first = rank * kQrWarps + warp;       // a warp's first column
   const float* B = a.B + a.boff[s];
   float* W = a.W + a.boff[s];
   float* R = a.R + (int64_t)k_max * a.coff[s];
@@ -128,11 +169,16 @@ __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a
   float* Bsk = a.Bskel + (int64_t)k_max * a.sklo[s];
   int32_t* J = a.J + (int64_t)s * k_max;
 
-  for (int64_t e = tid; e < (int64_t)k_max * n; e += kQrThreads) R[e] = 0.f;
+  // own columns of R start at zero; every rank tracks the pivot steps of all
+  for (int64_t e = tid; e < (int64_t)k_max * n; e += kQrThreads) {
+    const int i = (int)(e / n), c = (int)(e % n);
+    if ((c / kQrWarps) % G == rank) R[(int64_t)i * n + c] = 0.f;
+  }
+  for (int c = tid; c < n; c += kQrThreads) step[c] = -1;
   // initial column norms (B stays untouched: step 0 reads it and writes the
   // working copy W); non-finite check
   bool bad = false;
-  for (int c = warp; c < n; c += kQrWarps) {
+  for (int c = c_first; c < n; c += cstride) {
     const float* col = B + (int64_t)c * mc;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
     int i = lane;
@@ -150,28 +196,54 @@ __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a
       bad |= !isfinite(x);
     }
     const float acc = warp_sum((a0 + a1) + (a2 + a3));
-    if (lane == 0) {
-      nu[c] = acc;
-      step[c] = -1;
+    if (lane == 0) nu[c] = acc;
+  }
+  // own part of ||B||_F^2 (FP64, fixed order), non-finite flag; exchanged
+  {
+    const int any_bad = __syncthreads_or(bad);
+    double t = 0.0;
+    for (int c = c_first; c < n; c += cstride)
+      if (lane == 0) t += (double)nu[c];
+    if (lane == 0) wnb[warp] = t;
+    __syncthreads();
+    if (tid == 0) {
+      double u = 0.0;
+      for (int w = 0; w < kQrWarps; ++w) u += wnb[w];
+      xs[0].nb = u;
+      xs[0].bad = any_bad;
     }
   }
-  if (__syncthreads_or(bad)) {
-    if (tid == 0) {
+  cluster.sync();
+  if (tid == 0) {
+    double u = 0.0;
+    int any = 0;
+    for (int r = 0; r < G; ++r) {
+      const QrXchg* x = cluster.map_shared_rank(&xs[0], r);
+      u += x->nb;
+      any |= x->bad;
+    }
+    normB2_s = u;
+    dec_p = any;
+  }
+  __syncthreads();
+  if (dec_p) {   // the same decision on every rank
+    if (tid == 0 && rank == 0) {
       raise_status(a.status, kStatusNonfinite);
       a.k[s] = 0;
     }
-    for (int p = tid; p < k_max; p += kQrThreads) J[p] = -1;
-    for (int64_t e = tid; e < (int64_t)k_max * n; e += kQrThreads) C[e] = 0.f;
-    for (int64_t e = tid; e < (int64_t)k_max * mc; e += kQrThreads) Bsk[e] = 0.f;
+    if (rank == 0)
+      for (int p = tid; p < k_max; p += kQrThreads) J[p] = -1;
+    for (int o = tid;; o += kQrThreads) {   // own columns of C
+      const int c = owned_col(o, G, rank);
+      if (c >= n) break;
+      for (int i = 0; i < k_max; ++i) C[(int64_t)i * n + c] = 0.f;
+    }
+    for (int64_t e = (int64_t)rank * kQrThreads + tid; e < (int64_t)k_max * mc;
+         e += (int64_t)G * kQrThreads)
+      Bsk[e] = 0.f;
+    cluster.sync();   // no rank leaves while another may still read its slots
     return;
   }
-  if (warp == 0) {   // ||B||_F^2 in a fixed order
-    double t = 0.0;
-    for (int c = lane; c < n; c += 32) t += (double)nu[c];
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) normB2_s = t;
-  }
-  __syncthreads();
   const double normB2 = normB2_s;
   const double tol2 = a.tol * a.tol;
   int kcap = k_max;
@@ -180,12 +252,15 @@ __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a
   int k = 0;
   float r00 = 0.f;
   for (int j = 0; j < kcap; ++j) {
-    // ---- pivot: largest residual norm^2 among active columns, lowest index on ties
+    // ---- pivot: largest residual norm^2 among active columns, lowest index on
+    // ties; own columns first, then the ranks' results in rank order
     unsigned long long key = 0ull;
-    double rest = 0.0;
-    for (int c = tid; c < n; c += kQrThreads) {
+    float rh = 0.f, rl = 0.f;
+    for (int o = tid;; o += kQrThreads) {
+      const int c = owned_col(o, G, rank);
+      if (c >= n) break;
       if (step[c] != -1) continue;
-      rest += (double)nu[c];
+      df_add(rh, rl, nu[c], 0.f);
       const unsigned long long kc =
           ((unsigned long long)__float_as_uint(nu[c]) << 32) | (0xffffffffu - (uint32_t)c);
       key = kc > key ? kc : key;
@@ -193,37 +268,68 @@ __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a
     for (int o = 16; o > 0; o >>= 1) {
       const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, o);
       key = ok > key ? ok : key;
-      rest += __shfl_xor_sync(0xffffffffu, rest, o);
+      const float oh = __shfl_xor_sync(0xffffffffu, rh, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, rl, o);
+      df_add(rh, rl, oh, ol);
     }
-    if (lane == 0) { wkey[warp] = key; wrest[warp] = rest; }
+    if (lane == 0) { wkey[warp] = key; wrest_h[warp] = rh; wrest_l[warp] = rl; }
     __syncthreads();
-    key = 0ull;
-    rest = 0.0;
-    for (int w = 0; w < kQrWarps; ++w) {
-      key = wkey[w] > key ? wkey[w] : key;
-      rest += wrest[w];
+    if (warp == 0) {   // kQrWarps == 32: one warp's value per lane
+      key = wkey[lane];
+      rh = wrest_h[lane];
+      rl = wrest_l[lane];
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, o);
+        key = ok > key ? ok : key;
+        const float oh = __shfl_xor_sync(0xffffffffu, rh, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, rl, o);
+        df_add(rh, rl, oh, ol);
+      }
+      if (lane == 0) {
+        xs[j & 1].key = key;
+        xs[j & 1].rest_h = rh;
+        xs[j & 1].rest_l = rl;
+      }
     }
-    // every thread takes the same decisions from the same shared values
-    if (tol2 > 0.0 && rest <= tol2 * normB2) break;
-    if (key == 0ull) break;
-    const int p = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffull));
-    const float nu_p = __uint_as_float((uint32_t)(key >> 32));
-    if (!(nu_p > 0.f)) break;
-    const float rjj = sqrtf(nu_p);
+    cluster.sync();
+    if (tid == 0) {   // every rank takes the same decision from the same values
+      key = 0ull;
+      rh = 0.f;
+      rl = 0.f;
+      for (int r = 0; r < G; ++r) {
+        const QrXchg* x = cluster.map_shared_rank(&xs[j & 1], r);
+        const unsigned long long kr = x->key;
+        key = kr > key ? kr : key;
+        df_add(rh, rl, x->rest_h, x->rest_l);
+      }
+      const double rest = (double)rh + (double)rl;
+      const float nu_p = __uint_as_float((uint32_t)(key >> 32));
+      int p = (int)(0xffffffffu - (uint32_t)(key & 0xffffffffull));
+      if (tol2 > 0.0 && rest <= tol2 * normB2) p = -1;
+      if (key == 0ull || !(nu_p > 0.f)) p = -1;
+      // rank guard |R_jj| > 2 u |R_00|, u = 2^-24
+      if (p >= 0 && j > 0 && !(sqrtf(nu_p) > 0x1p-23f * r00)) p = -1;
+      dec_p = p;
+      dec_nu = nu_p;
+    }
+    __syncthreads();
+    const int p = dec_p;
+    if (p < 0) break;
+    const float rjj = sqrtf(dec_nu);
     if (j == 0) r00 = rjj;
-    else if (!(rjj > 0x1p-23f * r00)) break;   // rank guard |R_jj| > 2 u |R_00|, u = 2^-24
-    // ---- q_j = w_p / R_jj  (step 0 reads B itself)
+    // ---- q_j = w_p / R_jj  (step 0 reads B itself; w_p may come from another
+    // rank, hence the L2 loads)
     const float* src = (j == 0) ? B : W;
-    for (int i = tid; i < mc; i += kQrThreads) qv[i] = src[(int64_t)p * mc + i] / rjj;
+    for (int i = tid; i < mc; i += kQrThreads) qv[i] = __ldcg(src + (int64_t)p * mc + i) / rjj;
     if (tid == 0) {
-      J[j] = p;
+      if (rank == 0) J[j] = p;
+      if ((p / kQrWarps) % G == rank) R[(int64_t)j * n + p] = rjj;
       Js[j] = p;
-      R[(int64_t)j * n + p] = rjj;
       step[p] = j;
     }
     __syncthreads();
     // ---- modified Gram-Schmidt against q_j, norms from the updated columns
-    for (int c = warp; c < n; c += kQrWarps) {
+    for (int c = c_first; c < n; c += cstride) {
       if (step[c] != -1) continue;   // warp-uniform
       const float* x = src + (int64_t)c * mc;
       float* w = W + (int64_t)c * mc;
@@ -265,16 +371,23 @@ __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a
     __syncthreads();
     k = j + 1;
   }
+  // every rank's R columns are written; after this barrier no rank reads
+  // another's shared memory
+  cluster.sync();
   // ---- rank, pivots, coefficients
-  if (tid == 0) a.k[s] = k;
-  for (int p = k + tid; p < k_max; p += kQrThreads) J[p] = -1;
+  if (rank == 0) {
+    if (tid == 0) a.k[s] = k;
+    for (int p = k + tid; p < k_max; p += kQrThreads) J[p] = -1;
+  }
   float* R11 = qv;   // q_j is no longer needed
   for (int e = tid; e < k * k; e += kQrThreads) {
     const int i = e / k, p = e % k;
-    R11[e] = R[(int64_t)i * n + Js[p]];
+    R11[e] = __ldcg(R + (int64_t)i * n + Js[p]);
   }
   __syncthreads();
-  for (int c = tid; c < n; c += kQrThreads) {
+  for (int o = tid;; o += kQrThreads) {   // own columns
+    const int c = owned_col(o, G, rank);
+    if (c >= n) break;
     const int st = step[c];
     if (st >= 0) {
       for (int i = 0; i < k_max; ++i) C[(int64_t)i * n + c] = (i == st) ? 1.f : 0.f;
@@ -285,8 +398,9 @@ __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a
     df_back_substitute(R11, k, th, tl, rhs);
     for (int i = 0; i < k_max; ++i) C[(int64_t)i * n + c] = (i < k) ? th[i] : 0.f;
   }
-  // ---- coarse skeleton B(:, I_B)
-  for (int64_t e = tid; e < (int64_t)k_max * mc; e += kQrThreads) {
+  // ---- coarse skeleton B(:, I_B), split over the ranks
+  for (int64_t e = (int64_t)rank * kQrThreads + tid; e < (int64_t)k_max * mc;
+       e += (int64_t)G * kQrThreads) {
     const int p = (int)(e / mc), i = (int)(e % mc);
     Bsk[e] = (p < k) ? B[(int64_t)Js[p] * mc + i] : 0.f;
   }
@@ -645,14 +759,49 @@ size_t subid_qr_smem_bytes(int mc_max, int n_max, int k_max) {
   return sizeof(float) * ((size_t)qv + n_max) + sizeof(int32_t) * (size_t)n_max;
 }
 
+// Cluster size for the QR: up to 8 CTAs per subdomain while the clusters of
+// all subdomains still fit on the SMs at once, and no more CTAs than the
+// columns give warps.
+static int qr_cluster_size(int S, int n_max) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 1;
+  const int col_groups = (n_max + kQrWarps - 1) / kQrWarps;
+  int G = 8;
+  while (G > 1 && ((int64_t)G * S > sms || G > col_groups)) G /= 2;
+  return G;
+}
+
 cudaError_t launch_subid_qr(const SubArgs& a, int mc_max, int n_max, cudaStream_t st) {
   const int qv = mc_max > a.k_max * a.k_max ? mc_max : a.k_max * a.k_max;
   const size_t smem = subid_qr_smem_bytes(mc_max, n_max, a.k_max);
   cudaError_t e = cudaFuncSetAttribute(subid_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  subid_qr_kernel<<<a.S, kQrThreads, smem, st>>>(a, n_max, qv);
-  return cudaGetLastError();
+  int G = qr_cluster_size(a.S, n_max);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.S * G));
+  cfg.blockDim = dim3(kQrThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)G;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  while (G > 1) {   // a cluster shape the SMs cannot hold falls back to a smaller one
+    int fit = 0;
+    if (cudaOccupancyMaxActiveClusters(&fit, subid_qr_kernel, &cfg) == cudaSuccess && fit > 0)
+      break;
+    cudaGetLastError();
+    G /= 2;
+    cfg.gridDim = dim3((unsigned)(a.S * G));
+    attr[0].val.clusterDim.x = (unsigned)G;
+  }
+  return cudaLaunchKernelEx(&cfg, subid_qr_kernel, a, n_max, qv);
 }
 
 cudaError_t launch_coarse_recon(const SubArgs& a, int64_t max_work, cudaStream_t st) {
