@@ -33,6 +33,10 @@ namespace {
 
 constexpr int kQrThreads = 1024;
 constexpr int kQrWarps = kQrThreads / 32;
+// q_j slots: up to kQrMaxSlots - 1 MGS updates stay pending (re-applied from
+// shared memory) before the working copy W is rewritten
+constexpr int kQrMaxSlots = 4;
+constexpr int kQrSlotBudgetFloats = 24 * 1024;
 
 __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -129,6 +133,87 @@ __device__ __forceinline__ int owned_col(int o, int G, int rank) {
   return ((o / kQrWarps) * G + rank) * kQrWarps + o % kQrWarps;
 }
 
+// One column's MGS step j with the updates of steps base..base+NP-1 still
+// pending: the column is read as stored (B, or W as of step base), the pending
+// updates w -= R(t, c) q_t are re-applied on the fly -- the same fma sequence
+// as if every step had been stored, so the values are identical -- then
+// d = q_j . w, and a second pass over the column (from L1) forms
+// w - d q_j, its squared norm and, when wr, stores it as the new W.
+template <int NP>
+__device__ __forceinline__ void mgs_column(const float* x, float* w, const float* qv, int qs,
+                                           int P, int base, int j, const float* Rc, int n,
+                                           int mc, int lane, bool wr, float& d_out,
+                                           float& nu_out) {
+  float dc[NP > 0 ? NP : 1];
+  const float* qp[NP > 0 ? NP : 1];
+#pragma unroll
+  for (int t = 0; t < NP; ++t) {
+    dc[t] = -Rc[(int64_t)(base + t) * n];
+    qp[t] = qv + ((base + t) % P) * qs;
+  }
+  const float* qj = qv + (j % P) * qs;
+  float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+  int i = lane;
+  for (; i + 96 < mc; i += 128) {
+    float v0 = x[i], v1 = x[i + 32], v2 = x[i + 64], v3 = x[i + 96];
+#pragma unroll
+    for (int t = 0; t < NP; ++t) {
+      v0 = fmaf(dc[t], qp[t][i], v0);
+      v1 = fmaf(dc[t], qp[t][i + 32], v1);
+      v2 = fmaf(dc[t], qp[t][i + 64], v2);
+      v3 = fmaf(dc[t], qp[t][i + 96], v3);
+    }
+    d0 = fmaf(qj[i], v0, d0);
+    d1 = fmaf(qj[i + 32], v1, d1);
+    d2 = fmaf(qj[i + 64], v2, d2);
+    d3 = fmaf(qj[i + 96], v3, d3);
+  }
+  for (; i < mc; i += 32) {
+    float v = x[i];
+#pragma unroll
+    for (int t = 0; t < NP; ++t) v = fmaf(dc[t], qp[t][i], v);
+    d0 = fmaf(qj[i], v, d0);
+  }
+  const float d = warp_sum((d0 + d1) + (d2 + d3));
+  const float nd = -d;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  i = lane;
+  for (; i + 96 < mc; i += 128) {
+    float v0 = x[i], v1 = x[i + 32], v2 = x[i + 64], v3 = x[i + 96];
+#pragma unroll
+    for (int t = 0; t < NP; ++t) {
+      v0 = fmaf(dc[t], qp[t][i], v0);
+      v1 = fmaf(dc[t], qp[t][i + 32], v1);
+      v2 = fmaf(dc[t], qp[t][i + 64], v2);
+      v3 = fmaf(dc[t], qp[t][i + 96], v3);
+    }
+    v0 = fmaf(nd, qj[i], v0);
+    v1 = fmaf(nd, qj[i + 32], v1);
+    v2 = fmaf(nd, qj[i + 64], v2);
+    v3 = fmaf(nd, qj[i + 96], v3);
+    if (wr) {
+      w[i] = v0;
+      w[i + 32] = v1;
+      w[i + 64] = v2;
+      w[i + 96] = v3;
+    }
+    a0 = fmaf(v0, v0, a0);
+    a1 = fmaf(v1, v1, a1);
+    a2 = fmaf(v2, v2, a2);
+    a3 = fmaf(v3, v3, a3);
+  }
+  for (; i < mc; i += 32) {
+    float v = x[i];
+#pragma unroll
+    for (int t = 0; t < NP; ++t) v = fmaf(dc[t], qp[t][i], v);
+    v = fmaf(nd, qj[i], v);
+    if (wr) w[i] = v;
+    a0 = fmaf(v, v, a0);
+  }
+  d_out = d;
+  nu_out = warp_sum((a0 + a1) + (a2 + a3));
+}
+
 // What a CTA publishes to the other CTAs of its cluster (double-buffered by
 // pivot step: a slot is rewritten only after every rank has passed the
 // cluster barrier that follows its last read).
@@ -140,9 +225,9 @@ struct QrXchg {
 };
 
 __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a, int n_max,
-                                                                 int qv_floats) {
+                                                                 int qv_floats, int qs, int P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* qv = reinterpret_cast<float*>(smem_raw);          // q_j [mc], later R11 [k x k]
+  float* qv = reinterpret_cast<float*>(smem_raw);          // q_t in slot t % P (stride qs), later R11
   float* nu = qv + qv_floats;                              // residual norms^2 [n] (own columns)
   int32_t* step = reinterpret_cast<int32_t*>(nu + n_max);  // -1 active, >= 0 pivot step
   __shared__ unsigned long long wkey[kQrWarps];
@@ -250,6 +335,7 @@ __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a
   if (kcap > n) kcap = n;
   if (kcap > mc) kcap = mc;
   int k = 0;
+  int base = 0;   // W holds the columns as of step base (base 0: B itself)
   float r00 = 0.f;
   for (int j = 0; j < kcap; ++j) {
     // ---- pivot: largest residual norm^2 among active columns, lowest index on
@@ -317,10 +403,24 @@ __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a
     if (p < 0) break;
     const float rjj = sqrtf(dec_nu);
     if (j == 0) r00 = rjj;
-    // ---- q_j = w_p / R_jj  (step 0 reads B itself; w_p may come from another
-    // rank, hence the L2 loads)
-    const float* src = (j == 0) ? B : W;
-    for (int i = tid; i < mc; i += kQrThreads) qv[i] = __ldcg(src + (int64_t)p * mc + i) / rjj;
+    // ---- q_j = w_p / R_jj: w_p as stored (B until W is first written) with the
+    // pending updates re-applied; w_p may come from another rank, hence L2 loads
+    const int np = j - base;   // pending steps base..j-1, np < P
+    const float* src = (base == 0) ? B : W;
+    {
+      float rp[kQrMaxSlots];
+#pragma unroll
+      for (int t = 0; t < kQrMaxSlots; ++t)
+        rp[t] = t < np ? -__ldcg(R + (int64_t)(base + t) * n + p) : 0.f;
+      float* qj = qv + (j % P) * qs;
+      for (int i = tid; i < mc; i += kQrThreads) {
+        float v = __ldcg(src + (int64_t)p * mc + i);
+#pragma unroll
+        for (int t = 0; t < kQrMaxSlots; ++t)
+          if (t < np) v = fmaf(rp[t], qv[((base + t) % P) * qs + i], v);
+        qj[i] = v / rjj;
+      }
+    }
     if (tid == 0) {
       if (rank == 0) J[j] = p;
       if ((p / kQrWarps) % G == rank) R[(int64_t)j * n + p] = rjj;
@@ -328,46 +428,26 @@ __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a
       step[p] = j;
     }
     __syncthreads();
-    // ---- modified Gram-Schmidt against q_j, norms from the updated columns
+    // ---- modified Gram-Schmidt against q_j, norms from the updated columns;
+    // W is rewritten once P updates are pending
+    const bool wr = j + 1 - base >= P;
     for (int c = c_first; c < n; c += cstride) {
       if (step[c] != -1) continue;   // warp-uniform
       const float* x = src + (int64_t)c * mc;
       float* w = W + (int64_t)c * mc;
-      float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
-      int i = lane;
-      for (; i + 96 < mc; i += 128) {
-        d0 = fmaf(qv[i], x[i], d0);
-        d1 = fmaf(qv[i + 32], x[i + 32], d1);
-        d2 = fmaf(qv[i + 64], x[i + 64], d2);
-        d3 = fmaf(qv[i + 96], x[i + 96], d3);
+      float d = 0.f, acc = 0.f;
+      switch (np) {
+        case 0: mgs_column<0>(x, w, qv, qs, P, base, j, R + c, n, mc, lane, wr, d, acc); break;
+        case 1: mgs_column<1>(x, w, qv, qs, P, base, j, R + c, n, mc, lane, wr, d, acc); break;
+        case 2: mgs_column<2>(x, w, qv, qs, P, base, j, R + c, n, mc, lane, wr, d, acc); break;
+        default: mgs_column<3>(x, w, qv, qs, P, base, j, R + c, n, mc, lane, wr, d, acc); break;
       }
-      for (; i < mc; i += 32) d0 = fmaf(qv[i], x[i], d0);
-      const float d = warp_sum((d0 + d1) + (d2 + d3));
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-      i = lane;
-      for (; i + 96 < mc; i += 128) {
-        const float v0 = fmaf(-d, qv[i], x[i]), v1 = fmaf(-d, qv[i + 32], x[i + 32]);
-        const float v2 = fmaf(-d, qv[i + 64], x[i + 64]), v3 = fmaf(-d, qv[i + 96], x[i + 96]);
-        w[i] = v0;
-        w[i + 32] = v1;
-        w[i + 64] = v2;
-        w[i + 96] = v3;
-        a0 = fmaf(v0, v0, a0);
-        a1 = fmaf(v1, v1, a1);
-        a2 = fmaf(v2, v2, a2);
-        a3 = fmaf(v3, v3, a3);
-      }
-      for (; i < mc; i += 32) {
-        const float v = fmaf(-d, qv[i], x[i]);
-        w[i] = v;
-        a0 = fmaf(v, v, a0);
-      }
-      const float acc = warp_sum((a0 + a1) + (a2 + a3));
       if (lane == 0) {
         R[(int64_t)j * n + c] = d;
         nu[c] = acc;
       }
     }
+    if (wr) base = j + 1;
     __syncthreads();
     k = j + 1;
   }
@@ -754,9 +834,19 @@ cudaError_t launch_subsample(const SubArgs& a, const float* window, int col0, in
   return cudaGetLastError();
 }
 
+static int qr_slot_stride(int mc_max) { return (mc_max + 3) & ~3; }
+static int qr_slots(int mc_max) {
+  const int P = kQrSlotBudgetFloats / qr_slot_stride(mc_max);
+  return P < 1 ? 1 : (P > kQrMaxSlots ? kQrMaxSlots : P);
+}
+static int qr_qv_floats(int mc_max, int k_max) {
+  const int q = qr_slots(mc_max) * qr_slot_stride(mc_max);
+  return q > k_max * k_max ? q : k_max * k_max;
+}
+
 size_t subid_qr_smem_bytes(int mc_max, int n_max, int k_max) {
-  const int qv = mc_max > k_max * k_max ? mc_max : k_max * k_max;
-  return sizeof(float) * ((size_t)qv + n_max) + sizeof(int32_t) * (size_t)n_max;
+  return sizeof(float) * ((size_t)qr_qv_floats(mc_max, k_max) + n_max) +
+         sizeof(int32_t) * (size_t)n_max;
 }
 
 // Cluster size for the QR: up to 8 CTAs per subdomain while the clusters of
@@ -774,7 +864,8 @@ static int qr_cluster_size(int S, int n_max) {
 }
 
 cudaError_t launch_subid_qr(const SubArgs& a, int mc_max, int n_max, cudaStream_t st) {
-  const int qv = mc_max > a.k_max * a.k_max ? mc_max : a.k_max * a.k_max;
+  const int qv = qr_qv_floats(mc_max, a.k_max);
+  const int qs = qr_slot_stride(mc_max), P = qr_slots(mc_max);
   const size_t smem = subid_qr_smem_bytes(mc_max, n_max, a.k_max);
   cudaError_t e = cudaFuncSetAttribute(subid_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
@@ -801,7 +892,7 @@ cudaError_t launch_subid_qr(const SubArgs& a, int mc_max, int n_max, cudaStream_
     cfg.gridDim = dim3((unsigned)(a.S * G));
     attr[0].val.clusterDim.x = (unsigned)G;
   }
-  return cudaLaunchKernelEx(&cfg, subid_qr_kernel, a, n_max, qv);
+  return cudaLaunchKernelEx(&cfg, subid_qr_kernel, a, n_max, qv, qs, P);
 }
 
 cudaError_t launch_coarse_recon(const SubArgs& a, int64_t max_work, cudaStream_t st) {
