@@ -46,30 +46,57 @@ __device__ __forceinline__ float warp_sum(float v) {
 __device__ __forceinline__ int coarse_index(int a, int s, int e) { return min(a * s, e - 1); }
 
 // ---------------------------------------------------------------- subsample
+// One warp per (column j, part t): B(rows of part t, j) = A(coarse rows, j)
+// and the part's squared norm for the QR's first pivot (NaN when the part
+// holds a non-finite entry).  A column's nrm_parts parts split its m_c rows
+// evenly; the QR adds them in order.
+constexpr int kSampleColsPerBlock = 8;
+
+struct GatherPart {
+  int j, t, r0, r1;
+};
+
+__device__ __forceinline__ bool gather_part(const SubArgs& a, int s, int col0, int ncols, int mc,
+                                            GatherPart& g) {
+  const int R = a.nrm_parts;
+  const int wg = blockIdx.x * kSampleColsPerBlock + threadIdx.x / 32;
+  g.j = col0 + wg / R;
+  g.t = wg % R;
+  if (g.j >= min(col0 + ncols, a.n[s])) return false;
+  const int chunk = (mc + R - 1) / R;
+  g.r0 = min(mc, g.t * chunk);
+  g.r1 = min(mc, g.r0 + chunk);
+  return true;
+}
+
+__device__ __forceinline__ void finish_part_norm(const SubArgs& a, int s, const GatherPart& g,
+                                                 const float* acc, bool bad, int lane) {
+  const float v = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
+  const bool any_bad = __any_sync(0xffffffffu, bad);
+  if (lane == 0)
+    a.nrm[(a.coff[s] + g.j) * a.nrm_parts + g.t] = any_bad ? __int_as_float(0x7fc00000) : v;
+}
+
 __global__ void __launch_bounds__(256) subsample_kernel(const SubArgs a, const float* window,
                                                         int col0, int ncols) {
   const int s = blockIdx.y;
-  const int c1 = min(col0 + ncols, a.n[s]);
-  if (c1 <= col0) return;
-  const SubBox b = a.box[s];
   const int mc = a.mc[s];
-  const int work = mc * (c1 - col0);   // < 2^31: m_c <= 40960, n <= 1024
-  const float* A = window + a.off[s];
-  const int64_t ld = a.ld[s];
-  float* B = a.B + a.boff[s];
-  // four independent gathers in flight per thread
-  const int stride = gridDim.x * blockDim.x;
-  for (int e0 = blockIdx.x * blockDim.x + threadIdx.x; e0 < work; e0 += 4 * stride) {
+  GatherPart g;
+  if (!gather_part(a, s, col0, ncols, mc, g)) return;   // warp-uniform; no block barrier below
+  const int lane = threadIdx.x % 32;
+  const SubBox b = a.box[s];
+  const float* Aj = window + a.off[s] + (int64_t)g.j * a.ld[s];
+  float* Bj = a.B + a.boff[s] + (int64_t)g.j * mc;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  bool bad = false;
+  // four independent gathers in flight per lane
+  for (int i0 = g.r0 + lane; i0 < g.r1; i0 += 128) {
     float v[4];
-    int64_t dst[4];
 #pragma unroll
-    for (int uu = 0; uu < 4; ++uu) {
-      const int e = e0 + uu * stride;
-      dst[uu] = -1;
-      if (e < work) {
-        const int jj = (int)fdiv((uint32_t)e, b.div_mc);
-        const int j = col0 + jj;
-        const int cr = e - jj * mc;
+    for (int u = 0; u < 4; ++u) {
+      const int cr = i0 + 32 * u;
+      v[u] = 0.f;
+      if (cr < g.r1) {
         const int t1 = (int)fdiv((uint32_t)cr, b.div_cx);
         const int cx = cr - t1 * b.cx;
         const int t2 = (int)fdiv((uint32_t)t1, b.div_cy);
@@ -78,14 +105,20 @@ __global__ void __launch_bounds__(256) subsample_kernel(const SubArgs a, const f
         const int cz = t2 - q * b.cz;
         const int64_t r = (((int64_t)q * b.ez + coarse_index(cz, b.sz, b.ez)) * b.ey +
                            coarse_index(cy, b.sy, b.ey)) * b.ex + coarse_index(cx, b.sx, b.ex);
-        v[uu] = __ldg(A + (int64_t)j * ld + r);
-        dst[uu] = (int64_t)j * mc + cr;
+        v[u] = __ldg(Aj + r);
       }
     }
 #pragma unroll
-    for (int uu = 0; uu < 4; ++uu)
-      if (dst[uu] >= 0) B[dst[uu]] = v[uu];
+    for (int u = 0; u < 4; ++u) {
+      const int cr = i0 + 32 * u;
+      if (cr < g.r1) {
+        Bj[cr] = v[u];
+        acc[u] = fmaf(v[u], v[u], acc[u]);
+        bad |= !isfinite(v[u]);
+      }
+    }
   }
+  finish_part_norm(a, s, g, acc, bad, lane);
 }
 
 // ---------------------------------------------------------------- pivoted MGS QR
@@ -255,33 +288,24 @@ __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a
   int32_t* J = a.J + (int64_t)s * k_max;
 
   // own columns of R start at zero; every rank tracks the pivot steps of all
-  for (int64_t e = tid; e < (int64_t)k_max * n; e += kQrThreads) {
-    const int i = (int)(e / n), c = (int)(e % n);
-    if ((c / kQrWarps) % G == rank) R[(int64_t)i * n + c] = 0.f;
+  for (int o = tid;; o += kQrThreads) {
+    const int c = owned_col(o, G, rank);
+    if (c >= n) break;
+    for (int i = 0; i < k_max; ++i) R[(int64_t)i * n + c] = 0.f;
   }
   for (int c = tid; c < n; c += kQrThreads) step[c] = -1;
-  // initial column norms (B stays untouched: step 0 reads it and writes the
-  // working copy W); non-finite check
+  // initial column norms, from the gather (NaN: a non-finite entry); B stays
+  // untouched, W is written only once updates are due
   bool bad = false;
   for (int c = c_first; c < n; c += cstride) {
-    const float* col = B + (int64_t)c * mc;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    int i = lane;
-    for (; i + 96 < mc; i += 128) {
-      const float x0 = col[i], x1 = col[i + 32], x2 = col[i + 64], x3 = col[i + 96];
-      a0 = fmaf(x0, x0, a0);
-      a1 = fmaf(x1, x1, a1);
-      a2 = fmaf(x2, x2, a2);
-      a3 = fmaf(x3, x3, a3);
-      bad |= !isfinite(x0) || !isfinite(x1) || !isfinite(x2) || !isfinite(x3);
+    const float* parts = a.nrm + (a.coff[s] + c) * a.nrm_parts;
+    float v = 0.f;
+    for (int t = lane; t < a.nrm_parts; t += 32) v += parts[t];
+    v = warp_sum(v);
+    if (lane == 0) {
+      bad |= isnan(v);
+      nu[c] = v;
     }
-    for (; i < mc; i += 32) {
-      const float x = col[i];
-      a0 = fmaf(x, x, a0);
-      bad |= !isfinite(x);
-    }
-    const float acc = warp_sum((a0 + a1) + (a2 + a3));
-    if (lane == 0) nu[c] = acc;
   }
   // own part of ||B||_F^2 (FP64, fixed order), non-finite flag; exchanged
   {
@@ -706,11 +730,20 @@ __global__ void __launch_bounds__(256, 3) spid_interp_kernel(const SubErrArgs ar
 // subdomain's block) is the trilinear interpolation of each coarse skeleton
 // column to the fine grid.  The error pass is then the rank-k product F C_B
 // against A -- the same HBM-rate kernel as the column ID's error pass.
-__global__ void __launch_bounds__(256) fine_skeleton_kernel(const SubArgs a, float* F,
-                                                            const int64_t* foff) {
+__global__ void __launch_bounds__(256, 4) fine_skeleton_kernel(const SubArgs a, float* F,
+                                                               const int64_t* foff, int e_max) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int32_t* tab_a = reinterpret_cast<int32_t*>(smem_raw);   // [3][e_max] cell per z, y, x
+  float* tab_w = reinterpret_cast<float*>(tab_a + 3 * e_max);   // [3][e_max] weight
   const int s = blockIdx.y;
   const SubBox b = a.box[s];
   const int m = a.m[s], mc = a.mc[s], k = a.k[s];
+  for (int x = threadIdx.x; x < b.ez; x += blockDim.x) axis_cell(x, b.ez, b.sz, b.cz, tab_a[x], tab_w[x]);
+  for (int x = threadIdx.x; x < b.ey; x += blockDim.x)
+    axis_cell(x, b.ey, b.sy, b.cy, tab_a[e_max + x], tab_w[e_max + x]);
+  for (int x = threadIdx.x; x < b.ex; x += blockDim.x)
+    axis_cell(x, b.ex, b.sx, b.cx, tab_a[2 * e_max + x], tab_w[2 * e_max + x]);
+  __syncthreads();
   const float* Bsk = a.Bskel + (int64_t)a.k_max * a.sklo[s];
   float* Fs = F + foff[s];
   const int plane = b.ey * b.ex;
@@ -719,15 +752,13 @@ __global__ void __launch_bounds__(256) fine_skeleton_kernel(const SubArgs a, flo
     const int qz = (int)fdiv((uint32_t)r, b.div_plane), yx = r - qz * plane;
     const int q = qz / b.ez, z = qz - q * b.ez;
     const int y = (int)fdiv((uint32_t)yx, b.div_ex), x = yx - y * b.ex;
-    int az, ay, ax;
-    float wz, wy, wx;
-    axis_cell(z, b.ez, b.sz, b.cz, az, wz);
-    axis_cell(y, b.ey, b.sy, b.cy, ay, wy);
-    axis_cell(x, b.ex, b.sx, b.cx, ax, wx);
+    const int az = tab_a[z], ay = tab_a[e_max + y], ax = tab_a[2 * e_max + x];
+    const float wz = tab_w[z], wy = tab_w[e_max + y], wx = tab_w[2 * e_max + x];
     const int az1 = min(az + 1, b.cz - 1), ay1 = min(ay + 1, b.cy - 1), ax1 = min(ax + 1, b.cx - 1);
     const int base = q * b.cz * cplane;
     const int i00 = base + az * cplane + ay * b.cx, i01 = base + az * cplane + ay1 * b.cx;
     const int i10 = base + az1 * cplane + ay * b.cx, i11 = base + az1 * cplane + ay1 * b.cx;
+#pragma unroll 1
     for (int p = 0; p < k; ++p) {
       const float* c = Bsk + (int64_t)p * mc;
       const float v00 = fmaf(wx, c[i00 + ax1] - c[i00 + ax], c[i00 + ax]);
@@ -751,19 +782,33 @@ __global__ void __launch_bounds__(256) subsample_rows_kernel(const SubArgs a, co
                                                              const int32_t* crow,
                                                              const int64_t* crow_off) {
   const int s = blockIdx.y;
-  const int mc = a.mc[s], n = a.n[s];
-  const int nc = min(ncols, n - col0);
-  if (nc <= 0) return;
+  const int mc = a.mc[s];
+  GatherPart g;
+  if (!gather_part(a, s, col0, ncols, mc, g)) return;   // warp-uniform; no block barrier below
+  const int lane = threadIdx.x % 32;
   const int32_t* rows = crow + crow_off[s];
-  const float* A = window + a.off[s];
-  const int64_t ld = a.ld[s];
-  float* B = a.B + a.boff[s];
-  const int64_t work = (int64_t)mc * nc;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < work;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int j = (int)(e / mc), i = (int)(e - (int64_t)j * mc);
-    B[(int64_t)(col0 + j) * mc + i] = __ldg(A + (int64_t)(col0 + j) * ld + rows[i]);
+  const float* Aj = window + a.off[s] + (int64_t)g.j * a.ld[s];
+  float* Bj = a.B + a.boff[s] + (int64_t)g.j * mc;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  bool bad = false;
+  for (int i0 = g.r0 + lane; i0 < g.r1; i0 += 128) {
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + 32 * u;
+      v[u] = i < g.r1 ? __ldg(Aj + rows[i]) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + 32 * u;
+      if (i < g.r1) {
+        Bj[i] = v[u];
+        acc[u] = fmaf(v[u], v[u], acc[u]);
+        bad |= !isfinite(v[u]);
+      }
+    }
   }
+  finish_part_norm(a, s, g, acc, bad, lane);
 }
 
 // F_s(r, p) = sum_q w_s(r, q) B(:, I_B)(idx_s(r, q), p), p < k_s.
@@ -830,7 +875,9 @@ int grid_for(int64_t work) {
 cudaError_t launch_subsample(const SubArgs& a, const float* window, int col0, int ncols,
                              int64_t max_work, cudaStream_t st) {
   if (max_work <= 0) return cudaSuccess;
-  subsample_kernel<<<dim3(grid_for(max_work), a.S), 256, 0, st>>>(a, window, col0, ncols);
+  const unsigned gx =
+      (unsigned)(((int64_t)ncols * a.nrm_parts + kSampleColsPerBlock - 1) / kSampleColsPerBlock);
+  subsample_kernel<<<dim3(gx, a.S), 32 * kSampleColsPerBlock, 0, st>>>(a, window, col0, ncols);
   return cudaGetLastError();
 }
 
@@ -934,9 +981,15 @@ cudaError_t launch_spid_interp(const SubErrArgs& a, int64_t units, int mc_max, i
 }
 
 cudaError_t launch_fine_skeleton(const SubArgs& a, float* F, const int64_t* foff, int m_max,
-                                 cudaStream_t st) {
+                                 int e_max, cudaStream_t st) {
   if (m_max <= 0) return cudaSuccess;
-  fine_skeleton_kernel<<<dim3(grid_for(m_max), a.S), 256, 0, st>>>(a, F, foff);
+  const size_t smem = (sizeof(int32_t) + sizeof(float)) * 3 * (size_t)e_max;
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        fine_skeleton_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  fine_skeleton_kernel<<<dim3(grid_for(m_max), a.S), 256, smem, st>>>(a, F, foff, e_max);
   return cudaGetLastError();
 }
 
@@ -944,8 +997,10 @@ cudaError_t launch_subsample_rows(const SubArgs& a, const float* window, int col
                                   const int32_t* crow, const int64_t* crow_off, int64_t max_work,
                                   cudaStream_t st) {
   if (max_work <= 0) return cudaSuccess;
-  subsample_rows_kernel<<<dim3(grid_for(max_work), a.S), 256, 0, st>>>(a, window, col0, ncols,
-                                                                       crow, crow_off);
+  const unsigned gx =
+      (unsigned)(((int64_t)ncols * a.nrm_parts + kSampleColsPerBlock - 1) / kSampleColsPerBlock);
+  subsample_rows_kernel<<<dim3(gx, a.S), 32 * kSampleColsPerBlock, 0, st>>>(a, window, col0, ncols,
+                                                                           crow, crow_off);
   return cudaGetLastError();
 }
 

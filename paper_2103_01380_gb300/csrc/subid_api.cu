@@ -49,6 +49,8 @@ struct spid_sub_plan_s {
   int64_t *d_off = nullptr, *d_ld = nullptr, *d_boff = nullptr, *d_coff = nullptr,
           *d_sklo = nullptr, *d_ccoff = nullptr;   // d_ccoff = k_max * coff (C in elements)
   float *d_B = nullptr, *d_W = nullptr, *d_R = nullptr, *d_C = nullptr, *d_Bsk = nullptr;
+  float* d_nrm = nullptr;       // squared column norms of B in nrm_parts parts, from the gather
+  int nrm_parts = 1;
   float* d_F = nullptr;         // fine skeleton M B(:, I_B)
   int64_t* d_foff = nullptr;
   int32_t *d_J = nullptr, *d_k = nullptr;
@@ -83,6 +85,8 @@ struct spid_sub_plan_s {
     a.coff = d_coff;
     a.sklo = d_sklo;
     a.B = d_B;
+    a.nrm = d_nrm;
+    a.nrm_parts = nrm_parts;
     a.W = d_W;
     a.R = d_R;
     a.C = d_C;
@@ -184,6 +188,14 @@ spid_status finish_plan(spid_sub_plan_s* P, spid_sub_plan_t* out) {
                         std::string("cudaMalloc: ") + cudaGetErrorString(e_)));            \
   } while (0)
   const size_t S = (size_t)P->S;
+  // the gather splits each column over nrm_parts warps when the window has
+  // too few columns to fill the GPU (parts of >= 128 coarse rows)
+  {
+    const int64_t cols = (int64_t)P->S * P->n_max;
+    int64_t parts = cols >= kGatherWarps ? 1 : (kGatherWarps + cols - 1) / cols;
+    parts = std::min<int64_t>(parts, std::max<int64_t>(1, (P->mc_max + 127) / 128));
+    P->nrm_parts = (int)parts;
+  }
   SUB_ALLOC(P->d_box, sizeof(SubBox) * S);
   SUB_ALLOC(P->d_m, sizeof(int32_t) * S);
   SUB_ALLOC(P->d_n, sizeof(int32_t) * S);
@@ -195,6 +207,7 @@ spid_status finish_plan(spid_sub_plan_s* P, spid_sub_plan_t* out) {
   SUB_ALLOC(P->d_sklo, sizeof(int64_t) * S);
   SUB_ALLOC(P->d_ccoff, sizeof(int64_t) * S);
   SUB_ALLOC(P->d_B, sizeof(float) * P->b_elems);
+  SUB_ALLOC(P->d_nrm, sizeof(float) * (P->c_elems / P->k_max) * P->nrm_parts);
   SUB_ALLOC(P->d_W, sizeof(float) * P->b_elems);
   SUB_ALLOC(P->d_R, sizeof(float) * P->c_elems);
   SUB_ALLOC(P->d_C, sizeof(float) * P->c_elems);
@@ -258,6 +271,7 @@ spid_status finish_plan(spid_sub_plan_s* P, spid_sub_plan_t* out) {
         return bail(sfail(SPID_ERR_CUDA, "cudaMemcpy failed"));
   }
   if (cudaMemset(P->d_B, 0, sizeof(float) * P->b_elems) != cudaSuccess ||
+      cudaMemset(P->d_nrm, 0, sizeof(float) * (P->c_elems / P->k_max) * P->nrm_parts) != cudaSuccess ||
       cudaMemset(P->d_k, 0, sizeof(int32_t) * S) != cudaSuccess ||
       cudaMemset(P->d_status, 0, sizeof(int)) != cudaSuccess ||
       cudaMemset(P->d_cnt, 0, sizeof(int) * (S + 1)) != cudaSuccess ||
@@ -528,7 +542,7 @@ static spid_status run_sub_error(spid_sub_plan_t P, const float* window, int32_t
         return SPID_OK;
       }
     } else if (window) {
-      SUB_CUDA(launch_fine_skeleton(P->args(), P->d_F, P->d_foff, P->m_max, cs));
+      SUB_CUDA(launch_fine_skeleton(P->args(), P->d_F, P->d_foff, P->m_max, P->e_max, cs));
     }
     if (window) {
       // F = M B(:, I_B) once, then the rank-k error pass F C_B against A

@@ -10,6 +10,7 @@
 
 namespace spid {
 
+constexpr int kGatherWarps = 8192;     // warps the coarse gather aims for
 constexpr int kSubMaxK = 64;          // k_max bound (coefficient solve keeps k values per column)
 constexpr int kSubMaxN = 1024;        // window length bound (one residual norm per column in smem)
 constexpr int kSubMaxCoarse = 40960;  // coarse rows bound (one column of B in shared memory)
@@ -59,6 +60,9 @@ struct SubArgs {
   const int64_t* coff;        // [S] sum of n before s (R, C at k_max * coff[s])
   const int64_t* sklo;        // [S] sum of mc before s (Bskel at k_max * sklo[s])
   float* B;                   // gathered coarse matrices
+  float* nrm;                 // [sum n][nrm_parts] parts of ||B(:, c)||^2 from the gather
+                              // (NaN: a non-finite entry in that part)
+  int32_t nrm_parts;
   float* W;                   // MGS working copy; after finalize, the coarse reconstruction
   float* R;                   // k_max x n_s row-major per subdomain
   float* C;                   // k_max x n_s row-major per subdomain
@@ -91,7 +95,7 @@ cudaError_t launch_spid_interp(const SubErrArgs& a, int64_t units, int mc_max, i
 // F = M B(:, I_B): the trilinear interpolation of every coarse skeleton column
 // to the fine grid, m_s x k_s column-major at foff[s] (leading dimension m_s).
 cudaError_t launch_fine_skeleton(const SubArgs& a, float* F, const int64_t* foff, int m_max,
-                                 cudaStream_t st);
+                                 int e_max, cudaStream_t st);
 
 // Point-set plans: B = A(crow, :); F = M B(:, I_B) with a t-wide stencil
 // (iidx, iw: m_s x t per subdomain at ioff[s]); out = F C (no window).

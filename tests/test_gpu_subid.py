@@ -168,6 +168,17 @@ def test_nonfinite_coarse_matrix_is_reported():
     assert g["k"][0] == 0 and g["k"][1] > 0
 
 
+def test_nonfinite_in_a_later_gather_part_is_reported():
+    # two boxes x 10 snapshots are too few columns to fill the GPU, so the gather
+    # splits each 12^3-row coarse column into parts; the inf sits in the last one
+    boxes = [(1, 24, 24, 24), (1, 24, 24, 24)]
+    win = inputs.box_window(boxes, 10, seed=53)
+    win.block(1)[(22 * 24 + 22) * 24 + 22, 7] = np.inf   # coarse point (11, 11, 11)
+    g = run_sub(win, (2, 2, 2), 3, reconstruct=False)
+    assert g["status"] == 6
+    assert g["k"][1] == 0 and g["k"][0] > 0
+
+
 def test_sample_then_repeat_is_bit_identical():
     boxes = [(5, 16, 16, 16)] * 4
     win = inputs.box_window(boxes, 128, seed=61, noise=1e-4)
