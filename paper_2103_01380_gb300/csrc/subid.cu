@@ -812,7 +812,10 @@ __global__ void __launch_bounds__(256) subsample_rows_kernel(const SubArgs a, co
 }
 
 // F_s(r, p) = sum_q w_s(r, q) B(:, I_B)(idx_s(r, q), p), p < k_s.
-__global__ void __launch_bounds__(256) fine_skeleton_points_kernel(
+// TW > 0: the stencil width as a compile-time constant (the row's stencil in
+// registers); TW == 0: any width t <= 16, read per skeleton column.
+template <int TW>
+__global__ void __launch_bounds__(256, 4) fine_skeleton_points_kernel(
     const SubArgs a, float* F, const int64_t* foff, const int32_t* iidx, const float* iw,
     const int64_t* ioff, int t) {
   const int s = blockIdx.y;
@@ -822,11 +825,29 @@ __global__ void __launch_bounds__(256) fine_skeleton_points_kernel(
   const float* w = iw + ioff[s];
   float* Fs = F + foff[s];
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
-    for (int p = 0; p < k; ++p) {
-      const float* c = Bsk + (int64_t)p * mc;
-      float v = 0.f;
-      for (int q = 0; q < t; ++q) v = fmaf(w[(int64_t)r * t + q], c[idx[(int64_t)r * t + q]], v);
-      Fs[(int64_t)p * m + r] = v;
+    if (TW > 0) {
+      int32_t ri[TW > 0 ? TW : 1];
+      float rw[TW > 0 ? TW : 1];
+#pragma unroll
+      for (int q = 0; q < TW; ++q) {
+        ri[q] = idx[(int64_t)r * TW + q];
+        rw[q] = w[(int64_t)r * TW + q];
+      }
+#pragma unroll 1
+      for (int p = 0; p < k; ++p) {
+        const float* c = Bsk + (int64_t)p * mc;
+        float v = 0.f;
+#pragma unroll
+        for (int q = 0; q < TW; ++q) v = fmaf(rw[q], c[ri[q]], v);
+        Fs[(int64_t)p * m + r] = v;
+      }
+    } else {
+      for (int p = 0; p < k; ++p) {
+        const float* c = Bsk + (int64_t)p * mc;
+        float v = 0.f;
+        for (int q = 0; q < t; ++q) v = fmaf(w[(int64_t)r * t + q], c[idx[(int64_t)r * t + q]], v);
+        Fs[(int64_t)p * m + r] = v;
+      }
     }
   }
 }
@@ -980,6 +1001,17 @@ cudaError_t launch_spid_interp(const SubErrArgs& a, int64_t units, int mc_max, i
   return cudaGetLastError();
 }
 
+// CTAs per subdomain for the fine-skeleton kernels: about two resident waves in
+// all (four 256-thread CTAs per SM), each thread taking several rows (the box
+// kernel builds its per-axis tables once per CTA)
+static int fine_skeleton_blocks(int S, int m_max) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 1;
+  return std::max(1, std::min(grid_for(m_max), (8 * sms + S - 1) / S));
+}
+
 cudaError_t launch_fine_skeleton(const SubArgs& a, float* F, const int64_t* foff, int m_max,
                                  int e_max, cudaStream_t st) {
   if (m_max <= 0) return cudaSuccess;
@@ -989,7 +1021,8 @@ cudaError_t launch_fine_skeleton(const SubArgs& a, float* F, const int64_t* foff
         fine_skeleton_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  fine_skeleton_kernel<<<dim3(grid_for(m_max), a.S), 256, smem, st>>>(a, F, foff, e_max);
+  fine_skeleton_kernel<<<dim3(fine_skeleton_blocks(a.S, m_max), a.S), 256, smem, st>>>(
+      a, F, foff, e_max);
   return cudaGetLastError();
 }
 
@@ -1008,8 +1041,13 @@ cudaError_t launch_fine_skeleton_points(const SubArgs& a, float* F, const int64_
                                         const int32_t* iidx, const float* iw, const int64_t* ioff,
                                         int t, int m_max, cudaStream_t st) {
   if (m_max <= 0) return cudaSuccess;
-  fine_skeleton_points_kernel<<<dim3(grid_for(m_max), a.S), 256, 0, st>>>(a, F, foff, iidx, iw,
-                                                                          ioff, t);
+  const dim3 grid(fine_skeleton_blocks(a.S, m_max), a.S);
+  if (t == 3)
+    fine_skeleton_points_kernel<3><<<grid, 256, 0, st>>>(a, F, foff, iidx, iw, ioff, t);
+  else if (t == 4)
+    fine_skeleton_points_kernel<4><<<grid, 256, 0, st>>>(a, F, foff, iidx, iw, ioff, t);
+  else
+    fine_skeleton_points_kernel<0><<<grid, 256, 0, st>>>(a, F, foff, iidx, iw, ioff, t);
   return cudaGetLastError();
 }
 
