@@ -267,6 +267,23 @@ spid_status spid_graph_create(spid_plan_t plan, const void* window, int32_t col0
 /* Replay the captured step on `stream` (asynchronous). */
 spid_status spid_graph_launch(spid_graph_t graph, spid_stream_t stream);
 
+/* One end-to-end step from host memory.  Enqueues, in this order: on
+ * copy_stream, once the previous launch of this graph has finished with its
+ * window, the copy of the window -- the plan's extent, max_s off_s + ld_s
+ * (n_s - 1) + m_s elements -- from window_host to the device window the graph
+ * was created on; on `stream`, once that copy has landed, the graph; then, on
+ * `stream`, the copy of the graph's four error sums (total_dev) to total_host
+ * (may be NULL).  All asynchronous: synchronize `stream` before reading
+ * total_host.  window_host should be page-locked for the copy to run at the
+ * link's rate; copy_stream may be the same stream (no overlap).  Two graphs
+ * on two device windows, launched alternately, overlap one step's copy with
+ * the other's compute (the plan's workspace is shared: launch both on the
+ * same `stream`).  SPID_ERR_INVALID_ARG for a NULL graph or window_host, a
+ * graph without a window, or total_host without the graph's total_dev. */
+spid_status spid_graph_launch_host(spid_graph_t graph, const void* window_host,
+                                   double* total_host, spid_stream_t copy_stream,
+                                   spid_stream_t stream);
+
 /* Release the graph (synchronizes the device first). */
 spid_status spid_graph_destroy(spid_graph_t graph);
 

@@ -1383,6 +1383,13 @@ struct spid_graph_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   void* d_tmaps = nullptr;
+  // host-window launches: the device window, its extent, the error sums and
+  // the events that order the copy against this graph's previous launch
+  void* window = nullptr;
+  size_t window_bytes = 0;
+  double* total_dev = nullptr;
+  cudaEvent_t ev_uploaded = nullptr, ev_done = nullptr;
+  bool launched = false;
 };
 
 extern "C" spid_status spid_graph_destroy(spid_graph_t G) {
@@ -1392,6 +1399,8 @@ extern "C" spid_status spid_graph_destroy(spid_graph_t G) {
   if (G->exec) cudaGraphExecDestroy(G->exec);
   if (G->graph) cudaGraphDestroy(G->graph);
   if (G->d_tmaps) cudaFree(G->d_tmaps);
+  if (G->ev_uploaded) cudaEventDestroy(G->ev_uploaded);
+  if (G->ev_done) cudaEventDestroy(G->ev_done);
   if (G->plan) G->plan->live_graphs--;
   delete G;
   return SPID_OK;
@@ -1464,7 +1473,48 @@ extern "C" spid_status spid_graph_create(spid_plan_t P, const void* window, int3
   e = cudaGraphInstantiate(&G->exec, G->graph, 0);
   if (e != cudaSuccess)
     return bail(fail(SPID_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e)));
+  if (sketch || error) {
+    int64_t extent = 0;
+    for (int s = 0; s < P->S; ++s)
+      extent = std::max<int64_t>(extent, P->off[s] + P->ld[s] * (P->n[s] - 1) + P->m[s]);
+    G->window = const_cast<void*>(window);
+    G->window_bytes = (size_t)extent * P->esz;
+  }
+  G->total_dev = total_dev;
+  e = cudaEventCreateWithFlags(&G->ev_uploaded, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->ev_done, cudaEventDisableTiming);
+  if (e != cudaSuccess)
+    return bail(fail(SPID_ERR_CUDA, std::string("graph events: ") + cudaGetErrorString(e)));
   *out = G;
+  return SPID_OK;
+}
+
+extern "C" spid_status spid_graph_launch_host(spid_graph_t G, const void* window_host,
+                                              double* total_host, spid_stream_t copy_stream,
+                                              spid_stream_t stream) {
+  if (!G || !G->exec) return fail(SPID_ERR_INVALID_ARG, "graph is NULL");
+  if (!window_host) return fail(SPID_ERR_INVALID_ARG, "window_host is NULL");
+  if (!G->window) return fail(SPID_ERR_INVALID_ARG, "graph has no window (finalize only)");
+  if (total_host && !G->total_dev)
+    return fail(SPID_ERR_INVALID_ARG, "total_host given but the graph has no total_dev");
+  spid_status st = check_plan(G->plan);
+  if (st != SPID_OK) return st;
+  cudaStream_t cps = (cudaStream_t)copy_stream, cs = (cudaStream_t)stream;
+  const bool split = cps != cs;
+  if (split && G->launched) SPID_CUDA(cudaStreamWaitEvent(cps, G->ev_done, 0));
+  SPID_CUDA(cudaMemcpyAsync(G->window, window_host, G->window_bytes, cudaMemcpyHostToDevice, cps));
+  if (split) {
+    SPID_CUDA(cudaEventRecord(G->ev_uploaded, cps));
+    SPID_CUDA(cudaStreamWaitEvent(cs, G->ev_uploaded, 0));
+  }
+  SPID_CUDA(cudaGraphLaunch(G->exec, cs));
+  if (split) {
+    SPID_CUDA(cudaEventRecord(G->ev_done, cs));
+    G->launched = true;
+  }
+  if (total_host)
+    SPID_CUDA(cudaMemcpyAsync(total_host, G->total_dev, 4 * sizeof(double),
+                              cudaMemcpyDeviceToHost, cs));
   return SPID_OK;
 }
 

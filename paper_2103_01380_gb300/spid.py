@@ -38,7 +38,8 @@ EXPORTS = ["spid_plan_create", "spid_plan_destroy", "spid_plan_info", "spid_sket
            "spid_ts_error", "spid_ts_reconstruct", "spid_ts_get_factors",
            "spid_ts_get_block_factors", "spid_ts_device_status",
            "spid_plan_get_tuning", "spid_plan_set_tuning", "spid_plan_autotune",
-           "spid_plan_tuning_key", "spid_graph_create", "spid_graph_launch", "spid_graph_destroy",
+           "spid_plan_tuning_key", "spid_graph_create", "spid_graph_launch", "spid_graph_launch_host",
+           "spid_graph_destroy",
            "spid_sub_plan_create_points", "spid_producer_step"]
 GRAPH_SKETCH = 1
 GRAPH_FINALIZE = 2
@@ -182,6 +183,7 @@ def load_library(path: str = LIB_PATH):
             "spid_plan_tuning_key": ([vp, c.c_char_p, i32], c.c_int),
             "spid_graph_create": ([vp, vp, i32, i32, i32, u32, vp, vp, c.POINTER(vp)], c.c_int),
             "spid_graph_launch": ([vp, vp], c.c_int),
+            "spid_graph_launch_host": ([vp, vp, vp, vp, vp], c.c_int),
             "spid_graph_destroy": ([vp], c.c_int),
             "spid_sub_plan_create_points": ([c.POINTER(_SubPointsDesc), c.POINTER(vp)], c.c_int),
             "spid_producer_step": ([vp, i64, vp, i64, i32, i32, i32, c.c_float, c.c_float, vp],
@@ -218,6 +220,29 @@ def _ptr(t) -> int:
             raise ValueError("expected a CUDA tensor")
         return t.data_ptr()
     return int(t)
+
+
+def _host_ptr(t, dtype, min_bytes: int) -> int:
+    """Address of a host buffer (CPU torch tensor or numpy array) holding at
+    least min_bytes, contiguous, of dtype (None: any)."""
+    if hasattr(t, "data_ptr"):
+        if t.is_cuda:
+            raise ValueError("expected a host (CPU) tensor")
+        if not t.is_contiguous():
+            raise ValueError("host tensor must be contiguous")
+        if dtype is not None and t.element_size() != np.dtype(dtype).itemsize:
+            raise ValueError(f"host tensor must hold {np.dtype(dtype).name}")
+        nbytes, addr = t.numel() * t.element_size(), t.data_ptr()
+    else:
+        a = np.asarray(t)
+        if not a.flags.c_contiguous:
+            raise ValueError("host array must be contiguous")
+        if dtype is not None and a.dtype != np.dtype(dtype):
+            raise ValueError(f"host array must hold {np.dtype(dtype).name}")
+        nbytes, addr = a.nbytes, a.ctypes.data
+    if nbytes < min_bytes:
+        raise ValueError(f"host buffer holds {nbytes} bytes, needs {min_bytes}")
+    return addr
 
 
 def producer_step(state_in, state_out, grid: int, edge: int, nq: int, dt: float, nu: float,
@@ -405,6 +430,18 @@ class Graph:
     def launch(self, stream=None):
         _check(load_library().spid_graph_launch(self._h, _stream_handle(stream)),
                "spid_graph_launch")
+
+    def launch_host(self, window_host, total_host=None, copy_stream=None, stream=None):
+        """spid_graph_launch_host: copy the window from host memory (a pinned
+        CPU tensor or array), run the step, copy the four error sums to
+        total_host (a pinned CPU float64 tensor of 4, or None); asynchronous."""
+        p = self._plan
+        extent = int(np.max(p.off + p.ld * (p.n.astype(np.int64) - 1) + p.m))
+        win = _host_ptr(window_host, p.dtype, extent * np.dtype(p.dtype).itemsize)
+        tot = None if total_host is None else _host_ptr(total_host, np.float64, 32)
+        _check(load_library().spid_graph_launch_host(
+            self._h, win, tot, _stream_handle(copy_stream), _stream_handle(stream)),
+            "spid_graph_launch_host")
 
     def close(self):
         if getattr(self, "_h", None):

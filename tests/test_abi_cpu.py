@@ -58,6 +58,7 @@ def test_invalid_descriptors_are_rejected_without_a_gpu(lib, kw):
 
 
 def test_null_plan_is_rejected(lib):
+    assert lib.spid_graph_launch_host(None, None, None, None, None) == 1
     assert lib.spid_finalize(None, None) == 1
     assert lib.spid_sketch(None, None, 0, 1, None) == 1
 

@@ -117,6 +117,47 @@ def test_graph_microbatches_and_own_tensor_maps():
     plan.close()
 
 
+def test_graph_launch_host_matches_device_window():
+    # two graphs on two device windows, fed from one pinned host window on a
+    # copy stream, alternate as a pipelined end-to-end run would
+    win = _window(seed=70)
+    w = torch.from_numpy(win.data).cuda()
+    plan = spid.Plan.for_window(win, k_max=5, p=8, precision="tf32", seed=11)
+    err = torch.zeros(2 * win.num_sub, dtype=torch.float64, device="cuda")
+    tot = torch.zeros(4, dtype=torch.float64, device="cuda")
+    plan.sketch(w); plan.finalize(); plan.error(w, err, tot)
+    eager = _state(plan, err, tot)
+    host = torch.from_numpy(win.data).pin_memory()
+    wd = [torch.full_like(w, float("nan")) for _ in range(2)]
+    gs = [plan.graph(x, err=err, total=tot) for x in wd]
+    copy_stream = torch.cuda.Stream()
+    tot_h = [torch.zeros(4, dtype=torch.float64).pin_memory() for _ in range(4)]
+    plan.reset()
+    for i in range(4):
+        gs[i % 2].launch_host(host, tot_h[i], copy_stream=copy_stream)
+    torch.cuda.synchronize()
+    for t in tot_h:
+        assert np.array_equal(t.numpy(), eager["tot"])
+    _same(eager, _state(plan, err, tot))
+    # one stream for both (no overlap), no host totals
+    plan.reset()
+    gs[0].launch_host(host)
+    _same(eager, _state(plan, err, tot))
+    # a host buffer shorter than the window extent, a device tensor, a graph
+    # without a window
+    with pytest.raises(ValueError):
+        gs[0].launch_host(host[:100])
+    with pytest.raises(ValueError):
+        gs[0].launch_host(w)
+    gf = plan.graph(None, what=spid.GRAPH_FINALIZE)
+    with pytest.raises(spid.SpidError) as ei:
+        gf.launch_host(host)
+    assert ei.value.status == 1
+    for g in gs + [gf]:
+        g.close()
+    plan.close()
+
+
 def test_set_tuning_rejects_out_of_range_values():
     win = _window(seed=70, m=(100,), n=(50,))
     plan = spid.Plan.for_window(win, k_max=5, p=8, precision="fp32", seed=1)
