@@ -177,6 +177,7 @@ __device__ __forceinline__ void mgs_column(const float* x, float* w, const float
                                            int P, int base, int j, const float* Rc, int n,
                                            int mc, int lane, bool wr, float& d_out,
                                            float& nu_out) {
+  constexpr int U = 8;   // loads in flight per lane
   float dc[NP > 0 ? NP : 1];
   const float* qp[NP > 0 ? NP : 1];
 #pragma unroll
@@ -185,55 +186,43 @@ __device__ __forceinline__ void mgs_column(const float* x, float* w, const float
     qp[t] = qv + ((base + t) % P) * qs;
   }
   const float* qj = qv + (j % P) * qs;
-  float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+  float dd[4] = {0.f, 0.f, 0.f, 0.f};
   int i = lane;
-  for (; i + 96 < mc; i += 128) {
-    float v0 = x[i], v1 = x[i + 32], v2 = x[i + 64], v3 = x[i + 96];
+  for (; i + 32 * (U - 1) < mc; i += 32 * U) {
+    float v[U];
 #pragma unroll
-    for (int t = 0; t < NP; ++t) {
-      v0 = fmaf(dc[t], qp[t][i], v0);
-      v1 = fmaf(dc[t], qp[t][i + 32], v1);
-      v2 = fmaf(dc[t], qp[t][i + 64], v2);
-      v3 = fmaf(dc[t], qp[t][i + 96], v3);
-    }
-    d0 = fmaf(qj[i], v0, d0);
-    d1 = fmaf(qj[i + 32], v1, d1);
-    d2 = fmaf(qj[i + 64], v2, d2);
-    d3 = fmaf(qj[i + 96], v3, d3);
+    for (int u = 0; u < U; ++u) v[u] = x[i + 32 * u];
+#pragma unroll
+    for (int t = 0; t < NP; ++t)
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = fmaf(dc[t], qp[t][i + 32 * u], v[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) dd[u & 3] = fmaf(qj[i + 32 * u], v[u], dd[u & 3]);
   }
   for (; i < mc; i += 32) {
     float v = x[i];
 #pragma unroll
     for (int t = 0; t < NP; ++t) v = fmaf(dc[t], qp[t][i], v);
-    d0 = fmaf(qj[i], v, d0);
+    dd[0] = fmaf(qj[i], v, dd[0]);
   }
-  const float d = warp_sum((d0 + d1) + (d2 + d3));
+  const float d = warp_sum((dd[0] + dd[1]) + (dd[2] + dd[3]));
   const float nd = -d;
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  float aa[4] = {0.f, 0.f, 0.f, 0.f};
   i = lane;
-  for (; i + 96 < mc; i += 128) {
-    float v0 = x[i], v1 = x[i + 32], v2 = x[i + 64], v3 = x[i + 96];
+  for (; i + 32 * (U - 1) < mc; i += 32 * U) {
+    float v[U];
 #pragma unroll
-    for (int t = 0; t < NP; ++t) {
-      v0 = fmaf(dc[t], qp[t][i], v0);
-      v1 = fmaf(dc[t], qp[t][i + 32], v1);
-      v2 = fmaf(dc[t], qp[t][i + 64], v2);
-      v3 = fmaf(dc[t], qp[t][i + 96], v3);
+    for (int u = 0; u < U; ++u) v[u] = x[i + 32 * u];
+#pragma unroll
+    for (int t = 0; t < NP; ++t)
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = fmaf(dc[t], qp[t][i + 32 * u], v[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      v[u] = fmaf(nd, qj[i + 32 * u], v[u]);
+      if (wr) w[i + 32 * u] = v[u];
+      aa[u & 3] = fmaf(v[u], v[u], aa[u & 3]);
     }
-    v0 = fmaf(nd, qj[i], v0);
-    v1 = fmaf(nd, qj[i + 32], v1);
-    v2 = fmaf(nd, qj[i + 64], v2);
-    v3 = fmaf(nd, qj[i + 96], v3);
-    if (wr) {
-      w[i] = v0;
-      w[i + 32] = v1;
-      w[i + 64] = v2;
-      w[i + 96] = v3;
-    }
-    a0 = fmaf(v0, v0, a0);
-    a1 = fmaf(v1, v1, a1);
-    a2 = fmaf(v2, v2, a2);
-    a3 = fmaf(v3, v3, a3);
   }
   for (; i < mc; i += 32) {
     float v = x[i];
@@ -241,10 +230,10 @@ __device__ __forceinline__ void mgs_column(const float* x, float* w, const float
     for (int t = 0; t < NP; ++t) v = fmaf(dc[t], qp[t][i], v);
     v = fmaf(nd, qj[i], v);
     if (wr) w[i] = v;
-    a0 = fmaf(v, v, a0);
+    aa[0] = fmaf(v, v, aa[0]);
   }
   d_out = d;
-  nu_out = warp_sum((a0 + a1) + (a2 + a3));
+  nu_out = warp_sum((aa[0] + aa[1]) + (aa[2] + aa[3]));
 }
 
 // What a CTA publishes to the other CTAs of its cluster (double-buffered by
