@@ -37,6 +37,9 @@ constexpr int kQrWarps = kQrThreads / 32;
 // shared memory) before the working copy W is rewritten
 constexpr int kQrMaxSlots = 4;
 constexpr int kQrSlotBudgetFloats = 24 * 1024;
+// the per-warp column buffers are used while the kernel's shared memory stays
+// within this (m_c up to ~1400)
+constexpr size_t kQrColumnSmemMax = 200 * 1024;
 
 __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -175,7 +178,7 @@ __device__ __forceinline__ int owned_col(int o, int G, int rank) {
 template <int NP>
 __device__ __forceinline__ void mgs_column(const float* x, float* w, const float* qv, int qs,
                                            int P, int base, int j, const float* Rc, int n,
-                                           int mc, int lane, bool wr, float& d_out,
+                                           int mc, int lane, bool wr, float* cb, float& d_out,
                                            float& nu_out) {
   constexpr int U = 8;   // loads in flight per lane
   float dc[NP > 0 ? NP : 1];
@@ -197,18 +200,40 @@ __device__ __forceinline__ void mgs_column(const float* x, float* w, const float
 #pragma unroll
       for (int u = 0; u < U; ++u) v[u] = fmaf(dc[t], qp[t][i + 32 * u], v[u]);
 #pragma unroll
-    for (int u = 0; u < U; ++u) dd[u & 3] = fmaf(qj[i + 32 * u], v[u], dd[u & 3]);
+    for (int u = 0; u < U; ++u) {
+      dd[u & 3] = fmaf(qj[i + 32 * u], v[u], dd[u & 3]);
+      if (cb) cb[i + 32 * u] = v[u];
+    }
   }
   for (; i < mc; i += 32) {
     float v = x[i];
 #pragma unroll
     for (int t = 0; t < NP; ++t) v = fmaf(dc[t], qp[t][i], v);
     dd[0] = fmaf(qj[i], v, dd[0]);
+    if (cb) cb[i] = v;
   }
   const float d = warp_sum((dd[0] + dd[1]) + (dd[2] + dd[3]));
   const float nd = -d;
   float aa[4] = {0.f, 0.f, 0.f, 0.f};
   i = lane;
+  if (cb) {   // the lane's own values of pass 1, from shared memory
+    for (; i + 96 < mc; i += 128) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float v = fmaf(nd, qj[i + 32 * u], cb[i + 32 * u]);
+        if (wr) w[i + 32 * u] = v;
+        aa[u] = fmaf(v, v, aa[u]);
+      }
+    }
+    for (; i < mc; i += 32) {
+      const float v = fmaf(nd, qj[i], cb[i]);
+      if (wr) w[i] = v;
+      aa[0] = fmaf(v, v, aa[0]);
+    }
+    d_out = d;
+    nu_out = warp_sum((aa[0] + aa[1]) + (aa[2] + aa[3]));
+    return;
+  }
   for (; i + 32 * (U - 1) < mc; i += 32 * U) {
     float v[U];
 #pragma unroll
@@ -247,11 +272,17 @@ struct QrXchg {
 };
 
 __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a, int n_max,
-                                                                 int qv_floats, int qs, int P) {
+                                                                 int qv_floats, int qs, int P,
+                                                                 int cb_floats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* qv = reinterpret_cast<float*>(smem_raw);          // q_t in slot t % P (stride qs), later R11
   float* nu = qv + qv_floats;                              // residual norms^2 [n] (own columns)
   int32_t* step = reinterpret_cast<int32_t*>(nu + n_max);  // -1 active, >= 0 pivot step
+  // a warp's column values between its two MGS passes [kQrWarps][cb_floats], if
+  // they fit (cb_floats > 0)
+  float* cbw = cb_floats > 0 ? reinterpret_cast<float*>(step + n_max) +
+                                   (int64_t)(threadIdx.x / 32) * cb_floats
+                             : nullptr;
   __shared__ unsigned long long wkey[kQrWarps];
   __shared__ float wrest_h[kQrWarps], wrest_l[kQrWarps];
   __shared__ double wnb[kQrWarps];
@@ -450,10 +481,10 @@ __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a
       float* w = W + (int64_t)c * mc;
       float d = 0.f, acc = 0.f;
       switch (np) {
-        case 0: mgs_column<0>(x, w, qv, qs, P, base, j, R + c, n, mc, lane, wr, d, acc); break;
-        case 1: mgs_column<1>(x, w, qv, qs, P, base, j, R + c, n, mc, lane, wr, d, acc); break;
-        case 2: mgs_column<2>(x, w, qv, qs, P, base, j, R + c, n, mc, lane, wr, d, acc); break;
-        default: mgs_column<3>(x, w, qv, qs, P, base, j, R + c, n, mc, lane, wr, d, acc); break;
+        case 0: mgs_column<0>(x, w, qv, qs, P, base, j, R + c, n, mc, lane, wr, cbw, d, acc); break;
+        case 1: mgs_column<1>(x, w, qv, qs, P, base, j, R + c, n, mc, lane, wr, cbw, d, acc); break;
+        case 2: mgs_column<2>(x, w, qv, qs, P, base, j, R + c, n, mc, lane, wr, cbw, d, acc); break;
+        default: mgs_column<3>(x, w, qv, qs, P, base, j, R + c, n, mc, lane, wr, cbw, d, acc); break;
       }
       if (lane == 0) {
         R[(int64_t)j * n + c] = d;
@@ -923,7 +954,9 @@ static int qr_cluster_size(int S, int n_max) {
 cudaError_t launch_subid_qr(const SubArgs& a, int mc_max, int n_max, cudaStream_t st) {
   const int qv = qr_qv_floats(mc_max, a.k_max);
   const int qs = qr_slot_stride(mc_max), P = qr_slots(mc_max);
-  const size_t smem = subid_qr_smem_bytes(mc_max, n_max, a.k_max);
+  const size_t smem0 = subid_qr_smem_bytes(mc_max, n_max, a.k_max);
+  const int cbf = smem0 + sizeof(float) * (size_t)kQrWarps * qs <= kQrColumnSmemMax ? qs : 0;
+  const size_t smem = smem0 + sizeof(float) * (size_t)kQrWarps * cbf;
   cudaError_t e = cudaFuncSetAttribute(subid_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -949,7 +982,7 @@ cudaError_t launch_subid_qr(const SubArgs& a, int mc_max, int n_max, cudaStream_
     cfg.gridDim = dim3((unsigned)(a.S * G));
     attr[0].val.clusterDim.x = (unsigned)G;
   }
-  return cudaLaunchKernelEx(&cfg, subid_qr_kernel, a, n_max, qv, qs, P);
+  return cudaLaunchKernelEx(&cfg, subid_qr_kernel, a, n_max, qv, qs, P, cbf);
 }
 
 cudaError_t launch_coarse_recon(const SubArgs& a, int64_t max_work, cudaStream_t st) {
