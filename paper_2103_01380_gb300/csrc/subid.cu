@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256) subsample_kernel(const SubArgs a, const f
   const int lane = threadIdx.x % 32;
   const SubBox b = a.box[s];
   const float* Aj = window + a.off[s] + (int64_t)g.j * a.ld[s];
-  float* Bj = a.B + a.boff[s] + (int64_t)g.j * mc;
+  float* Bj = a.B + a.boff[s] + (int64_t)g.j * coarse_ld(mc);
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
   bool bad = false;
   // four independent gathers in flight per lane
@@ -169,93 +169,97 @@ __device__ __forceinline__ int owned_col(int o, int G, int rank) {
   return ((o / kQrWarps) * G + rank) * kQrWarps + o % kQrWarps;
 }
 
+__device__ __forceinline__ void fma4(float4& v, float c, const float4 q) {
+  v.x = fmaf(c, q.x, v.x);
+  v.y = fmaf(c, q.y, v.y);
+  v.z = fmaf(c, q.z, v.z);
+  v.w = fmaf(c, q.w, v.w);
+}
+__device__ __forceinline__ float dot4(const float4 q, const float4 v, float acc) {
+  return fmaf(q.w, v.w, fmaf(q.z, v.z, fmaf(q.y, v.y, fmaf(q.x, v.x, acc))));
+}
+
 // One column's MGS step j with the updates of steps base..base+NP-1 still
 // pending: the column is read as stored (B, or W as of step base), the pending
 // updates w -= R(t, c) q_t are re-applied on the fly -- the same fma sequence
 // as if every step had been stored, so the values are identical -- then
-// d = q_j . w, and a second pass over the column (from L1) forms
-// w - d q_j, its squared norm and, when wr, stores it as the new W.
+// d = q_j . w, and a second pass forms w - d q_j, its squared norm and, when
+// wr, stores it as the new W.  Columns are ldb = m_c rounded up to 4 floats
+// (16-byte aligned, zero past m_c, as are the q slots), so a lane moves four
+// rows per access: nf = ldb / 4 float4 per column.  cb (the warp's shared
+// buffer, or null) keeps the pass-1 values for the second pass.
 template <int NP>
-__device__ __forceinline__ void mgs_column(const float* x, float* w, const float* qv, int qs,
+__device__ __forceinline__ void mgs_column(const float4* x, float4* w, const float* qv, int qs,
                                            int P, int base, int j, const float* Rc, int n,
-                                           int mc, int lane, bool wr, float* cb, float& d_out,
+                                           int nf, int lane, bool wr, float4* cb, float& d_out,
                                            float& nu_out) {
-  constexpr int U = 8;   // loads in flight per lane
+  constexpr int U = NP >= 3 ? 2 : 4;   // float4 loads in flight per lane
   float dc[NP > 0 ? NP : 1];
-  const float* qp[NP > 0 ? NP : 1];
+  const float4* qp[NP > 0 ? NP : 1];
 #pragma unroll
   for (int t = 0; t < NP; ++t) {
     dc[t] = -Rc[(int64_t)(base + t) * n];
-    qp[t] = qv + ((base + t) % P) * qs;
+    qp[t] = reinterpret_cast<const float4*>(qv + ((base + t) % P) * qs);
   }
-  const float* qj = qv + (j % P) * qs;
+  const float4* qj = reinterpret_cast<const float4*>(qv + (j % P) * qs);
   float dd[4] = {0.f, 0.f, 0.f, 0.f};
-  int i = lane;
-  for (; i + 32 * (U - 1) < mc; i += 32 * U) {
-    float v[U];
+  int f = lane;
+  for (; f + 32 * (U - 1) < nf; f += 32 * U) {
+    float4 v[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) v[u] = x[i + 32 * u];
+    for (int u = 0; u < U; ++u) v[u] = x[f + 32 * u];
 #pragma unroll
     for (int t = 0; t < NP; ++t)
 #pragma unroll
-      for (int u = 0; u < U; ++u) v[u] = fmaf(dc[t], qp[t][i + 32 * u], v[u]);
+      for (int u = 0; u < U; ++u) fma4(v[u], dc[t], qp[t][f + 32 * u]);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      dd[u & 3] = fmaf(qj[i + 32 * u], v[u], dd[u & 3]);
-      if (cb) cb[i + 32 * u] = v[u];
+      dd[u] = dot4(qj[f + 32 * u], v[u], dd[u]);
+      if (cb) cb[f + 32 * u] = v[u];
     }
   }
-  for (; i < mc; i += 32) {
-    float v = x[i];
+  for (; f < nf; f += 32) {
+    float4 v = x[f];
 #pragma unroll
-    for (int t = 0; t < NP; ++t) v = fmaf(dc[t], qp[t][i], v);
-    dd[0] = fmaf(qj[i], v, dd[0]);
-    if (cb) cb[i] = v;
+    for (int t = 0; t < NP; ++t) fma4(v, dc[t], qp[t][f]);
+    dd[0] = dot4(qj[f], v, dd[0]);
+    if (cb) cb[f] = v;
   }
   const float d = warp_sum((dd[0] + dd[1]) + (dd[2] + dd[3]));
   const float nd = -d;
   float aa[4] = {0.f, 0.f, 0.f, 0.f};
-  i = lane;
-  if (cb) {   // the lane's own values of pass 1, from shared memory
-    for (; i + 96 < mc; i += 128) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float v = fmaf(nd, qj[i + 32 * u], cb[i + 32 * u]);
-        if (wr) w[i + 32 * u] = v;
-        aa[u] = fmaf(v, v, aa[u]);
-      }
-    }
-    for (; i < mc; i += 32) {
-      const float v = fmaf(nd, qj[i], cb[i]);
-      if (wr) w[i] = v;
-      aa[0] = fmaf(v, v, aa[0]);
-    }
-    d_out = d;
-    nu_out = warp_sum((aa[0] + aa[1]) + (aa[2] + aa[3]));
-    return;
-  }
-  for (; i + 32 * (U - 1) < mc; i += 32 * U) {
-    float v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) v[u] = x[i + 32 * u];
-#pragma unroll
-    for (int t = 0; t < NP; ++t)
-#pragma unroll
-      for (int u = 0; u < U; ++u) v[u] = fmaf(dc[t], qp[t][i + 32 * u], v[u]);
+  f = lane;
+  for (; f + 32 * (U - 1) < nf; f += 32 * U) {
+    float4 v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      v[u] = fmaf(nd, qj[i + 32 * u], v[u]);
-      if (wr) w[i + 32 * u] = v[u];
-      aa[u & 3] = fmaf(v[u], v[u], aa[u & 3]);
+      if (cb) {
+        v[u] = cb[f + 32 * u];
+      } else {
+        v[u] = x[f + 32 * u];
+#pragma unroll
+        for (int t = 0; t < NP; ++t) fma4(v[u], dc[t], qp[t][f + 32 * u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      fma4(v[u], nd, qj[f + 32 * u]);
+      if (wr) w[f + 32 * u] = v[u];
+      aa[u] = dot4(v[u], v[u], aa[u]);
     }
   }
-  for (; i < mc; i += 32) {
-    float v = x[i];
+  for (; f < nf; f += 32) {
+    float4 v;
+    if (cb) {
+      v = cb[f];
+    } else {
+      v = x[f];
 #pragma unroll
-    for (int t = 0; t < NP; ++t) v = fmaf(dc[t], qp[t][i], v);
-    v = fmaf(nd, qj[i], v);
-    if (wr) w[i] = v;
-    aa[0] = fmaf(v, v, aa[0]);
+      for (int t = 0; t < NP; ++t) fma4(v, dc[t], qp[t][f]);
+    }
+    fma4(v, nd, qj[f]);
+    if (wr) w[f] = v;
+    aa[0] = dot4(v, v, aa[0]);
   }
   d_out = d;
   nu_out = warp_sum((aa[0] + aa[1]) + (aa[2] + aa[3]));
@@ -275,14 +279,16 @@ __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a
                                                                  int qv_floats, int qs, int P,
                                                                  int cb_floats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  // qv_floats and the n_max-long arrays are multiples of 4 (16-byte alignment)
   float* qv = reinterpret_cast<float*>(smem_raw);          // q_t in slot t % P (stride qs), later R11
+  const int n_pad = (n_max + 3) & ~3;
   float* nu = qv + qv_floats;                              // residual norms^2 [n] (own columns)
-  int32_t* step = reinterpret_cast<int32_t*>(nu + n_max);  // -1 active, >= 0 pivot step
+  int32_t* step = reinterpret_cast<int32_t*>(nu + n_pad);  // -1 active, >= 0 pivot step
   // a warp's column values between its two MGS passes [kQrWarps][cb_floats], if
   // they fit (cb_floats > 0)
-  float* cbw = cb_floats > 0 ? reinterpret_cast<float*>(step + n_max) +
-                                   (int64_t)(threadIdx.x / 32) * cb_floats
-                             : nullptr;
+  float4* cbw = cb_floats > 0 ? reinterpret_cast<float4*>(reinterpret_cast<float*>(step + n_pad) +
+                                                          (int64_t)(threadIdx.x / 32) * cb_floats)
+                              : nullptr;
   __shared__ unsigned long long wkey[kQrWarps];
   __shared__ float wrest_h[kQrWarps], wrest_l[kQrWarps];
   __shared__ double wnb[kQrWarps];
@@ -297,6 +303,7 @@ __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a
   const int rank = (int)cluster.block_rank();
   const int s = blockIdx.x / G;
   const int n = a.n[s], mc = a.mc[s], k_max = a.k_max;
+  const int ldb = coarse_ld(mc);   // column stride of B and W
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int cstride = G * kQrWarps;                 // a warp's column stride
   const int c_first = rank * kQrWarps + warp;       // a warp's first column
@@ -457,12 +464,16 @@ __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a
       for (int t = 0; t < kQrMaxSlots; ++t)
         rp[t] = t < np ? -__ldcg(R + (int64_t)(base + t) * n + p) : 0.f;
       float* qj = qv + (j % P) * qs;
-      for (int i = tid; i < mc; i += kQrThreads) {
-        float v = __ldcg(src + (int64_t)p * mc + i);
+      for (int i = tid; i < ldb; i += kQrThreads) {   // zero past m_c
+        float v = 0.f;
+        if (i < mc) {
+          v = __ldcg(src + (int64_t)p * ldb + i);
 #pragma unroll
-        for (int t = 0; t < kQrMaxSlots; ++t)
-          if (t < np) v = fmaf(rp[t], qv[((base + t) % P) * qs + i], v);
-        qj[i] = v / rjj;
+          for (int t = 0; t < kQrMaxSlots; ++t)
+            if (t < np) v = fmaf(rp[t], qv[((base + t) % P) * qs + i], v);
+          v = v / rjj;
+        }
+        qj[i] = v;
       }
     }
     if (tid == 0) {
@@ -477,14 +488,15 @@ __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a
     const bool wr = j + 1 - base >= P;
     for (int c = c_first; c < n; c += cstride) {
       if (step[c] != -1) continue;   // warp-uniform
-      const float* x = src + (int64_t)c * mc;
-      float* w = W + (int64_t)c * mc;
+      const float4* x = reinterpret_cast<const float4*>(src + (int64_t)c * ldb);
+      float4* w = reinterpret_cast<float4*>(W + (int64_t)c * ldb);
+      const int nf = ldb / 4;
       float d = 0.f, acc = 0.f;
       switch (np) {
-        case 0: mgs_column<0>(x, w, qv, qs, P, base, j, R + c, n, mc, lane, wr, cbw, d, acc); break;
-        case 1: mgs_column<1>(x, w, qv, qs, P, base, j, R + c, n, mc, lane, wr, cbw, d, acc); break;
-        case 2: mgs_column<2>(x, w, qv, qs, P, base, j, R + c, n, mc, lane, wr, cbw, d, acc); break;
-        default: mgs_column<3>(x, w, qv, qs, P, base, j, R + c, n, mc, lane, wr, cbw, d, acc); break;
+        case 0: mgs_column<0>(x, w, qv, qs, P, base, j, R + c, n, nf, lane, wr, cbw, d, acc); break;
+        case 1: mgs_column<1>(x, w, qv, qs, P, base, j, R + c, n, nf, lane, wr, cbw, d, acc); break;
+        case 2: mgs_column<2>(x, w, qv, qs, P, base, j, R + c, n, nf, lane, wr, cbw, d, acc); break;
+        default: mgs_column<3>(x, w, qv, qs, P, base, j, R + c, n, nf, lane, wr, cbw, d, acc); break;
       }
       if (lane == 0) {
         R[(int64_t)j * n + c] = d;
@@ -526,7 +538,7 @@ __global__ void __launch_bounds__(kQrThreads, 1) subid_qr_kernel(const SubArgs a
   for (int64_t e = (int64_t)rank * kQrThreads + tid; e < (int64_t)k_max * mc;
        e += (int64_t)G * kQrThreads) {
     const int p = (int)(e / mc), i = (int)(e % mc);
-    Bsk[e] = (p < k) ? B[(int64_t)Js[p] * mc + i] : 0.f;
+    Bsk[e] = (p < k) ? B[(int64_t)Js[p] * ldb + i] : 0.f;
   }
 }
 
@@ -808,7 +820,7 @@ __global__ void __launch_bounds__(256) subsample_rows_kernel(const SubArgs a, co
   const int lane = threadIdx.x % 32;
   const int32_t* rows = crow + crow_off[s];
   const float* Aj = window + a.off[s] + (int64_t)g.j * a.ld[s];
-  float* Bj = a.B + a.boff[s] + (int64_t)g.j * mc;
+  float* Bj = a.B + a.boff[s] + (int64_t)g.j * coarse_ld(mc);
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
   bool bad = false;
   for (int i0 = g.r0 + lane; i0 < g.r1; i0 += 128) {
@@ -929,12 +941,12 @@ static int qr_slots(int mc_max) {
 }
 static int qr_qv_floats(int mc_max, int k_max) {
   const int q = qr_slots(mc_max) * qr_slot_stride(mc_max);
-  return q > k_max * k_max ? q : k_max * k_max;
+  return ((q > k_max * k_max ? q : k_max * k_max) + 3) & ~3;
 }
 
 size_t subid_qr_smem_bytes(int mc_max, int n_max, int k_max) {
-  return sizeof(float) * ((size_t)qr_qv_floats(mc_max, k_max) + n_max) +
-         sizeof(int32_t) * (size_t)n_max;
+  const size_t n_pad = (size_t)((n_max + 3) & ~3);
+  return sizeof(float) * ((size_t)qr_qv_floats(mc_max, k_max) + n_pad) + sizeof(int32_t) * n_pad;
 }
 
 // Cluster size for the QR: up to 8 CTAs per subdomain while the clusters of

@@ -357,7 +357,7 @@ spid_status spid_sub_plan_create(const spid_sub_desc* d, spid_sub_plan_t* out) {
     P->boff.push_back(bsum);
     P->coff.push_back(csum);
     P->sklo.push_back(ssum);
-    bsum += mc * ns;
+    bsum += (int64_t)coarse_ld((int)mc) * ns;
     csum += ns;
     ssum += mc;
     P->uptr[s] = (int32_t)units;
@@ -456,7 +456,7 @@ spid_status spid_sub_plan_create_points(const spid_sub_points_desc* d, spid_sub_
     P->ioff.push_back(isum);
     P->foff.push_back(P->f_elems);
     P->f_elems += (int64_t)m * d->k_max;
-    bsum += (int64_t)mc * ns;
+    bsum += (int64_t)coarse_ld(mc) * ns;
     csum += ns;
     ssum += mc;
     rsum += m;
@@ -623,7 +623,15 @@ spid_status spid_sub_get_coarse(spid_sub_plan_t P, float* B_host, spid_stream_t 
   if (st != SPID_OK) return st;
   if (!B_host) return sfail(SPID_ERR_INVALID_ARG, "B_host is NULL");
   SUB_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
-  SUB_CUDA(cudaMemcpy(B_host, P->d_B, sizeof(float) * P->b_elems, cudaMemcpyDeviceToHost));
+  // the device columns are padded to coarse_ld(m_c) rows; the host gets m_c
+  int64_t hoff = 0;
+  for (int s = 0; s < P->S; ++s) {
+    const size_t mc = (size_t)P->mc[s];
+    SUB_CUDA(cudaMemcpy2D(B_host + hoff, sizeof(float) * mc, P->d_B + P->boff[s],
+                          sizeof(float) * (size_t)coarse_ld((int)mc), sizeof(float) * mc,
+                          (size_t)P->n[s], cudaMemcpyDeviceToHost));
+    hoff += (int64_t)mc * P->n[s];
+  }
   return SPID_OK;
 }
 

@@ -49,6 +49,10 @@ struct SubBox {
   FastDiv div_cx, div_cy, div_cz, div_mc;   // coarse-row decodes
 };
 
+// Column stride of the coarse matrix B and its working copy W: m_c rounded up
+// to 4 floats, so every column starts 16-byte aligned (rows past m_c are zero).
+__host__ __device__ inline int coarse_ld(int mc) { return (mc + 3) & ~3; }
+
 struct SubArgs {
   const SubBox* box;          // [S]
   const int32_t* m;           // [S] fine rows
@@ -56,7 +60,8 @@ struct SubArgs {
   const int32_t* mc;          // [S] coarse rows
   const int64_t* off;         // [S] window offsets
   const int64_t* ld;          // [S]
-  const int64_t* boff;        // [S] B_s / W_s at boff[s], mc x n column-major
+  const int64_t* boff;        // [S] B_s / W_s at boff[s], column-major, column stride
+                              // coarse_ld(mc) (W as the coarse reconstruction: stride mc)
   const int64_t* coff;        // [S] sum of n before s (R, C at k_max * coff[s])
   const int64_t* sklo;        // [S] sum of mc before s (Bskel at k_max * sklo[s])
   float* B;                   // gathered coarse matrices
