@@ -130,6 +130,16 @@ def test_adaptive_rank_and_streamed_columns():
     assert np.all(g["k"] >= 1) and np.all(g["k"] <= 16)
 
 
+def test_large_coarse_grid_reads_columns_twice_and_rewrites_w():
+    # m_c = 8000 and 2400: too many rows for the per-warp shared column buffers, so
+    # each MGS pass reads the column from memory; a fixed rank of 5 makes the QR
+    # rewrite its working copy once the pending-update slots are full
+    boxes = [(1, 40, 40, 40), (1, 30, 20, 16)]
+    win = inputs.box_window(boxes, 40, seed=45, noise=1e-4)
+    g = check_sub_parity(win, (2, 2, 2), 5)
+    assert list(g["k"]) == [5, 5]
+
+
 def test_edge_cases_rank_capped_by_coarse_rows_and_columns():
     # k_max above n and above m_c; a single-point box; a one-column window
     boxes = [(1, 3, 3, 3), (1, 1, 1, 1), (2, 4, 4, 4)]
