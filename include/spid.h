@@ -410,12 +410,18 @@ typedef struct {
 } spid_sub_points_desc;
 
 /* Create a point-set plan (the host tables are copied; later calls allocate
- * nothing).  SPID_ERR_INVALID_ARG for a size, index or weight out of range. */
+ * nothing).  SPID_ERR_INVALID_ARG for a size, index or weight out of range.
+ * Like spid_sub_plan_create, it sets the current context's L2 fetch
+ * granularity (cudaLimitMaxL2FetchGranularity) to 32 bytes. */
 spid_status spid_sub_plan_create_points(const spid_sub_points_desc* desc, spid_sub_plan_t* plan);
 
 /* Create a plan: validates, allocates all workspace (later calls allocate
  * nothing).  m_c(s) <= 40960 coarse rows (the QR keeps one column of B in
- * shared memory); SPID_ERR_UNSUPPORTED beyond. */
+ * shared memory); SPID_ERR_UNSUPPORTED beyond.  Side effect: sets the current
+ * context's L2 fetch granularity (cudaLimitMaxL2FetchGranularity) to 32 bytes
+ * -- the gathers read scattered sectors, which whole-line fills from DRAM
+ * would double; the limit is a hint that belongs to the context (it ends with
+ * the process) and moved the streaming kernels' rates by < 1%. */
 spid_status spid_sub_plan_create(const spid_sub_desc* desc, spid_sub_plan_t* plan);
 spid_status spid_sub_plan_destroy(spid_sub_plan_t plan);
 
