@@ -1,7 +1,8 @@
 // subid.cu -- the coarse-grid column ID of Section 2 (SubID and SPID
 // paragraphs, Algorithms 2 and 3) and the trilinear reconstruction of
 // Section 5.2, FP32:
-//   subsample    B = A(J, :), the rows of the coarse grid of every box
+//   subsample    B = A(J, :), the rows of the coarse grid of every box, with
+//                each column's squared norm for the QR's first pivot
 //   subid_qr     pivoted modified Gram-Schmidt QR of B (the paper's mgsqr),
 //                rank decision, C_B = [I | R11^-1 R12] Z^T, skeleton B(:, I_B)
 //   coarse_recon G = B(:, I_B) C_B on the coarse grid
@@ -17,7 +18,9 @@
 // memory, and one warp per remaining column computes R(j, c) = q_j . w_c,
 // updates w_c -= R(j, c) q_j and recomputes ||w_c||^2 from the updated
 // values -- the residual norms are therefore taken from the current columns
-// at every step, as in the oracle, with no downdating.
+// at every step, as in the oracle, with no downdating.  W is rewritten only
+// every few steps: in between, the pending updates are re-applied as each
+// column is read (the same fma sequence, so the same values).
 #include <algorithm>
 
 #include <cooperative_groups.h>
