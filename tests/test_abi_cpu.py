@@ -100,3 +100,20 @@ def test_producer_rejects_bad_arguments(lib):
                  (p, be, p + 16, be, 16, 8, 5, 0.0, 0.01),      # dt <= 0
                  (p, be - 1, p + 16, be, 16, 8, 5, 0.01, 0.01)):   # box stride too small
         assert lib.spid_producer_step(*args, None) == 1
+
+
+def test_host_buffer_marshalling_checks():
+    # the binding's host-pointer checks for spid_graph_launch_host run on the CPU
+    import torch
+    a = np.zeros(16, dtype=np.float32)
+    assert spid._host_ptr(a, np.float32, 64) == a.ctypes.data
+    t = torch.zeros(16, dtype=torch.float32)
+    assert spid._host_ptr(t, np.float32, 64) == t.data_ptr()
+    with pytest.raises(ValueError):
+        spid._host_ptr(a, np.float32, 65)            # shorter than needed
+    with pytest.raises(ValueError):
+        spid._host_ptr(a, np.float64, 8)             # wrong element type
+    with pytest.raises(ValueError):
+        spid._host_ptr(a[::2], np.float32, 8)        # not contiguous
+    with pytest.raises(ValueError):
+        spid._host_ptr(t[::2], np.float32, 8)
