@@ -36,6 +36,7 @@ struct spid_ts_plan_s {
   spid_plan_t full = nullptr;
   // device
   void* d_G = nullptr;              // A0' buffer
+  int32_t* d_live = nullptr;        // [S][N k] slot holds a skeleton column (else zero)
   int64_t* d_goff = nullptr;        // [S]
   int64_t* d_gld = nullptr;         // [S]
   int64_t* d_off = nullptr;         // [S] window offsets
@@ -68,19 +69,28 @@ template <typename T>
 __global__ void __launch_bounds__(256) gather_skeleton_kernel(
     const T* window, const int64_t* off, const int64_t* ld, const int32_t* m,
     const int32_t* nb, int k, const int32_t* const* Jb, const int32_t* const* kb, T* G,
-    const int64_t* goff, const int64_t* gld) {
+    const int64_t* goff, const int64_t* gld, int32_t* live) {
   const int q = blockIdx.x, s = blockIdx.y;
   const int b = q / k, p = q - b * k;
   const int ms = m[s];
   T* dst = G + goff[s] + (int64_t)q * gld[s];
   const int kbs = kb[b][s];
+  int32_t* lv = live + (int64_t)s * gridDim.x + q;
+  const int was_live = *lv;
+  __syncthreads();   // every thread has read the flag before thread 0 rewrites it
   if (p >= kbs) {
-    for (int r = threadIdx.x; r < ms; r += blockDim.x) dst[r] = T(0);
+    // a slot past the block's rank reads as zero: only a slot the previous
+    // gather filled needs clearing
+    if (was_live) {
+      for (int r = threadIdx.x; r < ms; r += blockDim.x) dst[r] = T(0);
+      if (threadIdx.x == 0) *lv = 0;
+    }
     return;
   }
   const int64_t col = (int64_t)b * nb[s] + Jb[b][(int64_t)s * k + p];
   const T* src = window + off[s] + col * ld[s];
   for (int r = threadIdx.x; r < ms; r += blockDim.x) dst[r] = __ldg(src + r);
+  if (threadIdx.x == 0) *lv = 1;
 }
 
 // C1'(i, t) = sum_p C1(i, b k + p) C_b(p, t - b nb), b = t / nb; J(i) = b nb + I_b(p)
@@ -227,8 +237,11 @@ spid_status spid_ts_plan_create(const spid_ts_desc* d, spid_ts_plan_t* out) {
         cudaMemcpy(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(tfail(SPID_ERR_CUDA, "two-stage table upload failed"));
   }
+  const size_t slots = (size_t)S * (size_t)N * (size_t)P->k;
   if (dalloc(&P->d_G, P->esz * (size_t)gsum) != cudaSuccess ||
       cudaMemset(P->d_G, 0, P->esz * (size_t)gsum) != cudaSuccess ||
+      dalloc(reinterpret_cast<void**>(&P->d_live), sizeof(int32_t) * slots) != cudaSuccess ||
+      cudaMemset(P->d_live, 0, sizeof(int32_t) * slots) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess)
     return bail(tfail(SPID_ERR_OOM, "two-stage skeleton buffer"));
   *out = P;
@@ -269,11 +282,11 @@ spid_status spid_ts_finalize(spid_ts_plan_t P, const void* window, spid_stream_t
   if (P->esz == 8) {
     gather_skeleton_kernel<double><<<ggrid, 256, 0, cs>>>(
         static_cast<const double*>(window), P->d_off, P->d_ld, v2.m, P->d_nb, P->k, P->d_Jb,
-        P->d_kb, static_cast<double*>(P->d_G), P->d_goff, P->d_gld);
+        P->d_kb, static_cast<double*>(P->d_G), P->d_goff, P->d_gld, P->d_live);
   } else {
     gather_skeleton_kernel<float><<<ggrid, 256, 0, cs>>>(
         static_cast<const float*>(window), P->d_off, P->d_ld, v2.m, P->d_nb, P->k, P->d_Jb,
-        P->d_kb, static_cast<float*>(P->d_G), P->d_goff, P->d_gld);
+        P->d_kb, static_cast<float*>(P->d_G), P->d_goff, P->d_gld, P->d_live);
   }
   TS_CUDA(cudaGetLastError());
   spid_status st = spid_sketch(P->stage2, P->d_G, 0, P->N * P->k, stream);

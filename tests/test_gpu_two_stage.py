@@ -144,3 +144,41 @@ def test_two_stage_deduplicates_a_low_rank_window():
     assert list(g["k"]) == [3, 3, 3]
     rel = np.sqrt(g["total"][0] / g["total"][1])
     assert rel < 1e-5
+
+
+def test_reused_plan_clears_slots_a_lower_rank_leaves():
+    # the plan first sees a window whose blocks keep k columns each, then one
+    # where subdomain 0 is zero (its blocks keep none): stage 2 must see zero
+    # slots there, as a fresh plan does
+    N, k = 4, 4
+    wa = _window([300, 257], 64, 6, seed=150, noise=1e-3, dtype=np.float32)
+    wb = _window([300, 257], 64, 6, seed=150, noise=1e-3, dtype=np.float32)
+    wb.block(0)[:] = 0.0
+
+    def run(plan, win):
+        w = torch.from_numpy(win.data).cuda()
+        for b in range(N):
+            plan.block(w, b)
+        plan.finalize(w)
+        err = torch.zeros(2 * win.num_sub, dtype=torch.float64, device="cuda")
+        tot = torch.zeros(4, dtype=torch.float64, device="cuda")
+        plan.error(w, err, tot)
+        torch.cuda.synchronize()
+        k2, J, C = plan.factors()
+        return k2, J, C, err.cpu().numpy(), [plan.block_factors(b)[0] for b in range(N)]
+
+    mk = lambda: spid.TsPlan.for_window(wa, blocks=N, k=k, k2_max=8, tol2=1e-3, p=6,
+                                        precision="fp32", seed=SEED)
+    reused = mk()
+    ga = run(reused, wa)
+    assert all(int(v[0]) == k for v in ga[4])
+    gb = run(reused, wb)
+    fresh = mk()
+    gf = run(fresh, wb)
+    assert all(int(v[0]) == 0 for v in gb[4])
+    assert np.array_equal(gb[0], gf[0]) and np.array_equal(gb[1], gf[1])
+    for x, y in zip(gb[2], gf[2]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(gb[3], gf[3])
+    reused.close()
+    fresh.close()
