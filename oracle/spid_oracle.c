@@ -21,7 +21,7 @@
  *   - adaptive rank (Remark 2.1), relative Frobenius error (Section 5.1),
  *     compression factor CF = mn / (k(m+n)) (Section 2, Eq. for CF).
  *
- * Readings where the paper is silent (all stated in the design doc as well):
+ * Readings where the paper is silent:
  *   - Omega(i, r) = Box-Muller of Philox4x32-10 (Salmon et al., SC'11) words,
  *     key = (seed lo32, seed hi32), counter = (r, i/4, 0, 0); words (x0,x1)
  *     give rows 4g, 4g+1 and (x2,x3) give rows 4g+2, 4g+3 of group g = i/4;
