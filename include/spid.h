@@ -59,7 +59,7 @@ typedef enum {
   SPID_ERR_STATE = 4,        /* call out of order (e.g. factors before finalize) */
   SPID_ERR_TIMEOUT = 5,      /* a bounded device wait gave up (device status) */
   SPID_ERR_NONFINITE = 6,    /* NaN/Inf reached the sketch of some subdomain (device status) */
-  SPID_ERR_UNSUPPORTED = 7   /* valid request this build does not implement */
+  SPID_ERR_UNSUPPORTED = 7   /* valid request this library does not implement */
 } spid_status;
 
 /* Every FP32-window mode factors the sketch with FP32 Householder reflectors,
