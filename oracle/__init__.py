@@ -84,7 +84,12 @@ def _load():
         lib.orc_compression_factor.restype = c.c_double
         lib.orc_spid_batch.argtypes = [_f64p, c.c_int32, _i64p, _i64p, _i64p, _i64p,
                                        c.c_int32, c.c_int32, c.c_double, c.c_double, c.c_uint64,
-                                       c.c_void_p, _i32p, _i32p, _f64p, _f64p, _f64p]
+                                       c.c_void_p, _i32p, _i32p, _i32p, _f64p, _f64p, _f64p]
+        lib.orc_error_per_qoi.argtypes = [_f64p, c.c_int64, c.c_int64, c.c_int64, _i32p,
+                                          c.c_int32, _f64p, c.c_int32, _f64p, _f64p]
+        lib.orc_error_per_qoi.restype = None
+        lib.orc_qoi_totals.argtypes = [c.c_int32, _i32p, _f64p, _f64p, c.c_int32, _f64p, _f64p]
+        lib.orc_qoi_totals.restype = None
         lib.orc_spid_batch.restype = c.c_int
         lib.orc_coarse_axis.argtypes = [c.c_int32, c.c_int32, c.c_void_p]
         lib.orc_coarse_axis.restype = c.c_int
@@ -212,6 +217,36 @@ def reconstruct_error(A: np.ndarray, J: np.ndarray, C: np.ndarray, want_ahat: bo
     return (H.T.copy() if want_ahat else None), float(e2.value), float(a2.value)
 
 
+def error_per_qoi(A: np.ndarray, J: np.ndarray, C: np.ndarray, nq: int):
+    """Per-QoI (||A_q - A_hat_q||_F^2, ||A_q||_F^2) of one box whose rows hold
+    nq QoI blocks of m / nq rows each (QoI slowest): two arrays of nq."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    if m % nq:
+        raise ValueError("m must be a multiple of nq")
+    k = int(C.shape[0])
+    Af = np.ascontiguousarray(A.T).reshape(-1)
+    Cc = np.ascontiguousarray(C, dtype=np.float64).reshape(-1) if k > 0 else np.zeros(1)
+    Jc = np.ascontiguousarray(J[:k], dtype=np.int32) if k > 0 else np.zeros(1, dtype=np.int32)
+    e2 = np.zeros(nq, dtype=np.float64)
+    a2 = np.zeros(nq, dtype=np.float64)
+    _load().orc_error_per_qoi(Af, m, n, m, Jc, k, Cc, nq, e2, a2)
+    return e2, a2
+
+
+def qoi_totals(qoi, e2, a2, nqoi: int):
+    """Sums of per-subdomain e2 / a2 over the subdomains of each QoI."""
+    qoi = np.ascontiguousarray(qoi, dtype=np.int32)
+    e2 = np.ascontiguousarray(e2, dtype=np.float64)
+    a2 = np.ascontiguousarray(a2, dtype=np.float64)
+    if qoi.size and (qoi.min() < 0 or qoi.max() >= nqoi):
+        raise ValueError("qoi index out of range")
+    ge2 = np.zeros(nqoi, dtype=np.float64)
+    ga2 = np.zeros(nqoi, dtype=np.float64)
+    _load().orc_qoi_totals(len(qoi), qoi, e2, a2, nqoi, ge2, ga2)
+    return ge2, ga2
+
+
 def compression_factor(m, n, k, stored_rows=None) -> float:
     """Aggregate CF = sum m_i n_i / sum k_i (s_i + n_i) (s_i = m_i by default)."""
     m = np.ascontiguousarray(np.atleast_1d(m), dtype=np.int64)
@@ -239,14 +274,15 @@ def spid_batch(window: np.ndarray, m, n, off, ld, l: int, kmax: int, tol: float,
     ntot = int(n.sum())
     J = np.full(S * kmax, -1, dtype=np.int32)
     k = np.zeros(S, dtype=np.int32)
+    kqr = np.zeros(S, dtype=np.int32)
     C = np.zeros(kmax * ntot, dtype=np.float64)
     e2 = np.zeros(S, dtype=np.float64)
     a2 = np.zeros(S, dtype=np.float64)
     Y = np.zeros(l * ntot, dtype=np.float64) if want_y else None
     _load().orc_spid_batch(w, S, m, n, off, ld, l, kmax, tol, u_mode, seed,
-                           Y.ctypes.data if want_y else None, J, k, C, e2, a2)
+                           Y.ctypes.data if want_y else None, J, k, kqr, C, e2, a2)
     coff = np.concatenate([[0], np.cumsum(n)])
-    out = {"J": J.reshape(S, kmax), "k": k, "e2": e2, "a2": a2,
+    out = {"J": J.reshape(S, kmax), "k": k, "k_qr": kqr, "e2": e2, "a2": a2,
            "C": [C[kmax * coff[s]: kmax * coff[s + 1]].reshape(kmax, int(n[s]))
                  for s in range(S)]}
     if want_y:
@@ -261,7 +297,7 @@ def spid(A: np.ndarray, l: int, kmax: int, tol: float, u_mode: float, seed: int,
     m, n = A.shape
     out = spid_batch(np.ascontiguousarray(A.T).reshape(-1), [m], [n], [0], [m], l, kmax, tol,
                      u_mode, seed, want_y=want_y)
-    res = {"J": out["J"][0], "k": int(out["k"][0]), "C": out["C"][0],
+    res = {"J": out["J"][0], "k": int(out["k"][0]), "k_qr": int(out["k_qr"][0]), "C": out["C"][0],
            "e2": float(out["e2"][0]), "a2": float(out["a2"][0])}
     if want_y:
         res["Y"] = out["Y"][0]

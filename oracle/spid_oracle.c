@@ -317,6 +317,50 @@ void orc_reconstruct_error(const double* A, int64_t m, int64_t n, int64_t ld,
   *a2 = sa + ca;
 }
 
+/* Per-QoI errors of one subdomain (Section 5.1 reports the relative error of
+ * each quantity of interest separately; Section 5.3 compresses each QoI of a
+ * sub-domain on its own).  The rows of a box are ordered with the QoI
+ * slowest, r = ((q ez + z) ey + y) ex + x, so QoI q is the row block
+ * [q m / nq, (q + 1) m / nq) (m a multiple of nq).  e2[q] and a2[q] receive
+ * ||A_q - A_hat_q||_F^2 and ||A_q||_F^2 of that block, with A_hat = A(:, J) C
+ * formed exactly as in orc_reconstruct_error (Neumaier sums, columns outer). */
+void orc_error_per_qoi(const double* A, int64_t m, int64_t n, int64_t ld, const int32_t* J,
+                       int32_t k, const double* C, int32_t nq, double* e2, double* a2) {
+  const int64_t mq = m / nq;
+  for (int32_t q = 0; q < nq; ++q) {
+    double se = 0.0, ce = 0.0, sa = 0.0, ca = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+      for (int64_t r = q * mq; r < (q + 1) * mq; ++r) {
+        double ah = 0.0;
+        for (int32_t p = 0; p < k; ++p) ah += A[r + ld * J[p]] * C[(int64_t)p * n + j];
+        double a = A[r + ld * j];
+        double e = a - ah;
+        neu_add(&se, &ce, e * e);
+        neu_add(&sa, &ca, a * a);
+      }
+    }
+    e2[q] = se + ce;
+    a2[q] = sa + ca;
+  }
+}
+
+/* Per-QoI totals over a batch whose subdomains each hold one QoI of a box
+ * (Section 5.3: each QoI of each sub-domain compressed on its own):
+ * ge2[g] = sum of e2[s] and ga2[g] = sum of a2[s] over the subdomains s with
+ * qoi[s] == g, in subdomain order.  The relative error of QoI g over the
+ * whole domain is sqrt(ge2[g] / ga2[g]) (Section 5.1). */
+void orc_qoi_totals(int32_t num, const int32_t* qoi, const double* e2, const double* a2,
+                    int32_t nqoi, double* ge2, double* ga2) {
+  for (int32_t g = 0; g < nqoi; ++g) {
+    ge2[g] = 0.0;
+    ga2[g] = 0.0;
+  }
+  for (int32_t s = 0; s < num; ++s) {
+    ge2[qoi[s]] += e2[s];
+    ga2[qoi[s]] += a2[s];
+  }
+}
+
 /* Compression factor, aggregated over subdomains (Section 2 Eq. for CF;
  * Section 3.2 aggregate over partitions): sum m_i n_i / sum k_i (s_i + n_i),
  * where s_i is the number of rows stored for part i (s = NULL: s_i = m_i;
@@ -332,6 +376,10 @@ double orc_compression_factor(int32_t num, const int64_t* m, const int64_t* s_ro
   return den > 0.0 ? num_ / den : INFINITY;
 }
 
+int orc_spid_kqr(const double* A, int64_t m, int64_t n, int64_t ld, int32_t l, int32_t kmax,
+                 double tol, double u_mode, uint64_t seed, double* Y, int32_t* J, int32_t* k_out,
+                 int32_t* kqr_out, double* R, double* C, double* e2, double* a2);
+
 /* Whole SPID on one subdomain: sketch, mgsqr with pivoting, rank guard,
  * coefficients, reconstruction error.  Outputs may be NULL except J, k_out,
  * C.  Y: l x n, R: kmax x n row-major, C: kmax x n row-major (rows >= k are
@@ -339,6 +387,15 @@ double orc_compression_factor(int32_t num, const int64_t* m, const int64_t* s_ro
 int orc_spid(const double* A, int64_t m, int64_t n, int64_t ld, int32_t l, int32_t kmax,
              double tol, double u_mode, uint64_t seed, double* Y, int32_t* J, int32_t* k_out,
              double* R, double* C, double* e2, double* a2) {
+  return orc_spid_kqr(A, m, n, ld, l, kmax, tol, u_mode, seed, Y, J, k_out, NULL, R, C, e2, a2);
+}
+
+/* As orc_spid, and kqr_out (may be NULL) receives the number of pivots the
+ * QR produced before the rank guard: the guard cut the rank (an informational
+ * outcome, reading of the spec guard) exactly when *k_out < *kqr_out. */
+int orc_spid_kqr(const double* A, int64_t m, int64_t n, int64_t ld, int32_t l, int32_t kmax,
+                 double tol, double u_mode, uint64_t seed, double* Y, int32_t* J, int32_t* k_out,
+                 int32_t* kqr_out, double* R, double* C, double* e2, double* a2) {
   double* Yw = (double*)malloc(sizeof(double) * (size_t)l * (size_t)(n > 0 ? n : 1));
   double* Rw = (double*)malloc(sizeof(double) * (size_t)kmax * (size_t)(n > 0 ? n : 1));
   orc_sketch(A, m, n, ld, l, seed, Yw);
@@ -353,6 +410,7 @@ int orc_spid(const double* A, int64_t m, int64_t n, int64_t ld, int32_t l, int32
   if (R) memcpy(R, Rw, sizeof(double) * (size_t)kmax * (size_t)n);
   if (e2 && a2) orc_reconstruct_error(A, m, n, ld, J, keff, C, NULL, 0, e2, a2);
   *k_out = keff;
+  if (kqr_out) *kqr_out = k;
   free(Yw);
   free(Rw);
   return 0;
@@ -367,15 +425,16 @@ int orc_spid(const double* A, int64_t m, int64_t n, int64_t ld, int32_t l, int32
 int orc_spid_batch(const double* window, int32_t num, const int64_t* m, const int64_t* n,
                    const int64_t* off, const int64_t* ld, int32_t l, int32_t kmax, double tol,
                    double u_mode, uint64_t seed, double* Y, int32_t* J, int32_t* k,
-                   double* C, double* e2, double* a2) {
+                   int32_t* kqr, double* C, double* e2, double* a2) {
   int64_t* coff = (int64_t*)malloc(sizeof(int64_t) * (size_t)(num + 1));
   coff[0] = 0;
   for (int32_t s = 0; s < num; ++s) coff[s + 1] = coff[s] + n[s];
 #pragma omp parallel for schedule(dynamic, 1)
   for (int32_t s = 0; s < num; ++s) {
-    orc_spid(window + off[s], m[s], n[s], ld[s], l, kmax, tol, u_mode, seed,
-             Y ? Y + (int64_t)l * coff[s] : NULL, J + (int64_t)kmax * s, k + s, NULL,
-             C + (int64_t)kmax * coff[s], e2 ? e2 + s : NULL, a2 ? a2 + s : NULL);
+    orc_spid_kqr(window + off[s], m[s], n[s], ld[s], l, kmax, tol, u_mode, seed,
+                 Y ? Y + (int64_t)l * coff[s] : NULL, J + (int64_t)kmax * s, k + s,
+                 kqr ? kqr + s : NULL, NULL, C + (int64_t)kmax * coff[s], e2 ? e2 + s : NULL,
+                 a2 ? a2 + s : NULL);
   }
   free(coff);
   return 0;
