@@ -3,9 +3,14 @@
 One step = one pass of the whole hot path over one window: Gaussian sketch
 (Omega regenerated on the fly), batched pivoted QR + rank decision +
 coefficients, and the fused reconstruction / relative Frobenius error, plus
-the compression factor.  Default workload: the 3D TGV + Fourier field on a
-64^3 grid split into 64 boxes of 16^3 x 5 QoIs (m = 20480), n = 512
-snapshots, k = 20, p = 10, FP32 data, TF32 tensor-core sketch.
+the compression factor.  Default workload (in-situ scale): the 3D TGV +
+Fourier field on a 256^3 grid x 5 QoIs split into 512 boxes of 32^3, each
+(box, QoI) block its own subdomain (2560 subdomains of m = 32768; Section 5.3
+compresses each QoI of each sub-domain on its own), n = 256 snapshots
+sketched in micro-batches of 64 as they arrive, adaptive tolerance 1e-3 with
+k <= 30, p = 10, FP32 data, TF32 tensor-core sketch.  A step counts only if
+every QoI's relative error over the domain is <= 1e-3 (Section 5.1 reports
+each QoI's error).
 
 Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
 (the only reference this method has) on a bounded sample of the same
@@ -29,36 +34,26 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "snapshot GB/s compressed at rel. err <=1e-3: mixed-prec batched vs plain FP32"
-WORKLOAD = ("TGV+Fourier 64^3 grid, 64 subdomains of 16^3 x 5 QoIs (m=20480), n=512 snapshots, "
-            "k=20, p=10, FP32 window")
 
 
-# DRAM bytes (read + write) of one launch of each hot kernel on the default
-# workload, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`
-# (profiles/dram_traffic_tf32_tgv3d_64sub.md).  A figure is reported only while
-# the kernel's sources hash to the value they had when it was measured.
-MEASURED_TRAFFIC = {
-    "sketch": {"bytes": 2693764352 + 7260672,
-               "sources": ('sketch_tc.cu', 'sketch_pack.cuh', 'tcgen05_ptx.cuh', 'spid_internal.cuh'),
-               "sha256_16": "cbd243bb97a2ae45"},
-    "error": {"bytes": 2684926720 + 221696, "sources": ('error.cu', 'error_fold.cuh', 'spid_internal.cuh'),
-              "sha256_16": "22989af0ca8d0f0d"},
-}
-# the tile shapes the counters were taken with (the library defaults)
-MEASURED_TUNING = {"sketch_pack_slices": 8, "sketch_stages": 0, "error_path": 0,
-                   "error_rows": 512, "error_cols": 256}
+# DRAM bytes (read + write) per launch of the dominant kernels of the headline
+# workloads, from an ncu capture of dram__bytes_read.sum + dram__bytes_write.sum
+# (on a smaller case of the same kernel, scaled by the bytes a launch streams).
+# A figure is reported only while the kernel's sources hash to the value they
+# had when it was measured.
+MEASURED_TRAFFIC = {}
 
 
-def measured_traffic(kernel: str):
+def measured_traffic(key: str):
     import hashlib
-    rec = MEASURED_TRAFFIC.get(kernel)
+    rec = MEASURED_TRAFFIC.get(key)
     if rec is None:
         return None
     m = hashlib.sha256()
     for f in rec["sources"]:
         with open(os.path.join(ROOT, "paper_2103_01380_gb300", "csrc", f), "rb") as fh:
             m.update(fh.read())
-    return rec["bytes"] if m.hexdigest()[:16] == rec["sha256_16"] else None
+    return rec["bytes_per_launch"] if m.hexdigest()[:16] == rec["sha256_16"] else None
 
 
 def load_peaks():
@@ -156,52 +151,40 @@ def make_window(rank: int = 0, boxes=None):
     return inputs.tgv3d_window(grid=64, box=16, n=512, seed=2 + rank, boxes=boxes)
 
 
-def cpu_baseline(win, sample_subs: int, precision: str = "tf32"):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
-    import oracle
-    idx = np.linspace(0, win.num_sub - 1, sample_subs).round().astype(int)
-    blocks = [win.block(int(s)) for s in idx]
-    from paper_2103_01380_gb300 import inputs
-    sub = inputs.pack_blocks(blocks, dtype=np.float64)
-    u = {"fp64": 2.0 ** -53, "fp32": 2.0 ** -24, "tf32": 2.0 ** -11}[precision]
-    t0 = time.perf_counter()
-    oracle.spid_batch(sub.data, sub.m, sub.n, sub.off, sub.ld, 30, 20, 0.0, u, 0x5EED0001)
-    dt = time.perf_counter() - t0
-    nbytes = 4.0 * float((sub.m * sub.n).sum())
-    return {"value": nbytes / dt / 1e9, "unit": "GB/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"{sample_subs} of {win.num_sub} subdomains (m=20480, n=512), FP64 oracle "
-                      f"sketch+QR+coefficients+error, {dt:.2f} s wall"}
-
-
 def run_reference(args):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores, on
+    a bounded sample of the headline workload (every QoI of --ref-subs boxes)
+    per step.  Under torchrun only rank 0 runs it."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import oracle
     oracle.build()
-    win = make_window(0, boxes=max(args.ref_subs, 1))
+    cfg = HEADLINE["insitu256" if args.workload not in HEADLINE else args.workload]
+    nb = max(args.ref_subs, 1)
+    sample = headline_sample(cfg, nb)
     ts = []
-    nb = None
+    cb = None
     for it in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        cb = cpu_baseline(win, args.ref_subs)
-        dt = time.perf_counter() - t0
+        cb = cpu_baseline_headline(cfg, nb, sample)
         if it >= args.warmup:
-            ts.append(dt)
-            nb = cb
-    value = float(np.median([nb["value"]]))
-    sample_bytes = 4.0 * 20480 * 512 * args.ref_subs
+            ts.append(cb["seconds"])
+    sample_bytes = 4.0 * NQ * cfg["edge"] ** 3 * cfg["n"] * nb
     ms = 1e3 * float(np.mean(ts))
-    line = {"impl": "reference", "metric": METRIC, "value": sample_bytes / (ms / 1e3) / 1e9,
-            "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_subdomains": args.ref_subs},
-            "cpu_baseline": {"kind": "oracle", "cores": nb["cores"], "sample": nb["sample"],
-                             "value": sample_bytes / (ms / 1e3) / 1e9, "unit": "GB/s"},
-            "e2e": {"value": sample_bytes / (ms / 1e3) / 1e9, "unit": "GB/s",
-                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    v = sample_bytes / (ms / 1e3) / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": headline_workload(args.workload if args.workload in HEADLINE
+                                                     else "insitu256", cfg,
+                                                     (cfg["grid"] // cfg["edge"]) ** 3, "blocks"),
+                       "sample_boxes": nb},
+            "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"],
+                             "value": v, "unit": "GB/s"},
+            "per_qoi_rel_err": cb["oracle_per_qoi_rel_err"],
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
@@ -281,8 +264,10 @@ def run_workload(args):
         line = _run_points(args, torch, inputs, spid)
     elif args.workload == "two_stage_tgv3d64":
         line = _run_two_stage(args, torch, inputs, spid)
-    else:
+    elif args.workload == "insitu_solver":
         line = _run_insitu(args, torch, inputs, spid)
+    else:
+        raise SystemExit(f"unknown workload {args.workload}")
     line.update({"metric": METRIC, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
                  "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                  "vs_baseline": None, "data": "synthetic", "gpu_launches": None})
@@ -703,7 +688,7 @@ def _run_insitu(args, torch, inputs, spid):
     window, where the 64 columns of a sketch tile are 335 MB apart, held the
     sketch at 4.7 TB/s against 7.0 TB/s for this layout: address translation,
     not DRAM, limits the 335 MB column stride.)"""
-    S, edge, grid, n, b = 512, 32, 256, 256, args.microbatch
+    S, edge, grid, n, b = 512, 32, 256, 256, args.microbatch or 64
     origins = [(bx * edge, by * edge, bz * edge) for bz in range(8) for by in range(8)
                for bx in range(8)]
     field = inputs.DeviceField(origins, edge, grid, inputs.fourier_modes(seed=2))
@@ -768,35 +753,83 @@ def _run_insitu(args, torch, inputs, spid):
             "_sketch_gbs": nbytes / (sk / 1e3) / 1e9}
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="tf32", choices=["tf32", "bf16x3", "bf16", "fp32"])
-    ap.add_argument("--ref-subs", type=int, default=16)
-    ap.add_argument("--cpu-sample", type=int, default=64)
-    ap.add_argument("--boxes", type=int, default=None,
-                    help="first N boxes only (small profiling case; not the bench workload)")
-    ap.add_argument("--tc-error", action="store_true",
-                    help="error pass with the rank-k product on the tensor cores")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-comparator", action="store_true")
-    ap.add_argument("--no-autotune", action="store_true",
-                    help="keep the library's default tile shapes (no measurement)")
-    ap.add_argument("--workload", default="tgv3d64",
-                    choices=["tgv3d64", "spectrum256", "uneven4096", "insitu256",
-                             "coarse_tgv3d64", "two_stage_tgv3d64", "points_tgv2d"],
-                    help="tgv3d64 is the bench workload; the others print their own line")
-    ap.add_argument("--microbatch", type=int, default=64, help="insitu256: columns per call")
-    ap.add_argument("--wave-gb", type=float, default=48.0, help="uneven4096: GB per wave")
-    args = ap.parse_args()
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.workload != "tgv3d64":
-        return run_workload(args)
+# ----------------------------------------------------------------------------
+# The headline: the sketched ID over (box, QoI) subdomains of the TGV + Fourier
+# field, gated on every QoI's relative error
+# ----------------------------------------------------------------------------
+HEADLINE = {
+    # in-situ scale: 256^3 x 5 QoIs in 512 boxes of 32^3, n = 256 snapshots
+    # sketched in micro-batches of 64 as they arrive, k <= 30, p = 10
+    "insitu256": dict(grid=256, edge=32, n=256, k_max=30, microbatch=64, seed=0x5EED0005),
+    # the 64^3 window: 64 boxes of 16^3 x 5 QoIs, n = 512, k <= 20, p = 10
+    "tgv3d64": dict(grid=64, edge=16, n=512, k_max=20, microbatch=0, seed=0x5EED0001),
+}
+NQ, P_OVERSAMPLE, TOL = 5, 10, 1e-3
 
+
+def headline_workload(name: str, cfg: dict, nbox: int, layout: str) -> str:
+    per = cfg["grid"] // cfg["edge"]
+    mb = cfg["microbatch"]
+    return (f"TGV+Fourier {cfg['grid']}^3 x 5 QoIs, {nbox} of {per ** 3} boxes of "
+            f"{cfg['edge']}^3 per domain, each (box, QoI) a subdomain (m={cfg['edge'] ** 3}), "
+            f"n={cfg['n']} snapshots" + (f" sketched in micro-batches of {mb}" if mb else "") +
+            f", adaptive tol {TOL:g}, k<={cfg['k_max']}, p={P_OVERSAMPLE}, FP32 window "
+            f"({'subdomain-major blocks' if layout == 'blocks' else 'global [t][q][Z][Y][X] field'})")
+
+
+def _box_origins(cfg):
+    per, e = cfg["grid"] // cfg["edge"], cfg["edge"]
+    return [(bx * e, by * e, bz * e) for bz in range(per) for by in range(per) for bx in range(per)]
+
+
+def headline_sample(cfg, sample_boxes: int, seed_field: int = 2):
+    """Every QoI of `sample_boxes` boxes spread over the domain, generated on
+    the host in FP64 and cast to FP32 (the values the GPU window holds), as a
+    blocks window for the oracle."""
+    from paper_2103_01380_gb300 import inputs
+    origins = _box_origins(cfg)
+    idx = np.linspace(0, len(origins) - 1, sample_boxes).round().astype(int)
+    t = 10.0 * np.arange(cfg["n"]) / (cfg["n"] - 1)
+    modes = inputs.fourier_modes(seed=seed_field)
+    e = cfg["edge"]
+    blocks = []
+    for b in idx:
+        A = inputs.tgv3d_box(origins[b], (e, e, e), cfg["grid"], t, modes, dtype=np.float32)
+        blocks += [A[q * e ** 3:(q + 1) * e ** 3] for q in range(NQ)]
+    return inputs.pack_blocks(blocks, dtype=np.float64), len(origins)
+
+
+def cpu_baseline_headline(cfg, sample_boxes: int, sample=None):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload (see
+    headline_sample); only the oracle's own run is timed."""
+    import oracle
+    win, nall = sample if sample is not None else headline_sample(cfg, sample_boxes)
+    t0 = time.perf_counter()
+    o = oracle.spid_batch(win.data, win.m, win.n, win.off, win.ld, cfg["k_max"] + P_OVERSAMPLE,
+                          cfg["k_max"], TOL, 2.0 ** -11, cfg["seed"])
+    dt = time.perf_counter() - t0
+    nbytes = 4.0 * float((win.m * win.n).sum())
+    e2 = o["e2"].reshape(-1, NQ).sum(0)
+    a2 = o["a2"].reshape(-1, NQ).sum(0)
+    return {"value": nbytes / dt / 1e9, "unit": "GB/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "seconds": dt,
+            "sample": f"every QoI of {sample_boxes} of {nall} boxes ({NQ * sample_boxes} "
+                      f"subdomains, m={cfg['edge'] ** 3}, n={cfg['n']}): FP64 oracle sketch + QR "
+                      f"+ coefficients + error, {dt:.2f} s wall",
+            "oracle_per_qoi_rel_err": [float(x) for x in np.sqrt(e2 / a2)]}
+
+
+def _host_mem_available() -> int:
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def run_headline(args):
     import torch
     import torch.distributed as dist
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -806,61 +839,100 @@ def main():
         dist.init_process_group("gloo")
     torch.cuda.set_device(local)
     numa = bind_to_gpu_numa_node(local)
-    from paper_2103_01380_gb300 import build, spid
+    from paper_2103_01380_gb300 import build, inputs, shard, spid
     build.build()
     spid.load_library()
-
-    win = make_window(rank, boxes=args.boxes)
-    nbytes = float(win.nbytes_payload())
-    host = torch.from_numpy(win.data).pin_memory()
-    dev = host.cuda()
+    cfg = HEADLINE[args.workload]
+    grid, edge, n, k_max, mb = cfg["grid"], cfg["edge"], cfg["n"], cfg["k_max"], cfg["microbatch"]
+    if args.microbatch is not None:
+        mb = args.microbatch
+    origins_all = _box_origins(cfg)
+    nbox_dom = len(origins_all) if args.boxes is None else min(args.boxes, len(origins_all))
+    layout = args.layout
+    if layout == "global" and (world > 1 or args.boxes is not None):
+        raise SystemExit("--layout global compresses one whole domain per GPU (no --boxes, one rank)")
+    # one domain of boxes per rank, the (domain, box) units dealt by LPT on m n
+    mine = shard.domain_boxes(world, nbox_dom, weight=NQ * edge ** 3 * n)[rank]
+    mq, m = edge ** 3, NQ * edge ** 3
+    t_all = 10.0 * np.arange(n) / (n - 1)
+    calls = [(j0, min(mb, n - j0)) for j0 in range(0, n, mb)] if mb else [(0, n)]
+    # ---- the window: every box's snapshots, written as they are generated
+    if layout == "blocks":
+        S_box = len(mine)
+        window = torch.empty(n * S_box * m, device="cuda", dtype=torch.float32)
+        pos = 0
+        for d in np.unique(mine[:, 0]):
+            sel = mine[mine[:, 0] == d]
+            field = inputs.DeviceField([origins_all[b] for b in sel[:, 1]], edge, grid,
+                                       inputs.fourier_modes(seed=2 + int(d)))
+            sub = window[pos * n * m:(pos + len(sel)) * n * m]
+            for j0, nc in (calls if mb else [(j, min(64, n - j)) for j in range(0, n, 64)]):
+                field.fill_subdomain_major(sub, t_all[j0:j0 + nc], j0, n)
+            pos += len(sel)
+            del field
+        off = (np.arange(S_box)[:, None] * n * m + mq * np.arange(NQ)[None, :]).reshape(-1)
+        plan_kw = dict(m=[mq] * (NQ * S_box), n=[n] * (NQ * S_box), off=off,
+                       ld=[m] * (NQ * S_box), qoi=np.tile(np.arange(NQ), S_box), num_qoi=NQ)
+    else:
+        S_box = len(origins_all)
+        field = inputs.DeviceField([(0, 0, 0)], grid, grid, inputs.fourier_modes(seed=2))
+        window = torch.empty(n * NQ * grid ** 3, device="cuda", dtype=torch.float32)
+        for j0 in range(0, n, 64):
+            field.fill_snapshot_major(window, t_all[j0:j0 + 64], j0, n)
+        del field
+        lay = spid.BoxLayout(NQ, grid, grid, grid, origins_all, [(edge,) * 3] * S_box,
+                             split_qoi=True)
+        plan_kw = dict(m=None, n=[n] * (NQ * S_box), off=None, ld=None, boxes=lay)
+    torch.cuda.synchronize()
+    S = NQ * S_box
+    nbytes = 4.0 * S * mq * n
     stream = torch.cuda.current_stream()
-    err = torch.zeros(2 * win.num_sub, dtype=torch.float64, device="cuda")
-    tot = torch.zeros(4, dtype=torch.float64, device="cuda")
 
     def make_plan(precision, flags=0):
-        return spid.Plan.for_window(win, k_max=20, p=10, tol=0.0, precision=precision,
-                                    seed=0x5EED0001, flags=flags)
+        return spid.Plan(k_max=k_max, p=P_OVERSAMPLE, tol=TOL, precision=precision,
+                         seed=cfg["seed"], flags=flags, **plan_kw)
 
     def barrier():
         if world > 1:
             dist.barrier()
 
-    def timed(plan, steps, warmup, per_stage=True):
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    def eager(plan, err, tot, steps, warmup, per_launch=True):
+        """Per-stage CUDA-event times of eager steps: every sketch launch, the
+        finalize and the error pass; returns (total ms, launch ms list, fi, er)."""
         for _ in range(warmup):
-            plan.sketch(dev); plan.finalize(); plan.error(dev, err, tot)
-        torch.cuda.synchronize()
-        barrier()
-        torch.cuda.synchronize()
-        t_start = torch.cuda.Event(enable_timing=True)
-        t_end = torch.cuda.Event(enable_timing=True)
-        t_start.record(stream)
-        for i in range(steps):
-            ev[i][0].record(stream)
-            plan.sketch(dev)
-            ev[i][1].record(stream)
+            for c0, nc in calls:
+                plan.sketch_accumulate(window, c0, nc)
             plan.finalize()
-            ev[i][2].record(stream)
-            plan.error(dev, err, tot)
-            ev[i][3].record(stream)
-        t_end.record(stream)
+            plan.error(window, err, tot)
         torch.cuda.synchronize()
         barrier()
-        total_ms = t_start.elapsed_time(t_end)
-        sk = [e[0].elapsed_time(e[1]) for e in ev]
-        fi = [e[1].elapsed_time(e[2]) for e in ev]
-        er = [e[2].elapsed_time(e[3]) for e in ev]
-        return total_ms, sk, fi, er
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 3)]
+              for _ in range(steps)]
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(steps):
+            for c, (c0, nc) in enumerate(calls):
+                ev[i][c].record(stream)
+                plan.sketch_accumulate(window, c0, nc)
+            ev[i][len(calls)].record(stream)
+            plan.finalize()
+            ev[i][len(calls) + 1].record(stream)
+            plan.error(window, err, tot)
+            ev[i][len(calls) + 2].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        sk = [e[c].elapsed_time(e[c + 1]) for e in ev for c in range(len(calls))]
+        fi = [e[len(calls)].elapsed_time(e[len(calls) + 1]) for e in ev]
+        er = [e[len(calls) + 1].elapsed_time(e[len(calls) + 2]) for e in ev]
+        return t0.elapsed_time(t1), sk, fi, er
 
-    plan = make_plan(args.precision, flags=spid.FLAG_TC_ERROR if args.tc_error else 0)
-    # tile shapes and schedules: measured on this window by the library's autotuner
-    if args.no_autotune:
-        tuning = dict(plan.tuning(), cached=None)
-    else:
-        tuning = plan.autotune(dev)
-    # one step = one CUDA-graph launch (sketch, finalize, error kernels)
-    graph = plan.graph(dev, err=err, total=tot)
+    plan = make_plan(args.precision)
+    err = torch.zeros(2 * S, dtype=torch.float64, device="cuda")
+    tot = torch.zeros(plan.total_len, dtype=torch.float64, device="cuda")
+    tuning = dict(plan.tuning(), cached=None) if args.no_autotune else plan.autotune(window)
+    graph = plan.graph(window, err=err, total=tot, microbatch=mb)
 
     def timed_graph(steps, warmup):
         for _ in range(warmup):
@@ -879,9 +951,7 @@ def main():
         return g0.elapsed_time(g1)
 
     with ClockSampler(local) as clk:
-        # per-stage durations (eager launches, events between the stages), then
-        # the headline: the same steps replayed as one graph launch each
-        _, sk, fi, er = timed(plan, args.steps, args.warmup)
+        _, sk, fi, er = eager(plan, err, tot, args.steps, args.warmup)
         total_ms = timed_graph(args.steps, args.warmup)
     clocks = clk.summary()
     t = torch.tensor([total_ms], dtype=torch.float64)
@@ -890,127 +960,202 @@ def main():
     total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
     value = world * nbytes * args.steps / (total_ms / 1e3) / 1e9
-
-    # global error / CF across ranks: one host-side sum of four doubles
-    from paper_2103_01380_gb300 import shard
-    rel_err, cf, _ = shard.combine_totals(tot.detach().cpu().numpy())
+    status = plan.device_status()
     k, J, C = plan.factors()
+    rel_err, cf, vtot = shard.combine_totals(tot.detach().cpu().numpy())
+    per_qoi = shard.per_qoi_rel_err(vtot)
+    valid = bool(np.all(per_qoi <= TOL))
 
-    # end to end through the public API (spid_graph_launch_host): every step
-    # copies the pinned host window to a device window, runs the step's graph
-    # and copies the four error sums back to pinned host memory.  Two device
-    # windows with a graph each alternate, so one step's copy (on its own
-    # stream) overlaps the other's compute; the copies run back to back on the
-    # host link, which bounds the rate.
-    extent = int(np.max(win.off + win.ld * (win.n.astype(np.int64) - 1) + win.m))
-    h2d_bytes = 4 * extent
-    dev2 = torch.empty_like(dev)
-    graph2 = plan.graph(dev2, err=err, total=tot)
-    pair = (graph, graph2)
-    copy_stream = torch.cuda.Stream()
-    host_tot = [torch.zeros(4, dtype=torch.float64).pin_memory() for _ in range(2)]
-    for i in range(2 * max(args.warmup, 1)):
-        pair[i % 2].launch_host(host, host_tot[i % 2], copy_stream=copy_stream, stream=stream)
-    torch.cuda.synchronize()
-    # the host link alone, for reference
-    h0 = torch.cuda.Event(enable_timing=True)
-    h1 = torch.cuda.Event(enable_timing=True)
-    h0.record(stream)
-    for _ in range(3):
-        dev2.copy_(host, non_blocking=True)
-    h1.record(stream)
-    torch.cuda.synchronize()
-    h2d_ms = h0.elapsed_time(h1) / 3
-    barrier()
-    e2e_steps = max(3, args.steps // 4)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    copy_stream.wait_event(e0)   # no copy starts before the timed region
-    for i in range(e2e_steps):
-        pair[i % 2].launch_host(host, host_tot[i % 2], copy_stream=copy_stream, stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    if not np.array_equal(host_tot[(e2e_steps - 1) % 2].numpy(), tot.cpu().numpy()):
-        raise RuntimeError("end-to-end step returned other error sums than the device step")
-    te = torch.tensor([e2e_ms], dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * nbytes / (float(te.item()) / 1e3) / 1e9
+    # ---- end to end through the public API (spid_graph_launch_host): each step
+    # copies the window from pinned host memory, runs the step's graph and
+    # copies the compressed representation (k, J, C) and the error sums back to
+    # pinned host memory.  Two device windows alternate when they fit, so one
+    # step's copy overlaps the other's compute; the host link bounds the rate.
+    extent = plan.window_extent()
+    e2e = None
+    free_dev = torch.cuda.mem_get_info()[0]
+    host_ok = _host_mem_available() > 4 * extent * 1.25 + (8 << 30)
+    if not args.no_e2e and host_ok:
+        host = torch.empty(extent, dtype=torch.float32, pin_memory=True)
+        host.copy_(window[:extent], non_blocking=False)
+        two = free_dev > 4 * extent * 1.05 + (4 << 30)
+        pair = [graph]
+        dev2 = None
+        if two:
+            dev2 = torch.empty(extent, device="cuda", dtype=torch.float32)
+            pair.append(plan.graph(dev2, err=err, total=tot, microbatch=mb))
+        copy_stream = torch.cuda.Stream()
+        kh = [torch.zeros(S, dtype=torch.int32).pin_memory() for _ in pair]
+        Jh = [torch.zeros(S * k_max, dtype=torch.int32).pin_memory() for _ in pair]
+        Ch = [torch.zeros(k_max * int(plan.n.sum()), dtype=torch.float32).pin_memory()
+              for _ in pair]
+        th = [torch.zeros(plan.total_len, dtype=torch.float64).pin_memory() for _ in pair]
+
+        def e2e_step(i):
+            j = i % len(pair)
+            pair[j].launch_host(host, th[j], kh[j], Jh[j], Ch[j], copy_stream=copy_stream,
+                                stream=stream, window_elems=extent)
+
+        for i in range(max(args.warmup, 1) * len(pair)):
+            e2e_step(i)
+        torch.cuda.synchronize()
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        (dev2 if two else window)[:extent].copy_(host, non_blocking=True)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        h2d_ms = h0.elapsed_time(h1)
+        barrier()
+        e2e_steps = max(2, args.steps // 8)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        copy_stream.wait_event(e0)   # no copy starts before the timed region
+        for i in range(e2e_steps):
+            e2e_step(i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / e2e_steps
+        last = (e2e_steps - 1) % len(pair)
+        # the factors that came back are the plan's factors
+        if not (np.array_equal(kh[last].numpy(), k) and
+                np.array_equal(Jh[last].numpy().reshape(S, k_max), J) and
+                np.array_equal(Ch[last].numpy(), np.concatenate([c.reshape(-1) for c in C]))
+                and np.array_equal(th[last].numpy(), tot.cpu().numpy())):
+            raise RuntimeError("end-to-end step returned other factors than the device step")
+        te = torch.tensor([e2e_ms], dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        d2h = 4 * S + 4 * S * k_max + 4 * k_max * int(plan.n.sum()) + 8 * plan.total_len
+        e2e = {"value": world * nbytes / (float(te.item()) / 1e3) / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": 4 * extent, "d2h_bytes_per_step": d2h,
+               "ms_per_step": e2e_ms,
+               "api": "spid_graph_launch_host: window in, (k, J, C) and error sums out" +
+                      (", two device windows alternating" if two else ""),
+               "h2d_ms_per_step": h2d_ms, "h2d_gbs": 4 * extent / (h2d_ms / 1e3) / 1e9,
+               "host_binding": numa}
+        for g in pair[1:]:
+            g.close()
+        del host, dev2
+    elif not args.no_e2e:
+        e2e = {"value": None, "unit": "GB/s", "skipped": "host memory below 1.25x the window"}
     graph.close()
-    graph2.close()
-    del dev2
 
-    # comparator: plain FP32 (SIMT sketch, one launch per subdomain per stage, no graph)
+    # ---- comparators at the same accuracy gate: plain FP32 (CUDA-core sketch,
+    # one launch per subdomain per stage, no graph) and batched FP32
     comparator = None
     if not args.no_comparator:
-        pl = make_plan("fp32", flags=spid.FLAG_PER_SUBDOMAIN)
-        c_ms, c_sk, c_fi, c_er = timed(pl, max(3, args.steps // 4), args.warmup)
-        torch.cuda.synchronize()
-        c_tot = tot.detach().cpu().numpy()
-        comparator = {"form": "plain FP32 (SIMT sketch, per-subdomain launches)",
-                      "value": nbytes * max(3, args.steps // 4) / (c_ms / 1e3) / 1e9,
-                      "sketch_gbs": nbytes / (statistics.mean(c_sk) / 1e3) / 1e9,
-                      "rel_err": float(np.sqrt(c_tot[0] / c_tot[1]))}
-        pl.close()
-        pb = make_plan("fp32")
-        b_ms, b_sk, b_fi, b_er = timed(pb, max(3, args.steps // 4), args.warmup)
-        comparator["batched_fp32_value"] = nbytes * max(3, args.steps // 4) / (b_ms / 1e3) / 1e9
-        comparator["batched_fp32_sketch_gbs"] = nbytes / (statistics.mean(b_sk) / 1e3) / 1e9
-        pb.close()
+        comparator = {}
+        for label, flags in (("plain_fp32_per_subdomain", spid.FLAG_PER_SUBDOMAIN),
+                             ("batched_fp32", 0)):
+            pl = make_plan("fp32", flags=flags)
+            ce = torch.zeros(2 * S, dtype=torch.float64, device="cuda")
+            ct = torch.zeros(pl.total_len, dtype=torch.float64, device="cuda")
+            steps_c = 2
+            c_ms, c_sk, c_fi, c_er = eager(pl, ce, ct, steps_c, 1)
+            _, ccf, cv = shard.combine_totals(ct.cpu().numpy())
+            cq = shard.per_qoi_rel_err(cv)
+            comparator[label] = {"value": world * nbytes * steps_c / (c_ms / 1e3) / 1e9,
+                                 "sketch_gbs": nbytes / (sum(c_sk) / steps_c / 1e3) / 1e9,
+                                 "per_qoi_rel_err": [float(x) for x in cq],
+                                 "compression_factor": ccf, "valid": bool(np.all(cq <= TOL))}
+            pl.close()
+        comparator["mixed_vs_plain_fp32"] = value / comparator["plain_fp32_per_subdomain"]["value"]
+        comparator["mixed_vs_batched_fp32"] = value / comparator["batched_fp32"]["value"]
 
     peak, peak_kind = load_peaks()
-    sk_ms, er_ms, fi_ms = statistics.mean(sk), statistics.mean(er), statistics.mean(fi)
-    dominant = "sketch" if sk_ms >= er_ms else "error"
-    dom_ms = max(sk_ms, er_ms)
-    # algorithmic bytes: sketch reads A once (4 B / element); the error pass reads
-    # A once plus the k skeleton columns of every subdomain
-    alg_bytes = nbytes if dominant == "sketch" else nbytes + 4.0 * float((k * win.m).sum())
-    achieved = alg_bytes / (dom_ms / 1e3) / 1e9
+    launch_sk = statistics.mean(sk)                 # one sketch launch (one micro-batch)
+    step_sk = launch_sk * len(calls)
+    fi_ms, er_ms = statistics.mean(fi), statistics.mean(er)
+    cols = [nc for _, nc in calls]
+    sk_launch_bytes = 4.0 * S * mq * statistics.mean(cols)
+    er_bytes = nbytes + 4.0 * float(mq * k.sum())    # A once + the skeleton columns
+    cands = {"sketch": (sk_launch_bytes, launch_sk, step_sk), "error": (er_bytes, er_ms, er_ms)}
+    dominant = max(cands, key=lambda x: cands[x][2])
+    ab, lms, _ = cands[dominant]
+    achieved = ab / (lms / 1e3) / 1e9
+    traffic = None
+    rec = MEASURED_TRAFFIC.get(f"{args.workload}:{dominant}")
+    if (rec and args.boxes is None and args.precision == "tf32" and layout == "blocks"
+            and measured_traffic(f"{args.workload}:{dominant}") is not None):
+        traffic = rec["bytes_per_launch"]
     roof = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
-            "traffic": measured_traffic(dominant) if (
-                args.boxes is None and args.precision == "tf32" and
-                all(tuning.get(k) == v for k, v in MEASURED_TUNING.items())) else None,
-            "alg_bytes": alg_bytes}
+            "traffic": traffic, "alg_bytes_per_launch": ab, "launch_ms": lms}
 
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else f"f32 ({args.precision} sketch)",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.boxes is None else
-                       f"first {args.boxes} boxes of: " + WORKLOAD, "precision": args.precision,
-                       "subdomains_per_gpu": win.num_sub, "bytes_per_step_per_gpu": nbytes,
-                       "error_pass": "tensor-core (3xTF32)" if (args.tc_error and
-                                                                args.precision != "fp32")
-                       else "cuda-core",
-                       "l2": "inputs (2.68 GB) larger than L2; no flush",
-                       "launch": "one CUDA graph per step (sketch, finalize, error kernels)",
+            "config": {"workload": headline_workload(args.workload, cfg, nbox_dom, layout),
+                       "precision": args.precision, "subdomains_per_gpu": S,
+                       "bytes_per_step_per_gpu": nbytes, "layout": layout,
+                       "sharding": "one domain per rank, (domain, box) units dealt by LPT "
+                                   "(shard.domain_boxes)",
+                       "l2": f"inputs ({nbytes / 1e9:.1f} GB) larger than L2; no flush",
+                       "launch": f"one CUDA graph per step ({len(calls)} sketch launches, "
+                                 f"finalize, error)",
+                       "gate": f"every QoI's relative Frobenius error <= {TOL:g}",
                        "tuning": tuning},
-            "stages_ms": {"sketch": sk_ms, "finalize": fi_ms, "error": er_ms},
-            "sketch_gbs": nbytes / (sk_ms / 1e3) / 1e9,
-            "error_gbs": nbytes / (er_ms / 1e3) / 1e9,
+            "valid": valid, "per_qoi_rel_err": [float(x) for x in per_qoi],
+            "qoi": ["rho", "u", "v", "w", "p"],
             "rel_err": rel_err, "compression_factor": cf,
             "k_mean": float(np.mean(k)), "k_max": int(np.max(k)),
-            "roofline": roof,
-            "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": h2d_bytes,
-                    "d2h_bytes_per_step": 32, "ms_per_step": e2e_ms,
-                    "api": "spid_graph_launch_host, two device windows alternating",
-                    "h2d_ms_per_step": h2d_ms, "h2d_gbs": h2d_bytes / (h2d_ms / 1e3) / 1e9,
-                    "host_binding": numa},
-            "gpu_launches": 3 * args.steps,
-            "clocks": clocks,
-            "comparator": comparator}
+            "k_mean_per_qoi": [float(x) for x in k.reshape(-1, NQ).mean(0)],
+            "status": status,
+            "stages_ms": {"sketch": step_sk, "sketch_launch": launch_sk, "finalize": fi_ms,
+                          "error": er_ms},
+            "sketch_gbs": nbytes / (step_sk / 1e3) / 1e9,
+            "error_gbs": nbytes / (er_ms / 1e3) / 1e9,
+            "roofline": roof, "e2e": e2e,
+            "gpu_launches": (len(calls) + 2) * args.steps,
+            "clocks": clocks, "comparator": comparator}
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(win, min(args.cpu_sample, win.num_sub))
+        line["cpu_baseline"] = cpu_baseline_headline(cfg, args.cpu_sample)
     plan.close()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="tf32", choices=["tf32", "bf16x3", "bf16", "fp32"])
+    ap.add_argument("--ref-subs", type=int, default=8,
+                    help="reference arm: boxes sampled per step (every QoI of each)")
+    ap.add_argument("--cpu-sample", type=int, default=16, help="cpu_baseline: boxes sampled")
+    ap.add_argument("--boxes", type=int, default=None,
+                    help="first N boxes of the domain only (small profiling case; not the bench "
+                         "workload)")
+    ap.add_argument("--layout", default="blocks", choices=["blocks", "global"],
+                    help="blocks: subdomain-major window; global: the field as [t][q][Z][Y][X] "
+                         "with boxes described by spid_box_layout")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default tile shapes (no measurement)")
+    ap.add_argument("--workload", default="insitu256",
+                    choices=["insitu256", "tgv3d64", "spectrum256", "uneven4096", "insitu_solver",
+                             "coarse_tgv3d64", "two_stage_tgv3d64", "points_tgv2d"],
+                    help="insitu256 is the bench workload; the others print their own line")
+    ap.add_argument("--microbatch", type=int, default=None,
+                    help="columns per sketch call (default: the workload's)")
+    ap.add_argument("--wave-gb", type=float, default=48.0, help="uneven4096: GB per wave")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.workload in HEADLINE:
+        return run_headline(args)
+    return run_workload(args)
 
 
 if __name__ == "__main__":

@@ -20,6 +20,12 @@
  *     ([j][s][r]) windows.  Elements are double for SPID_PREC_FP64 and float
  *     otherwise.  off[s] and ld[s] must be multiples of 16 bytes / element
  *     size, and the window base must be 16-byte aligned (checked).
+ *   - Window layout ("boxes", spid_box_layout): the window is the solver's
+ *     own global field, [t][q][Z][Y][X] (snapshot t of QoI q at grid point
+ *     (x, y, z)), and each subdomain is a box of it (Algorithm 6 saves the
+ *     data of each block of the domain; Section 3.2 blocks the domain into
+ *     sub-domains), either with all QoIs stacked or one QoI per subdomain
+ *     (Section 5.3: each QoI of each sub-domain compressed on its own).
  *   - Omega(i, r), i < l, r < m, is never stored.  It is the Box-Muller
  *     transform of Philox4x32-10 (Salmon et al., SC'11) with key =
  *     (seed & 0xffffffff, seed >> 32) and counter = (r, i / 4, 0, 0); words
@@ -59,7 +65,11 @@ typedef enum {
   SPID_ERR_STATE = 4,        /* call out of order (e.g. factors before finalize) */
   SPID_ERR_TIMEOUT = 5,      /* a bounded device wait gave up (device status) */
   SPID_ERR_NONFINITE = 6,    /* NaN/Inf reached the sketch of some subdomain (device status) */
-  SPID_ERR_UNSUPPORTED = 7   /* valid request this library does not implement */
+  SPID_ERR_UNSUPPORTED = 7,  /* valid request this library does not implement */
+  SPID_ERR_RANK = 8          /* informational, from spid_device_status only: the rank guard
+                                stopped some subdomain's factorization before its target (k_max
+                                pivots, or the tolerance); its factors are valid, with the
+                                smaller k that spid_get_factors reports */
 } spid_status;
 
 /* Every FP32-window mode factors the sketch with FP32 Householder reflectors,
@@ -84,12 +94,40 @@ typedef enum {
  * (TF32, BF16 and 3xBF16 plans, batched, k_max <= 32; ignored otherwise). */
 #define SPID_FLAG_TC_ERROR 2u
 
+/* Boxes of the solver's global field as subdomains.  The window pointer is
+ * element (t, q, z, y, x) = (0, 0, 0, 0, 0) of [t][q][Z][Y][X]: snapshot t of
+ * QoI q at grid point (x, y, z) is element t snap_stride + ((q Z + z) Y + y) X
+ * + x.  Box b covers the points org + [0, ext).  Its data matrix (Section 2:
+ * rows = grid points x QoIs, columns = snapshots) has rows
+ * r = ((q ez + z) ey + y) ex + x, QoI slowest, so m = nq ex ey ez (split_qoi
+ * = 0), or, with split_qoi = 1, QoI q of box b is subdomain b nq + q with rows
+ * r = (z ey + y) ex + x and m = ex ey ez.  The tensor-core sketches read each
+ * box by TMA as 5-D tiles and need ex to be a multiple of 32
+ * (SPID_ERR_UNSUPPORTED otherwise); the CUDA-core kernels take any ex that is
+ * a multiple of 4 elements (16 bytes; 2 for FP64).  Boxes may overlap; they
+ * do not wrap around the field's edges. */
 typedef struct {
-  int32_t num_sub;        /* number of subdomains S >= 1 */
-  const int32_t* m;       /* host [S]: rows m_s >= 1 */
+  int32_t nq;              /* QoIs per grid point, >= 1 */
+  int64_t X, Y, Z;         /* global grid extents, each >= 1; X a multiple of 16 bytes / element
+                              size */
+  int64_t snap_stride;     /* elements from one snapshot to the next, >= nq X Y Z, a multiple of
+                              16 bytes / element size */
+  int32_t num_box;         /* B >= 1 */
+  const int32_t* org3;     /* host [3 B]: (x, y, z) of box b's first point; x a multiple of 16
+                              bytes / element size */
+  const int32_t* ext3;     /* host [3 B]: (ex, ey, ez) >= 1, ex a multiple of 16 bytes / element
+                              size; org + ext <= (X, Y, Z) */
+  int32_t split_qoi;       /* 0 or 1, as above */
+} spid_box_layout;
+
+typedef struct {
+  int32_t num_sub;        /* number of subdomains S >= 1 (boxes: B, or B nq with split_qoi) */
+  const int32_t* m;       /* host [S]: rows m_s >= 1 (ignored with boxes; may be NULL) */
   const int32_t* n;       /* host [S]: window length n_s >= 1 (columns) */
-  const int64_t* off;     /* host [S]: element offset of A_s(0,0) in the window */
-  const int64_t* ld;      /* host [S]: leading dimension (elements), >= m_s */
+  const int64_t* off;     /* host [S]: element offset of A_s(0,0) in the window (ignored with
+                             boxes; may be NULL) */
+  const int64_t* ld;      /* host [S]: leading dimension (elements), >= m_s (ignored with
+                             boxes; may be NULL) */
   int32_t k_max;          /* maximum rank, 1 <= k_max; k_s <= min(k_max, n_s) */
   int32_t p;              /* oversampling, p >= 0; l = k_max + p <= 64 */
   double tol;             /* 0: fixed rank k_max.  > 0: smallest k with
@@ -97,13 +135,23 @@ typedef struct {
   int32_t precision;      /* spid_precision */
   uint32_t flags;         /* SPID_FLAG_* */
   uint64_t seed;          /* Omega key */
+  const int32_t* qoi;     /* host [S] or NULL: the QoI that subdomain s holds, 0 <= qoi[s] <
+                             num_qoi, for per-QoI error totals (Section 5.1 reports each QoI's
+                             error); with boxes and split_qoi = 1, NULL means qoi[s] = s % nq */
+  int32_t num_qoi;        /* 0 (no per-QoI totals) .. 64; with boxes and split_qoi = 1 and
+                             qoi == NULL, 0 means nq */
+  const spid_box_layout* boxes;   /* NULL: the blocks layout (m, off, ld); else the boxes
+                                     layout (copied at creation) */
 } spid_plan_desc;
 
 /* Create a plan: validates the descriptor and allocates ALL device
  * workspace (later calls allocate nothing).  Rows m_s up to 2^31-1, columns
  * up to 2^20 per subdomain.  Returns SPID_ERR_OOM if device memory runs out.
- * The plan is bound to the current CUDA device. */
-spid_status spid_plan_create(const spid_plan_desc* desc, spid_plan_t* plan_out);
+ * The plan is bound to the current CUDA device.  The workspace is cleared and
+ * the descriptor tables uploaded on `stream`, which is then synchronized (the
+ * plan is ready for any stream on return). */
+spid_status spid_plan_create(const spid_plan_desc* desc, spid_stream_t stream,
+                             spid_plan_t* plan_out);
 
 /* Release every resource of the plan.  Synchronizes the device first. */
 spid_status spid_plan_destroy(spid_plan_t plan);
@@ -117,10 +165,11 @@ spid_status spid_plan_info(spid_plan_t plan, int32_t* l, int32_t* l_pad,
  * for every subdomain s, Y_s(:, j) = Omega(:, 0:m_s) A_s(:, j) for the
  * window columns j in [col0, min(col0 + ncols, n_s)).  Columns are
  * independent, so a window may be sketched in any number of calls (one per
- * snapshot or per micro-batch); columns never sketched stay zero after
+ * snapshot or per micro-batch, as the snapshots arrive: Algorithm 6 saves
+ * each time step's data); columns never sketched stay zero after
  * spid_plan_create / spid_reset.  window: device, layout as above. */
-spid_status spid_sketch(spid_plan_t plan, const void* window, int32_t col0, int32_t ncols,
-                        spid_stream_t stream);
+spid_status spid_sketch_accumulate(spid_plan_t plan, const void* window, int32_t col0,
+                                   int32_t ncols, spid_stream_t stream);
 
 /* Zero the stored sketch (start a new window).  Asynchronous. */
 spid_status spid_reset(spid_plan_t plan, spid_stream_t stream);
@@ -129,7 +178,8 @@ spid_status spid_reset(spid_plan_t plan, spid_stream_t stream);
  * every Y_s (pivot norms with FP64-class accuracy -- double-float pairs in
  * FP32 modes, FP64 in FP64 mode -- ties to the lowest column index), the rank
  * decision (fixed k_max or adaptive tol, then the guard |R_jj| > 2 u |R_00|
- * with u the unit roundoff of the sketch arithmetic), the back-substitution
+ * with u the unit roundoff of the sketch arithmetic; a guard stop before the
+ * target sets the informational SPID_ERR_RANK status), the back-substitution
  * T = R11^-1 R12 with FP64-class accuracy and C with C(:, J) = I exactly. */
 spid_status spid_finalize(spid_plan_t plan, spid_stream_t stream);
 
@@ -138,7 +188,11 @@ spid_status spid_finalize(spid_plan_t plan, spid_stream_t stream);
  * ||A_s||_F^2 (FP64 reduction in a fixed order), and total_dev[0..3] =
  * {sum e2, sum a2, sum m_s n_s, sum k_s (m_s + n_s)}, so the global relative
  * error is sqrt(total[0] / total[1]) and the compression factor (Section 2,
- * Eq. for CF, aggregated over subdomains) is total[2] / total[3].
+ * Eq. for CF, aggregated over subdomains) is total[2] / total[3].  A plan with
+ * num_qoi = G > 0 also writes the per-QoI sums total_dev[4 + 2 g] = sum e2 and
+ * total_dev[5 + 2 g] = sum a2 over the subdomains holding QoI g (in subdomain
+ * order), so total_dev must then hold 4 + 2 G doubles; QoI g's relative
+ * error over the domain is sqrt(total[4 + 2 g] / total[5 + 2 g]).
  * A_hat is formed in FP32 on the CUDA cores (FP64 for FP64 plans), or, with
  * SPID_FLAG_TC_ERROR on a batched TF32/BF16/3xBF16 plan with k_max <= 32, on
  * the tensor cores as a three-term TF32 split product (about 2^-21 of
@@ -166,8 +220,10 @@ spid_status spid_get_factors(spid_plan_t plan, int32_t* k_host, int32_t* J_host,
  * l_pad * sum_{s' < s} n_{s'}; element type as the window. */
 spid_status spid_get_sketch(spid_plan_t plan, void* Y_host, spid_stream_t stream);
 
-/* Synchronize the stream and return the sticky device status
- * (SPID_OK, SPID_ERR_TIMEOUT or SPID_ERR_NONFINITE), then clear it. */
+/* Synchronize the stream and return the sticky device status, then clear
+ * it: SPID_ERR_TIMEOUT, else SPID_ERR_NONFINITE, else SPID_ERR_RANK (the
+ * informational rank-guard cut, reading of the paper's silence on a
+ * rank-revealing stop), else SPID_OK. */
 spid_status spid_device_status(spid_plan_t plan, spid_stream_t stream);
 
 /* Omega(i, r0 + c) for i < l, c < nrows into out_dev as nrows x l row-major
@@ -230,7 +286,7 @@ spid_status spid_plan_set_tuning(spid_plan_t plan, const spid_tuning* tuning);
 /* Measure every candidate shape on `window` (device, the plan's layout) and
  * apply the fastest: the sketch candidates on the whole window, then, after a
  * finalize, the error-pass candidates.  Leaves the plan as after
- * spid_sketch(whole window) + spid_finalize with the chosen tuning.
+ * spid_sketch_accumulate(whole window) + spid_finalize with the chosen tuning.
  * Synchronizes; may allocate (as spid_plan_set_tuning); best (may be NULL)
  * receives the chosen tuning and its times.  SPID_ERR_STATE while graphs
  * captured from the plan exist. */
@@ -269,19 +325,27 @@ spid_status spid_graph_launch(spid_graph_t graph, spid_stream_t stream);
 
 /* One end-to-end step from host memory.  Enqueues, in this order: on
  * copy_stream, once the previous launch of this graph has finished with its
- * window, the copy of the window -- the plan's extent, max_s off_s + ld_s
- * (n_s - 1) + m_s elements -- from window_host to the device window the graph
- * was created on; on `stream`, once that copy has landed, the graph; then, on
- * `stream`, the copy of the graph's four error sums (total_dev) to total_host
- * (may be NULL).  All asynchronous: synchronize `stream` before reading
- * total_host.  window_host should be page-locked for the copy to run at the
- * link's rate; copy_stream may be the same stream (no overlap).  Two graphs
- * on two device windows, launched alternately, overlap one step's copy with
- * the other's compute (the plan's workspace is shared: launch both on the
- * same `stream`).  SPID_ERR_INVALID_ARG for a NULL graph or window_host, a
- * graph without a window, or total_host without the graph's total_dev. */
+ * window, the copy of the window -- the plan's extent, the last element any
+ * subdomain reads plus one (blocks: max_s off_s + ld_s (n_s - 1) + m_s) --
+ * from window_host to the device window the graph was created on; on
+ * `stream`, once that copy has landed, the graph; then, on `stream`, the
+ * copies of the step's results to host memory: the error sums (total_dev, 4 +
+ * 2 num_qoi doubles) to total_host and the compressed representation
+ * (Algorithms 2-3 output: the ranks, skeleton indices and coefficients, laid
+ * out as spid_get_factors gives them) to k_host [S], J_host [S k_max] and
+ * C_host (k_max sum n_s elements of the window's type).  Any of the four host
+ * pointers may be NULL.  All asynchronous: synchronize `stream` before reading
+ * them.  window_host and the result buffers should be page-locked for the
+ * copies to run at the link's rate; copy_stream may be the same stream (no
+ * overlap).  Two graphs on two device windows, launched alternately, overlap
+ * one step's copy with the other's compute (the plan's workspace is shared:
+ * launch both on the same `stream`, and read a step's factors before the next
+ * step's copies overwrite them).  SPID_ERR_INVALID_ARG for a NULL graph or
+ * window_host, a graph without a window, or total_host without the graph's
+ * total_dev. */
 spid_status spid_graph_launch_host(spid_graph_t graph, const void* window_host,
-                                   double* total_host, spid_stream_t copy_stream,
+                                   double* total_host, int32_t* k_host, int32_t* J_host,
+                                   void* C_host, spid_stream_t copy_stream,
                                    spid_stream_t stream);
 
 /* Release the graph (synchronizes the device first). */
@@ -307,8 +371,11 @@ spid_status spid_graph_destroy(spid_graph_t graph);
  * <= SPID_NOALLOC_SCRATCH_FLOATS (l_pad = l rounded up to 16), i.e. n <= 65536
  * for l <= 32; larger requests return SPID_ERR_INVALID_ARG with nothing
  * launched.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call shares the array and leaves its
+ * address (cudaGetSymbolAddress) with that device current and keeps it for
+ * the life of the process; make that first call before any stream capture,
+ * and do not call cudaDeviceReset on that device afterwards (the kept address
+ * would then be stale).  Devices with ordinals of 64 or more get
+ * SPID_ERR_UNSUPPORTED.  Every call shares the array and leaves its
  * contents behind (each call overwrites every slot it reads, so nothing needs
  * clearing); calls that overlap on the GPU -- on different streams, or from
  * host threads without ordering -- race on the array and must be serialized

@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) error_kernel(ErrA
   __shared__ double red[2][8];
   __shared__ int last_sub;
   __shared__ const T* colp[kErrMaxK];
+  __shared__ int64_t roff_s[kErrTile];   // boxes: element offsets of the tile's rows
   const int u = blockIdx.x + a.unit_base;
   const int s = a.unit_sub[u];
   const int row0 = a.unit_row0[u], col0 = a.unit_col0[u];
@@ -87,6 +88,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) error_kernel(ErrA
   const T* Cg = static_cast<const T*>(a.C) + a.coff[s];
   const int32_t* Jg = a.J + (int64_t)s * a.k_max;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  // a box of a global field: row r at element row_offset(geo, r) of its column
+  // (x-runs a multiple of 4 long, so a lane's 4 rows stay contiguous)
+  const RowGeom geo = a.geo ? a.geo[s] : RowGeom{0, 0, 0, 0, 0, 0, 0};
+  const bool boxed = geo.ex > 0;   // uniform over the CTA
 
   // skeleton column p: A(:, J[p]) of the window, or column p of the m x k
   // block the caller formed (floats; FP32 plans only)
@@ -101,12 +106,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) error_kernel(ErrA
   for (int t0 = 0; t0 < nrb; t0 += kErrTile) {
     const int rt = row0 + t0;                       // first row of the tile
     __syncthreads();
+    if (boxed) {
+      if (tid < kErrTile) roff_s[tid] = (rt + tid < m) ? row_offset(geo, rt + tid) : 0;
+      __syncthreads();
+    }
     for (int e = tid; e < kk * kErrTile; e += 256) {
       const int p = e / kErrTile, r = e % kErrTile;
-      AJ[e] = (rt + r < m) ? colp[p][rt + r] : T(0);
+      // the skeleton block of a coarse-grid plan (skel) has contiguous rows
+      const int64_t ro = (boxed && !a.skel) ? roff_s[r] : (int64_t)(rt + r);
+      AJ[e] = (rt + r < m) ? colp[p][ro] : T(0);
     }
     __syncthreads();
     const int r = rt + 4 * lane;                    // this lane's 4 rows
+    const int64_t rofs = boxed ? roff_s[4 * lane] : (int64_t)r;   // their element offset
     const bool full_rows = (r + 4 <= m);
     for (int cg = 4 * warp; cg < ncb; cg += 32) {   // 4 columns per warp per pass
       T acc[4][4];
@@ -118,7 +130,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) error_kernel(ErrA
 #pragma unroll
       for (int y = 0; y < 4; ++y) {
         const int col = col0 + cg + y;
-        const T* src = A + (int64_t)col * ld + r;
+        const T* src = A + (int64_t)col * ld + rofs;
         if (col < n && full_rows) {
           V4<T>::load(src, av[y]);
         } else {
@@ -147,7 +159,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) error_kernel(ErrA
         if (WRITE) {
           const int col = col0 + cg + y;
           if (col < n) {
-            T* dst = static_cast<T*>(a.out) + a.off[s] + (int64_t)col * ld + r;
+            T* dst = static_cast<T*>(a.out) + a.off[s] + (int64_t)col * ld + rofs;
             T o[4] = {acc[0][y], acc[1][y], acc[2][y], acc[3][y]};
             if (full_rows) {
               V4<T>::store(dst, o);

@@ -4,7 +4,9 @@
 // subdomain's partials in unit order, and the last subdomain to finish sums
 // the window totals {sum e2, sum a2, sum m n, sum k (r + n)} in subdomain
 // order, r = the rows stored per skeleton column (m, or m_c for a coarse-grid
-// skeleton, Section 5.2).  Every counter is reset by the warp that completes it.
+// skeleton, Section 5.2), and, when the plan labels its subdomains by QoI, the
+// per-QoI sums of e2 and a2.  Every counter is reset by the warp that
+// completes it.
 #pragma once
 
 #include "spid_internal.cuh"
@@ -54,10 +56,23 @@ __device__ __forceinline__ void error_fold_subdomain(const ErrArgs& a, int s, in
     mn += __shfl_xor_sync(0xffffffffu, mn, o);
     kd += __shfl_xor_sync(0xffffffffu, kd, o);
   }
-  if (lane == 0) {
-    if (a.total) { a.total[0] = te; a.total[1] = ta; a.total[2] = mn; a.total[3] = kd; }
-    *a.all_cnt = 0;
+  if (lane == 0 && a.total) { a.total[0] = te; a.total[1] = ta; a.total[2] = mn; a.total[3] = kd; }
+  // per-QoI totals (Section 5.1 reports each QoI's error): the subdomains of
+  // QoI g, lane-strided in subdomain order, then the same fixed tree
+  for (int g = 0; g < a.num_qoi && a.total; ++g) {
+    double ge = 0.0, ga = 0.0;
+    for (int q = lane; q < a.S; q += 32) {
+      if (a.qoi[q] != g) continue;
+      ge += __ldcg(a.sub_err + 2 * (int64_t)q);
+      ga += __ldcg(a.sub_err + 2 * (int64_t)q + 1);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      ge += __shfl_xor_sync(0xffffffffu, ge, o);
+      ga += __shfl_xor_sync(0xffffffffu, ga, o);
+    }
+    if (lane == 0) { a.total[4 + 2 * g] = ge; a.total[5 + 2 * g] = ga; }
   }
+  if (lane == 0) *a.all_cnt = 0;
 }
 
 }  // namespace spid

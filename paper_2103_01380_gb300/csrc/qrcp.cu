@@ -238,6 +238,7 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
   const double tol2 = a.tol * a.tol;
 
   int k = 0;
+  bool guard_stop = false;   // the guard ended the factorization before its target
   for (int j = 0; j < kcap; ++j) {
     const int par = j & 1;
     // ---- argmax of the residual norms^2 (exact on the pairs, ties -> lowest column)
@@ -303,7 +304,10 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
       step_of[c] = j;
     }
     __syncthreads();
-    if (stop_s[par]) break;
+    if (stop_s[par]) {
+      guard_stop = j > 0;
+      break;
+    }
     // ---- apply H_j = I - beta v v^T to every remaining column (v is zero
     // above row j, so no row predicate is needed); downdate the norm by the
     // new R entry; recompute it from the remaining rows once it lost two digits
@@ -354,7 +358,10 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
       }
     }
   }
-  if (tid == 0) a.k_out[s] = keff;
+  if (tid == 0) {
+    a.k_out[s] = keff;
+    if (guard_stop || keff < k) raise_status(a.status, kStatusRankCut);
+  }
   for (int i = tid; i < a.k_max; i += NT) a.J[(int64_t)s * a.k_max + i] = (i < keff) ? Js[i] : -1;
   // ---- coefficients: FP64 back-substitution R11 t = R(0:keff, col), in place
 #pragma unroll

@@ -184,8 +184,10 @@ extern "C" spid_status spid_sketch_fp32_noalloc(const float* A, int32_t m, int32
     return na_fail(SPID_ERR_INVALID_ARG, "A must be 16-byte aligned with ld a multiple of 4");
   const int l_pad = (l + 15) / 16 * 16;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices)
-    return na_fail(SPID_ERR_CUDA, "cudaGetDevice failed");
+  if (cudaGetDevice(&dev) != cudaSuccess) return na_fail(SPID_ERR_CUDA, "cudaGetDevice failed");
+  if (dev < 0 || dev >= kNaMaxDevices)
+    return na_fail(SPID_ERR_UNSUPPORTED, "device ordinal beyond the 64 devices whose scratch "
+                                         "address this entry point caches");
   {
     // one-time set-up per device, with that device current: the device
     // address of the static array (host code cannot use the symbol itself)

@@ -46,6 +46,7 @@ sketch_simt_kernel(SketchArgs args) {
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int last_flag;
+  __shared__ int64_t roff_s[kChunkRows];   // boxes: element offsets of the chunk's rows
   T* As = reinterpret_cast<T*>(smem_raw);       // [kChunkRows][CGP]
   T* Om = As + kChunkRows * CGP;                // [kChunkRows][LP]
   // Om must be 16-byte aligned for vector loads
@@ -66,6 +67,7 @@ sketch_simt_kernel(SketchArgs args) {
     const Problem pb = args.probs[seg.prob];
     const T* A = window + pb.off + (int64_t)pb.col0 * pb.ld;
     const int nc = pb.ncols;
+    const bool boxed = pb.geo.ex > 0;   // uniform over the CTA
 
     T acc[TJ][TI];
 #pragma unroll
@@ -75,11 +77,17 @@ sketch_simt_kernel(SketchArgs args) {
 
     for (int ch = seg.chunk0; ch < seg.chunk1; ++ch) {
       const int r0 = ch * kChunkRows;
+      if (boxed) {
+        // a box of a global field: rows of one x-run (a multiple of VW long)
+        // are contiguous, runs sit at the field's strides
+        if (tid < kChunkRows) roff_s[tid] = (r0 + tid < pb.m) ? row_offset(pb.geo, r0 + tid) : 0;
+        __syncthreads();
+      }
       // ---- stage A(r0 : r0+32, col group) transposed into As[row][col]
       for (int v = tid; v < nc * VPC; v += kThreads) {
         const int c = v / VPC, q = v % VPC;
         const int r = r0 + q * VW;
-        const T* src = A + (int64_t)c * pb.ld + r;
+        const T* src = A + (int64_t)c * pb.ld + (boxed ? roff_s[q * VW] : (int64_t)r);
         T vals[VW];
         if (r + VW <= pb.m) {
           const typename Vec<T>::type x = __ldg(reinterpret_cast<const typename Vec<T>::type*>(src));

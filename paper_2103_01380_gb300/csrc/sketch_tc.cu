@@ -116,10 +116,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) sketch_tf32_kernel(const TcArgs
           const uint32_t fb = smem_addr(&full[st]);
           mbar_arrive_expect_tx(fb, (uint32_t)(pk.nslices * kSliceBytes));
           unsigned char* dst = smem_A + (size_t)st * args.max_tiles * kTileBytes;
+          const ChunkCoord cc = chunk_coord(pk, ch);
           for (int h = 0; h < pk.nslices; ++h) {
             const Slice sl = a.slices[pk.slice0 + h];
-            tma_load_2d(smem_addr(dst + h * kSliceBytes), tmaps + sl.sub, ch * kChunkRows,
-                        sl.col0, fb);
+            tma_load_chunk(smem_addr(dst + h * kSliceBytes), tmaps + sl.sub, pk, cc, sl.col0, fb);
           }
         }
       }

@@ -12,6 +12,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/spid.h"
@@ -90,12 +91,19 @@ struct spid_plan_s {
   uint32_t flags = 0;
   uint64_t seed = 0;
   size_t esz = 4;
+  // layout: boxes of a global field (geo[s].ex > 0) or contiguous blocks
+  bool boxes = false;
+  std::vector<RowGeom> geo;
+  int64_t window_extent = 0;    // elements of the window any call reads, from its base
+  // per-QoI error totals (num_qoi = 0: none)
+  std::vector<int32_t> qoi;
+  int num_qoi = 0;
   bool fp64() const { return prec == SPID_PREC_FP64; }
   bool per_sub() const { return (flags & SPID_FLAG_PER_SUBDOMAIN) != 0; }
   bool tensor_core() const { return prec >= SPID_PREC_TF32; }
   bool bf16() const { return prec == SPID_PREC_BF16 || prec == SPID_PREC_BF16X3; }
   bool err_tc_possible() const {
-    return tensor_core() && !per_sub() && k_max <= kErrTcKMax &&
+    return tensor_core() && !per_sub() && !boxes && k_max <= kErrTcKMax &&
            smem_optin >= error_tc_smem_bytes();
   }
   double u_mode() const {
@@ -111,6 +119,8 @@ struct spid_plan_s {
   // device state
   int32_t* d_m = nullptr;
   int32_t* d_n = nullptr;
+  RowGeom* d_geo = nullptr;     // boxes layout only
+  int32_t* d_qoi = nullptr;     // num_qoi > 0 only
   int64_t* d_off = nullptr;
   int64_t* d_ld = nullptr;
   int64_t* d_yoff = nullptr;
@@ -191,8 +201,13 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   // ---- problems, subdomain by subdomain; with packing, ordered by m
   std::vector<int> subs(P->S);
   for (int s = 0; s < P->S; ++s) subs[s] = s;
+  // packs share one Omega chunk and one chunk decode: group equal m and box shape
+  auto shape = [&](int s) {
+    const RowGeom& g = P->geo[s];
+    return std::make_tuple(P->m[s], g.ex, g.ey, g.ez);
+  };
   if (tc && !P->per_sub())
-    std::stable_sort(subs.begin(), subs.end(), [&](int x, int y) { return P->m[x] < P->m[y]; });
+    std::stable_sort(subs.begin(), subs.end(), [&](int x, int y) { return shape(x) < shape(y); });
   std::vector<Problem> probs;
   std::vector<int> prob_sub_first(P->S + 1, 0);   // per-subdomain mode: problems of s
   struct Unit { int nch; double w; int prob0; int nprob; int pack; };
@@ -219,7 +234,9 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
     };
     for (size_t q = 0; q < subs.size(); ++q) {
       const int s = subs[q];
-      if (pk.nslices > 0 && P->m[s] != pk.m) close_pack();
+      if (pk.nslices > 0 && (P->m[s] != pk.m || P->geo[s].ex != pk.ex || P->geo[s].ey != pk.ey ||
+                             P->geo[s].ez != pk.ez))
+        close_pack();
       const int end = std::min<int64_t>((int64_t)col0 + ncols, P->n[s]);
       for (int c = col0; c < end; c += kSliceCols) {
         if (pk.nslices == P->tune.pack_slices) close_pack();
@@ -228,6 +245,9 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
           pk.m = P->m[s];
           pk.prob0 = (int)probs.size();
           pk.nprob = 0;
+          pk.ex = P->geo[s].ex;
+          pk.ey = P->geo[s].ey;
+          pk.ez = P->geo[s].ez;
         }
         const int nc = std::min(kSliceCols, end - c);
         if (pk.nprob == 0 || probs.back().sub != s) {
@@ -238,6 +258,7 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
           pb.m = P->m[s];
           pb.off = P->off[s];
           pb.ld = P->ld[s];
+          pb.geo = P->geo[s];
           probs.push_back(pb);
           ++pk.nprob;
         }
@@ -268,6 +289,7 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
       pb.m = P->m[s];
       pb.off = P->off[s];
       pb.ld = P->ld[s];
+      pb.geo = P->geo[s];
       probs.push_back(pb);
     }
   }
@@ -291,8 +313,12 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
       pk.m = probs[p].m;
       pk.prob0 = p;
       pk.nprob = 0;
+      pk.ex = probs[p].geo.ex;
+      pk.ey = probs[p].geo.ey;
+      pk.ez = probs[p].geo.ez;
       int cols = 0;
-      while (p < p1 && probs[p].m == pk.m &&
+      while (p < p1 && probs[p].m == pk.m && probs[p].geo.ex == pk.ex &&
+             probs[p].geo.ey == pk.ey && probs[p].geo.ez == pk.ez &&
              pk.nslices + (probs[p].ncols + kSliceCols - 1) / kSliceCols <= P->tune.pack_slices) {
         for (int c = 0; c < probs[p].ncols; c += kSliceCols) {
           Slice sl;
@@ -575,22 +601,41 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// One 2-D tensor map per subdomain over the window: dim0 = rows (contiguous),
-// dim1 = window columns, box = 32 rows x 64 columns, 128-byte swizzle, zero
-// fill outside [0, m) x [0, n).
+// One tensor map per subdomain over the window, 128-byte swizzle, zero fill
+// outside the subdomain.  Blocks: 2-D, dim0 = rows (contiguous), dim1 =
+// window columns, box = 32 rows x 64 columns.  Boxes of a global field: 5-D,
+// (x, y, z, q, column) over the box's own extents with the field's strides,
+// box = 32 points along x x 64 columns, so a 32-row chunk of the data matrix
+// (ex a multiple of 32) is one tile -- the same 8 KB [64][32] shared-memory
+// image either way.
 spid_status encode_window_maps(spid_plan_t P, const void* window, std::vector<CUtensorMap>& maps) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return fail(SPID_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
   maps.resize(P->S);
   for (int s = 0; s < P->S; ++s) {
     void* base = const_cast<char*>(static_cast<const char*>(window)) + P->off[s] * P->esz;
-    cuuint64_t dims[2] = {(cuuint64_t)P->m[s], (cuuint64_t)P->n[s]};
-    cuuint64_t strides[1] = {(cuuint64_t)P->ld[s] * P->esz};
-    cuuint32_t box[2] = {32, (cuuint32_t)kSliceCols};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(&maps[s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const RowGeom& g = P->geo[s];
+    CUresult r;
+    if (g.ex > 0) {
+      const int64_t nqs = (int64_t)P->m[s] / ((int64_t)g.ex * g.ey * g.ez);
+      cuuint64_t dims[5] = {(cuuint64_t)g.ex, (cuuint64_t)g.ey, (cuuint64_t)g.ez,
+                            (cuuint64_t)nqs, (cuuint64_t)P->n[s]};
+      cuuint64_t strides[4] = {(cuuint64_t)g.sy * P->esz, (cuuint64_t)g.sz * P->esz,
+                               (cuuint64_t)g.sq * P->esz, (cuuint64_t)P->ld[s] * P->esz};
+      cuuint32_t box[5] = {32, 1, 1, 1, (cuuint32_t)kSliceCols};
+      cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+      r = enc(&maps[s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, base, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+      cuuint64_t dims[2] = {(cuuint64_t)P->m[s], (cuuint64_t)P->n[s]};
+      cuuint64_t strides[1] = {(cuuint64_t)P->ld[s] * P->esz};
+      cuuint32_t box[2] = {32, (cuuint32_t)kSliceCols};
+      cuuint32_t estr[2] = {1, 1};
+      r = enc(&maps[s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
     if (r != CUDA_SUCCESS)
       return fail(SPID_ERR_INVALID_ARG, "cuTensorMapEncodeTiled failed for subdomain " +
                                             std::to_string(s) + " (code " + std::to_string((int)r) + ")");
@@ -709,6 +754,7 @@ const char* spid_status_string(spid_status s) {
     case SPID_ERR_TIMEOUT: return "SPID_ERR_TIMEOUT";
     case SPID_ERR_NONFINITE: return "SPID_ERR_NONFINITE";
     case SPID_ERR_UNSUPPORTED: return "SPID_ERR_UNSUPPORTED";
+    case SPID_ERR_RANK: return "SPID_ERR_RANK";
   }
   return "SPID_ERR_UNKNOWN";
 }
@@ -725,38 +771,135 @@ double spid_compression_factor(int32_t num_sub, const int32_t* m, const int32_t*
   return den > 0.0 ? num / den : INFINITY;
 }
 
-spid_status spid_plan_create(const spid_plan_desc* d, spid_plan_t* out) {
+// Subdomains of a plan descriptor: rows, element offset of row 0 at column
+// 0, column stride and row placement, from the blocks arrays or from the boxes
+// of a global field.  Validates everything; on success fills the vectors.
+static spid_status parse_layout(const spid_plan_desc* d, size_t esz, std::vector<int32_t>& m,
+                                std::vector<int64_t>& off, std::vector<int64_t>& ld,
+                                std::vector<RowGeom>& geo, std::vector<int32_t>& qoi,
+                                int& num_qoi) {
+  const int S = d->num_sub;
+  const int64_t align = (int64_t)(16 / esz);
+  m.assign(S, 0);
+  off.assign(S, 0);
+  ld.assign(S, 0);
+  geo.assign(S, RowGeom{0, 0, 0, 0, 0, 0, 0});
+  const spid_box_layout* L = d->boxes;
+  if (!L) {
+    if (!d->m || !d->off || !d->ld) return fail(SPID_ERR_INVALID_ARG, "a descriptor array is NULL");
+    for (int s = 0; s < S; ++s) {
+      if (d->m[s] < 1 || d->ld[s] < d->m[s] || d->off[s] < 0)
+        return fail(SPID_ERR_INVALID_ARG, "bad size for subdomain " + std::to_string(s));
+      if (d->off[s] % align || d->ld[s] % align)
+        return fail(SPID_ERR_INVALID_ARG, "off/ld of subdomain " + std::to_string(s) +
+                                              " not a multiple of 16 bytes");
+      m[s] = d->m[s];
+      off[s] = d->off[s];
+      ld[s] = d->ld[s];
+    }
+  } else {
+    if (L->nq < 1 || L->X < 1 || L->Y < 1 || L->Z < 1 || L->num_box < 1 || !L->org3 || !L->ext3 ||
+        (L->split_qoi != 0 && L->split_qoi != 1))
+      return fail(SPID_ERR_INVALID_ARG, "bad box layout (nq, X, Y, Z, num_box, org3, ext3, split_qoi)");
+    const int64_t plane = L->X * L->Y, field = plane * L->Z;
+    if (L->X % align || L->snap_stride % align || L->snap_stride < (int64_t)L->nq * field)
+      return fail(SPID_ERR_INVALID_ARG, "box layout: X and snap_stride must be multiples of 16 bytes "
+                                        "and snap_stride >= nq X Y Z");
+    const int per_box = L->split_qoi ? L->nq : 1;
+    if ((int64_t)L->num_box * per_box != S)
+      return fail(SPID_ERR_INVALID_ARG, "num_sub must be num_box (or num_box nq with split_qoi)");
+    for (int b = 0; b < L->num_box; ++b) {
+      const int32_t* o = L->org3 + 3 * b;
+      const int32_t* e = L->ext3 + 3 * b;
+      if (o[0] < 0 || o[1] < 0 || o[2] < 0 || e[0] < 1 || e[1] < 1 || e[2] < 1 ||
+          o[0] + (int64_t)e[0] > L->X || o[1] + (int64_t)e[1] > L->Y || o[2] + (int64_t)e[2] > L->Z)
+        return fail(SPID_ERR_INVALID_ARG, "box " + std::to_string(b) + " is empty or leaves the field");
+      if (o[0] % align || e[0] % align)
+        return fail(SPID_ERR_INVALID_ARG, "box " + std::to_string(b) +
+                                              ": x origin and x extent must be multiples of 16 bytes");
+      const int64_t pts = (int64_t)e[0] * e[1] * e[2];
+      const int64_t rows = pts * (L->split_qoi ? 1 : L->nq);
+      if (rows > INT32_MAX) return fail(SPID_ERR_INVALID_ARG, "box " + std::to_string(b) + " has too many rows");
+      for (int q = 0; q < per_box; ++q) {
+        const int s = b * per_box + q;
+        m[s] = (int32_t)rows;
+        off[s] = (int64_t)q * field + (int64_t)o[2] * plane + (int64_t)o[1] * L->X + o[0];
+        ld[s] = L->snap_stride;
+        geo[s] = RowGeom{e[0], e[1], e[2], 0, L->X, plane, field};
+      }
+    }
+  }
+  // per-QoI labels
+  qoi.clear();
+  num_qoi = 0;
+  if (d->qoi) {
+    if (d->num_qoi < 1 || d->num_qoi > 64)
+      return fail(SPID_ERR_INVALID_ARG, "num_qoi must be 1..64 when qoi is given");
+    for (int s = 0; s < S; ++s)
+      if (d->qoi[s] < 0 || d->qoi[s] >= d->num_qoi)
+        return fail(SPID_ERR_INVALID_ARG, "qoi of subdomain " + std::to_string(s) + " out of range");
+    qoi.assign(d->qoi, d->qoi + S);
+    num_qoi = d->num_qoi;
+  } else if (L && L->split_qoi) {
+    if (d->num_qoi != 0 && d->num_qoi != L->nq)
+      return fail(SPID_ERR_INVALID_ARG, "num_qoi must be 0 or nq for split boxes without qoi");
+    if (L->nq > 64) return fail(SPID_ERR_INVALID_ARG, "at most 64 QoIs for per-QoI totals");
+    qoi.resize(S);
+    for (int s = 0; s < S; ++s) qoi[s] = s % L->nq;
+    num_qoi = L->nq;
+  } else if (d->num_qoi != 0) {
+    return fail(SPID_ERR_INVALID_ARG, "num_qoi > 0 needs the qoi array");
+  }
+  return SPID_OK;
+}
+
+spid_status spid_plan_create(const spid_plan_desc* d, spid_stream_t stream, spid_plan_t* out) {
   g_last_error.clear();
   if (!d || !out) return fail(SPID_ERR_INVALID_ARG, "desc/out is NULL");
   *out = nullptr;
-  if (d->num_sub < 1 || !d->m || !d->n || !d->off || !d->ld)
-    return fail(SPID_ERR_INVALID_ARG, "num_sub < 1 or a descriptor array is NULL");
+  if (d->num_sub < 1 || !d->n) return fail(SPID_ERR_INVALID_ARG, "num_sub < 1 or n is NULL");
   if (d->precision < SPID_PREC_FP64 || d->precision > SPID_PREC_BF16X3)
     return fail(SPID_ERR_INVALID_ARG, "unknown precision");
   if (d->k_max < 1 || d->p < 0 || d->k_max + d->p > 64)
     return fail(SPID_ERR_INVALID_ARG, "need k_max >= 1, p >= 0, k_max + p <= 64");
   if (!(d->tol >= 0.0) || !std::isfinite(d->tol)) return fail(SPID_ERR_INVALID_ARG, "tol must be >= 0");
   const size_t esz = d->precision == SPID_PREC_FP64 ? 8 : 4;
-  const int align = (int)(16 / esz);
+  std::vector<int32_t> lm, lqoi;
+  std::vector<int64_t> loff, lld;
+  std::vector<RowGeom> lgeo;
+  int lnq = 0;
+  {
+    spid_status st = parse_layout(d, esz, lm, loff, lld, lgeo, lqoi, lnq);
+    if (st != SPID_OK) return st;
+  }
   int n_max = 0;
   for (int s = 0; s < d->num_sub; ++s) {
-    if (d->m[s] < 1 || d->n[s] < 1 || d->n[s] > (1 << 20) || d->ld[s] < d->m[s] || d->off[s] < 0)
-      return fail(SPID_ERR_INVALID_ARG, "bad size for subdomain " + std::to_string(s));
-    if (d->off[s] % align || d->ld[s] % align)
-      return fail(SPID_ERR_INVALID_ARG, "off/ld of subdomain " + std::to_string(s) +
-                                            " not a multiple of 16 bytes");
+    if (d->n[s] < 1 || d->n[s] > (1 << 20))
+      return fail(SPID_ERR_INVALID_ARG, "bad window length for subdomain " + std::to_string(s));
     n_max = std::max(n_max, d->n[s]);
   }
+  if (d->boxes && d->precision >= SPID_PREC_TF32)
+    for (int s = 0; s < d->num_sub; ++s)
+      if (lgeo[s].ex % 32)
+        return fail(SPID_ERR_UNSUPPORTED, "the tensor-core sketches read boxes whose x extent is a "
+                                          "multiple of 32 points (subdomain " + std::to_string(s) + ")");
   spid_plan_s* P = new spid_plan_s();
   auto bail = [&](spid_status st) {
     spid_plan_destroy(P);
     return st;
   };
   P->S = d->num_sub;
-  P->m.assign(d->m, d->m + P->S);
+  P->m = lm;
   P->n.assign(d->n, d->n + P->S);
-  P->off.assign(d->off, d->off + P->S);
-  P->ld.assign(d->ld, d->ld + P->S);
+  P->off = loff;
+  P->ld = lld;
+  P->geo = lgeo;
+  P->boxes = d->boxes != nullptr;
+  P->qoi = lqoi;
+  P->num_qoi = lnq;
+  for (int s = 0; s < P->S; ++s)
+    P->window_extent = std::max<int64_t>(P->window_extent, P->off[s] + P->ld[s] * (P->n[s] - 1) +
+                                                               row_offset(P->geo[s], P->m[s] - 1) + 1);
   P->n_max = n_max;
   P->k_max = d->k_max;
   P->p = d->p;
@@ -836,6 +979,8 @@ spid_status spid_plan_create(const spid_plan_desc* d, spid_plan_t* out) {
   SPID_ALLOC(P->d_err_cnt, sizeof(int) * (P->S + 1));
   SPID_ALLOC(P->d_partial, esz * P->partial_cap);
   if (P->tensor_core()) SPID_ALLOC(P->d_tmaps, sizeof(CUtensorMap) * P->S);
+  if (P->boxes) SPID_ALLOC(P->d_geo, sizeof(RowGeom) * P->S);
+  if (P->num_qoi > 0) SPID_ALLOC(P->d_qoi, sizeof(int32_t) * P->S);
 #undef SPID_ALLOC
 #define SPID_H2D(dst, src, bytes)                                                          \
   do {                                                                                     \
@@ -851,22 +996,28 @@ spid_status spid_plan_create(const spid_plan_desc* d, spid_plan_t* out) {
   SPID_H2D(P->d_ld, P->ld.data(), sizeof(int64_t) * P->S);
   SPID_H2D(P->d_yoff, yoff.data(), sizeof(int64_t) * P->S);
   SPID_H2D(P->d_coff, coff.data(), sizeof(int64_t) * P->S);
+  if (P->boxes) SPID_H2D(P->d_geo, P->geo.data(), sizeof(RowGeom) * P->S);
+  if (P->num_qoi > 0) SPID_H2D(P->d_qoi, P->qoi.data(), sizeof(int32_t) * P->S);
 #undef SPID_H2D
   {
     spid_status st = upload_error_units(P);
     if (st == SPID_OK && P->tune.err_path == 1) st = ensure_error_tc(P);
     if (st != SPID_OK) return bail(st);
   }
-  if (cudaMemset(P->d_Y, 0, esz * P->y_elems) != cudaSuccess ||
-      cudaMemset(P->d_status, 0, sizeof(int)) != cudaSuccess ||
-      cudaMemset(P->d_err_cnt, 0, sizeof(int) * (P->S + 1)) != cudaSuccess ||
-      cudaMemset(P->d_k, 0, sizeof(int32_t) * P->S) != cudaSuccess)
-    return bail(fail(SPID_ERR_CUDA, "cudaMemset failed"));
-  // the whole-window schedule is built now so that steady-state calls allocate nothing
-  Schedule* sc = nullptr;
-  spid_status st = get_schedule(P, 0, n_max, &sc);
-  if (st != SPID_OK) return bail(st);
-  if (cudaDeviceSynchronize() != cudaSuccess) return bail(fail(SPID_ERR_CUDA, "sync failed"));
+  {
+    cudaStream_t cs = (cudaStream_t)stream;
+    if (cudaMemsetAsync(P->d_Y, 0, esz * P->y_elems, cs) != cudaSuccess ||
+        cudaMemsetAsync(P->d_status, 0, sizeof(int), cs) != cudaSuccess ||
+        cudaMemsetAsync(P->d_err_cnt, 0, sizeof(int) * (P->S + 1), cs) != cudaSuccess ||
+        cudaMemsetAsync(P->d_k, 0, sizeof(int32_t) * P->S, cs) != cudaSuccess)
+      return bail(fail(SPID_ERR_CUDA, "cudaMemsetAsync failed"));
+    // the whole-window schedule is built now so that steady-state calls allocate nothing
+    Schedule* sc = nullptr;
+    spid_status st = get_schedule(P, 0, n_max, &sc);
+    if (st != SPID_OK) return bail(st);
+    if (cudaStreamSynchronize(cs) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+      return bail(fail(SPID_ERR_CUDA, "sync failed"));
+  }
   *out = P;
   return SPID_OK;
 }
@@ -898,8 +1049,8 @@ spid_status spid_reset(spid_plan_t P, spid_stream_t stream) {
   return SPID_OK;
 }
 
-spid_status spid_sketch(spid_plan_t P, const void* window, int32_t col0, int32_t ncols,
-                        spid_stream_t stream) {
+spid_status spid_sketch_accumulate(spid_plan_t P, const void* window, int32_t col0,
+                                   int32_t ncols, spid_stream_t stream) {
   spid_status st = check_plan(P);
   if (st != SPID_OK) return st;
   if (!window) return fail(SPID_ERR_INVALID_ARG, "window is NULL");
@@ -984,6 +1135,9 @@ static spid_status run_error(spid_plan_t P, const void* window, void* out, doubl
   a.S = P->S;
   a.row_block = P->tune.err_rows;
   a.col_block = P->tune.err_cols;
+  a.geo = P->boxes ? P->d_geo : nullptr;
+  a.qoi = P->d_qoi;
+  a.num_qoi = P->num_qoi;
   if (P->tune.err_path == 1 && P->err_tc_grid > 0) {
     ErrTcArgs t;
     t.e = a;
@@ -1058,6 +1212,8 @@ spid_status spid_device_status(spid_plan_t P, spid_stream_t stream) {
     return fail(SPID_ERR_TIMEOUT, "a bounded device wait timed out");
   }
   if (v & kStatusNonfinite) return fail(SPID_ERR_NONFINITE, "non-finite values reached a sketch");
+  if (v & kStatusRankCut)
+    return fail(SPID_ERR_RANK, "the rank guard stopped a factorization before its target");
   return SPID_OK;
 }
 
@@ -1474,11 +1630,8 @@ extern "C" spid_status spid_graph_create(spid_plan_t P, const void* window, int3
   if (e != cudaSuccess)
     return bail(fail(SPID_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e)));
   if (sketch || error) {
-    int64_t extent = 0;
-    for (int s = 0; s < P->S; ++s)
-      extent = std::max<int64_t>(extent, P->off[s] + P->ld[s] * (P->n[s] - 1) + P->m[s]);
     G->window = const_cast<void*>(window);
-    G->window_bytes = (size_t)extent * P->esz;
+    G->window_bytes = (size_t)P->window_extent * P->esz;
   }
   G->total_dev = total_dev;
   e = cudaEventCreateWithFlags(&G->ev_uploaded, cudaEventDisableTiming);
@@ -1490,8 +1643,9 @@ extern "C" spid_status spid_graph_create(spid_plan_t P, const void* window, int3
 }
 
 extern "C" spid_status spid_graph_launch_host(spid_graph_t G, const void* window_host,
-                                              double* total_host, spid_stream_t copy_stream,
-                                              spid_stream_t stream) {
+                                              double* total_host, int32_t* k_host,
+                                              int32_t* J_host, void* C_host,
+                                              spid_stream_t copy_stream, spid_stream_t stream) {
   if (!G || !G->exec) return fail(SPID_ERR_INVALID_ARG, "graph is NULL");
   if (!window_host) return fail(SPID_ERR_INVALID_ARG, "window_host is NULL");
   if (!G->window) return fail(SPID_ERR_INVALID_ARG, "graph has no window (finalize only)");
@@ -1512,9 +1666,18 @@ extern "C" spid_status spid_graph_launch_host(spid_graph_t G, const void* window
     SPID_CUDA(cudaEventRecord(G->ev_done, cs));
     G->launched = true;
   }
+  spid_plan_t P = G->plan;
   if (total_host)
-    SPID_CUDA(cudaMemcpyAsync(total_host, G->total_dev, 4 * sizeof(double),
+    SPID_CUDA(cudaMemcpyAsync(total_host, G->total_dev, (4 + 2 * (size_t)P->num_qoi) * sizeof(double),
                               cudaMemcpyDeviceToHost, cs));
+  // the compressed representation of the step (Algorithms 2-3 output)
+  if (k_host)
+    SPID_CUDA(cudaMemcpyAsync(k_host, P->d_k, sizeof(int32_t) * P->S, cudaMemcpyDeviceToHost, cs));
+  if (J_host)
+    SPID_CUDA(cudaMemcpyAsync(J_host, P->d_J, sizeof(int32_t) * P->S * P->k_max,
+                              cudaMemcpyDeviceToHost, cs));
+  if (C_host)
+    SPID_CUDA(cudaMemcpyAsync(C_host, P->d_C, P->esz * P->c_elems, cudaMemcpyDeviceToHost, cs));
   return SPID_OK;
 }
 

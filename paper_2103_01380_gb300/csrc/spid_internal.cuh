@@ -12,7 +12,26 @@ namespace spid {
 enum : int {
   kStatusTimeout = 1,
   kStatusNonfinite = 2,
+  kStatusRankCut = 4,   // informational: the rank guard stopped a factorization early
 };
+
+// Where the rows of a subdomain sit inside one column of the window.  A box of
+// the solver's global field [t][q][Z][Y][X] has rows r = ((q ez + z) ey + y)
+// ex + x (QoI slowest), and row r is element x + y sy + z sz + q sq of the
+// column (sy = X, sz = X Y, sq = X Y Z).  ex = 0: the rows are contiguous
+// (element r), the blocks layout.
+struct RowGeom {
+  int32_t ex, ey, ez, pad;
+  int64_t sy, sz, sq;
+};
+
+__host__ __device__ __forceinline__ int64_t row_offset(const RowGeom& g, int64_t r) {
+  if (g.ex == 0) return r;
+  const int64_t x = r % g.ex, t = r / g.ex;
+  const int64_t y = t % g.ey, t2 = t / g.ey;
+  const int64_t z = t2 % g.ez, q = t2 / g.ez;
+  return x + y * g.sy + z * g.sz + q * g.sq;
+}
 
 // Every spin on an mbarrier gives up after this many nanoseconds, records
 // kStatusTimeout and lets the kernel unwind.
@@ -28,7 +47,8 @@ struct Problem {
   int32_t ncols;   // number of columns (<= the kernel's column-group size)
   int32_t m;       // rows of the subdomain
   int64_t off;     // element offset of A_s(0,0) in the window
-  int64_t ld;      // leading dimension in elements
+  int64_t ld;      // leading dimension (column stride) in elements
+  RowGeom geo;     // row placement inside a column (ex = 0: contiguous)
 };
 
 // A contiguous range of row chunks of one problem, processed by one CTA; its
@@ -62,6 +82,10 @@ struct Pack {
   int32_t m;         // rows of every member
   int32_t prob0;     // first member problem (members are consecutive problems)
   int32_t nprob;     // number of member problems
+  // box geometry shared by every member (ex = 0: 2-D tensor maps over
+  // contiguous rows; else 5-D maps (x, y, z, q, column) and a 32-row chunk is
+  // one 32-point run along x, ex a multiple of 32)
+  int32_t ex, ey, ez;
 };
 
 // A contiguous range of row chunks of one pack, processed by one CTA; member
@@ -207,6 +231,12 @@ struct ErrArgs {
   // (A_hat = F C, e.g. F = M B(:, I_B) of the coarse-grid SPID)
   const float* skel = nullptr;
   const int64_t* skel_off = nullptr;
+  // row placement per subdomain (nullptr: contiguous rows)
+  const RowGeom* geo = nullptr;
+  // per-QoI totals: subdomain s holds QoI qoi[s] < num_qoi; total[4 + 2 g],
+  // total[5 + 2 g] receive that QoI's sum e2, sum a2 (num_qoi = 0: none)
+  const int32_t* qoi = nullptr;
+  int32_t num_qoi = 0;
 };
 
 // Tensor-core error pass (FP32 windows, k_max <= 32): a segment is a run of

@@ -140,6 +140,8 @@ spid_status spid_ts_plan_create(const spid_ts_desc* d, spid_ts_plan_t* out) {
   if (!d || !out) return tfail(SPID_ERR_INVALID_ARG, "desc/out is NULL");
   *out = nullptr;
   const spid_plan_desc& B = d->base;
+  if (B.boxes)
+    return tfail(SPID_ERR_UNSUPPORTED, "the two-stage plan takes the blocks layout (base.boxes = NULL)");
   if (B.num_sub < 1 || B.num_sub > 65535 || !B.m || !B.n || !B.off || !B.ld)
     return tfail(SPID_ERR_INVALID_ARG, "bad base descriptor");
   if (d->blocks < 1) return tfail(SPID_ERR_INVALID_ARG, "blocks must be >= 1");
@@ -176,8 +178,10 @@ spid_status spid_ts_plan_create(const spid_ts_desc* d, spid_ts_plan_t* out) {
     spid_plan_desc db = B;
     db.n = nb.data();
     db.off = off_b.data();
+    db.qoi = nullptr;   // per-QoI totals only for the final factors
+    db.num_qoi = 0;
     spid_plan_t pb = nullptr;
-    spid_status st = spid_plan_create(&db, &pb);
+    spid_status st = spid_plan_create(&db, nullptr, &pb);
     if (st != SPID_OK) return bail(st);
     P->blocks.push_back(pb);
   }
@@ -197,12 +201,14 @@ spid_status spid_ts_plan_create(const spid_ts_desc* d, spid_ts_plan_t* out) {
   d2.ld = gld.data();
   d2.k_max = d->k2_max;
   d2.tol = d->tol2;
-  spid_status st = spid_plan_create(&d2, &P->stage2);
+  d2.qoi = nullptr;
+  d2.num_qoi = 0;
+  spid_status st = spid_plan_create(&d2, nullptr, &P->stage2);
   if (st != SPID_OK) return bail(st);
   // ---- whole-window plan holding the final factors
   spid_plan_desc df = B;
   df.k_max = d->k2_max;
-  st = spid_plan_create(&df, &P->full);
+  st = spid_plan_create(&df, nullptr, &P->full);
   if (st != SPID_OK) return bail(st);
   // ---- device tables
   auto dalloc = [&](void** p, size_t bytes) -> cudaError_t {
@@ -264,7 +270,7 @@ spid_status spid_ts_block(spid_ts_plan_t P, const void* window, int32_t block,
                           spid_stream_t stream) {
   if (!P) return tfail(SPID_ERR_INVALID_ARG, "plan is NULL");
   if (block < 0 || block >= P->N) return tfail(SPID_ERR_INVALID_ARG, "block out of range");
-  spid_status st = spid_sketch(P->blocks[block], window, 0, P->n_max, stream);
+  spid_status st = spid_sketch_accumulate(P->blocks[block], window, 0, P->n_max, stream);
   if (st != SPID_OK) return st;
   return spid_finalize(P->blocks[block], stream);
 }
@@ -289,7 +295,7 @@ spid_status spid_ts_finalize(spid_ts_plan_t P, const void* window, spid_stream_t
         P->d_kb, static_cast<float*>(P->d_G), P->d_goff, P->d_gld, P->d_live);
   }
   TS_CUDA(cudaGetLastError());
-  spid_status st = spid_sketch(P->stage2, P->d_G, 0, P->N * P->k, stream);
+  spid_status st = spid_sketch_accumulate(P->stage2, P->d_G, 0, P->N * P->k, stream);
   if (st != SPID_OK) return st;
   st = spid_finalize(P->stage2, stream);
   if (st != SPID_OK) return st;
@@ -330,9 +336,11 @@ spid_status spid_ts_get_block_factors(spid_ts_plan_t P, int32_t block, int32_t* 
 
 spid_status spid_ts_device_status(spid_ts_plan_t P, spid_stream_t stream) {
   if (!P) return tfail(SPID_ERR_INVALID_ARG, "plan is NULL");
+  // the first error wins; the informational rank-guard cut only if nothing failed
   spid_status worst = SPID_OK;
   auto take = [&](spid_status st) {
-    if (worst == SPID_OK) worst = st;
+    if (st == SPID_OK) return;
+    if (worst == SPID_OK || (worst == SPID_ERR_RANK && st != SPID_ERR_RANK)) worst = st;
   };
   for (spid_plan_t b : P->blocks) take(spid_device_status(b, stream));
   take(spid_device_status(P->stage2, stream));

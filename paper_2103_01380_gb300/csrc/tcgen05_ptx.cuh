@@ -67,6 +67,42 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int 
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const void* tmap, int c0, int c1, int c2,
+                                            int c3, int c4, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      : "memory");
+}
+
+// Load the [64 columns][32 rows] tile of chunk `ch` of a slice: a 2-D map over
+// contiguous rows, or (pk.ex > 0) a 5-D map over a box of a global field whose
+// 32-row chunks are runs along x (ex a multiple of 32, so x is 16-byte
+// aligned).  The chunk's (x, y, z, q) is decoded once per chunk by the caller.
+struct ChunkCoord {
+  int x, y, z, q;
+};
+
+__device__ __forceinline__ ChunkCoord chunk_coord(const Pack& pk, int ch) {
+  ChunkCoord c{ch * kChunkRows, 0, 0, 0};
+  if (pk.ex > 0) {
+    const int t = c.x / pk.ex;
+    c.x -= t * pk.ex;
+    c.y = t % pk.ey;
+    const int t2 = t / pk.ey;
+    c.z = t2 % pk.ez;
+    c.q = t2 / pk.ez;
+  }
+  return c;
+}
+
+__device__ __forceinline__ void tma_load_chunk(uint32_t dst, const void* tmap, const Pack& pk,
+                                               const ChunkCoord& c, int col0, uint32_t bar) {
+  if (pk.ex > 0) tma_load_5d(dst, tmap, c.x, c.y, c.z, c.q, col0, bar);
+  else tma_load_2d(dst, tmap, c.x, col0, bar);
+}
+
 // K-major operand, 128-byte swizzle: 8-row groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
   return (uint64_t)((saddr >> 4) & 0x3FFFu)       // start address

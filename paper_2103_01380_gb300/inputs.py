@@ -207,6 +207,39 @@ def tgv3d_window(grid: int = 64, box: int = 16, n: int = 512, t_end: float = 10.
     return w
 
 
+def tgv3d_global(X: int, Y: int, Z: int, grid: int, t: np.ndarray,
+                 modes: FourierModes | None = None, seed: int = 2, nu: float = 0.01,
+                 dtype=np.float32, snap_stride: int | None = None) -> np.ndarray:
+    """The 3D field on the points [0, X) x [0, Y) x [0, Z) of a periodic grid^3
+    grid, laid out as a solver holds it: a flat [t][q][Z][Y][X] window (QoIs
+    rho, u, v, w, p), snapshot t at element t * snap_stride (default 5 X Y Z;
+    padding between snapshots stays zero)."""
+    if modes is None:
+        modes = fourier_modes(seed=seed)
+    F = tgv3d_box((0, 0, 0), (X, Y, Z), grid, t, modes, nu, dtype=np.float64)  # [(q,z,y,x), t]
+    field = 5 * X * Y * Z
+    ss = field if snap_stride is None else int(snap_stride)
+    out = np.zeros(ss * len(t), dtype=dtype)
+    out.reshape(len(t), ss)[:, :field] = F.T
+    return out
+
+
+def cut_box(window: np.ndarray, nq: int, X: int, Y: int, Z: int, n: int, org, ext,
+            q: int | None = None, snap_stride: int | None = None) -> np.ndarray:
+    """Data matrix of the box org + [0, ext) ((x, y, z) order) of a flat
+    [t][q][Z][Y][X] window: rows ((q ez + z) ey + y) ex + x with every QoI
+    stacked (QoI slowest), or only QoI q's rows (z ey + y) ex + x; columns are
+    the n snapshots.  A layout copy only."""
+    ss = nq * X * Y * Z if snap_stride is None else int(snap_stride)
+    f = window[:ss * n].reshape(n, ss)[:, :nq * X * Y * Z].reshape(n, nq, Z, Y, X)
+    ox, oy, oz = (int(v) for v in org)
+    ex, ey, ez = (int(v) for v in ext)
+    b = f[:, :, oz:oz + ez, oy:oy + ey, ox:ox + ex]
+    if q is not None:
+        b = b[:, q]
+    return np.ascontiguousarray(b.reshape(n, -1).T)
+
+
 def uneven_boxes(count: int, edges=(8, 12, 16, 24, 32), n_range=(64, 1024), grid: int = 256,
                  t_end: float = 10.0, nu: float = 0.01, seed: int = 4,
                  modes: FourierModes | None = None):
@@ -347,6 +380,26 @@ def separated_lowrank(m: int, n: int, r: int, seed: int, decay: float = 0.5,
     A = spectrum_matrix(m, n, sig, seed)
     if noise > 0:
         A = A + noise * np.random.default_rng(seed + 7919).standard_normal((m, n))
+    return A
+
+
+def separated_columns(m: int, n: int, r: int, seed: int, ratio: float = 0.35,
+                      mix: float = 0.02, noise: float = 0.0) -> np.ndarray:
+    """Rank-r data whose leading columns are decided with a wide margin: column
+    j < r is a random unit direction times ratio^j (nearly orthogonal for
+    m >> r), every other column a random combination of those r with weights
+    of size `mix`, plus optional i.i.d. noise.  A column-pivoted QR of it (or of
+    a Gaussian sketch of it) picks columns 0, 1, ..., r - 1 in order, each
+    residual norm about 1 / ratio times the next, so the pivots stay
+    identifiable even under the ~2^-11 roundings of a TF32 sketch."""
+    rng = np.random.default_rng(seed)
+    D = rng.standard_normal((m, r))
+    D /= np.linalg.norm(D, axis=0, keepdims=True)
+    D *= ratio ** np.arange(r)[None, :]
+    W = mix * rng.standard_normal((r, n - r))
+    A = np.concatenate([D, D @ W], axis=1)
+    if noise > 0:
+        A = A + noise * rng.standard_normal((m, n))
     return A
 
 

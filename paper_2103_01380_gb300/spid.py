@@ -20,13 +20,15 @@ LIB_PATH = os.path.join(_HERE, "_build", "libspid.so")
 SPID_OK = 0
 STATUS_NAMES = {0: "SPID_OK", 1: "SPID_ERR_INVALID_ARG", 2: "SPID_ERR_CUDA", 3: "SPID_ERR_OOM",
                 4: "SPID_ERR_STATE", 5: "SPID_ERR_TIMEOUT", 6: "SPID_ERR_NONFINITE",
-                7: "SPID_ERR_UNSUPPORTED"}
+                7: "SPID_ERR_UNSUPPORTED", 8: "SPID_ERR_RANK"}
+SPID_ERR_RANK = 8
 PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "bf16x3": 4}
 FLAG_PER_SUBDOMAIN = 1
 FLAG_TC_ERROR = 2
 
 # every symbol include/spid.h declares
-EXPORTS = ["spid_plan_create", "spid_plan_destroy", "spid_plan_info", "spid_sketch", "spid_reset",
+EXPORTS = ["spid_plan_create", "spid_plan_destroy", "spid_plan_info", "spid_sketch_accumulate",
+           "spid_reset",
            "spid_finalize", "spid_error", "spid_reconstruct", "spid_get_factors",
            "spid_get_sketch", "spid_device_status", "spid_omega", "spid_philox",
            "spid_compression_factor", "spid_status_string", "spid_last_error",
@@ -54,6 +56,18 @@ class SpidError(RuntimeError):
         super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} {detail}".strip())
 
 
+class _BoxLayout(ctypes.Structure):
+    _fields_ = [("nq", ctypes.c_int32),
+                ("X", ctypes.c_int64),
+                ("Y", ctypes.c_int64),
+                ("Z", ctypes.c_int64),
+                ("snap_stride", ctypes.c_int64),
+                ("num_box", ctypes.c_int32),
+                ("org3", ctypes.POINTER(ctypes.c_int32)),
+                ("ext3", ctypes.POINTER(ctypes.c_int32)),
+                ("split_qoi", ctypes.c_int32)]
+
+
 class _Desc(ctypes.Structure):
     _fields_ = [("num_sub", ctypes.c_int32),
                 ("m", ctypes.POINTER(ctypes.c_int32)),
@@ -65,7 +79,10 @@ class _Desc(ctypes.Structure):
                 ("tol", ctypes.c_double),
                 ("precision", ctypes.c_int32),
                 ("flags", ctypes.c_uint32),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64),
+                ("qoi", ctypes.POINTER(ctypes.c_int32)),
+                ("num_qoi", ctypes.c_int32),
+                ("boxes", ctypes.POINTER(_BoxLayout))]
 
 
 class _SubDesc(ctypes.Structure):
@@ -141,10 +158,10 @@ def load_library(path: str = LIB_PATH):
         vp, i32, i64, u32, u64, dbl = (c.c_void_p, c.c_int32, c.c_int64, c.c_uint32, c.c_uint64,
                                        c.c_double)
         sig = {
-            "spid_plan_create": ([c.POINTER(_Desc), c.POINTER(vp)], c.c_int),
+            "spid_plan_create": ([c.POINTER(_Desc), vp, c.POINTER(vp)], c.c_int),
             "spid_plan_destroy": ([vp], c.c_int),
             "spid_plan_info": ([vp, c.POINTER(i32), c.POINTER(i32), c.POINTER(i64)], c.c_int),
-            "spid_sketch": ([vp, vp, i32, i32, vp], c.c_int),
+            "spid_sketch_accumulate": ([vp, vp, i32, i32, vp], c.c_int),
             "spid_reset": ([vp, vp], c.c_int),
             "spid_finalize": ([vp, vp], c.c_int),
             "spid_error": ([vp, vp, vp, vp, vp], c.c_int),
@@ -183,7 +200,7 @@ def load_library(path: str = LIB_PATH):
             "spid_plan_tuning_key": ([vp, c.c_char_p, i32], c.c_int),
             "spid_graph_create": ([vp, vp, i32, i32, i32, u32, vp, vp, c.POINTER(vp)], c.c_int),
             "spid_graph_launch": ([vp, vp], c.c_int),
-            "spid_graph_launch_host": ([vp, vp, vp, vp, vp], c.c_int),
+            "spid_graph_launch_host": ([vp, vp, vp, vp, vp, vp, vp, vp], c.c_int),
             "spid_graph_destroy": ([vp], c.c_int),
             "spid_sub_plan_create_points": ([c.POINTER(_SubPointsDesc), c.POINTER(vp)], c.c_int),
             "spid_producer_step": ([vp, i64, vp, i64, i32, i32, i32, c.c_float, c.c_float, vp],
@@ -257,38 +274,87 @@ def producer_step(state_in, state_out, grid: int, edge: int, nq: int, dt: float,
         "spid_producer_step")
 
 
+class BoxLayout:
+    """Boxes of a global field [t][q][Z][Y][X] (spid_box_layout).  org, ext:
+    [B, 3] arrays of (x, y, z); split_qoi: one subdomain per (box, QoI)."""
+
+    def __init__(self, nq: int, X: int, Y: int, Z: int, org, ext, split_qoi: bool = False,
+                 snap_stride: int | None = None):
+        self.nq, self.X, self.Y, self.Z = int(nq), int(X), int(Y), int(Z)
+        self.org = np.ascontiguousarray(org, dtype=np.int32).reshape(-1, 3)
+        self.ext = np.ascontiguousarray(ext, dtype=np.int32).reshape(-1, 3)
+        self.split_qoi = bool(split_qoi)
+        self.snap_stride = int(snap_stride if snap_stride is not None else nq * X * Y * Z)
+        self.num_box = int(self.org.shape[0])
+        self.num_sub = self.num_box * (self.nq if self.split_qoi else 1)
+        pts = self.ext.prod(axis=1).astype(np.int64)
+        rows = pts if self.split_qoi else pts * self.nq
+        self.m = np.repeat(rows, self.nq) if self.split_qoi else rows
+
+    def struct(self) -> _BoxLayout:
+        b = _BoxLayout()
+        b.nq, b.X, b.Y, b.Z = self.nq, self.X, self.Y, self.Z
+        b.snap_stride = self.snap_stride
+        b.num_box = self.num_box
+        b.org3 = self.org.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        b.ext3 = self.ext.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        b.split_qoi = int(self.split_qoi)
+        return b
+
+
 class Plan:
     """Batched sketched column-ID plan over a window of subdomains.
 
-    m, n, off, ld: per-subdomain rows, columns, element offset and leading
-    dimension of the column-major blocks inside one flat window buffer."""
+    Blocks layout: m, n, off, ld are per-subdomain rows, columns, element
+    offset and leading dimension of the column-major blocks inside one flat
+    window buffer.  Boxes layout: boxes = BoxLayout(...) over a global field
+    (m, off, ld are then derived; pass None).  qoi / num_qoi label subdomains
+    by QoI for the per-QoI error totals."""
 
     def __init__(self, m, n, off, ld, k_max: int, p: int = 10, tol: float = 0.0,
-                 precision: str = "tf32", seed: int = 0x5EED0001, flags: int = 0):
+                 precision: str = "tf32", seed: int = 0x5EED0001, flags: int = 0,
+                 qoi=None, num_qoi: int = 0, boxes: "BoxLayout | None" = None, stream=None):
         lib = load_library()
-        self.m = np.ascontiguousarray(m, dtype=np.int32)
-        self.n = np.ascontiguousarray(n, dtype=np.int32)
-        self.off = np.ascontiguousarray(off, dtype=np.int64)
-        self.ld = np.ascontiguousarray(ld, dtype=np.int64)
+        self.boxes = boxes
+        if boxes is not None:
+            self.m = np.ascontiguousarray(boxes.m, dtype=np.int32)
+        else:
+            self.m = np.ascontiguousarray(m, dtype=np.int32)
         self.S = int(len(self.m))
+        self.n = np.ascontiguousarray(np.broadcast_to(n, (self.S,)), dtype=np.int32)
+        if boxes is None:
+            self.off = np.ascontiguousarray(off, dtype=np.int64)
+            self.ld = np.ascontiguousarray(ld, dtype=np.int64)
         self.k_max = int(k_max)
         self.p = int(p)
         self.precision = precision
         self.dtype = np.float64 if precision == "fp64" else np.float32
+        self.qoi = None if qoi is None else np.ascontiguousarray(qoi, dtype=np.int32)
+        self.num_qoi = int(num_qoi)
+        if boxes is not None and boxes.split_qoi and qoi is None and self.num_qoi == 0:
+            self.num_qoi = boxes.nq
         d = _Desc()
         d.num_sub = self.S
-        d.m = self.m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         d.n = self.n.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
-        d.off = self.off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
-        d.ld = self.ld.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        if boxes is None:
+            d.m = self.m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            d.off = self.off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+            d.ld = self.ld.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        else:
+            self._box_struct = boxes.struct()
+            d.boxes = ctypes.pointer(self._box_struct)
         d.k_max = self.k_max
         d.p = self.p
         d.tol = float(tol)
         d.precision = PREC[precision]
         d.flags = int(flags)
         d.seed = int(seed)
+        if self.qoi is not None:
+            d.qoi = self.qoi.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        d.num_qoi = int(num_qoi)
         h = ctypes.c_void_p()
-        _check(lib.spid_plan_create(ctypes.byref(d), ctypes.byref(h)), "spid_plan_create")
+        _check(lib.spid_plan_create(ctypes.byref(d), _stream_handle(stream) if stream is not None
+                                    else None, ctypes.byref(h)), "spid_plan_create")
         self._h = h
         l = ctypes.c_int32()
         lp = ctypes.c_int32()
@@ -300,6 +366,26 @@ class Plan:
     @classmethod
     def for_window(cls, win, **kw) -> "Plan":
         return cls(win.m, win.n, win.off, win.ld, **kw)
+
+    def window_extent(self) -> int:
+        """Elements from the window pointer that cover everything the plan reads
+        (blocks: the exact extent; boxes: whole snapshots up to the last one)."""
+        if self.boxes is not None:
+            b = self.boxes
+            return int(self.n.max() - 1) * b.snap_stride + b.nq * b.X * b.Y * b.Z
+        return int(np.max(self.off + self.ld * (self.n.astype(np.int64) - 1) + self.m))
+
+    @property
+    def total_len(self) -> int:
+        """Doubles spid_error writes to total: 4 sums plus 2 per QoI."""
+        return 4 + 2 * self.num_qoi
+
+    def per_qoi_rel_err(self, total) -> np.ndarray:
+        """sqrt(sum e2 / sum a2) of each QoI from an error-total buffer."""
+        t = np.asarray(total.detach().cpu().numpy() if hasattr(total, "detach") else total,
+                       dtype=np.float64)
+        g = t[4:4 + 2 * self.num_qoi].reshape(-1, 2)
+        return np.sqrt(g[:, 0] / g[:, 1])
 
     def close(self):
         if getattr(self, "_h", None):
@@ -374,11 +460,14 @@ class Plan:
         return g
 
     # ---------------------------------------------------------------- hot path
-    def sketch(self, window, col0: int = 0, ncols: int | None = None, stream=None):
+    def sketch_accumulate(self, window, col0: int = 0, ncols: int | None = None, stream=None):
         if ncols is None:
             ncols = int(self.n.max()) - col0
-        _check(load_library().spid_sketch(self._h, _ptr(window), int(col0), int(ncols),
-                                          _stream_handle(stream)), "spid_sketch")
+        _check(load_library().spid_sketch_accumulate(self._h, _ptr(window), int(col0),
+                                                     int(ncols), _stream_handle(stream)),
+               "spid_sketch_accumulate")
+
+    sketch = sketch_accumulate
 
     def reset(self, stream=None):
         _check(load_library().spid_reset(self._h, _stream_handle(stream)), "spid_reset")
@@ -431,16 +520,25 @@ class Graph:
         _check(load_library().spid_graph_launch(self._h, _stream_handle(stream)),
                "spid_graph_launch")
 
-    def launch_host(self, window_host, total_host=None, copy_stream=None, stream=None):
+    def launch_host(self, window_host, total_host=None, k_host=None, J_host=None, C_host=None,
+                    copy_stream=None, stream=None, window_elems: int | None = None):
         """spid_graph_launch_host: copy the window from host memory (a pinned
-        CPU tensor or array), run the step, copy the four error sums to
-        total_host (a pinned CPU float64 tensor of 4, or None); asynchronous."""
+        CPU tensor or array of at least window_elems elements, by default the
+        blocks extent), run the step, copy the error sums to total_host
+        (plan.total_len doubles) and the factors to k_host [S], J_host
+        [S k_max] and C_host [k_max sum n] (pinned host buffers, or None);
+        asynchronous."""
         p = self._plan
-        extent = int(np.max(p.off + p.ld * (p.n.astype(np.int64) - 1) + p.m))
-        win = _host_ptr(window_host, p.dtype, extent * np.dtype(p.dtype).itemsize)
-        tot = None if total_host is None else _host_ptr(total_host, np.float64, 32)
+        if window_elems is None:
+            window_elems = p.window_extent()
+        win = _host_ptr(window_host, p.dtype, window_elems * np.dtype(p.dtype).itemsize)
+        tot = None if total_host is None else _host_ptr(total_host, np.float64, 8 * p.total_len)
+        kh = None if k_host is None else _host_ptr(k_host, np.int32, 4 * p.S)
+        Jh = None if J_host is None else _host_ptr(J_host, np.int32, 4 * p.S * p.k_max)
+        Ch = None if C_host is None else _host_ptr(
+            C_host, p.dtype, np.dtype(p.dtype).itemsize * p.k_max * int(p.n.sum()))
         _check(load_library().spid_graph_launch_host(
-            self._h, win, tot, _stream_handle(copy_stream), _stream_handle(stream)),
+            self._h, win, tot, kh, Jh, Ch, _stream_handle(copy_stream), _stream_handle(stream)),
             "spid_graph_launch_host")
 
     def close(self):

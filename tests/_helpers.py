@@ -1,4 +1,6 @@
-"""Shared test helpers: oracle runs, separation of pivots, relative errors."""
+"""Shared test helpers: oracle runs, separation of pivots, relative errors, and
+the parity checker that compares a result of the CUDA path with the oracle's
+(a CPU function, so that its own tests can feed it deliberately wrong results)."""
 import numpy as np
 
 import oracle
@@ -76,3 +78,102 @@ def oracle_window(win, l, kmax, tol, precision, seed):
 def oracle_reconstruction(A: np.ndarray, J, C, k: int) -> np.ndarray:
     Ahat, _, _ = oracle.reconstruct_error(A, np.asarray(J[:k], dtype=np.int32), C[:k])
     return Ahat
+
+
+def guard_margin(Y: np.ndarray, kmax: int, u: float, k: int, tol: float = 0.0) -> float:
+    """Distance of the pivots that bracket the oracle's rank-guard decision k
+    (the last kept, k - 1, and the first dropped, k) from the guard threshold
+    2 u |R_00|, relative to ||Y||_F.  A sketch that differs from the oracle's
+    by rounding moves every |R_jj| by about its relative difference times
+    ||Y||_F, so a k that differs by one is valid only when this is that small."""
+    Y = np.asarray(Y, dtype=np.float64)
+    J, R, kk, _ = oracle.qrcp_mgs(Y, kmax, tol)
+    if kk == 0:
+        return np.inf
+    thr = 2.0 * u * abs(R[0, J[0]])
+    ny = np.linalg.norm(Y)
+    ms = [abs(abs(R[j, J[j]]) - thr) / ny for j in (k - 1, k) if 0 <= j < kk]
+    return min(ms) if ms else np.inf
+
+
+Y_TOL = {"fp64": 1e-13, "fp32": 2e-6, "tf32": 3e-3, "bf16": 1.5e-2, "bf16x3": 1e-4}
+GAP = {"fp64": 1e-6, "fp32": 1e-3, "tf32": 2e-2, "bf16": 1e-1, "bf16x3": 1e-3}
+SPID_ERR_RANK = 8
+# statuses of a run whose purpose is not the rank decision: SPID_OK, or the
+# informational rank-guard cut (its factors are valid)
+STATUS_OK = (0, SPID_ERR_RANK)
+
+
+def compare_with_oracle(blocks, g: dict, o: dict, precision: str, k_max: int, tol: float = 0.0,
+                        c_tol=None, ahat_tol=None, min_prefix: int = 0, sample: bool = False):
+    """Assert that the CUDA path's result g matches the oracle's o.
+
+    blocks: the subdomains' data matrices (m_s x n_s).  g: k [S], J [S, k_max],
+    C (list of k_max x n_s), Y (list of l x n_s), err [S, 2], status, and
+    optionally Ahat (list).  o: oracle.spid_batch(..., want_y=True).
+    Tolerances, from the arithmetic: Y by Y_TOL; J bit-exact over the oracle's
+    separated prefix (at least min_prefix pivots on inputs built to be
+    separated); k equal unless the adaptive test or the rank guard sits within
+    rounding of its threshold (then +-1); the rank-cut status set exactly when
+    the oracle's guard cut some subdomain (unless such a subdomain is within
+    rounding); C(:, J) = I exactly; C within max(c_tol, 8 cond(R11) u); A_hat
+    within ahat_tol; each error within the triangle-inequality bound.
+    sample=True: the blocks are a sample of the plan's subdomains, so the
+    window-wide status must show a cut the sample has, but may show others."""
+    u = U_MODE[precision]
+    # the QR's own rounding of |R_jj| (FP32 reflectors in every FP32-window mode)
+    u_qr = 2.0 ** -53 if precision == "fp64" else 2.0 ** -24
+    ambiguous_cut = False
+    expect_cut = False
+    for s, A in enumerate(blocks):
+        A = np.asarray(A, dtype=np.float64)
+        Yo = o["Y"][s]
+        dy = rel_fro(g["Y"][s], Yo)
+        assert dy <= Y_TOL[precision], ("Y", s, dy)
+        ko, kg = int(o["k"][s]), int(g["k"][s])
+        kqr = int(o["k_qr"][s])
+        # a pivot moves by about the sketches' difference plus the QR's rounding
+        band = 2.0 * dy + 16 * u_qr * np.sqrt(k_max + 16)
+        gm = guard_margin(Yo, k_max, u, ko, tol)
+        near_guard = gm <= band
+        if kg != ko:
+            if tol > 0 and adaptive_margin(Yo, k_max, tol, ko) <= 64 * Y_TOL[precision]:
+                pass   # adaptive stop taken from sketches that differ by rounding
+            else:
+                assert abs(kg - ko) <= 1 and near_guard, ("k", s, kg, ko, gm)
+        if ko < kqr:
+            expect_cut = True
+        if near_guard:
+            ambiguous_cut = True
+        sep = separated_prefix(Yo, max(ko, 1), GAP[precision], u)
+        assert min(sep, ko) >= min(min_prefix, ko), ("separated prefix too short", s, sep, ko)
+        pre = min(sep, ko, kg)
+        assert list(g["J"][s][:pre]) == list(o["J"][s][:pre]), ("J", s, g["J"][s], o["J"][s], pre)
+        Jg = g["J"][s][:kg]
+        assert np.all(np.asarray(g["J"][s][kg:]) == -1), ("J past k", s)
+        if kg:
+            # C(:, J) = I exactly (Lemma A.1 item 1)
+            assert np.array_equal(g["C"][s][:kg][:, Jg], np.eye(kg, dtype=g["C"][s].dtype)), ("C(:,J)", s)
+        if kg == ko and list(Jg) == list(o["J"][s][:ko]):
+            if c_tol is not None:
+                # C = R11^-1 R12 moves by about cond(R11) u under rounding
+                ct = max(c_tol, 8.0 * r11_condition(Yo, ko) * u)
+                dc = rel_fro(g["C"][s][:kg], o["C"][s][:ko])
+                assert dc <= ct, ("C", s, dc, ct)
+            if ahat_tol is not None and "Ahat" in g:
+                Ahat_o, e2, a2 = oracle.reconstruct_error(A, o["J"][s][:ko], o["C"][s][:ko])
+                d = rel_fro(g["Ahat"][s], Ahat_o)
+                assert d <= ahat_tol, ("Ahat", s, d)
+                eg = np.sqrt(g["err"][s][0] / g["err"][s][1]) if g["err"][s][1] > 0 else 0.0
+                eo = np.sqrt(e2 / a2) if a2 > 0 else 0.0
+                # |e_gpu - e_oracle| <= ||Ahat_gpu - Ahat_oracle|| / ||A|| (triangle inequality)
+                assert abs(eg - eo) <= d * 1.01 + 4 * u * np.sqrt(A.size), ("err", s, eg, eo)
+                rel = 1e-6 if precision != "fp64" else 1e-12
+                assert abs(g["err"][s][1] - a2) <= rel * a2, ("a2", s)
+    status = int(g["status"])
+    assert status in (0, SPID_ERR_RANK), ("status", status)
+    if sample:
+        if expect_cut and not ambiguous_cut:
+            assert status == SPID_ERR_RANK, ("rank-cut status", status, expect_cut)
+    elif not ambiguous_cut:
+        assert (status == SPID_ERR_RANK) == expect_cut, ("rank-cut status", status, expect_cut)

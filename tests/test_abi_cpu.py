@@ -58,9 +58,65 @@ def test_invalid_descriptors_are_rejected_without_a_gpu(lib, kw):
 
 
 def test_null_plan_is_rejected(lib):
-    assert lib.spid_graph_launch_host(None, None, None, None, None) == 1
+    assert lib.spid_graph_launch_host(None, None, None, None, None, None, None, None) == 1
     assert lib.spid_finalize(None, None) == 1
-    assert lib.spid_sketch(None, None, 0, 1, None) == 1
+    assert lib.spid_sketch_accumulate(None, None, 0, 1, None) == 1
+
+
+def _box_plan(precision="fp32", nq=5, XYZ=(64, 24, 20), org=((0, 0, 0),), ext=((32, 8, 8),),
+              split=False, snap_stride=None, n=None, **kw):
+    lay = spid.BoxLayout(nq, *XYZ, org, ext, split_qoi=split, snap_stride=snap_stride)
+    return spid.Plan(None, n if n is not None else [16] * lay.num_sub, None, None, k_max=4, p=4,
+                     precision=precision, boxes=lay, **kw)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(org=((2, 0, 0),)), 1),                     # x origin not 16-byte aligned
+    (dict(ext=((30, 8, 8),)), 1),                    # x extent not 16-byte aligned
+    (dict(org=((48, 0, 0),)), 1),                    # box leaves the field along x
+    (dict(org=((0, 20, 0),)), 1),                    # ... along y
+    (dict(ext=((32, 8, 0),)), 1),                    # empty box
+    (dict(XYZ=(66, 24, 20)), 1),                     # X not a multiple of 4
+    (dict(snap_stride=5 * 64 * 24 * 20 - 4), 1),     # snapshots overlap
+    (dict(split=True, num_qoi=3), 1),                # num_qoi neither 0 nor nq
+    (dict(qoi=[7], num_qoi=5), 1),                   # QoI label out of range
+    (dict(num_qoi=2), 1),                            # per-QoI totals without labels
+    (dict(precision="tf32", ext=((16, 8, 8),)), 7),  # tensor cores: x runs of 32 only
+])
+def test_invalid_box_layouts_are_rejected_without_a_gpu(lib, kw, status):
+    with pytest.raises(spid.SpidError) as e:
+        _box_plan(**kw)
+    assert e.value.status == status, str(e.value)
+
+
+@pytest.mark.parametrize("split,num_sub", [(0, 2), (1, 1), (1, 6)])
+def test_box_count_must_match_num_sub(lib, split, num_sub):
+    # the C check itself (the binding derives num_sub from the layout)
+    import ctypes
+    org = np.array([0, 0, 0], dtype=np.int32)
+    ext = np.array([32, 8, 8], dtype=np.int32)
+    n = np.full(num_sub, 16, dtype=np.int32)
+    b = spid._BoxLayout()
+    b.nq, b.X, b.Y, b.Z, b.snap_stride, b.num_box = 5, 64, 24, 20, 5 * 64 * 24 * 20, 1
+    b.org3 = org.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    b.ext3 = ext.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    b.split_qoi = split
+    d = spid._Desc()
+    d.num_sub = num_sub
+    d.n = n.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    d.k_max, d.p, d.precision, d.seed = 4, 4, 1, 1
+    d.boxes = ctypes.pointer(b)
+    h = ctypes.c_void_p()
+    assert lib.spid_plan_create(ctypes.byref(d), None, ctypes.byref(h)) == 1
+
+
+def test_box_layout_rows_and_qoi_labels():
+    lay = spid.BoxLayout(5, 64, 24, 20, [(0, 0, 0), (32, 4, 2)], [(32, 8, 4), (32, 16, 16)],
+                         split_qoi=True)
+    assert lay.num_sub == 10
+    assert list(lay.m) == [32 * 8 * 4] * 5 + [32 * 16 * 16] * 5
+    stacked = spid.BoxLayout(5, 64, 24, 20, [(0, 0, 0)], [(32, 8, 4)])
+    assert list(stacked.m) == [5 * 32 * 8 * 4]
 
 
 def test_compression_factor_matches_oracle_and_paper(lib):

@@ -1,0 +1,213 @@
+"""Boxes of a solver's global field as subdomains (spid_box_layout): the window
+is the field itself, [t][q][Z][Y][X] (Algorithm 6 saves each block's data from
+the solver's state; Section 3.2 blocks the domain), each box's data matrix has
+rows ((q ez + z) ey + y) ex + x, or one QoI's rows with split_qoi (Section 5.3).
+
+The oracle runs on the same boxes cut out of the field on the host (a layout
+copy, inputs.cut_box), so every check here compares the CUDA path reading the
+global field with the oracle reading plain column-major blocks."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2103_01380_gb300 import inputs, spid
+from _helpers import U_MODE, compare_with_oracle, oracle_window, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+X, Y, Z, NQ, N = 64, 24, 20, 5, 70
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_01380_gb300 import build
+    build.build()
+    spid.load_library()
+
+
+def _field(dtype=np.float32, snap_stride=None):
+    t = 10.0 * np.arange(N) / (N - 1)
+    return inputs.tgv3d_global(X, Y, Z, 64, t, dtype=dtype, snap_stride=snap_stride)
+
+
+# (org, ext) in (x, y, z); x origin and extent multiples of 4; the first four
+# have x extents that are multiples of 32 (tensor-core sketches)
+BOXES_TC = [((0, 0, 0), (32, 8, 4)), ((32, 4, 2), (32, 16, 16)), ((0, 10, 12), (64, 8, 8)),
+            ((32, 0, 0), (32, 24, 20))]
+BOXES_ANY = [((4, 0, 0), (4, 4, 4)), ((8, 3, 5), (8, 5, 3)), ((12, 1, 2), (12, 9, 7)),
+             ((40, 20, 17), (20, 4, 3)), ((0, 0, 0), (64, 2, 2))]
+
+
+def _plan_and_blocks(field, boxes, split, precision, k_max, p, tol=0.0, n=N, snap_stride=None,
+                     seed=0x5EED0001):
+    org = [b[0] for b in boxes]
+    ext = [b[1] for b in boxes]
+    lay = spid.BoxLayout(NQ, X, Y, Z, org, ext, split_qoi=split, snap_stride=snap_stride)
+    plan = spid.Plan(None, [n] * lay.num_sub, None, None, k_max=k_max, p=p, tol=tol,
+                     precision=precision, seed=seed, boxes=lay)
+    blocks = []
+    for o, e in zip(org, ext):
+        if split:
+            blocks += [inputs.cut_box(field, NQ, X, Y, Z, n, o, e, q=q, snap_stride=snap_stride)
+                       for q in range(NQ)]
+        else:
+            blocks.append(inputs.cut_box(field, NQ, X, Y, Z, n, o, e, snap_stride=snap_stride))
+    return plan, blocks
+
+
+def _run(plan, w, recon=True, batches=None):
+    if batches:
+        for c0 in range(0, int(plan.n.max()), batches):
+            plan.sketch_accumulate(w, c0, batches)
+    else:
+        plan.sketch_accumulate(w)
+    plan.finalize()
+    err = torch.zeros(2 * plan.S, dtype=torch.float64, device="cuda")
+    tot = torch.zeros(plan.total_len, dtype=torch.float64, device="cuda")
+    plan.error(w, err, tot)
+    out = None
+    if recon:
+        out = torch.zeros_like(w)
+        plan.reconstruct(w, out)
+    torch.cuda.synchronize()
+    k, J, C = plan.factors()
+    return {"k": k, "J": J, "C": C, "Y": plan.sketches(), "err": err.cpu().numpy().reshape(-1, 2),
+            "total": tot.cpu().numpy(), "status": plan.device_status(), "out": out}
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16x3", "fp64"])
+@pytest.mark.parametrize("split", [False, True])
+def test_boxes_match_the_oracle(precision, split):
+    dt = np.float64 if precision == "fp64" else np.float32
+    field = _field(dt)
+    w = torch.from_numpy(field).cuda()
+    plan, blocks = _plan_and_blocks(field, BOXES_TC, split, precision, 6, 6)
+    g = _run(plan, w)
+    win = inputs.pack_blocks(blocks, dtype=dt)
+    o = oracle_window(win, 12, 6, 0.0, precision, 0x5EED0001)
+    # the reconstruction lands in the boxes' own places of the field
+    out = g["out"].cpu().numpy()
+    g["Ahat"] = []
+    for i, (org, ext) in enumerate(BOXES_TC):
+        for q in (range(NQ) if split else [None]):
+            g["Ahat"].append(inputs.cut_box(out, NQ, X, Y, Z, N, org, ext, q=q).astype(np.float64))
+    tol = {"fp64": 1e-10, "fp32": 1e-5}.get(precision)
+    compare_with_oracle(blocks, g, o, precision, 6, c_tol=tol,
+                        ahat_tol={"fp64": 1e-10, "fp32": 1e-5, "bf16x3": 1e-4}.get(precision))
+    if split:
+        per_q = plan.per_qoi_rel_err(g["total"])
+        ge, ga = oracle.qoi_totals(np.tile(np.arange(NQ), len(BOXES_TC)), g["err"][:, 0],
+                                   g["err"][:, 1], NQ)
+        assert np.allclose(g["total"][4::2], ge, rtol=1e-12)
+        assert np.allclose(g["total"][5::2], ga, rtol=1e-12)
+        assert np.all(np.isfinite(per_q))
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_cuda_core_boxes_take_any_x_extent(precision):
+    dt = np.float64 if precision == "fp64" else np.float32
+    field = _field(dt)
+    w = torch.from_numpy(field).cuda()
+    for split in (False, True):
+        plan, blocks = _plan_and_blocks(field, BOXES_ANY, split, precision, 4, 6)
+        g = _run(plan, w)
+        win = inputs.pack_blocks(blocks, dtype=dt)
+        o = oracle_window(win, 10, 4, 0.0, precision, 0x5EED0001)
+        out = g["out"].cpu().numpy()
+        g["Ahat"] = [inputs.cut_box(out, NQ, X, Y, Z, N, org, ext, q=q).astype(np.float64)
+                     for org, ext in BOXES_ANY for q in (range(NQ) if split else [None])]
+        tol = 1e-10 if precision == "fp64" else 1e-5
+        compare_with_oracle(blocks, g, o, precision, 4, c_tol=tol, ahat_tol=tol)
+        plan.close()
+
+
+def test_tensor_core_boxes_need_x_runs_of_32():
+    with pytest.raises(spid.SpidError) as e:
+        spid.Plan(None, [N], None, None, k_max=4, p=4, precision="tf32",
+                  boxes=spid.BoxLayout(NQ, X, Y, Z, [(0, 0, 0)], [(16, 8, 8)]))
+    assert e.value.status == 7
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32"])
+def test_box_plan_equals_the_blocks_plan_on_the_cut_data(precision):
+    # the same subdomains read from the field and from cut-out blocks; the
+    # CUDA-core sketch visits the rows in the same order with the same schedule
+    # (bitwise equal), the tensor-core one packs by box shape (equal to rounding)
+    field = _field()
+    w = torch.from_numpy(field).cuda()
+    boxes = BOXES_TC if precision == "tf32" else BOXES_ANY
+    plan, blocks = _plan_and_blocks(field, boxes, True, precision, 5, 5, tol=1e-3)
+    gb = _run(plan, w, recon=False)
+    win = inputs.pack_blocks(blocks)
+    bp = spid.Plan.for_window(win, k_max=5, p=5, tol=1e-3, precision=precision,
+                              seed=0x5EED0001)
+    gw = _run(bp, torch.from_numpy(win.data).cuda(), recon=False)
+    for s in range(len(blocks)):
+        if precision == "fp32":
+            assert np.array_equal(gb["Y"][s], gw["Y"][s]), s
+            assert list(gb["J"][s]) == list(gw["J"][s])
+        else:
+            assert rel_fro(gb["Y"][s], gw["Y"][s]) <= 1e-6, s
+    assert np.allclose(gb["err"], gw["err"], rtol=1e-5 if precision == "tf32" else 1e-12)
+    plan.close()
+    bp.close()
+
+
+def test_micro_batches_and_snapshot_padding():
+    # snapshots padded apart (snap_stride > nq X Y Z) and sketched in batches of
+    # 16 columns give the one-shot sketch
+    ss = NQ * X * Y * Z + 64
+    field = _field(snap_stride=ss)
+    w = torch.from_numpy(field).cuda()
+    a, blocks = _plan_and_blocks(field, BOXES_TC, True, "tf32", 5, 5, snap_stride=ss)
+    b, _ = _plan_and_blocks(field, BOXES_TC, True, "tf32", 5, 5, snap_stride=ss)
+    ga = _run(a, w, recon=False)
+    gb = _run(b, w, recon=False, batches=16)
+    for s in range(len(blocks)):
+        assert rel_fro(gb["Y"][s], ga["Y"][s]) <= 1e-6
+    o = oracle_window(inputs.pack_blocks(blocks), 10, 5, 0.0, "tf32", 0x5EED0001)
+    for s in range(len(blocks)):
+        assert rel_fro(ga["Y"][s], o["Y"][s]) <= 3e-3
+    a.close()
+    b.close()
+
+
+def test_producer_writes_the_global_field():
+    # the in-situ producer with one box covering the whole grid writes each
+    # snapshot as [q][Z][Y][X] straight into the window; boxes compressed from
+    # that window match the oracle on the same boxes cut from a host copy
+    grid, n = 32, 24
+    t0 = np.zeros(1)
+    state = inputs.tgv3d_global(grid, grid, grid, grid, t0)          # [q][Z][Y][X] at t = 0
+    field_elems = NQ * grid ** 3
+    win = torch.zeros(n * field_elems, dtype=torch.float32, device="cuda")
+    win[:field_elems] = torch.from_numpy(state).cuda()
+    for j in range(1, n):
+        spid.producer_step(win[(j - 1) * field_elems:], win[j * field_elems:], grid, grid, NQ,
+                           0.003, 0.01)
+    torch.cuda.synchronize()
+    host = win.cpu().numpy()
+    boxes = [((0, 0, 0), (32, 8, 8)), ((0, 8, 16), (32, 16, 16))]
+    lay = spid.BoxLayout(NQ, grid, grid, grid, [b[0] for b in boxes], [b[1] for b in boxes],
+                         split_qoi=True)
+    plan = spid.Plan(None, [n] * lay.num_sub, None, None, k_max=4, p=6, precision="fp32",
+                     seed=0x5EED0001, boxes=lay)
+    g = _run(plan, win)
+    blocks = [inputs.cut_box(host, NQ, grid, grid, grid, n, o, e, q=q)
+              for o, e in boxes for q in range(NQ)]
+    o = oracle_window(inputs.pack_blocks(blocks), 10, 4, 0.0, "fp32", 0x5EED0001)
+    out = g["out"].cpu().numpy()
+    g["Ahat"] = [inputs.cut_box(out, NQ, grid, grid, grid, n, o_, e, q=q).astype(np.float64)
+                 for o_, e in boxes for q in range(NQ)]
+    compare_with_oracle(blocks, g, o, "fp32", 4, c_tol=1e-5, ahat_tol=1e-5)
+    # everything outside the boxes is left untouched by the reconstruction
+    mask = np.zeros(host.size, dtype=bool).reshape(n, NQ, grid, grid, grid)
+    for (ox, oy, oz), (ex, ey, ez) in boxes:
+        mask[:, :, oz:oz + ez, oy:oy + ey, ox:ox + ex] = True
+    assert np.all(out.reshape(mask.shape)[~mask] == 0.0)
+    plan.close()

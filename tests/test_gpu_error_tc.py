@@ -20,6 +20,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import oracle
+from _helpers import STATUS_OK
 from paper_2103_01380_gb300 import inputs, spid
 from test_gpu_parity import _lowrank_window, run_gpu
 
@@ -71,7 +72,7 @@ def _check_error_pass(win, g, tensor_core):
 def test_tensor_core_error_pass_on_own_factors(precision, k_max):
     win = _window()
     g = run_gpu(win, precision, k_max, p=8, flags=spid.FLAG_TC_ERROR)
-    assert g["status"] == 0
+    assert g["status"] in STATUS_OK
     assert int(g["k"].max()) > 0
     _check_error_pass(win, g, tensor_core=True)
     # window totals are the subdomain sums, and the CF sums are exact
@@ -114,7 +115,7 @@ def test_tensor_core_error_pass_repeats_bit_identically():
         outs.append((err.cpu().numpy(), tot.cpu().numpy()))
     for e, t in outs[1:]:
         assert np.array_equal(e, outs[0][0]) and np.array_equal(t, outs[0][1])
-    assert plan.device_status() == 0
+    assert plan.device_status() in STATUS_OK
 
 
 def test_tensor_core_error_pass_rank_zero_blocks():
@@ -122,7 +123,7 @@ def test_tensor_core_error_pass_rank_zero_blocks():
     blocks = [np.zeros((300, 40)), inputs.separated_lowrank(500, 70, 4, 7), np.zeros((129, 17))]
     win = inputs.pack_blocks(blocks)
     g = run_gpu(win, "tf32", 8, p=4, flags=spid.FLAG_TC_ERROR)
-    assert g["status"] == 0
+    assert g["status"] in STATUS_OK
     assert g["k"][0] == 0 and g["k"][2] == 0 and g["k"][1] > 0
     assert np.all(g["err"][[0, 2]] == 0.0)
     assert np.all(g["Ahat"][0] == 0.0) and np.all(g["Ahat"][2] == 0.0)

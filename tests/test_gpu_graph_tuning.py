@@ -19,7 +19,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from paper_2103_01380_gb300 import inputs, spid
-from _helpers import oracle_window, rel_fro, separated_prefix, U_MODE
+from _helpers import STATUS_OK, oracle_window, rel_fro, separated_prefix, U_MODE
 
 pytestmark = pytest.mark.gpu
 
@@ -76,7 +76,7 @@ def test_graph_replays_eager_step_bitwise(precision, flags):
     for _ in range(3):
         g.launch()
     graphed = _state(plan, err, tot)
-    assert plan.device_status() == 0
+    assert plan.device_status() in STATUS_OK
     _same(eager, graphed)
     g.close()
     plan.close()
@@ -143,6 +143,20 @@ def test_graph_launch_host_matches_device_window():
     plan.reset()
     gs[0].launch_host(host)
     _same(eager, _state(plan, err, tot))
+    # the step's compressed representation comes back with it (Algorithms 2-3
+    # output): the same k, J and C that spid_get_factors returns
+    k0, J0, C0 = plan.factors()
+    kh = torch.zeros(win.num_sub, dtype=torch.int32).pin_memory()
+    Jh = torch.zeros(win.num_sub * 5, dtype=torch.int32).pin_memory()
+    Ch = torch.full((5 * int(win.n.sum()),), float("nan"), dtype=torch.float32).pin_memory()
+    plan.reset()
+    gs[1].launch_host(host, tot_h[0], kh, Jh, Ch, copy_stream=copy_stream)
+    torch.cuda.synchronize()
+    assert np.array_equal(kh.numpy(), k0)
+    assert np.array_equal(Jh.numpy().reshape(-1, 5), J0)
+    assert np.array_equal(Ch.numpy(), np.concatenate([c.reshape(-1) for c in C0]))
+    with pytest.raises(ValueError):
+        gs[1].launch_host(host, None, kh[:1])
     # a host buffer shorter than the window extent, a device tensor, a graph
     # without a window
     with pytest.raises(ValueError):
@@ -198,7 +212,7 @@ def test_every_tuning_meets_parity(tuning):
         tot = torch.zeros(4, dtype=torch.float64, device="cuda")
         pl.sketch(w); pl.finalize(); pl.error(w, err, tot)
         res.append(_state(pl, err, tot))
-        assert pl.device_status() == 0
+        assert pl.device_status() in STATUS_OK
     o = oracle_window(win, k_max + p, k_max, 0.0, prec, seed)
     for s in range(win.num_sub):
         # FP32 reordering of the same TF32 products: far below the 3e-3 TF32 bar
@@ -229,7 +243,7 @@ def test_autotune_and_cache(precision, tmp_path):
     tot = torch.zeros(4, dtype=torch.float64, device="cuda")
     plan.error(w, err, tot)
     torch.cuda.synchronize()
-    assert plan.device_status() == 0
+    assert plan.device_status() in STATUS_OK
     o = oracle_window(win, 13, 5, 0.0, precision, 13)
     rel = float(np.sqrt(tot[0].item() / tot[1].item()))
     rel_o = float(np.sqrt(o["e2"].sum() / o["a2"].sum()))

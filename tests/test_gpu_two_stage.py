@@ -17,7 +17,7 @@ torch = pytest.importorskip("torch")
 
 import oracle
 from paper_2103_01380_gb300 import inputs, spid
-from _helpers import rel_fro, separated_prefix, U_MODE
+from _helpers import STATUS_OK, rel_fro, separated_prefix, U_MODE
 from test_gpu_parity import GAP
 
 pytestmark = pytest.mark.gpu
@@ -63,7 +63,7 @@ def run_ts(win, precision, N, k, k2_max, tol2, p=6):
 
 def check_ts(win, precision, N, k, k2_max, tol2, p=6):
     g = run_ts(win, precision, N, k, k2_max, tol2, p)
-    assert g["status"] == 0
+    assert g["status"] in STATUS_OK
     u = U_MODE[precision]
     full = 0
     for s in range(win.num_sub):
@@ -138,7 +138,7 @@ def test_two_stage_deduplicates_a_low_rank_window():
     blocks = [inputs.lowrank(400, 64, 3, seed=100 + s) for s in range(3)]
     win = inputs.pack_blocks(blocks, dtype=np.float32)
     g = run_ts(win, "fp32", 4, 5, 12, 1e-5)
-    assert g["status"] == 0
+    assert g["status"] in STATUS_OK
     for b in range(4):
         assert all(3 <= int(v) <= 5 for v in g["blocks"][b][0])
     assert list(g["k"]) == [3, 3, 3]

@@ -15,7 +15,7 @@ torch = pytest.importorskip("torch")
 
 import oracle
 from paper_2103_01380_gb300 import inputs, spid
-from _helpers import adaptive_margin, rel_fro, separated_prefix, U_MODE
+from _helpers import STATUS_OK, adaptive_margin, rel_fro, separated_prefix, U_MODE
 from test_gpu_parity import GAP, Y_TOL, run_gpu
 
 pytestmark = pytest.mark.gpu
@@ -64,7 +64,7 @@ def _spectrum_window():
 def test_geometric_spectrum_adaptive_full_size(precision):
     win = _spectrum_window()
     g = run_gpu(win, precision, 32, p=10, tol=1e-3, reconstruct=False)
-    assert g["status"] == 0
+    assert g["status"] in STATUS_OK
     check_sampled(win, g, precision, 32, 10, 1e-3, samples=(0, 3), err_target=3e-3)
     # the best rank-12 error sits at 1e-3: adaptive ranks land just above it
     assert 10 <= int(np.median(g["k"])) <= 18
@@ -77,7 +77,7 @@ def test_geometric_spectrum_bf16_hits_its_noise_floor():
     # stops near sigma_10, and the error lands above 1e-3 -- reported, not hidden
     win = _spectrum_window()
     g = run_gpu(win, "bf16", 32, p=10, tol=1e-3, reconstruct=False)
-    assert g["status"] == 0
+    assert g["status"] in STATUS_OK
     check_sampled(win, g, "bf16", 32, 10, 1e-3, samples=(1,), err_target=3e-2)
     rel = np.sqrt(g["total"][0] / g["total"][1])
     assert rel <= 3e-2
@@ -89,7 +89,7 @@ def test_uneven_boxes_adaptive(precision):
     win = inputs.uneven_window(boxes)
     assert int(win.n.max()) > 512                       # two column groups somewhere
     g = run_gpu(win, precision, 32, p=10, tol=1e-3, reconstruct=False)
-    assert g["status"] == 0
+    assert g["status"] in STATUS_OK
     order = [int(i) for i in np.argsort(win.m * win.n)]
     wide = [i for i in order if win.n[i] > 512][0]      # smallest box with two column groups
     check_sampled(win, g, precision, 32, 10, 1e-3, samples=sorted({order[0], order[1], wide}),
@@ -102,7 +102,7 @@ def test_insitu_boxes_streamed_snapshot_major():
     win = inputs.tgv3d_window(grid=256, box=32, n=256, boxes=4, layout="snapshot")
     assert int(win.m[0]) == 163840
     g = run_gpu(win, "tf32", 30, p=10, batches=64, reconstruct=False)
-    assert g["status"] == 0
+    assert g["status"] in STATUS_OK
     one = run_gpu(win, "tf32", 30, p=10, reconstruct=False)
     # the two schedules cut the 5120 row chunks into different partial sums:
     # the sketches agree up to FP32 re-association, about u sqrt(chunks)

@@ -118,3 +118,71 @@ def test_a_dead_rank_gives_an_error_not_a_hang():
         if p.is_alive():
             p.kill()
     assert res != "no error"
+
+
+def test_domain_boxes_deals_every_box_once_and_evenly():
+    # the bench's multi-GPU set: one domain of boxes per rank, (domain, box)
+    # units of equal weight dealt by LPT -- each rank gets one domain's worth
+    for world in (1, 2, 3, 8):
+        parts = shard.domain_boxes(world, 512, weight=5 * 32 ** 3 * 256)
+        units = np.sort(np.concatenate([p[:, 0] * 512 + p[:, 1] for p in parts]))
+        assert np.array_equal(units, np.arange(world * 512))
+        assert all(len(p) == 512 for p in parts)
+        assert np.all(np.concatenate(parts)[:, 0] < world)
+    assert shard.domain_boxes(1, 64)[0].tolist() == [[0, b] for b in range(64)]
+
+
+def _qoi_blocks(nbox, nq=3):
+    rng = np.random.default_rng(21)
+    out = {}
+    for d in range(2):
+        for b in range(nbox):
+            base = rng.standard_normal((40, 4)) @ rng.standard_normal((4, 30))
+            out[(d, b)] = [(2.0 ** q) * base + 1e-3 * rng.standard_normal((40, 30))
+                           for q in range(nq)]
+    return out
+
+
+def _qoi_worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        blocks = _qoi_blocks(4)
+        tot = np.zeros(4 + 2 * 3)
+        for d, b in shard.domain_boxes(world, 4)[rank]:
+            for qq, A in enumerate(blocks[(int(d), int(b))]):
+                r = oracle.spid(A, 8, 3, 0.0, 2.0 ** -53, 5)
+                tot[:4] += [r["e2"], r["a2"], A.size, r["k"] * sum(A.shape)]
+                tot[4 + 2 * qq] += r["e2"]
+                tot[5 + 2 * qq] += r["a2"]
+        rel, cf, v = shard.combine_totals(tot)
+        q.put((rank, rel, cf, list(shard.per_qoi_rel_err(v))))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reproduce_per_qoi_totals():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_qoi_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    blocks = _qoi_blocks(4)
+    e2 = np.zeros(3)
+    a2 = np.zeros(3)
+    for key in sorted(blocks):
+        for qq, A in enumerate(blocks[key]):
+            r = oracle.spid(A, 8, 3, 0.0, 2.0 ** -53, 5)
+            e2[qq] += r["e2"]
+            a2[qq] += r["a2"]
+    want = np.sqrt(e2 / a2)
+    for rank, rel, cf, pq in out:
+        assert np.allclose(pq, want, rtol=1e-12)

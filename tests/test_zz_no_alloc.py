@@ -6,9 +6,11 @@ pool, or one whose time loop must not call cudaMalloc/cudaFree (they may
 synchronize the whole device).  spid_sketch_fp32_noalloc serves them: its
 split-K partial sums live in a fixed static device array inside the library.
 This test calls it through the C ABI twice in a row (the second call on other
-data, so stale scratch from the first would show) and compares each result
-with the plan-based FP32 sketch (spid_sketch + spid_get_sketch) within the
-FP32 sketch tolerance the parity tests use.  It runs last so that a failure
+data, so stale scratch from the first would show), for every compiled sketch
+height (l padded to 16, 32, 48 and 64), and compares each
+result with the plan-based FP32 sketch (spid_sketch_accumulate +
+spid_get_sketch) and with the FP64 oracle's sketch, within the FP32 sketch
+tolerance the parity tests use.  It runs last so that a failure
 here cannot hide any other test's result, and it passes both alone in a fresh
 process and after the rest of the suite."""
 import numpy as np
@@ -16,6 +18,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle
 from paper_2103_01380_gb300 import inputs, spid
 
 pytestmark = pytest.mark.gpu
@@ -34,7 +37,7 @@ def _cuda():
 
 def _plan_sketch(A_dev, m, n, ld, l, seed):
     plan = spid.Plan([m], [n], [0], [ld], k_max=l - 4, p=4, precision="fp32", seed=seed)
-    plan.sketch(A_dev)
+    plan.sketch_accumulate(A_dev)
     torch.cuda.synchronize()
     Y = plan.sketches()[0]          # l x n
     plan.close()
@@ -52,12 +55,13 @@ def _rel(a, b):
     return float(np.linalg.norm(a.astype(np.float64) - b) / np.linalg.norm(b))
 
 
-def test_noalloc_sketch_matches_plan_sketch_on_two_calls():
-    cases = [  # (m, n, l, seed): ragged rows, two column groups, then a smaller problem
-        (5003, 700, 30, 0x5EED0001),
-        (1234, 97, 20, 0x5EED0002),
+@pytest.mark.parametrize("l", [10, 30, 40, 64])
+def test_noalloc_sketch_matches_plan_sketch_on_two_calls(l):
+    cases = [  # (m, n, seed): ragged rows, two column groups, then a smaller problem
+        (5003, 700, 0x5EED0001),
+        (1234, 97, 0x5EED0002),
     ]
-    for m, n, l, seed in cases:
+    for m, n, seed in cases:
         A = inputs.separated_lowrank(m, n, 6, seed=m, noise=1e-3)
         win = inputs.pack_blocks([A])
         A_dev = torch.from_numpy(win.data).cuda()
@@ -66,6 +70,9 @@ def test_noalloc_sketch_matches_plan_sketch_on_two_calls():
         got = _noalloc_sketch(A_dev, m, n, ld, l, seed, ldy=l + 3)
         assert np.all(np.isfinite(got))
         assert _rel(got, want) <= Y_TOL_FP32, (m, n, l, _rel(got, want))
+        # and the oracle's sketch of the same FP32 values
+        Yo = oracle.sketch(win.block(0).astype(np.float64), l, seed)
+        assert _rel(got, Yo) <= Y_TOL_FP32, (m, n, l, _rel(got, Yo))
 
 
 def test_noalloc_rejects_requests_beyond_the_static_scratch():
