@@ -556,9 +556,9 @@ typedef struct {
   double tol2;           /* stage-2 tolerance (> 0; Remark 2.1 reading as spid_plan_desc) */
 } spid_ts_desc;
 
-/* Create: allocates every workspace (N stage-1 plans, the skeleton buffer
- * holding A0' (m_s x N k per subdomain, element type of the window), the
- * stage-2 plan and the final factors).  Later calls allocate nothing. */
+/* Create: allocates every workspace (N stage-1 plans, the stage-2 plan over
+ * the N k skeleton slots per subdomain and the final factors).  Later calls
+ * allocate nothing.  k_max + p and k2_max + p must both be <= 64. */
 spid_status spid_ts_plan_create(const spid_ts_desc* desc, spid_ts_plan_t* plan);
 spid_status spid_ts_plan_destroy(spid_ts_plan_t plan);
 
@@ -568,8 +568,12 @@ spid_status spid_ts_plan_destroy(spid_ts_plan_t plan);
 spid_status spid_ts_block(spid_ts_plan_t plan, const void* window, int32_t block,
                           spid_stream_t stream);
 
-/* Stage 2 (after every block): gathers A0' from the window, its sketched ID
- * with tol2, and the composition C1' = C1 C0', J = I_U(J2). */
+/* Stage 2 (after every block): the sketched ID of A0' with tol2 and the
+ * composition C1' = C1 C0', J = I_U(J2).  Both stages draw the same rows of
+ * Omega, so the sketch of A0' is the blocks' sketch columns at their
+ * skeleton indices (the block plans sketch k2_max + p rows for it): stage 2
+ * gathers them and reads no window data.  window must be the block window
+ * (16-byte aligned); it is checked, not read. */
 spid_status spid_ts_finalize(spid_ts_plan_t plan, const void* window, spid_stream_t stream);
 
 /* Error / reconstruction of the final factors, as spid_error / spid_reconstruct. */

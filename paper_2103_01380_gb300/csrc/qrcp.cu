@@ -203,8 +203,9 @@ __global__ void __launch_bounds__(512) qrcp_kernel(QrcpArgs a) {
       if (col < n)
         v = __ldg(reinterpret_cast<const typename Vec16<T>::type*>(Y + (int64_t)col * LP + i4));
       const T* vs_ = reinterpret_cast<const T*>(&v);
+      // rows at and past l (a plan may sketch more rows of Omega than its QR reads)
 #pragma unroll
-      for (int u = 0; u < VW; ++u) y[c][i4 + u] = vs_[u];
+      for (int u = 0; u < VW; ++u) y[c][i4 + u] = (i4 + u < a.l) ? vs_[u] : T(0);
     }
 #pragma unroll
     for (int i = 0; i < LP; ++i) {

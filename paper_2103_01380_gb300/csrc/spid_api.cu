@@ -65,6 +65,10 @@ void spid::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 
 namespace spid {
 PlanView plan_view(spid_plan_t P);
+// A plan whose sketch draws l_sketch >= k_max + p rows of Omega while its QR
+// reads the first k_max + p (the two-stage driver's block plans).
+spid_status plan_create_sketch_rows(const spid_plan_desc* d, spid_stream_t stream, int l_sketch,
+                                    spid_plan_t* out);
 }
 
 // Tile shapes and schedules of one plan (spid_tuning without the timings).
@@ -86,6 +90,7 @@ struct spid_plan_s {
   std::vector<int64_t> off, ld;
   int n_max = 0;
   int k_max = 0, p = 0, l = 0, l_pad = 0;
+  int l_sk = 0;                 // rows of Omega the sketch draws (>= l; the QR reads the first l)
   double tol = 0.0;
   int prec = SPID_PREC_FP32;
   uint32_t flags = 0;
@@ -669,7 +674,7 @@ spid_status launch_sketch_range(spid_plan_t P, const Schedule* sc, const void* w
   a.window = window;
   a.tmaps = tmaps;
   a.cta_base = 0;
-  a.l = P->l;
+  a.l = P->l_sk;
   a.l_pad = P->l_pad;
   a.seed = P->seed;
   a.status = P->d_status;
@@ -739,6 +744,10 @@ spid::PlanView spid::plan_view(spid_plan_t P) {
   v.C = P->d_C;
   v.coff = P->d_coff;
   v.status = P->d_status;
+  v.Y = P->d_Y;
+  v.yoff = P->d_yoff;
+  v.l = P->l;
+  v.l_pad = P->l_pad;
   return v;
 }
 
@@ -853,7 +862,24 @@ static spid_status parse_layout(const spid_plan_desc* d, size_t esz, std::vector
   return SPID_OK;
 }
 
+static spid_status plan_create(const spid_plan_desc* d, spid_stream_t stream, int l_sketch,
+                               spid_plan_t* out);
+
 spid_status spid_plan_create(const spid_plan_desc* d, spid_stream_t stream, spid_plan_t* out) {
+  return plan_create(d, stream, 0, out);
+}
+
+}  // extern "C"
+
+spid_status spid::plan_create_sketch_rows(const spid_plan_desc* d, spid_stream_t stream,
+                                          int l_sketch, spid_plan_t* out) {
+  return plan_create(d, stream, l_sketch, out);
+}
+
+extern "C" {
+
+static spid_status plan_create(const spid_plan_desc* d, spid_stream_t stream, int l_sketch,
+                               spid_plan_t* out) {
   g_last_error.clear();
   if (!d || !out) return fail(SPID_ERR_INVALID_ARG, "desc/out is NULL");
   *out = nullptr;
@@ -904,7 +930,12 @@ spid_status spid_plan_create(const spid_plan_desc* d, spid_stream_t stream, spid
   P->k_max = d->k_max;
   P->p = d->p;
   P->l = d->k_max + d->p;
-  P->l_pad = (P->l + 15) / 16 * 16;
+  P->l_sk = std::max(P->l, l_sketch);
+  if (P->l_sk > 64) {
+    delete P;
+    return fail(SPID_ERR_INVALID_ARG, "at most 64 sketch rows");
+  }
+  P->l_pad = (P->l_sk + 15) / 16 * 16;
   P->tol = d->tol;
   P->prec = d->precision;
   P->flags = d->flags;

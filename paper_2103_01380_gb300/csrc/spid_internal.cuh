@@ -277,6 +277,10 @@ struct PlanView {
   void* C;
   const int64_t* coff;    // device [S]
   int* status;
+  void* Y;                // stored sketches, Y_s at yoff[s], [n_s][l_pad]
+  const int64_t* yoff;    // device [S]
+  int32_t l;              // rows the QR reads
+  int32_t l_pad;          // row stride of the stored sketch
 };
 
 // Launchers (one translation unit each).

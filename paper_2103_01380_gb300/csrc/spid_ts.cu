@@ -2,12 +2,16 @@
 // a composition of batched sketched-ID plans:
 //   stage 1   one plan per time block b over the columns b n/N .. (b+1) n/N - 1
 //             of every subdomain (target rank k): A_b ~ A_b(:, I_b) C_b
-//   gather    A0' = [A_0(:, I_0) .. A_{N-1}(:, I_{N-1})] into a plan-owned
-//             buffer (m_s x N k per subdomain; slots past k_{b,s} are zero
-//             columns, which the stage-2 QR never picks)
-//   stage 2   one plan over A0' with the tolerance tol2: A0' ~ A0'(:, J2) C1
+//   stage 2   a sketched ID with the tolerance tol2 of the union of skeleton
+//             columns A0' = [A_0(:, I_0) .. A_{N-1}(:, I_{N-1})]: A0' ~ A0'(:, J2) C1
 //   compose   C1' = C1 C0' with C0' = blockdiag(C_b), J = I_U(J2): the index of
 //             A0' column q = b k + p in the window is b n/N + I_b(p)
+// Both stages draw the same rows of Omega (one key), and the sketch is linear
+// in the columns, so stage 2's sketch Omega A0' is the stage-1 sketches'
+// skeleton columns, Y_b(:, I_b): the block plans sketch l2 = k2_max + p rows
+// (their QR still reads the first k + p), and stage 2 gathers those columns
+// (slots past k_{b,s} are zero and never picked) instead of streaming A0'
+// from the window again -- no second pass over the data, no A0' buffer.
 // The final factors are written into a third plan over the whole window,
 // whose error / reconstruction passes then serve as spid_ts_error /
 // spid_ts_reconstruct.
@@ -22,6 +26,8 @@
 
 namespace spid {
 PlanView plan_view(spid_plan_t P);
+spid_status plan_create_sketch_rows(const spid_plan_desc* d, spid_stream_t stream, int l_sketch,
+                                    spid_plan_t* out);
 }
 
 using namespace spid;
@@ -35,17 +41,14 @@ struct spid_ts_plan_s {
   spid_plan_t stage2 = nullptr;
   spid_plan_t full = nullptr;
   // device
-  void* d_G = nullptr;              // A0' buffer
-  int32_t* d_live = nullptr;        // [S][N k] slot holds a skeleton column (else zero)
-  int64_t* d_goff = nullptr;        // [S]
-  int64_t* d_gld = nullptr;         // [S]
-  int64_t* d_off = nullptr;         // [S] window offsets
-  int64_t* d_ld = nullptr;          // [S]
   int32_t* d_nb = nullptr;          // [S] block length n_s / N
   const int32_t** d_Jb = nullptr;   // [N] block plans' J
   const int32_t** d_kb = nullptr;   // [N] block plans' k
   const void** d_Cb = nullptr;      // [N] block plans' C
   const int64_t** d_cboff = nullptr;   // [N] block plans' C offsets
+  const void** d_Yb = nullptr;      // [N] block plans' stored sketches
+  const int64_t** d_yboff = nullptr;   // [N] block plans' sketch offsets
+  int32_t yb_pad = 0;               // row stride of the block plans' sketches
   std::vector<void*> allocs;
 };
 
@@ -64,33 +67,29 @@ spid_status tfail(spid_status st, const std::string& msg) {
                    std::string(#call) + ": " + cudaGetErrorString(e_));                    \
   } while (0)
 
-// A0'(:, q) of subdomain s = window column b nb + I_b(p), q = b k + p; zero past k_{b,s}.
+// Stage 2's sketch of A0': column q = b k + p of subdomain s is column I_b(p)
+// of block b's sketch (rows 0 .. l2 - 1; the rest of the stored rows zero), or
+// zero past the block's rank k_{b,s}.  One CTA per subdomain.
 template <typename T>
-__global__ void __launch_bounds__(256) gather_skeleton_kernel(
-    const T* window, const int64_t* off, const int64_t* ld, const int32_t* m,
-    const int32_t* nb, int k, const int32_t* const* Jb, const int32_t* const* kb, T* G,
-    const int64_t* goff, const int64_t* gld, int32_t* live) {
-  const int q = blockIdx.x, s = blockIdx.y;
-  const int b = q / k, p = q - b * k;
-  const int ms = m[s];
-  T* dst = G + goff[s] + (int64_t)q * gld[s];
-  const int kbs = kb[b][s];
-  int32_t* lv = live + (int64_t)s * gridDim.x + q;
-  const int was_live = *lv;
-  __syncthreads();   // every thread has read the flag before thread 0 rewrites it
-  if (p >= kbs) {
-    // a slot past the block's rank reads as zero: only a slot the previous
-    // gather filled needs clearing
-    if (was_live) {
-      for (int r = threadIdx.x; r < ms; r += blockDim.x) dst[r] = T(0);
-      if (threadIdx.x == 0) *lv = 0;
+__global__ void __launch_bounds__(256) gather_sketch_kernel(PlanView s2, int k, int yb_pad,
+                                                            const void* const* Yb,
+                                                            const int64_t* const* yboff,
+                                                            const int32_t* const* Jb,
+                                                            const int32_t* const* kb) {
+  const int s = blockIdx.x;
+  const int lp = s2.l_pad, l2 = s2.l;
+  const int nq = s2.n[s];                       // N k
+  T* Y2 = static_cast<T*>(s2.Y) + s2.yoff[s];
+  for (int64_t e = threadIdx.x; e < (int64_t)nq * lp; e += blockDim.x) {
+    const int q = (int)(e / lp), i = (int)(e - (int64_t)q * lp);
+    const int b = q / k, p = q - b * k;
+    T v = T(0);
+    if (i < l2 && p < kb[b][s]) {
+      const int j = Jb[b][(int64_t)s * k + p];
+      v = static_cast<const T*>(Yb[b])[yboff[b][s] + (int64_t)j * yb_pad + i];
     }
-    return;
+    Y2[e] = v;
   }
-  const int64_t col = (int64_t)b * nb[s] + Jb[b][(int64_t)s * k + p];
-  const T* src = window + off[s] + col * ld[s];
-  for (int r = threadIdx.x; r < ms; r += blockDim.x) dst[r] = __ldg(src + r);
-  if (threadIdx.x == 0) *lv = 1;
 }
 
 // C1'(i, t) = sum_p C1(i, b k + p) C_b(p, t - b nb), b = t / nb; J(i) = b nb + I_b(p)
@@ -169,9 +168,10 @@ spid_status spid_ts_plan_create(const spid_ts_desc* d, spid_ts_plan_t* out) {
     delete P;
     return tfail(SPID_ERR_CUDA, "cudaGetDevice failed");
   }
-  // ---- stage 1: one plan per time block
+  // ---- stage 1: one plan per time block, sketching the l2 rows stage 2 reads
+  const int l2 = d->k2_max + B.p;
   std::vector<int32_t> nb(S), n2(S, N * k), m(B.m, B.m + S);
-  std::vector<int64_t> off_b(S), goff(S), gld(S);
+  std::vector<int64_t> off_b(S), goff(S, 0), gld(S);
   for (int s = 0; s < S; ++s) nb[s] = B.n[s] / N;
   for (int b = 0; b < N; ++b) {
     for (int s = 0; s < S; ++s) off_b[s] = B.off[s] + (int64_t)b * nb[s] * B.ld[s];
@@ -181,17 +181,16 @@ spid_status spid_ts_plan_create(const spid_ts_desc* d, spid_ts_plan_t* out) {
     db.qoi = nullptr;   // per-QoI totals only for the final factors
     db.num_qoi = 0;
     spid_plan_t pb = nullptr;
-    spid_status st = spid_plan_create(&db, nullptr, &pb);
+    spid_status st = plan_create_sketch_rows(&db, nullptr, l2, &pb);
     if (st != SPID_OK) return bail(st);
     P->blocks.push_back(pb);
   }
-  // ---- A0' buffer and stage 2
+  // ---- stage 2: a plan over A0' (N k columns per subdomain) whose sketch is
+  // gathered from the blocks' sketches; it never reads a window, so its
+  // offsets only need to be valid
   const int64_t align = 16 / (int64_t)P->esz;
-  int64_t gsum = 0;
   for (int s = 0; s < S; ++s) {
     gld[s] = ((int64_t)m[s] + align - 1) / align * align;
-    goff[s] = gsum;
-    gsum += gld[s] * N * k;
     P->m_max = std::max(P->m_max, m[s]);
     P->n_max = std::max(P->n_max, B.n[s]);
   }
@@ -217,22 +216,23 @@ spid_status spid_ts_plan_create(const spid_ts_desc* d, spid_ts_plan_t* out) {
     return e;
   };
   std::vector<const int32_t*> Jb(N), kb(N);
-  std::vector<const void*> Cb(N);
-  std::vector<const int64_t*> cboff(N);
+  std::vector<const void*> Cb(N), Yb(N);
+  std::vector<const int64_t*> cboff(N), yboff(N);
   for (int b = 0; b < N; ++b) {
     const PlanView v = plan_view(P->blocks[b]);
     Jb[b] = v.J;
     kb[b] = v.k;
     Cb[b] = v.C;
     cboff[b] = v.coff;
+    Yb[b] = v.Y;
+    yboff[b] = v.yoff;
+    P->yb_pad = v.l_pad;
   }
   struct Up { void** dst; const void* src; size_t bytes; };
   const Up ups[] = {
-      {reinterpret_cast<void**>(&P->d_goff), goff.data(), sizeof(int64_t) * S},
-      {reinterpret_cast<void**>(&P->d_gld), gld.data(), sizeof(int64_t) * S},
-      {reinterpret_cast<void**>(&P->d_off), B.off, sizeof(int64_t) * S},
-      {reinterpret_cast<void**>(&P->d_ld), B.ld, sizeof(int64_t) * S},
       {reinterpret_cast<void**>(&P->d_nb), nb.data(), sizeof(int32_t) * S},
+      {reinterpret_cast<void**>(&P->d_Yb), Yb.data(), sizeof(void*) * N},
+      {reinterpret_cast<void**>(&P->d_yboff), yboff.data(), sizeof(void*) * N},
       {reinterpret_cast<void**>(&P->d_Jb), Jb.data(), sizeof(void*) * N},
       {reinterpret_cast<void**>(&P->d_kb), kb.data(), sizeof(void*) * N},
       {reinterpret_cast<void**>(&P->d_Cb), Cb.data(), sizeof(void*) * N},
@@ -243,13 +243,7 @@ spid_status spid_ts_plan_create(const spid_ts_desc* d, spid_ts_plan_t* out) {
         cudaMemcpy(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(tfail(SPID_ERR_CUDA, "two-stage table upload failed"));
   }
-  const size_t slots = (size_t)S * (size_t)N * (size_t)P->k;
-  if (dalloc(&P->d_G, P->esz * (size_t)gsum) != cudaSuccess ||
-      cudaMemset(P->d_G, 0, P->esz * (size_t)gsum) != cudaSuccess ||
-      dalloc(reinterpret_cast<void**>(&P->d_live), sizeof(int32_t) * slots) != cudaSuccess ||
-      cudaMemset(P->d_live, 0, sizeof(int32_t) * slots) != cudaSuccess ||
-      cudaDeviceSynchronize() != cudaSuccess)
-    return bail(tfail(SPID_ERR_OOM, "two-stage skeleton buffer"));
+  if (cudaDeviceSynchronize() != cudaSuccess) return bail(tfail(SPID_ERR_CUDA, "sync failed"));
   *out = P;
   return SPID_OK;
 }
@@ -283,21 +277,15 @@ spid_status spid_ts_finalize(spid_ts_plan_t P, const void* window, spid_stream_t
   if (cudaGetDevice(&cur) != cudaSuccess || cur != P->device) TS_CUDA(cudaSetDevice(P->device));
   cudaStream_t cs = (cudaStream_t)stream;
   const PlanView v2 = plan_view(P->stage2);
-  const dim3 ggrid(P->N * P->k, P->S);
   const PlanView vf = plan_view(P->full);
-  if (P->esz == 8) {
-    gather_skeleton_kernel<double><<<ggrid, 256, 0, cs>>>(
-        static_cast<const double*>(window), P->d_off, P->d_ld, v2.m, P->d_nb, P->k, P->d_Jb,
-        P->d_kb, static_cast<double*>(P->d_G), P->d_goff, P->d_gld, P->d_live);
-  } else {
-    gather_skeleton_kernel<float><<<ggrid, 256, 0, cs>>>(
-        static_cast<const float*>(window), P->d_off, P->d_ld, v2.m, P->d_nb, P->k, P->d_Jb,
-        P->d_kb, static_cast<float*>(P->d_G), P->d_goff, P->d_gld, P->d_live);
-  }
+  if (P->esz == 8)
+    gather_sketch_kernel<double><<<P->S, 256, 0, cs>>>(v2, P->k, P->yb_pad, P->d_Yb, P->d_yboff,
+                                                       P->d_Jb, P->d_kb);
+  else
+    gather_sketch_kernel<float><<<P->S, 256, 0, cs>>>(v2, P->k, P->yb_pad, P->d_Yb, P->d_yboff,
+                                                      P->d_Jb, P->d_kb);
   TS_CUDA(cudaGetLastError());
-  spid_status st = spid_sketch_accumulate(P->stage2, P->d_G, 0, P->N * P->k, stream);
-  if (st != SPID_OK) return st;
-  st = spid_finalize(P->stage2, stream);
+  spid_status st = spid_finalize(P->stage2, stream);
   if (st != SPID_OK) return st;
   if (P->esz == 8)
     compose_kernel<double><<<P->S, 256, 0, cs>>>(v2, vf, P->k, P->d_nb, P->d_Jb, P->d_Cb,

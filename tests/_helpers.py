@@ -177,3 +177,19 @@ def compare_with_oracle(blocks, g: dict, o: dict, precision: str, k_max: int, to
             assert status == SPID_ERR_RANK, ("rank-cut status", status, expect_cut)
     elif not ambiguous_cut:
         assert (status == SPID_ERR_RANK) == expect_cut, ("rank-cut status", status, expect_cut)
+
+
+def ahat_matches_factors(A, J, C, Ahat, k: int, fp64: bool = False) -> bool:
+    """The CUDA path's reconstruction of its OWN factors (J, C) against the
+    oracle's reconstruction of the same factors, element-wise: products and
+    sums of k terms in the working precision u,
+    |d| <= 2 [(k + 1) u (|A_J| |C|) + u |A_hat|].  Unlike a comparison with
+    the oracle's factors, this holds however ill-conditioned R11 is."""
+    A = np.asarray(A, dtype=np.float64)
+    if k == 0:
+        return bool(np.all(np.asarray(Ahat) == 0))
+    u = 2.0 ** -53 if fp64 else 2.0 ** -24
+    Cf = np.asarray(C[:k], dtype=np.float64)
+    Ao, _, _ = oracle.reconstruct_error(A, np.asarray(J[:k], dtype=np.int32), Cf)
+    bound = 2.0 * ((k + 1) * u * (np.abs(A[:, J[:k]]) @ np.abs(Cf)) + u * np.abs(Ao))
+    return bool(np.all(np.abs(np.asarray(Ahat, dtype=np.float64) - Ao) <= bound + 1e-300))

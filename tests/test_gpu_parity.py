@@ -20,7 +20,7 @@ torch = pytest.importorskip("torch")
 
 import oracle
 from paper_2103_01380_gb300 import inputs, spid
-from _helpers import (GAP, Y_TOL, compare_with_oracle, oracle_window, rel_fro,
+from _helpers import (GAP, Y_TOL, ahat_matches_factors, compare_with_oracle, oracle_window, rel_fro,
                       separated_prefix, U_MODE)
 
 pytestmark = pytest.mark.gpu
@@ -263,18 +263,6 @@ def _split_qoi(win, nq=5):
                          np.repeat(win.ld, nq), dict(win.meta))
 
 
-def _ahat_elementwise_ok(A, J, C, Ahat_g, k):
-    """The GPU's reconstruction of its own factors against the oracle's
-    reconstruction of the same factors: FP32 products and sums of k terms,
-    |d| <= 2 [(k + 1) 2^-24 (|A_J| |C|) + 2^-24 |A_hat|]."""
-    if k == 0:
-        return np.all(Ahat_g == 0)
-    Ao, _, _ = oracle.reconstruct_error(A, J[:k], C[:k].astype(np.float64))
-    bound = 2.0 * ((k + 1) * 2.0 ** -24 * (np.abs(A[:, J[:k]]) @ np.abs(C[:k].astype(np.float64)))
-                   + 2.0 ** -24 * np.abs(Ao))
-    return np.all(np.abs(Ahat_g - Ao) <= bound + 1e-30)
-
-
 @pytest.mark.parametrize("precision", ["tf32", "fp32"])
 def test_tgv3d_full_size_per_qoi(precision):
     # 64 boxes of 16^3 x 5 QoIs (n = 512) as 320 (box, QoI) subdomains, adaptive
@@ -301,7 +289,7 @@ def test_tgv3d_full_size_per_qoi(precision):
             eg = np.sqrt(g["err"][s, 0] / g["err"][s, 1])
             eo = np.sqrt(o["e2"][i] / o["a2"][i])
             assert eg <= max(1e-3, 2 * eo), (s, eg, eo)
-            assert _ahat_elementwise_ok(A, g["J"][s], g["C"][s], g["Ahat"][s], int(g["k"][s])), s
+            assert ahat_matches_factors(A, g["J"][s], g["C"][s], g["Ahat"][s], int(g["k"][s])), s
 
 
 def test_insitu_full_size_per_qoi_sampled():

@@ -66,10 +66,13 @@ def test_noalloc_sketch_matches_plan_sketch_on_two_calls(l):
         win = inputs.pack_blocks([A])
         A_dev = torch.from_numpy(win.data).cuda()
         ld = int(win.ld[0])
-        want = _plan_sketch(A_dev, m, n, ld, l, seed)
         got = _noalloc_sketch(A_dev, m, n, ld, l, seed, ldy=l + 3)
         assert np.all(np.isfinite(got))
-        assert _rel(got, want) <= Y_TOL_FP32, (m, n, l, _rel(got, want))
+        # the plan-based sketch, where a plan's QR takes the shape (more than
+        # 512 columns needs the sketch padded to at most 48 rows)
+        if n <= 512 or l <= 48:
+            want = _plan_sketch(A_dev, m, n, ld, l, seed)
+            assert _rel(got, want) <= Y_TOL_FP32, (m, n, l, _rel(got, want))
         # and the oracle's sketch of the same FP32 values
         Yo = oracle.sketch(win.block(0).astype(np.float64), l, seed)
         assert _rel(got, Yo) <= Y_TOL_FP32, (m, n, l, _rel(got, Yo))
