@@ -41,7 +41,14 @@ METRIC = "snapshot GB/s compressed at rel. err <=1e-3: mixed-prec batched vs pla
 # (on a smaller case of the same kernel, scaled by the bytes a launch streams).
 # A figure is reported only while the kernel's sources hash to the value they
 # had when it was measured.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # 16-box capture: (677,398,784 + 3,732,992 + 677,200,128 + 770,560) / 2 bytes per launch
+    # of 671,088,640 algorithmic = 1.0126, times the full launch's 21,474,836,480
+    "insitu256:sketch": {"bytes_per_launch": 21745420000,
+                          "sources": ("sketch_tc.cu", "sketch_pack.cuh", "tcgen05_ptx.cuh",
+                                      "spid_internal.cuh"),
+                          "sha256_16": "e61f07c53c596135"},
+}
 
 
 def measured_traffic(key: str):

@@ -253,8 +253,9 @@ double spid_compression_factor(int32_t num_sub, const int32_t* m, const int32_t*
  * their own.  Results depend on the tuning only through the order of FP32
  * partial sums (sketch slots, error-pass units); each tuning is deterministic. */
 typedef struct {
-  int32_t sketch_pack_slices;  /* tensor-core sketch: 64-column slices of equal-m subdomains
-                                  sharing one generated Omega chunk: 1, 2, 4 or 8 (default 8) */
+  int32_t sketch_pack_slices;  /* tensor-core sketch: 64-column slices of equal-shape subdomains
+                                  sharing one generated Omega chunk: 1, 2, 4 or 8 (default 8);
+                                  spid_plan_autotune also tries both sketch_slice_major orders */
   int32_t sketch_stages;       /* tensor-core sketch pipeline depth: 0 = as many as fit in
                                   shared memory (default), else 2..8 (capped by what fits) */
   int32_t sketch_ctas_per_sm;  /* CUDA-core (FP32/FP64) sketch: persistent CTAs per SM, 1 or 2;
@@ -265,6 +266,9 @@ typedef struct {
                                   or 1024 */
   int32_t error_cols;          /* CUDA-core error pass: columns per work unit, 128 or 256
                                   (default) */
+  int32_t sketch_slice_major;  /* tensor-core sketch: 0 = a pack holds consecutive 64-column
+                                  slices of one subdomain (default), 1 = slice j of consecutive
+                                  subdomains (same columns) */
   float sketch_ms;             /* spid_plan_autotune: measured whole-window sketch time of the
                                   chosen shape (0 if the tuning was set, not measured) */
   float error_ms;              /* spid_plan_autotune: measured error-pass time */

@@ -74,6 +74,7 @@ spid_status plan_create_sketch_rows(const spid_plan_desc* d, spid_stream_t strea
 // Tile shapes and schedules of one plan (spid_tuning without the timings).
 struct TuneCfg {
   int pack_slices = kPackSlices;   // tensor-core sketch: 64-column slices per Omega chunk
+  int slice_major = 0;             // tensor-core sketch: packs cut slice index major
   int stages = 0;                  // tensor-core sketch pipeline depth, 0 = as many as fit
   int ctas_per_sm = 0;             // CUDA-core sketch CTAs per SM, 0 = by register budget
   int err_path = 0;                // 0 CUDA cores, 1 tensor cores
@@ -206,13 +207,19 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   // ---- problems, subdomain by subdomain; with packing, ordered by m
   std::vector<int> subs(P->S);
   for (int s = 0; s < P->S; ++s) subs[s] = s;
-  // packs share one Omega chunk and one chunk decode: group equal m and box shape
+  // packs share one Omega chunk and one chunk decode: group equal m and box
+  // shape; inside a class, order by position in the window, so that a pack's
+  // subdomains are neighbours in memory (for one-QoI boxes of a global field:
+  // boxes adjacent along x with the same QoI, whose x-runs form one contiguous
+  // row of each snapshot)
   auto shape = [&](int s) {
     const RowGeom& g = P->geo[s];
     return std::make_tuple(P->m[s], g.ex, g.ey, g.ez);
   };
   if (tc && !P->per_sub())
-    std::stable_sort(subs.begin(), subs.end(), [&](int x, int y) { return shape(x) < shape(y); });
+    std::stable_sort(subs.begin(), subs.end(), [&](int x, int y) {
+      return std::make_tuple(shape(x), P->off[x]) < std::make_tuple(shape(y), P->off[y]);
+    });
   std::vector<Problem> probs;
   std::vector<int> prob_sub_first(P->S + 1, 0);   // per-subdomain mode: problems of s
   struct Unit { int nch; double w; int prob0; int nprob; int pack; };
@@ -227,58 +234,89 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   // it regenerates.
   const bool streamed = tc && !P->per_sub();
   if (streamed) {
+    // Packs are cut from the stream of 64-column slices of one shape class,
+    // either subdomain major (all slices of one subdomain, then the next: a
+    // pack holds up to 512 consecutive columns of one subdomain; the default)
+    // or slice index major (slice j of every subdomain, then slice j + 1: a
+    // pack holds 8 subdomains at the same columns); the tuner measures both.
+    // A chunk's weight counts its columns, a share for the Omega chunk it
+    // regenerates, and the pack's epilogue (TMEM drain and fold) spread over
+    // the pack's chunks, so CTAs that get many short packs (small m) get fewer
+    // chunks.
     Pack pk{};
     int cols = 0;
     auto close_pack = [&]() {
       if (pk.nslices == 0) return;
-      units.push_back({(pk.m + kChunkRows - 1) / kChunkRows, (double)(cols + kSliceCols / 2),
+      const int nch = (pk.m + kChunkRows - 1) / kChunkRows;
+      units.push_back({nch, (double)(cols + kSliceCols / 2) * (1.0 + kPackOverheadChunks / nch),
                        pk.prob0, pk.nprob, (int)packs.size()});
       packs.push_back(pk);
       pk = Pack{};
       cols = 0;
     };
-    for (size_t q = 0; q < subs.size(); ++q) {
-      const int s = subs[q];
-      if (pk.nslices > 0 && (P->m[s] != pk.m || P->geo[s].ex != pk.ex || P->geo[s].ey != pk.ey ||
-                             P->geo[s].ez != pk.ez))
-        close_pack();
-      const int end = std::min<int64_t>((int64_t)col0 + ncols, P->n[s]);
-      for (int c = col0; c < end; c += kSliceCols) {
-        if (pk.nslices == P->tune.pack_slices) close_pack();
-        if (pk.nslices == 0) {
-          pk.slice0 = (int)slices.size();
-          pk.m = P->m[s];
-          pk.prob0 = (int)probs.size();
-          pk.nprob = 0;
-          pk.ex = P->geo[s].ex;
-          pk.ey = P->geo[s].ey;
-          pk.ez = P->geo[s].ez;
-        }
-        const int nc = std::min(kSliceCols, end - c);
-        if (pk.nprob == 0 || probs.back().sub != s) {
-          Problem pb;
-          pb.sub = s;
-          pb.col0 = c;
-          pb.ncols = 0;
-          pb.m = P->m[s];
-          pb.off = P->off[s];
-          pb.ld = P->ld[s];
-          pb.geo = P->geo[s];
-          probs.push_back(pb);
-          ++pk.nprob;
-        }
-        Slice sl;
-        sl.prob = (int)probs.size() - 1;
-        sl.sub = s;
-        sl.col0 = c;
-        sl.ncols = nc;
-        sl.out_col = c - probs.back().col0;
-        sl.member = pk.nprob - 1;
-        slices.push_back(sl);
-        probs.back().ncols += nc;
-        ++pk.nslices;
-        cols += nc;
+    auto add_slice = [&](int s, int c, int end) {
+      if (pk.nslices == P->tune.pack_slices) close_pack();
+      if (pk.nslices == 0) {
+        pk.slice0 = (int)slices.size();
+        pk.m = P->m[s];
+        pk.prob0 = (int)probs.size();
+        pk.nprob = 0;
+        pk.ex = P->geo[s].ex;
+        pk.ey = P->geo[s].ey;
+        pk.ez = P->geo[s].ez;
       }
+      const int nc = std::min(kSliceCols, end - c);
+      // consecutive slices of one subdomain in a pack share a problem
+      if (pk.nprob == 0 || probs.back().sub != s || probs.back().col0 + probs.back().ncols != c) {
+        Problem pb;
+        pb.sub = s;
+        pb.col0 = c;
+        pb.ncols = 0;
+        pb.m = P->m[s];
+        pb.off = P->off[s];
+        pb.ld = P->ld[s];
+        pb.geo = P->geo[s];
+        probs.push_back(pb);
+        ++pk.nprob;
+      }
+      Slice sl;
+      sl.prob = (int)probs.size() - 1;
+      sl.sub = s;
+      sl.col0 = c;
+      sl.ncols = nc;
+      sl.out_col = c - probs.back().col0;
+      sl.member = pk.nprob - 1;
+      slices.push_back(sl);
+      probs.back().ncols += nc;
+      ++pk.nslices;
+      cols += nc;
+    };
+    for (size_t q0 = 0; q0 < subs.size();) {
+      // one shape class: subs[q0 .. q1)
+      size_t q1 = q0 + 1;
+      while (q1 < subs.size() && shape(subs[q1]) == shape(subs[q0])) ++q1;
+      close_pack();
+      int jmax = 0;
+      for (size_t q = q0; q < q1; ++q) {
+        const int end = std::min<int64_t>((int64_t)col0 + ncols, P->n[subs[q]]);
+        jmax = std::max(jmax, end > col0 ? (end - col0 + kSliceCols - 1) / kSliceCols : 0);
+      }
+      if (P->tune.slice_major) {
+        for (int j = 0; j < jmax; ++j)
+          for (size_t q = q0; q < q1; ++q) {
+            const int s = subs[q];
+            const int end = std::min<int64_t>((int64_t)col0 + ncols, P->n[s]);
+            const int c = col0 + j * kSliceCols;
+            if (c < end) add_slice(s, c, end);
+          }
+      } else {
+        for (size_t q = q0; q < q1; ++q) {
+          const int s = subs[q];
+          const int end = std::min<int64_t>((int64_t)col0 + ncols, P->n[s]);
+          for (int c = col0; c < end; c += kSliceCols) add_slice(s, c, end);
+        }
+      }
+      q0 = q1;
     }
     close_pack();
   }
@@ -1322,12 +1360,14 @@ bool valid_tuning(const spid_tuning& t) {
   return in(t.sketch_pack_slices, {1, 2, 4, 8}) && (t.sketch_stages == 0 ||
          (t.sketch_stages >= 2 && t.sketch_stages <= 8)) &&
          in(t.sketch_ctas_per_sm, {0, 1, 2}) && in(t.error_path, {0, 1}) &&
-         in(t.error_rows, {256, 512, 1024}) && in(t.error_cols, {128, 256});
+         in(t.error_rows, {256, 512, 1024}) && in(t.error_cols, {128, 256}) &&
+         in(t.sketch_slice_major, {0, 1});
 }
 
 TuneCfg cfg_of(const spid_tuning& t) {
   TuneCfg c;
   c.pack_slices = t.sketch_pack_slices;
+  c.slice_major = t.sketch_slice_major;
   c.stages = t.sketch_stages;
   c.ctas_per_sm = t.sketch_ctas_per_sm;
   c.err_path = t.error_path;
@@ -1339,6 +1379,7 @@ TuneCfg cfg_of(const spid_tuning& t) {
 spid_tuning tuning_of(const TuneCfg& c, float sk, float er) {
   spid_tuning t;
   t.sketch_pack_slices = c.pack_slices;
+  t.sketch_slice_major = c.slice_major;
   t.sketch_stages = c.stages;
   t.sketch_ctas_per_sm = c.ctas_per_sm;
   t.error_path = c.err_path;
@@ -1353,6 +1394,7 @@ spid_tuning tuning_of(const TuneCfg& c, float sk, float er) {
 // whole-window one.  The device is idle.
 spid_status apply_sketch_cfg(spid_plan_t P, const TuneCfg& c) {
   P->tune.pack_slices = c.pack_slices;
+  P->tune.slice_major = c.slice_major;
   P->tune.stages = c.stages;
   P->tune.ctas_per_sm = c.ctas_per_sm;
   drop_schedules(P);
@@ -1443,13 +1485,16 @@ extern "C" spid_status spid_plan_autotune(spid_plan_t P, const void* window, spi
   // ---- sketch candidates
   std::vector<TuneCfg> cands;
   if (P->tensor_core()) {
-    for (int ps : {8, 4, 2, 1})
-      for (int stg : {0, 4, 2}) {
-        TuneCfg c = P->tune;
-        c.pack_slices = ps;
-        c.stages = stg;
-        cands.push_back(c);
-      }
+    for (int order : {0, 1})
+      for (int ps : {8, 4, 2, 1})
+        for (int stg : {0, 4, 2}) {
+          if (order == 1 && ps < 4) continue;   // small packs: the order hardly matters
+          TuneCfg c = P->tune;
+          c.slice_major = order;
+          c.pack_slices = ps;
+          c.stages = stg;
+          cands.push_back(c);
+        }
   } else {
     for (int cps : {1, 2}) {
       TuneCfg c = P->tune;
@@ -1459,7 +1504,7 @@ extern "C" spid_status spid_plan_autotune(spid_plan_t P, const void* window, spi
   }
   TuneCfg best_cfg = P->tune;
   float best_sk = 0.f;
-  int seen_stages = -1, seen_pack = -1;
+  int seen_stages = -1, seen_pack = -1, seen_order = -1;
   for (const TuneCfg& c : cands) {
     st = apply_sketch_cfg(P, c);
     if (st == SPID_ERR_UNSUPPORTED) continue;   // e.g. too few stages fit
@@ -1468,9 +1513,12 @@ extern "C" spid_status spid_plan_autotune(spid_plan_t P, const void* window, spi
     st = get_schedule(P, 0, P->n_max, &sc);
     if (st != SPID_OK) return st;
     // stage counts above what fits collapse onto the same launch: skip repeats
-    if (P->tensor_core() && sc->stages == seen_stages && c.pack_slices == seen_pack) continue;
+    if (P->tensor_core() && sc->stages == seen_stages && c.pack_slices == seen_pack &&
+        c.slice_major == seen_order)
+      continue;
     seen_stages = sc->stages;
     seen_pack = c.pack_slices;
+    seen_order = c.slice_major;
     float ms = 0.f;
     st = time_median(cs, kReps, [&] { return launch_sketch_range(P, sc, window, P->d_tmaps, cs); },
                      &ms);
@@ -1480,6 +1528,7 @@ extern "C" spid_status spid_plan_autotune(spid_plan_t P, const void* window, spi
     if (best_sk == 0.f || ms < best_sk * (1.f - kTuneMargin)) {
       best_sk = ms;
       best_cfg.pack_slices = c.pack_slices;
+      best_cfg.slice_major = c.slice_major;
       best_cfg.stages = c.stages;
       best_cfg.ctas_per_sm = c.ctas_per_sm;
     }
@@ -1554,7 +1603,7 @@ extern "C" spid_status spid_plan_tuning_key(spid_plan_t P, char* buf, int32_t le
   }
   auto lg = [](double x) { return x >= 1.0 ? (int)std::floor(std::log2(x)) : 0; };
   const int w = std::snprintf(buf, (size_t)len,
-                              "spid-tune-1;cc=%d.%d;sms=%d;prec=%d;flags=%u;l_pad=%d;k_max=%d;"
+                              "spid-tune-2;cc=%d.%d;sms=%d;prec=%d;flags=%u;l_pad=%d;k_max=%d;"
                               "log2S=%d;log2m=%d;log2n=%d",
                               prop.major, prop.minor, P->num_sms, P->prec, P->flags, P->l_pad,
                               P->k_max, lg(P->S), lg(msum / P->S), lg(nsum / P->S));

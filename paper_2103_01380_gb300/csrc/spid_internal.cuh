@@ -66,6 +66,10 @@ struct Segment {
 // the same m, streamed together as 4 MMA tiles of 128 rows (two slices each).
 constexpr int kSliceCols = 64;
 constexpr int kPackSlices = 8;
+// Cost of a pack's epilogue (TMEM drain, partial slots, fold) in chunks of
+// streaming, for balancing the chunks over the persistent CTAs: measured on
+// uneven windows, a 16-chunk pack (m = 512) took about as long as 16 more.
+constexpr double kPackOverheadChunks = 16.0;
 
 struct Slice {
   int32_t prob;      // problem index (the fold unit)

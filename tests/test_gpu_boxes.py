@@ -34,12 +34,28 @@ def _field(dtype=np.float32, snap_stride=None):
     return inputs.tgv3d_global(X, Y, Z, 64, t, dtype=dtype, snap_stride=snap_stride)
 
 
-# (org, ext) in (x, y, z); x origin and extent multiples of 4; the first four
-# have x extents that are multiples of 32 (tensor-core sketches)
-BOXES_TC = [((0, 0, 0), (32, 8, 4)), ((32, 4, 2), (32, 16, 16)), ((0, 10, 12), (64, 8, 8)),
-            ((32, 0, 0), (32, 24, 20))]
-BOXES_ANY = [((4, 0, 0), (4, 4, 4)), ((8, 3, 5), (8, 5, 3)), ((12, 1, 2), (12, 9, 7)),
-             ((40, 20, 17), (20, 4, 3)), ((0, 0, 0), (64, 2, 2))]
+# (org, ext) in (x, y, z); x origin and extent multiples of 4; disjoint, so
+# every box's reconstruction has its own place in the output field.
+# BOXES_TC: x extents multiples of 32 (tensor-core sketches)
+BOXES_TC = [((0, 0, 0), (32, 8, 4)), ((32, 4, 2), (32, 16, 16)), ((0, 10, 12), (32, 8, 8)),
+            ((0, 20, 0), (64, 4, 20)), ((0, 0, 4), (32, 8, 8))]
+BOXES_ANY = [((4, 0, 0), (4, 4, 4)), ((8, 3, 5), (8, 5, 3)), ((16, 1, 2), (12, 9, 7)),
+             ((40, 20, 17), (20, 4, 3)), ((0, 22, 0), (64, 2, 2))]
+
+
+def _disjoint(boxes):
+    for i, (o1, e1) in enumerate(boxes):
+        for o2, e2 in boxes[i + 1:]:
+            if all(o1[a] < o2[a] + e2[a] and o2[a] < o1[a] + e1[a] for a in range(3)):
+                return False
+    return True
+
+
+def test_the_test_boxes_are_disjoint_and_inside_the_field():
+    for boxes in (BOXES_TC, BOXES_ANY):
+        assert _disjoint(boxes)
+        for (ox, oy, oz), (ex, ey, ez) in boxes:
+            assert ox + ex <= X and oy + ey <= Y and oz + ez <= Z
 
 
 def _plan_and_blocks(field, boxes, split, precision, k_max, p, tol=0.0, n=N, snap_stride=None,
