@@ -42,12 +42,12 @@ METRIC = "snapshot GB/s compressed at rel. err <=1e-3: mixed-prec batched vs pla
 # A figure is reported only while the kernel's sources hash to the value they
 # had when it was measured.
 MEASURED_TRAFFIC = {
-    # 16-box capture: (677,398,784 + 3,732,992 + 677,200,128 + 770,560) / 2 bytes per launch
-    # of 671,088,640 algorithmic = 1.0126, times the full launch's 21,474,836,480
-    "insitu256:sketch": {"bytes_per_launch": 21745420000,
+    # 16-box capture: (677,298,688 + 3,954,688 + 677,203,712 + 780,032) / 2 bytes per launch
+    # of 671,088,640 algorithmic = 1.0127, times the full launch's 21,474,836,480
+    "insitu256:sketch": {"bytes_per_launch": 21747790000,
                           "sources": ("sketch_tc.cu", "sketch_pack.cuh", "tcgen05_ptx.cuh",
                                       "spid_internal.cuh"),
-                          "sha256_16": "e61f07c53c596135"},
+                          "sha256_16": "780fdffa8272e949"},
 }
 
 
@@ -1135,6 +1135,22 @@ def run_headline(args):
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_headline(cfg, args.cpu_sample)
     plan.close()
+    # the uneven-batching workload (4096 boxes of edges 8..32, windows of 64..1024
+    # snapshots, 454 GB in waves) as a secondary measurement of the same run
+    if world == 1 and args.secondary and args.workload == "insitu256" and args.boxes is None:
+        del window
+        torch.cuda.empty_cache()
+        sec_args = argparse.Namespace(**vars(args))
+        sec_args.steps, sec_args.warmup, sec_args.waves = 8, 2, 0
+        u = _run_uneven(sec_args, torch, inputs, spid)
+        usk = u.pop("_sketch_gbs")
+        line["secondary"] = {"uneven4096": {
+            "workload": u["config"]["workload"], "value": u["value"], "unit": "GB/s",
+            "ms_per_step": u["ms_per_step"], "valid": u["valid"],
+            "per_qoi_rel_err": u["per_qoi_rel_err"], "compression_factor": u["compression_factor"],
+            "k_mean": u["k_mean"], "sketch_gbs": usk,
+            "sketch_roofline_frac": usk / peak, "peak": peak, "peak_kind": peak_kind,
+            "tuning": u["config"]["tuning"]}}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -1161,6 +1177,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-secondary", dest="secondary", action="store_false",
+                    help="skip the uneven-batching workload the default run also measures")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default tile shapes (no measurement)")
     ap.add_argument("--workload", default="insitu256",
