@@ -392,7 +392,7 @@ int orc_spid(const double* A, int64_t m, int64_t n, int64_t ld, int32_t l, int32
 
 /* As orc_spid, and kqr_out (may be NULL) receives the number of pivots the
  * QR produced before the rank guard: the guard cut the rank (an informational
- * outcome, reading of the spec guard) exactly when *k_out < *kqr_out. */
+ * outcome of the rank guard) exactly when *k_out < *kqr_out. */
 int orc_spid_kqr(const double* A, int64_t m, int64_t n, int64_t ld, int32_t l, int32_t kmax,
                  double tol, double u_mode, uint64_t seed, double* Y, int32_t* J, int32_t* k_out,
                  int32_t* kqr_out, double* R, double* C, double* e2, double* a2) {
