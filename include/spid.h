@@ -167,7 +167,12 @@ spid_status spid_plan_info(spid_plan_t plan, int32_t* l, int32_t* l_pad,
  * independent, so a window may be sketched in any number of calls (one per
  * snapshot or per micro-batch, as the snapshots arrive: Algorithm 6 saves
  * each time step's data); columns never sketched stay zero after
- * spid_plan_create / spid_reset.  window: device, layout as above. */
+ * spid_plan_create / spid_reset.  window: device, layout as above.  The
+ * tensor-core sketches read columns in TMA tiles of the slice width (64
+ * columns, or 32 / 16 when tuned so): a range that ends inside a tile still
+ * reads the whole tile from memory (past n_s the tile is zero-filled and costs
+ * nothing), so micro-batches that are multiples of the slice width read every
+ * column once. */
 spid_status spid_sketch_accumulate(spid_plan_t plan, const void* window, int32_t col0,
                                    int32_t ncols, spid_stream_t stream);
 
@@ -266,9 +271,14 @@ typedef struct {
                                   or 1024 */
   int32_t error_cols;          /* CUDA-core error pass: columns per work unit, 128 or 256
                                   (default) */
-  int32_t sketch_slice_major;  /* tensor-core sketch: 0 = a pack holds consecutive 64-column
-                                  slices of one subdomain (default), 1 = slice j of consecutive
-                                  subdomains (same columns) */
+  int32_t sketch_slice_major;  /* tensor-core sketch: 0 = a pack holds consecutive slices of one
+                                  subdomain (default), 1 = slice j of consecutive subdomains
+                                  (same columns) */
+  int32_t sketch_slice_cols;   /* TF32 sketch: window columns per slice (one TMA box), 64
+                                  (default; 0 means 64), 32 or 16; packs still hold up to
+                                  sketch_pack_slices x 64 columns.  Narrower slices cover fewer
+                                  snapshots per chunk, which helps windows whose snapshots lie far
+                                  apart (a global field).  Other precisions: 64 only. */
   float sketch_ms;             /* spid_plan_autotune: measured whole-window sketch time of the
                                   chosen shape (0 if the tuning was set, not measured) */
   float error_ms;              /* spid_plan_autotune: measured error-pass time */

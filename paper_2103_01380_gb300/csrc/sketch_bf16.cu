@@ -64,7 +64,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
 template <bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1) sketch_bf16_kernel(const Bf16Args args) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ int epi_last[kPackSlices];
+  __shared__ int epi_last[kMaxPackMembers];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const SketchArgs& a = args.s;

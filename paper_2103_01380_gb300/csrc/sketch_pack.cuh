@@ -10,8 +10,10 @@
 namespace spid {
 namespace tc {
 
-// Accumulator layout: tile t (two slices) at TMEM columns t * acc_stride, row r
-// of the tile = TMEM lane r; slice 2t owns rows 0..63, slice 2t+1 rows 64..127.
+// Accumulator layout: tile t (128 window columns) at TMEM columns
+// t * acc_stride, row r of the tile = TMEM lane r; with slices of `slice_cols`
+// columns (64, 32 or 16), row r of tile t is column (t 128 + r) % slice_cols
+// of slice (t 128 + r) / slice_cols.
 // Called by all `nthreads` epilogue threads (whole warps); warp w reads TMEM
 // lanes 32 (w % 4) .. +31 and the warps sharing a quadrant (`part` of
 // `nparts`) take alternate 16-column slices.  `ok` (uniform per warp) false:
@@ -24,12 +26,13 @@ __device__ __forceinline__ void pack_epilogue(const SketchArgs& a, const PackSeg
                                               bool ok) {
   const Pack pk = a.packs[sg.pack];
   const int l_pad = a.l_pad;
-  const int nt = (pk.nslices + 1) / 2;
+  const int sc = a.slice_cols;
+  const int nt = (pk.nslices * sc + 127) / 128;
   float* partial = static_cast<float*>(a.partial);
   const int row = quad * 32 + lane;                 // TMEM lane = tile row
   for (int t = 0; t < nt && ok; ++t) {
-    const int h = 2 * t + (row >> 6);
-    const int jj = row & 63;
+    const int h = (t * 128 + row) / sc;
+    const int jj = (t * 128 + row) % sc;
     bool valid = false;
     float* out = nullptr;
     if (h < pk.nslices) {

@@ -6,9 +6,10 @@
 //   K = rows of A, 32 rows (one 128-byte swizzle row of FP32) per chunk.
 // A's columns are contiguous in rows, so a [32 rows x 64 columns] box loaded
 // by TMA with 128-byte swizzling is half of the K-major canonical tile the MMA
-// reads.  Omega does not depend on the subdomain, so one chunk of rows serves
-// a whole pack: up to 8 such boxes (64-column slices of subdomains with equal
-// m) stacked into 4 MMA tiles.  Omega(:, rows) is regenerated from Philox each
+// reads (a 32- or 16-column box a quarter or an eighth of it, when the plan is
+// tuned to narrower slices).  Omega does not depend on the subdomain, so one
+// chunk of rows serves a whole pack: up to 512 columns of such boxes (slices of
+// subdomains with equal shape) stacked into 4 MMA tiles.  Omega(:, rows) is regenerated from Philox each
 // chunk by the generator warps directly into the same swizzled K-major layout;
 // the accumulators live in TMEM.
 //
@@ -40,7 +41,6 @@ constexpr int kGenThreads = 32 * kGenWarps;
 constexpr int kTcThreads = 64 + kGenThreads;
 constexpr int kTileCols = 128;                 // MMA M
 constexpr int kTileBytes = kTileCols * 128;    // 128 columns x 32 FP32 rows
-constexpr int kSliceBytes = kSliceCols * 128;  // one TMA box: 64 columns x 32 rows
 constexpr int kMaxStages = 8;
 
 struct TcArgs {
@@ -53,7 +53,7 @@ struct TcArgs {
 
 __global__ void __launch_bounds__(kTcThreads, 1) sketch_tf32_kernel(const TcArgs args) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ int epi_last[kPackSlices];
+  __shared__ int epi_last[kMaxPackMembers];
   // 1024-byte alignment for the 128-byte swizzle atoms
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -114,12 +114,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) sketch_tf32_kernel(const TcArgs
           const uint32_t ph = (uint32_t)(it / S) & 1u;
           if (!mbar_wait(smem_addr(&empty[st]), ph ^ 1u, abort_flag, a.status)) { ok = false; break; }
           const uint32_t fb = smem_addr(&full[st]);
-          mbar_arrive_expect_tx(fb, (uint32_t)(pk.nslices * kSliceBytes));
+          // one TMA box per slice: slice_cols columns x 32 rows, back to back, so
+          // a tile of 128 columns is 128 / slice_cols boxes
+          const int slice_bytes = a.slice_cols * 128;
+          mbar_arrive_expect_tx(fb, (uint32_t)(pk.nslices * slice_bytes));
           unsigned char* dst = smem_A + (size_t)st * args.max_tiles * kTileBytes;
           const ChunkCoord cc = chunk_coord(pk, ch);
           for (int h = 0; h < pk.nslices; ++h) {
             const Slice sl = a.slices[pk.slice0 + h];
-            tma_load_chunk(smem_addr(dst + h * kSliceBytes), tmaps + sl.sub, pk, cc, sl.col0, fb);
+            tma_load_chunk(smem_addr(dst + h * slice_bytes), tmaps + sl.sub, pk, cc, sl.col0, fb);
           }
         }
       }
@@ -136,7 +139,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) sketch_tf32_kernel(const TcArgs
       const uint32_t idesc = tf32_idesc(kTileCols, l_pad);
       for (int si = seg0; si < seg1 && ok; ++si) {
         const PackSegment sg = a.psegs[si];
-        const int nt = (a.packs[sg.pack].nslices + 1) / 2;
+        const int nt = (a.packs[sg.pack].nslices * a.slice_cols + kTileCols - 1) / kTileCols;
         for (int ch = sg.chunk0; ch < sg.chunk1; ++ch, ++it) {
           const int st = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;

@@ -75,6 +75,7 @@ spid_status plan_create_sketch_rows(const spid_plan_desc* d, spid_stream_t strea
 struct TuneCfg {
   int pack_slices = kPackSlices;   // tensor-core sketch: 64-column slices per Omega chunk
   int slice_major = 0;             // tensor-core sketch: packs cut slice index major
+  int slice_cols = kSliceCols;     // tensor-core sketch: columns per slice (TMA box width)
   int stages = 0;                  // tensor-core sketch pipeline depth, 0 = as many as fit
   int ctas_per_sm = 0;             // CUDA-core sketch CTAs per SM, 0 = by register budget
   int err_path = 0;                // 0 CUDA cores, 1 tensor cores
@@ -204,6 +205,8 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   const int CG = P->group_cols();
   const int G = P->sketch_grid();
   const bool tc = P->tensor_core();
+  const int W = tc ? P->tune.slice_cols : kSliceCols;                 // slice width
+  const int pack_cap = tc ? P->tune.pack_slices * kSliceCols / W : 1;   // slices per pack
   // ---- problems, subdomain by subdomain; with packing, ordered by m
   std::vector<int> subs(P->S);
   for (int s = 0; s < P->S; ++s) subs[s] = s;
@@ -255,7 +258,7 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
       cols = 0;
     };
     auto add_slice = [&](int s, int c, int end) {
-      if (pk.nslices == P->tune.pack_slices) close_pack();
+      if (pk.nslices == pack_cap) close_pack();
       if (pk.nslices == 0) {
         pk.slice0 = (int)slices.size();
         pk.m = P->m[s];
@@ -265,7 +268,7 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
         pk.ey = P->geo[s].ey;
         pk.ez = P->geo[s].ez;
       }
-      const int nc = std::min(kSliceCols, end - c);
+      const int nc = std::min(W, end - c);
       // consecutive slices of one subdomain in a pack share a problem
       if (pk.nprob == 0 || probs.back().sub != s || probs.back().col0 + probs.back().ncols != c) {
         Problem pb;
@@ -299,21 +302,21 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
       int jmax = 0;
       for (size_t q = q0; q < q1; ++q) {
         const int end = std::min<int64_t>((int64_t)col0 + ncols, P->n[subs[q]]);
-        jmax = std::max(jmax, end > col0 ? (end - col0 + kSliceCols - 1) / kSliceCols : 0);
+        jmax = std::max(jmax, end > col0 ? (end - col0 + W - 1) / W : 0);
       }
       if (P->tune.slice_major) {
         for (int j = 0; j < jmax; ++j)
           for (size_t q = q0; q < q1; ++q) {
             const int s = subs[q];
             const int end = std::min<int64_t>((int64_t)col0 + ncols, P->n[s]);
-            const int c = col0 + j * kSliceCols;
+            const int c = col0 + j * W;
             if (c < end) add_slice(s, c, end);
           }
       } else {
         for (size_t q = q0; q < q1; ++q) {
           const int s = subs[q];
           const int end = std::min<int64_t>((int64_t)col0 + ncols, P->n[s]);
-          for (int c = col0; c < end; c += kSliceCols) add_slice(s, c, end);
+          for (int c = col0; c < end; c += W) add_slice(s, c, end);
         }
       }
       q0 = q1;
@@ -362,13 +365,13 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
       int cols = 0;
       while (p < p1 && probs[p].m == pk.m && probs[p].geo.ex == pk.ex &&
              probs[p].geo.ey == pk.ey && probs[p].geo.ez == pk.ez &&
-             pk.nslices + (probs[p].ncols + kSliceCols - 1) / kSliceCols <= P->tune.pack_slices) {
-        for (int c = 0; c < probs[p].ncols; c += kSliceCols) {
+             pk.nslices + (probs[p].ncols + W - 1) / W <= pack_cap) {
+        for (int c = 0; c < probs[p].ncols; c += W) {
           Slice sl;
           sl.prob = p;
           sl.sub = probs[p].sub;
           sl.col0 = probs[p].col0 + c;
-          sl.ncols = std::min(kSliceCols, probs[p].ncols - c);
+          sl.ncols = std::min(W, probs[p].ncols - c);
           sl.out_col = c;
           sl.member = pk.nprob;
           slices.push_back(sl);
@@ -453,7 +456,7 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
 
   sc.grid = G;
   sc.nprob = (int)probs.size();
-  sc.max_tiles = tc ? (max_slices + 1) / 2 : 1;
+  sc.max_tiles = tc ? (max_slices * W + 127) / 128 : 1;
   sc.partial_elems = slot_total;
   if (slot_total > P->partial_cap)
     return fail(SPID_ERR_INVALID_ARG, "sketch schedule exceeds the partial workspace");
@@ -665,7 +668,7 @@ spid_status encode_window_maps(spid_plan_t P, const void* window, std::vector<CU
                             (cuuint64_t)nqs, (cuuint64_t)P->n[s]};
       cuuint64_t strides[4] = {(cuuint64_t)g.sy * P->esz, (cuuint64_t)g.sz * P->esz,
                                (cuuint64_t)g.sq * P->esz, (cuuint64_t)P->ld[s] * P->esz};
-      cuuint32_t box[5] = {32, 1, 1, 1, (cuuint32_t)kSliceCols};
+      cuuint32_t box[5] = {32, 1, 1, 1, (cuuint32_t)P->tune.slice_cols};
       cuuint32_t estr[5] = {1, 1, 1, 1, 1};
       r = enc(&maps[s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, base, dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -673,7 +676,7 @@ spid_status encode_window_maps(spid_plan_t P, const void* window, std::vector<CU
     } else {
       cuuint64_t dims[2] = {(cuuint64_t)P->m[s], (cuuint64_t)P->n[s]};
       cuuint64_t strides[1] = {(cuuint64_t)P->ld[s] * P->esz};
-      cuuint32_t box[2] = {32, (cuuint32_t)kSliceCols};
+      cuuint32_t box[2] = {32, (cuuint32_t)P->tune.slice_cols};
       cuuint32_t estr[2] = {1, 1};
       r = enc(&maps[s], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -724,6 +727,7 @@ spid_status launch_sketch_range(spid_plan_t P, const Schedule* sc, const void* w
   a.slices = sc->slices;
   a.packs = sc->packs;
   a.psegs = sc->psegs;
+  a.slice_cols = P->tune.slice_cols;
   const int nlaunch = P->per_sub() ? P->S : 1;
   for (int q = 0; q < nlaunch; ++q) {
     a.cta_base = P->per_sub() ? sc->cta_base_of_sub[q] : 0;
@@ -1361,13 +1365,14 @@ bool valid_tuning(const spid_tuning& t) {
          (t.sketch_stages >= 2 && t.sketch_stages <= 8)) &&
          in(t.sketch_ctas_per_sm, {0, 1, 2}) && in(t.error_path, {0, 1}) &&
          in(t.error_rows, {256, 512, 1024}) && in(t.error_cols, {128, 256}) &&
-         in(t.sketch_slice_major, {0, 1});
+         in(t.sketch_slice_major, {0, 1}) && in(t.sketch_slice_cols, {0, 16, 32, 64});
 }
 
 TuneCfg cfg_of(const spid_tuning& t) {
   TuneCfg c;
   c.pack_slices = t.sketch_pack_slices;
   c.slice_major = t.sketch_slice_major;
+  c.slice_cols = t.sketch_slice_cols ? t.sketch_slice_cols : kSliceCols;
   c.stages = t.sketch_stages;
   c.ctas_per_sm = t.sketch_ctas_per_sm;
   c.err_path = t.error_path;
@@ -1380,6 +1385,7 @@ spid_tuning tuning_of(const TuneCfg& c, float sk, float er) {
   spid_tuning t;
   t.sketch_pack_slices = c.pack_slices;
   t.sketch_slice_major = c.slice_major;
+  t.sketch_slice_cols = c.slice_cols;
   t.sketch_stages = c.stages;
   t.sketch_ctas_per_sm = c.ctas_per_sm;
   t.error_path = c.err_path;
@@ -1395,6 +1401,8 @@ spid_tuning tuning_of(const TuneCfg& c, float sk, float er) {
 spid_status apply_sketch_cfg(spid_plan_t P, const TuneCfg& c) {
   P->tune.pack_slices = c.pack_slices;
   P->tune.slice_major = c.slice_major;
+  if (P->tune.slice_cols != c.slice_cols) P->bound_window = nullptr;   // maps carry the box width
+  P->tune.slice_cols = c.slice_cols;
   P->tune.stages = c.stages;
   P->tune.ctas_per_sm = c.ctas_per_sm;
   drop_schedules(P);
@@ -1457,6 +1465,8 @@ extern "C" spid_status spid_plan_set_tuning(spid_plan_t P, const spid_tuning* t)
   if (t->error_path == 1 && !P->err_tc_possible())
     return fail(SPID_ERR_UNSUPPORTED, "the tensor-core error pass needs a batched TF32/BF16/3xBF16 "
                                       "plan with k_max <= 32");
+  if (t->sketch_slice_cols && t->sketch_slice_cols != kSliceCols && P->prec != SPID_PREC_TF32)
+    return fail(SPID_ERR_UNSUPPORTED, "slices narrower than 64 columns: TF32 plans only");
   std::lock_guard<std::mutex> g(P->tune_mu);
   SPID_CUDA(cudaDeviceSynchronize());
   const TuneCfg c = cfg_of(*t);
@@ -1493,6 +1503,18 @@ extern "C" spid_status spid_plan_autotune(spid_plan_t P, const void* window, spi
           c.slice_major = order;
           c.pack_slices = ps;
           c.stages = stg;
+          c.slice_cols = kSliceCols;
+          cands.push_back(c);
+        }
+    // narrower slices (fewer window columns per chunk), full 512-column packs
+    if (P->prec == SPID_PREC_TF32)
+      for (int order : {0, 1})
+        for (int w : {32, 16}) {
+          TuneCfg c = P->tune;
+          c.slice_major = order;
+          c.pack_slices = kPackSlices;
+          c.stages = 0;
+          c.slice_cols = w;
           cands.push_back(c);
         }
   } else {
@@ -1504,21 +1526,27 @@ extern "C" spid_status spid_plan_autotune(spid_plan_t P, const void* window, spi
   }
   TuneCfg best_cfg = P->tune;
   float best_sk = 0.f;
-  int seen_stages = -1, seen_pack = -1, seen_order = -1;
+  int seen_stages = -1, seen_pack = -1, seen_order = -1, seen_width = -1;
   for (const TuneCfg& c : cands) {
     st = apply_sketch_cfg(P, c);
     if (st == SPID_ERR_UNSUPPORTED) continue;   // e.g. too few stages fit
     if (st != SPID_OK) return st;
+    // the tensor maps carry the slice width: re-encode them for this candidate
+    if (P->tensor_core()) {
+      st = bind_window(P, window, cs);
+      if (st != SPID_OK) return st;
+    }
     Schedule* sc = nullptr;
     st = get_schedule(P, 0, P->n_max, &sc);
     if (st != SPID_OK) return st;
     // stage counts above what fits collapse onto the same launch: skip repeats
     if (P->tensor_core() && sc->stages == seen_stages && c.pack_slices == seen_pack &&
-        c.slice_major == seen_order)
+        c.slice_major == seen_order && c.slice_cols == seen_width)
       continue;
     seen_stages = sc->stages;
     seen_pack = c.pack_slices;
     seen_order = c.slice_major;
+    seen_width = c.slice_cols;
     float ms = 0.f;
     st = time_median(cs, kReps, [&] { return launch_sketch_range(P, sc, window, P->d_tmaps, cs); },
                      &ms);
@@ -1529,11 +1557,13 @@ extern "C" spid_status spid_plan_autotune(spid_plan_t P, const void* window, spi
       best_sk = ms;
       best_cfg.pack_slices = c.pack_slices;
       best_cfg.slice_major = c.slice_major;
+      best_cfg.slice_cols = c.slice_cols;
       best_cfg.stages = c.stages;
       best_cfg.ctas_per_sm = c.ctas_per_sm;
     }
   }
   st = apply_sketch_cfg(P, best_cfg);
+  if (st == SPID_OK && P->tensor_core()) st = bind_window(P, window, cs);
   if (st != SPID_OK) return st;
   {
     Schedule* sc = nullptr;

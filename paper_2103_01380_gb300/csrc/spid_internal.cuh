@@ -61,11 +61,15 @@ struct Segment {
 };
 
 // Tensor-core packing: Omega does not depend on the subdomain, so one chunk of
-// rows can serve several subdomains at once.  A slice is up to 64 columns of
-// one problem (one 8 KB TMA box); a pack is up to 8 slices of problems with
-// the same m, streamed together as 4 MMA tiles of 128 rows (two slices each).
+// rows can serve several subdomains at once.  A slice is up to kSliceCols
+// columns of one problem (one TMA box of 32 rows; 64 columns by default, 32 or
+// 16 in the TF32 sketch when tuned so, which narrows the range of window
+// columns -- snapshots -- one chunk touches); a pack is up to 512 columns of
+// slices of problems with the same shape, streamed together as 4 MMA tiles of
+// 128 rows.
 constexpr int kSliceCols = 64;
-constexpr int kPackSlices = 8;
+constexpr int kPackSlices = 8;                 // pack width in 64-column units
+constexpr int kMaxPackMembers = 32;            // slices (and problems) per pack, 512 / 16
 // Cost of a pack's epilogue (TMEM drain, partial slots, fold) in chunks of
 // streaming, for balancing the chunks over the persistent CTAs: measured on
 // uneven windows, a 16-chunk pack (m = 512) took about as long as 16 more.
@@ -75,14 +79,14 @@ struct Slice {
   int32_t prob;      // problem index (the fold unit)
   int32_t sub;       // subdomain (tensor map)
   int32_t col0;      // first window column of the slice
-  int32_t ncols;     // <= kSliceCols
+  int32_t ncols;     // <= the plan's slice width
   int32_t out_col;   // column of the slice inside its problem's partial slot
   int32_t member;    // index of its problem among the pack's problems
 };
 
 struct Pack {
   int32_t slice0;    // first slice
-  int32_t nslices;   // 1 .. kPackSlices
+  int32_t nslices;   // 1 .. 512 / slice width
   int32_t m;         // rows of every member
   int32_t prob0;     // first member problem (members are consecutive problems)
   int32_t nprob;     // number of member problems
@@ -126,6 +130,7 @@ struct SketchArgs {
   const Slice* slices;
   const Pack* packs;
   const PackSegment* psegs;
+  int32_t slice_cols = kSliceCols;   // columns per slice (TMA box width)
 };
 
 template <typename T> struct Vec16;   // 16-byte vector of T

@@ -105,6 +105,7 @@ class _Tuning(ctypes.Structure):
                 ("error_rows", ctypes.c_int32),
                 ("error_cols", ctypes.c_int32),
                 ("sketch_slice_major", ctypes.c_int32),
+                ("sketch_slice_cols", ctypes.c_int32),
                 ("sketch_ms", ctypes.c_float),
                 ("error_ms", ctypes.c_float)]
 

@@ -157,15 +157,20 @@ def test_tensor_core_boxes_need_x_runs_of_32():
     assert e.value.status == 7
 
 
-@pytest.mark.parametrize("precision", ["fp32", "tf32"])
-def test_box_plan_equals_the_blocks_plan_on_the_cut_data(precision):
+@pytest.mark.parametrize("precision,slice_cols", [("fp32", 64), ("tf32", 64), ("tf32", 32),
+                                                  ("tf32", 16)])
+def test_box_plan_equals_the_blocks_plan_on_the_cut_data(precision, slice_cols):
     # the same subdomains read from the field and from cut-out blocks; the
     # CUDA-core sketch visits the rows in the same order with the same schedule
-    # (bitwise equal), the tensor-core one packs by box shape (equal to rounding)
+    # (bitwise equal), the tensor-core one packs by box shape (equal to rounding),
+    # with 64-column slices or, tuned, 32- and 16-column ones (fewer snapshots per
+    # chunk) on the field
     field = _field()
     w = torch.from_numpy(field).cuda()
     boxes = BOXES_TC if precision == "tf32" else BOXES_ANY
     plan, blocks = _plan_and_blocks(field, boxes, True, precision, 5, 5, tol=1e-3)
+    if slice_cols != 64:
+        plan.set_tuning(dict(plan.tuning(), sketch_slice_cols=slice_cols))
     gb = _run(plan, w, recon=False)
     win = inputs.pack_blocks(blocks)
     bp = spid.Plan.for_window(win, k_max=5, p=5, tol=1e-3, precision=precision,
