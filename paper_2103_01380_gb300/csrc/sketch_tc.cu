@@ -102,31 +102,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) sketch_tf32_kernel(const TcArgs
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
-    if (lane == 0) {
-      int it = 0;
-      bool ok = true;
-      const CUtensorMap* tmaps = static_cast<const CUtensorMap*>(a.tmaps);
-      for (int si = seg0; si < seg1 && ok; ++si) {
-        const PackSegment sg = a.psegs[si];
-        const Pack pk = a.packs[sg.pack];
-        for (int ch = sg.chunk0; ch < sg.chunk1; ++ch, ++it) {
-          const int st = it % S;
-          const uint32_t ph = (uint32_t)(it / S) & 1u;
-          if (!mbar_wait(smem_addr(&empty[st]), ph ^ 1u, abort_flag, a.status)) { ok = false; break; }
-          const uint32_t fb = smem_addr(&full[st]);
-          // one TMA box per slice: slice_cols columns x 32 rows, back to back, so
-          // a tile of 128 columns is 128 / slice_cols boxes
-          const int slice_bytes = a.slice_cols * 128;
-          mbar_arrive_expect_tx(fb, (uint32_t)(pk.nslices * slice_bytes));
-          unsigned char* dst = smem_A + (size_t)st * args.max_tiles * kTileBytes;
-          const ChunkCoord cc = chunk_coord(pk, ch);
-          for (int h = 0; h < pk.nslices; ++h) {
-            const Slice sl = a.slices[pk.slice0 + h];
-            tma_load_chunk(smem_addr(dst + h * slice_bytes), tmaps + sl.sub, pk, cc, sl.col0, fb);
-          }
+    // Lane h holds slice h of the current pack (its map and box origin) in
+    // registers for the whole segment and issues that slice's box each chunk;
+    // lane 0 waits for the stage and arms its barrier first.  A pack has at
+    // most 32 slices (512 columns of slices at least 16 wide).
+    int it = 0;
+    bool ok = true;
+    const CUtensorMap* tmaps = static_cast<const CUtensorMap*>(a.tmaps);
+    const int slice_bytes = a.slice_cols * 128;   // one box: slice_cols columns x 32 rows
+    for (int si = seg0; si < seg1 && ok; ++si) {
+      const PackSegment sg = a.psegs[si];
+      const Pack pk = a.packs[sg.pack];
+      const bool mine = lane < pk.nslices;
+      Slice sl{};
+      if (mine) sl = a.slices[pk.slice0 + lane];
+      for (int ch = sg.chunk0; ch < sg.chunk1; ++ch, ++it) {
+        const int st = it % S;
+        const uint32_t ph = (uint32_t)(it / S) & 1u;
+        const uint32_t fb = smem_addr(&full[st]);
+        if (lane == 0) {
+          ok = mbar_wait(smem_addr(&empty[st]), ph ^ 1u, abort_flag, a.status);
+          if (ok) mbar_arrive_expect_tx(fb, (uint32_t)(pk.nslices * slice_bytes));
         }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        // the boxes of a pack's slices sit back to back, so a tile of 128
+        // columns is 128 / slice_cols boxes
+        unsigned char* dst = smem_A + (size_t)st * args.max_tiles * kTileBytes;
+        const ChunkCoord cc = chunk_coord(pk, ch);
+        if (mine) tma_load_chunk(smem_addr(dst + lane * slice_bytes), tmaps, pk, cc, sl, fb);
       }
-      // Drain: every issued stage's bytes must have landed before the CTA exits.
+    }
+    // Drain: every issued stage's bytes must have landed before the CTA exits.
+    if (lane == 0) {
       const int first = it - S > 0 ? it - S : 0;
       for (int j = first; j < it; ++j)
         mbar_wait(smem_addr(&full[j % S]), (uint32_t)(j / S) & 1u, abort_flag, a.status, false);

@@ -105,6 +105,21 @@ struct spid_plan_s {
   // per-QoI error totals (num_qoi = 0: none)
   std::vector<int32_t> qoi;
   int num_qoi = 0;
+  // Tensor maps of the window (tensor-core plans): map s < S covers subdomain
+  // s alone; map S + g is shared by every subdomain with tma_group[s] == g,
+  // which sits at origin tma_org[4 s .. 4 s + 3] of it.  A pack whose slices
+  // read through one shared map touches one descriptor instead of one per
+  // subdomain.
+  struct TmaGroup {
+    int64_t base;        // element offset of the map's origin in the window
+    int rank;            // 2 (rows, columns) or 5 (x, y, z, q, columns)
+    int64_t dims[5];     // extents, innermost first
+    int64_t strides[4];  // element strides of dims 1 ..
+  };
+  std::vector<TmaGroup> tma_groups;
+  std::vector<int32_t> tma_group;
+  std::vector<int32_t> tma_org;
+  int num_tmaps() const { return S + (int)tma_groups.size(); }
   bool fp64() const { return prec == SPID_PREC_FP64; }
   bool per_sub() const { return (flags & SPID_FLAG_PER_SUBDOMAIN) != 0; }
   bool tensor_core() const { return prec >= SPID_PREC_TF32; }
@@ -229,6 +244,23 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   std::vector<Unit> units;
   std::vector<Slice> slices;
   std::vector<Pack> packs;
+  // The map a slice's TMA box reads: the subdomain's shared map when the whole
+  // box lies inside its columns, else its own map, whose column extent
+  // zero-fills the box past the subdomain's last column.
+  auto place = [&](Slice& sl) {
+    const int s = sl.sub;
+    const int g = tc && !P->tma_group.empty() ? P->tma_group[s] : -1;
+    if (g >= 0 && sl.col0 + W <= P->n[s]) {
+      sl.map = P->S + g;
+      sl.tx = P->tma_org[4 * s + 0];
+      sl.ty = P->tma_org[4 * s + 1];
+      sl.tz = P->tma_org[4 * s + 2];
+      sl.tq = P->tma_org[4 * s + 3];
+    } else {
+      sl.map = s;
+      sl.tx = sl.ty = sl.tz = sl.tq = 0;
+    }
+  };
   // Batched tensor-core plans: the 64-column slices of every subdomain of one m
   // form a stream that is cut into packs of pack_slices slices, so every pack
   // but the last of an m-class is full whatever the window lengths; a problem
@@ -289,6 +321,7 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
       sl.ncols = nc;
       sl.out_col = c - probs.back().col0;
       sl.member = pk.nprob - 1;
+      place(sl);
       slices.push_back(sl);
       probs.back().ncols += nc;
       ++pk.nslices;
@@ -374,6 +407,7 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
           sl.ncols = std::min(W, probs[p].ncols - c);
           sl.out_col = c;
           sl.member = pk.nprob;
+          place(sl);
           slices.push_back(sl);
           ++pk.nslices;
         }
@@ -657,7 +691,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 spid_status encode_window_maps(spid_plan_t P, const void* window, std::vector<CUtensorMap>& maps) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return fail(SPID_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
-  maps.resize(P->S);
+  maps.resize(P->num_tmaps());
   for (int s = 0; s < P->S; ++s) {
     void* base = const_cast<char*>(static_cast<const char*>(window)) + P->off[s] * P->esz;
     const RowGeom& g = P->geo[s];
@@ -686,6 +720,23 @@ spid_status encode_window_maps(spid_plan_t P, const void* window, std::vector<CU
       return fail(SPID_ERR_INVALID_ARG, "cuTensorMapEncodeTiled failed for subdomain " +
                                             std::to_string(s) + " (code " + std::to_string((int)r) + ")");
   }
+  // shared maps: the same box over a whole field or a run of equally strided blocks
+  for (size_t gi = 0; gi < P->tma_groups.size(); ++gi) {
+    const spid_plan_s::TmaGroup& g = P->tma_groups[gi];
+    void* base = const_cast<char*>(static_cast<const char*>(window)) + g.base * P->esz;
+    cuuint64_t dims[5], strides[4];
+    cuuint32_t box[5] = {32, 1, 1, 1, 1};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    for (int i = 0; i < g.rank; ++i) dims[i] = (cuuint64_t)g.dims[i];
+    for (int i = 0; i + 1 < g.rank; ++i) strides[i] = (cuuint64_t)g.strides[i] * P->esz;
+    box[g.rank - 1] = (cuuint32_t)P->tune.slice_cols;
+    CUresult r = enc(&maps[P->S + gi], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, g.rank, base, dims, strides,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+      return fail(SPID_ERR_INVALID_ARG, "cuTensorMapEncodeTiled failed for shared map " +
+                                            std::to_string(gi) + " (code " + std::to_string((int)r) + ")");
+  }
   return SPID_OK;
 }
 
@@ -697,7 +748,8 @@ spid_status bind_window(spid_plan_t P, const void* window, cudaStream_t st) {
   spid_status rc = encode_window_maps(P, window, maps);
   if (rc != SPID_OK) return rc;
   SPID_CUDA(cudaStreamSynchronize(st));
-  SPID_CUDA(cudaMemcpy(P->d_tmaps, maps.data(), sizeof(CUtensorMap) * P->S, cudaMemcpyHostToDevice));
+  SPID_CUDA(cudaMemcpy(P->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                       cudaMemcpyHostToDevice));
   P->bound_window = window;
   return SPID_OK;
 }
@@ -904,6 +956,72 @@ static spid_status parse_layout(const spid_plan_desc* d, size_t esz, std::vector
   return SPID_OK;
 }
 
+// Shared tensor maps of a tensor-core plan.  Boxes of a global field: one
+// 5-D map over the whole field [t][q][Z][Y][X]; a box is placed by its origin
+// (and its QoI when QoIs are split).  Blocks: the subdomains with equal ld,
+// equal m and equal offset modulo ld form a 2-D map of m rows whose columns are
+// the window's runs of ld elements from that residue; subdomain s starts at
+// column off / ld.  Subdomains of whole 32-row chunks that fit inside one run
+// share a map of whole runs of every residue instead.  A group of one keeps
+// only its own map.
+static void build_tma_groups(spid_plan_s* P, const spid_box_layout* L) {
+  P->tma_groups.clear();
+  P->tma_group.assign(P->S, -1);
+  P->tma_org.assign(4 * (size_t)P->S, 0);
+  if (!P->tensor_core() || P->S < 2) return;
+  if (L) {
+    spid_plan_s::TmaGroup g{};
+    g.base = 0;
+    g.rank = 5;
+    const int64_t plane = (int64_t)L->X * L->Y;
+    const int64_t d[5] = {L->X, L->Y, L->Z, L->nq, P->n_max};
+    const int64_t st[4] = {L->X, plane, plane * L->Z, L->snap_stride};
+    std::copy(d, d + 5, g.dims);
+    std::copy(st, st + 4, g.strides);
+    P->tma_groups.push_back(g);
+    const int per_box = L->split_qoi ? L->nq : 1;
+    for (int s = 0; s < P->S; ++s) {
+      const int32_t* o = L->org3 + 3 * (s / per_box);
+      P->tma_group[s] = 0;
+      P->tma_org[4 * s + 0] = o[0];
+      P->tma_org[4 * s + 1] = o[1];
+      P->tma_org[4 * s + 2] = o[2];
+      P->tma_org[4 * s + 3] = L->split_qoi ? s % per_box : 0;
+    }
+    return;
+  }
+  // key (ld, r, m): a map of m rows from residue r; key (ld, -1, 0): a map of
+  // whole ld-runs that places each subdomain at x = r, for subdomains whose
+  // rows are whole 32-row chunks inside one run (no chunk reads past them)
+  std::map<std::tuple<int64_t, int64_t, int32_t>, std::vector<int>> runs;
+  for (int s = 0; s < P->S; ++s) {
+    const int64_t c0 = P->off[s] / P->ld[s], r = P->off[s] % P->ld[s];
+    if (c0 + P->n[s] > INT32_MAX) continue;   // the column coordinate is 32-bit
+    const bool whole = P->m[s] % kChunkRows == 0 && r + P->m[s] <= P->ld[s] && P->ld[s] <= INT32_MAX;
+    runs[whole ? std::make_tuple(P->ld[s], (int64_t)-1, 0) : std::make_tuple(P->ld[s], r, P->m[s])]
+        .push_back(s);
+  }
+  for (const auto& kv : runs) {
+    if (kv.second.size() < 2) continue;
+    const bool whole = std::get<1>(kv.first) < 0;
+    spid_plan_s::TmaGroup g{};
+    g.base = whole ? 0 : std::get<1>(kv.first);
+    g.rank = 2;
+    g.dims[0] = whole ? std::get<0>(kv.first) : std::get<2>(kv.first);
+    g.dims[1] = 0;
+    g.strides[0] = std::get<0>(kv.first);
+    const int gi = (int)P->tma_groups.size();
+    for (int s : kv.second) {
+      const int64_t c0 = P->off[s] / P->ld[s];
+      g.dims[1] = std::max<int64_t>(g.dims[1], c0 + P->n[s]);
+      P->tma_group[s] = gi;
+      P->tma_org[4 * s + 0] = whole ? (int32_t)(P->off[s] % P->ld[s]) : 0;
+      P->tma_org[4 * s + 1] = (int32_t)c0;
+    }
+    P->tma_groups.push_back(g);
+  }
+}
+
 static spid_status plan_create(const spid_plan_desc* d, spid_stream_t stream, int l_sketch,
                                spid_plan_t* out);
 
@@ -983,6 +1101,7 @@ static spid_status plan_create(const spid_plan_desc* d, spid_stream_t stream, in
   P->flags = d->flags;
   P->seed = d->seed;
   P->esz = esz;
+  build_tma_groups(P, d->boxes);
   if (qrcp_cols_per_thread(n_max, P->l_pad, P->fp64()) == 0) {
     delete P;
     return fail(SPID_ERR_UNSUPPORTED, "window length / oversampled rank beyond the QR kernel's range");
@@ -1051,7 +1170,7 @@ static spid_status plan_create(const spid_plan_desc* d, spid_stream_t stream, in
   SPID_ALLOC(P->d_sub_err, sizeof(double) * 2 * P->S);
   SPID_ALLOC(P->d_err_cnt, sizeof(int) * (P->S + 1));
   SPID_ALLOC(P->d_partial, esz * P->partial_cap);
-  if (P->tensor_core()) SPID_ALLOC(P->d_tmaps, sizeof(CUtensorMap) * P->S);
+  if (P->tensor_core()) SPID_ALLOC(P->d_tmaps, sizeof(CUtensorMap) * P->num_tmaps());
   if (P->boxes) SPID_ALLOC(P->d_geo, sizeof(RowGeom) * P->S);
   if (P->num_qoi > 0) SPID_ALLOC(P->d_qoi, sizeof(int32_t) * P->S);
 #undef SPID_ALLOC
@@ -1710,9 +1829,10 @@ extern "C" spid_status spid_graph_create(spid_plan_t P, const void* window, int3
     std::vector<CUtensorMap> maps;
     st = encode_window_maps(P, window, maps);
     if (st != SPID_OK) return bail(st);
-    cudaError_t e = cudaMalloc(&G->d_tmaps, sizeof(CUtensorMap) * P->S);
+    cudaError_t e = cudaMalloc(&G->d_tmaps, sizeof(CUtensorMap) * maps.size());
     if (e == cudaSuccess)
-      e = cudaMemcpy(G->d_tmaps, maps.data(), sizeof(CUtensorMap) * P->S, cudaMemcpyHostToDevice);
+      e = cudaMemcpy(G->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                     cudaMemcpyHostToDevice);
     if (e != cudaSuccess)
       return bail(fail(e == cudaErrorMemoryAllocation ? SPID_ERR_OOM : SPID_ERR_CUDA,
                        std::string("graph tensor maps: ") + cudaGetErrorString(e)));

@@ -82,6 +82,13 @@ struct Slice {
   int32_t ncols;     // <= the plan's slice width
   int32_t out_col;   // column of the slice inside its problem's partial slot
   int32_t member;    // index of its problem among the pack's problems
+  // The TMA box that loads the slice: tensor map `map`, with the subdomain's
+  // first element at coordinate (tx, ty, tz, tq) of that map.  2-D maps load
+  // (tx + row, ty + col0); 5-D maps load (tx + x, ty + y, tz + z, tq + q, col0).
+  // A subdomain's own map has origin 0; a map shared by many subdomains (one
+  // over the whole field, or one per run of equally strided blocks) places it.
+  int32_t map;
+  int32_t tx, ty, tz, tq;
 };
 
 struct Pack {

@@ -4,6 +4,7 @@
 // commit / fences, TMEM loads, named barriers.
 #pragma once
 
+#include <cuda.h>
 #include <stdint.h>
 
 #include "spid_internal.cuh"
@@ -97,10 +98,11 @@ __device__ __forceinline__ ChunkCoord chunk_coord(const Pack& pk, int ch) {
   return c;
 }
 
-__device__ __forceinline__ void tma_load_chunk(uint32_t dst, const void* tmap, const Pack& pk,
-                                               const ChunkCoord& c, int col0, uint32_t bar) {
-  if (pk.ex > 0) tma_load_5d(dst, tmap, c.x, c.y, c.z, c.q, col0, bar);
-  else tma_load_2d(dst, tmap, c.x, col0, bar);
+__device__ __forceinline__ void tma_load_chunk(uint32_t dst, const CUtensorMap* tmaps, const Pack& pk,
+                                               const ChunkCoord& c, const Slice& sl, uint32_t bar) {
+  const void* tm = tmaps + sl.map;
+  if (pk.ex > 0) tma_load_5d(dst, tm, sl.tx + c.x, sl.ty + c.y, sl.tz + c.z, sl.tq + c.q, sl.col0, bar);
+  else tma_load_2d(dst, tm, sl.tx + c.x, sl.ty + sl.col0, bar);
 }
 
 // K-major operand, 128-byte swizzle: 8-row groups 1024 bytes apart.
