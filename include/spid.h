@@ -263,8 +263,10 @@ typedef struct {
                                   spid_plan_autotune also tries both sketch_slice_major orders */
   int32_t sketch_stages;       /* tensor-core sketch pipeline depth: 0 = as many as fit in
                                   shared memory (default), else 2..8 (capped by what fits) */
-  int32_t sketch_ctas_per_sm;  /* CUDA-core (FP32/FP64) sketch: persistent CTAs per SM, 1 or 2;
-                                  0 = by the kernel's register budget (default) */
+  int32_t sketch_ctas_per_sm;  /* CUDA-core (FP32/FP64) sketch: persistent CTAs per SM, 1..4;
+                                  0 = by the register budget of the kernel variant the call's
+                                  widest column group selects (default).  One launch per
+                                  subdomain (SPID_FLAG_PER_SUBDOMAIN) uses at most 2 */
   int32_t error_path;          /* 0 = CUDA-core error pass (default); 1 = tensor-core pass
                                   (batched TF32/BF16/3xBF16 plans with k_max <= 32 only) */
   int32_t error_rows;          /* CUDA-core error pass: rows per work unit, 256, 512 (default)

@@ -33,10 +33,18 @@ __device__ __forceinline__ void store_vec<double>(double* d, const double2& v) {
 constexpr int kThreads = 256;
 constexpr int kJGroups = 64;  // thread = (i-group in 0..3) x (j-group in 0..63)
 
+// CTAs per SM that a thread's TI x TJ accumulators (in 32-bit registers) leave
+// room for; the launch bounds cap registers to match.
+constexpr int simt_min_blocks(int acc_regs) {
+  return acc_regs <= 8 ? 4 : acc_regs <= 32 ? 3 : acc_regs <= 64 ? 2 : 1;
+}
+
 // TI: Omega rows per thread (l_pad = 4 TI); TJ: columns per thread (the
-// column group holds up to 64 TJ columns).
+// column group holds up to 64 TJ columns).  A launch uses the smallest TJ that
+// holds its widest problem, so narrow column ranges (micro-batches) do not pay
+// for a 512-column register tile.
 template <typename T, int TI, int TJ>
-__global__ void __launch_bounds__(kThreads, (TI * TJ <= 64) ? 2 : 1)
+__global__ void __launch_bounds__(kThreads, simt_min_blocks(TI * TJ * (int)(sizeof(T) / 4)))
 sketch_simt_kernel(SketchArgs args) {
   constexpr int LP = 4 * TI;
   constexpr int CG = kJGroups * TJ;
@@ -191,21 +199,51 @@ cudaError_t launch_one(const SketchArgs& a, int grid, cudaStream_t st) {
 // Column-group size of the SIMT sketch for a given element size.
 int sketch_simt_group_cols(bool fp64) { return fp64 ? kJGroups * 4 : kJGroups * 8; }
 
-cudaError_t launch_sketch_simt(const SketchArgs& a, int grid, bool fp64, cudaStream_t st) {
+// Columns per thread for a launch whose widest problem has max_cols columns.
+int sketch_simt_tj(bool fp64, int max_cols) {
+  const int cap = fp64 ? 4 : 8;
+  int tj = 1;
+  while (tj < cap && kJGroups * tj < max_cols) tj *= 2;
+  return tj;
+}
+
+// CTAs per SM the launch bounds of the (l_pad, tj) variant are built for.
+int sketch_simt_ctas_per_sm(bool fp64, int l_pad, int tj) {
+  return simt_min_blocks((l_pad / 4) * tj * (fp64 ? 2 : 1));
+}
+
+namespace {
+
+template <typename T, int TI>
+cudaError_t launch_tj(const SketchArgs& a, int grid, int tj, cudaStream_t st) {
+  switch (tj) {
+    case 1: return launch_one<T, TI, 1>(a, grid, st);
+    case 2: return launch_one<T, TI, 2>(a, grid, st);
+    case 4: return launch_one<T, TI, 4>(a, grid, st);
+    case 8:
+      if constexpr (sizeof(T) == 4) return launch_one<T, TI, 8>(a, grid, st);
+      break;
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_sketch_simt(const SketchArgs& a, int grid, bool fp64, int tj, cudaStream_t st) {
   if (grid <= 0) return cudaSuccess;
   if (fp64) {
     switch (a.l_pad) {
-      case 16: return launch_one<double, 4, 4>(a, grid, st);
-      case 32: return launch_one<double, 8, 4>(a, grid, st);
-      case 48: return launch_one<double, 12, 4>(a, grid, st);
-      case 64: return launch_one<double, 16, 4>(a, grid, st);
+      case 16: return launch_tj<double, 4>(a, grid, tj, st);
+      case 32: return launch_tj<double, 8>(a, grid, tj, st);
+      case 48: return launch_tj<double, 12>(a, grid, tj, st);
+      case 64: return launch_tj<double, 16>(a, grid, tj, st);
     }
   } else {
     switch (a.l_pad) {
-      case 16: return launch_one<float, 4, 8>(a, grid, st);
-      case 32: return launch_one<float, 8, 8>(a, grid, st);
-      case 48: return launch_one<float, 12, 8>(a, grid, st);
-      case 64: return launch_one<float, 16, 8>(a, grid, st);
+      case 16: return launch_tj<float, 4>(a, grid, tj, st);
+      case 32: return launch_tj<float, 8>(a, grid, tj, st);
+      case 48: return launch_tj<float, 12>(a, grid, tj, st);
+      case 64: return launch_tj<float, 16>(a, grid, tj, st);
     }
   }
   return cudaErrorInvalidValue;

@@ -44,6 +44,7 @@ struct Schedule {
   int nprob = 0;
   int max_tiles = 1;       // 128-column tiles of the widest problem (TF32)
   int stages = 1;          // TF32 pipeline depth
+  int simt_tj = 1;         // CUDA-core sketch: columns per thread (64 tj >= widest problem)
   std::vector<int> cta_base_of_sub, prob_base_of_sub, nprob_of_sub;
   void* dev = nullptr;     // one device block holding every table below
   const Problem* probs = nullptr;
@@ -207,6 +208,11 @@ struct spid_plan_s {
 
 namespace {
 
+// One launch per subdomain (SPID_FLAG_PER_SUBDOMAIN) keeps at most this many
+// CUDA-core CTAs per SM: its partial-sum workspace holds a slot per CTA per
+// subdomain.
+constexpr int kPerSubMaxCtasPerSm = 2;
+
 // Build the sketch schedule for window columns [col0, col0 + ncols).
 //
 // Problems: every subdomain restricted to groups of up to group_cols()
@@ -218,7 +224,7 @@ namespace {
 // problem it touches.
 spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   const int CG = P->group_cols();
-  const int G = P->sketch_grid();
+  int G = P->sketch_grid();
   const bool tc = P->tensor_core();
   const int W = tc ? P->tune.slice_cols : kSliceCols;                 // slice width
   const int pack_cap = tc ? P->tune.pack_slices * kSliceCols / W : 1;   // slices per pack
@@ -376,6 +382,17 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   for (int s : subs) {
     const int end = std::min<int64_t>((int64_t)col0 + ncols, P->n[s]);
     prob_sub_last[s] = prob_sub_first[s] + (end > col0 ? (end - col0 + CG - 1) / CG : 0);
+  }
+  // CUDA-core kernels: the register tile fits the widest problem of this
+  // column range, and the grid holds as many CTAs per SM as that tile allows
+  if (!tc) {
+    int max_cols = 1;
+    for (const Problem& pb : probs) max_cols = std::max(max_cols, pb.ncols);
+    sc.simt_tj = sketch_simt_tj(P->fp64(), max_cols);
+    int cps = P->tune.ctas_per_sm > 0 ? P->tune.ctas_per_sm
+                                      : sketch_simt_ctas_per_sm(P->fp64(), P->l_pad, sc.simt_tj);
+    if (P->per_sub()) cps = std::min(cps, kPerSubMaxCtasPerSm);
+    G = cps * P->num_sms;
   }
   // ---- work units
   auto make_units = [&](int p0, int p1) {
@@ -603,7 +620,7 @@ spid_status get_schedule(spid_plan_t P, int col0, int ncols, Schedule** out) {
 // Unit shapes the tuner may choose for the CUDA-core error pass.
 constexpr int kTuneErrRows[] = {256, 512, 1024};
 constexpr int kTuneErrCols[] = {128, 256};
-constexpr int kTuneMaxCtasPerSm = 2;
+constexpr int kTuneMaxCtasPerSm = 4;
 
 int count_error_units(spid_plan_t P, int rows, int cols) {
   int64_t u = 0;
@@ -787,7 +804,7 @@ spid_status launch_sketch_range(spid_plan_t P, const Schedule* sc, const void* w
         P->bf16() ? launch_sketch_bf16(a, sc->grid, sc->stages, sc->max_tiles,
                                        P->prec == SPID_PREC_BF16X3, cs)
         : P->tensor_core() ? launch_sketch_tc(a, sc->grid, sc->stages, sc->max_tiles, cs)
-                           : launch_sketch_simt(a, sc->grid, P->fp64(), cs);
+                           : launch_sketch_simt(a, sc->grid, P->fp64(), sc->simt_tj, cs);
     if (e != cudaSuccess) return fail(SPID_ERR_CUDA, std::string("sketch launch: ") + cudaGetErrorString(e));
   }
   return SPID_OK;
@@ -1138,8 +1155,9 @@ static spid_status plan_create(const spid_plan_desc* d, spid_stream_t stream, in
   const int CG = P->group_cols_max();
   int64_t nprob_full = 0;
   for (int s = 0; s < P->S; ++s) nprob_full += (P->n[s] + CG - 1) / CG;
-  const int64_t ctas = (int64_t)std::max(P->sketch_grid(), kTuneMaxCtasPerSm * P->num_sms) *
-                       (P->per_sub() ? P->S : 1);
+  const int64_t ctas =
+      P->per_sub() ? (int64_t)std::max(P->sketch_grid(), kPerSubMaxCtasPerSm * P->num_sms) * P->S
+                   : (int64_t)std::max(P->sketch_grid(), kTuneMaxCtasPerSm * P->num_sms);
   P->partial_cap = (ctas + nprob_full) * (int64_t)CG * P->l_pad;
   if (P->flags & SPID_FLAG_TC_ERROR) P->tune.err_path = P->err_tc_possible() ? 1 : 0;
 
@@ -1482,7 +1500,7 @@ bool valid_tuning(const spid_tuning& t) {
   };
   return in(t.sketch_pack_slices, {1, 2, 4, 8}) && (t.sketch_stages == 0 ||
          (t.sketch_stages >= 2 && t.sketch_stages <= 8)) &&
-         in(t.sketch_ctas_per_sm, {0, 1, 2}) && in(t.error_path, {0, 1}) &&
+         in(t.sketch_ctas_per_sm, {0, 1, 2, 3, 4}) && in(t.error_path, {0, 1}) &&
          in(t.error_rows, {256, 512, 1024}) && in(t.error_cols, {128, 256}) &&
          in(t.sketch_slice_major, {0, 1}) && in(t.sketch_slice_cols, {0, 16, 32, 64});
 }
@@ -1637,7 +1655,7 @@ extern "C" spid_status spid_plan_autotune(spid_plan_t P, const void* window, spi
           cands.push_back(c);
         }
   } else {
-    for (int cps : {1, 2}) {
+    for (int cps : {1, 2, 4}) {
       TuneCfg c = P->tune;
       c.ctas_per_sm = cps;
       cands.push_back(c);

@@ -301,7 +301,9 @@ struct PlanView {
 
 // Launchers (one translation unit each).
 int sketch_simt_group_cols(bool fp64);
-cudaError_t launch_sketch_simt(const SketchArgs& a, int grid, bool fp64, cudaStream_t st);
+int sketch_simt_tj(bool fp64, int max_cols);
+int sketch_simt_ctas_per_sm(bool fp64, int l_pad, int tj);
+cudaError_t launch_sketch_simt(const SketchArgs& a, int grid, bool fp64, int tj, cudaStream_t st);
 int sketch_tc_group_cols();
 size_t sketch_tc_smem_bytes(int stages, int max_tiles, int l_pad);
 int sketch_tc_max_stages();

@@ -178,7 +178,7 @@ def test_set_tuning_rejects_out_of_range_values():
     base = plan.tuning()
     assert base["sketch_pack_slices"] == 8 and base["error_rows"] == 512
     for key, bad in [("sketch_pack_slices", 3), ("sketch_stages", 1), ("sketch_stages", 9),
-                     ("sketch_ctas_per_sm", 3), ("error_rows", 300), ("error_cols", 64),
+                     ("sketch_ctas_per_sm", 5), ("error_rows", 300), ("error_cols", 64),
                      ("error_path", 2), ("sketch_slice_cols", 8), ("sketch_slice_major", 2)]:
         with pytest.raises(spid.SpidError) as ei:
             plan.set_tuning(dict(base, **{key: bad}))
