@@ -51,10 +51,15 @@ sketch_simt_kernel(SketchArgs args) {
   constexpr int CGP = CG + 1;  // odd row stride: conflict-free transposed stores
   constexpr int VW = Vec<T>::width;
   constexpr int VPC = kChunkRows / VW;  // vectors per column per chunk
+  using VT = typename Vec<T>::type;
+  // vectors of A each thread stages per chunk; narrow tiles (at most 64 bytes of
+  // them) load the next chunk into registers while the current one is computed
+  constexpr int NV = (CG * VPC + kThreads - 1) / kThreads;
+  constexpr bool kPrefetch = NV * (int)sizeof(VT) <= 64;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int last_flag;
-  __shared__ int64_t roff_s[kChunkRows];   // boxes: element offsets of the chunk's rows
+  __shared__ int64_t roff_s[2][kChunkRows];   // boxes: element offsets of a chunk's rows
   T* As = reinterpret_cast<T*>(smem_raw);       // [kChunkRows][CGP]
   T* Om = As + kChunkRows * CGP;                // [kChunkRows][LP]
   // Om must be 16-byte aligned for vector loads
@@ -83,22 +88,57 @@ sketch_simt_kernel(SketchArgs args) {
 #pragma unroll
       for (int v = 0; v < TI; ++v) acc[u][v] = T(0);
 
-    for (int ch = seg.chunk0; ch < seg.chunk1; ++ch) {
+    // a box of a global field: rows of one x-run (a multiple of VW long) are
+    // contiguous, runs sit at the field's strides; table b holds a chunk's offsets
+    auto table = [&](int ch, int b) {
+      const int r = ch * kChunkRows + tid;
+      if (boxed && tid < kChunkRows) roff_s[b][tid] = (r < pb.m) ? row_offset(pb.geo, r) : 0;
+    };
+    // A(rows of chunk ch, col group) into registers, 16-byte loads
+    auto fetch = [&](int ch, int b, VT* buf) {
       const int r0 = ch * kChunkRows;
-      if (boxed) {
-        // a box of a global field: rows of one x-run (a multiple of VW long)
-        // are contiguous, runs sit at the field's strides
-        if (tid < kChunkRows) roff_s[tid] = (r0 + tid < pb.m) ? row_offset(pb.geo, r0 + tid) : 0;
-        __syncthreads();
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        const int v = tid + i * kThreads;
+        if (v < nc * VPC) {
+          const int c = v / VPC, q = v % VPC;
+          const int r = r0 + q * VW;
+          const T* src = A + (int64_t)c * pb.ld + (boxed ? roff_s[b][q * VW] : (int64_t)r);
+          if (r + VW <= pb.m) {
+            buf[i] = __ldg(reinterpret_cast<const VT*>(src));
+          } else {
+            T* xs = reinterpret_cast<T*>(&buf[i]);
+#pragma unroll
+            for (int u = 0; u < VW; ++u) xs[u] = (r + u < pb.m) ? src[u] : T(0);
+          }
+        }
       }
-      // ---- stage A(r0 : r0+32, col group) transposed into As[row][col]
+    };
+    // ... transposed into As[row][col]; columns of the group past nc stay
+    // stale: their accumulators are never stored
+    auto put = [&](const VT* buf) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        const int v = tid + i * kThreads;
+        if (v < nc * VPC) {
+          const int c = v / VPC, q = v % VPC;
+          const T* xs = reinterpret_cast<const T*>(&buf[i]);
+#pragma unroll
+          for (int u = 0; u < VW; ++u) As[(q * VW + u) * CGP + c] = xs[u];
+        }
+      }
+    };
+
+    // wide tiles: one vector at a time, loaded and stored (no register buffer)
+    auto stage_direct = [&](int ch, int b) {
+      const int r0 = ch * kChunkRows;
       for (int v = tid; v < nc * VPC; v += kThreads) {
         const int c = v / VPC, q = v % VPC;
         const int r = r0 + q * VW;
-        const T* src = A + (int64_t)c * pb.ld + (boxed ? roff_s[q * VW] : (int64_t)r);
+        const T* src = A + (int64_t)c * pb.ld + (boxed ? roff_s[b][q * VW] : (int64_t)r);
         T vals[VW];
         if (r + VW <= pb.m) {
-          const typename Vec<T>::type x = __ldg(reinterpret_cast<const typename Vec<T>::type*>(src));
+          const VT x = __ldg(reinterpret_cast<const VT*>(src));
           const T* xs = reinterpret_cast<const T*>(&x);
 #pragma unroll
           for (int u = 0; u < VW; ++u) vals[u] = xs[u];
@@ -109,7 +149,24 @@ sketch_simt_kernel(SketchArgs args) {
 #pragma unroll
         for (int u = 0; u < VW; ++u) As[(q * VW + u) * CGP + c] = vals[u];
       }
-      // columns of the group past nc stay stale: their accumulators are never stored
+    };
+
+    VT buf[kPrefetch ? NV : 1];
+    int b = 0;
+    if constexpr (kPrefetch) {
+      table(seg.chunk0, 0);
+      __syncthreads();
+      fetch(seg.chunk0, 0, buf);
+    }
+    for (int ch = seg.chunk0; ch < seg.chunk1; ++ch, b ^= 1) {
+      const int r0 = ch * kChunkRows;
+      if constexpr (kPrefetch) {
+        put(buf);
+      } else {
+        table(ch, b);
+        __syncthreads();
+        stage_direct(ch, b);
+      }
       // ---- Omega(:, r0 : r0+32) into Om[row][i]
       for (int task = tid; task < kChunkRows * (LP / 4); task += kThreads) {
         const int k = task % kChunkRows, g = task / kChunkRows;
@@ -120,7 +177,7 @@ sketch_simt_kernel(SketchArgs args) {
           for (int u = 0; u < 4; ++u)
             if (4 * g + u >= l) w[u] = T(0);
         }
-        typename Vec<T>::type* dst = reinterpret_cast<typename Vec<T>::type*>(Om + k * LP + 4 * g);
+        VT* dst = reinterpret_cast<VT*>(Om + k * LP + 4 * g);
         if constexpr (VW == 4) {
           dst[0] = make_float4(w[0], w[1], w[2], w[3]);
         } else {
@@ -128,7 +185,11 @@ sketch_simt_kernel(SketchArgs args) {
           dst[1] = make_double2(w[2], w[3]);
         }
       }
+      const bool more = kPrefetch && ch + 1 < seg.chunk1;
+      if (more) table(ch + 1, b ^ 1);
       __syncthreads();
+      if constexpr (kPrefetch)
+        if (more) fetch(ch + 1, b ^ 1, buf);   // in flight during the FMAs below
       // ---- acc[j][i] += A(r, j) Omega(i, r), rows in ascending order
 #pragma unroll 4
       for (int k = 0; k < kChunkRows; ++k) {
@@ -137,8 +198,7 @@ sketch_simt_kernel(SketchArgs args) {
         for (int u = 0; u < TJ; ++u) a[u] = As[k * CGP + jg + kJGroups * u];
 #pragma unroll
         for (int v = 0; v < TI; v += VW) {
-          const typename Vec<T>::type x =
-              *reinterpret_cast<const typename Vec<T>::type*>(Om + k * LP + ig * TI + v);
+          const VT x = *reinterpret_cast<const VT*>(Om + k * LP + ig * TI + v);
           const T* xs = reinterpret_cast<const T*>(&x);
 #pragma unroll
           for (int u = 0; u < VW; ++u) w[v + u] = xs[u];

@@ -212,6 +212,7 @@ namespace {
 // CUDA-core CTAs per SM: its partial-sum workspace holds a slot per CTA per
 // subdomain.
 constexpr int kPerSubMaxCtasPerSm = 2;
+constexpr int kPerSubMinChunks = 8;
 
 // Build the sketch schedule for window columns [col0, col0 + ncols).
 //
@@ -444,18 +445,26 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   int64_t slot_total = 0;
   std::vector<std::vector<int32_t>> slots_of_prob(probs.size());
   // chunk i of the units [u0, u1) goes to the CTA whose equal share of the
-  // total weight contains the chunk's midpoint; appends G + 1 entries to seg_ptr
+  // total weight contains the chunk's midpoint; appends G + 1 entries to
+  // seg_ptr.  A CUDA-core launch for one subdomain spreads its chunks over only
+  // as many CTAs as keep kPerSubMinChunks each (the rest find no work): every
+  // CTA that works writes a partial slot, and one CTA folds them all.
   auto partition = [&](int u0, int u1) {
     double W = 0.0;
-    for (int u = u0; u < u1; ++u) W += units[u].nch * units[u].w;
+    int nch_all = 0;
+    for (int u = u0; u < u1; ++u) {
+      W += units[u].nch * units[u].w;
+      nch_all += units[u].nch;
+    }
+    const int Gw = (!tc && P->per_sub()) ? std::max(1, std::min(G, nch_all / kPerSubMinChunks)) : G;
     struct Run { int unit, chunk0, chunk1; };
     std::vector<std::vector<Run>> per_cta(G);
     double acc = 0.0;
     for (int u = u0; u < u1; ++u) {
       const double w = units[u].w;
       for (int ch = 0; ch < units[u].nch; ++ch) {
-        int c = W > 0 ? (int)((acc + 0.5 * w) * G / W) : 0;
-        c = std::min(std::max(c, 0), G - 1);
+        int c = W > 0 ? (int)((acc + 0.5 * w) * Gw / W) : 0;
+        c = std::min(std::max(c, 0), Gw - 1);
         std::vector<Run>& v = per_cta[c];
         if (!v.empty() && v.back().unit == u && v.back().chunk1 == ch) v.back().chunk1 = ch + 1;
         else v.push_back({u, ch, ch + 1});

@@ -162,7 +162,8 @@ template <> struct Vec16<double> {
 template <typename T>
 __device__ __forceinline__ void reduce_problem_slots(const SketchArgs& a, int p, int t, int nt) {
   using V = typename Vec16<T>::type;
-  constexpr int U = 4;
+  constexpr int U = 4;   // 16-byte vectors per thread per pass
+  constexpr int G = 2;   // slots whose loads are in flight together (added in slot order)
   const Problem pb = a.probs[p];
   const int q0 = a.pslot_ptr[p], q1 = a.pslot_ptr[p + 1];
   const T* part = static_cast<const T*>(a.partial);
@@ -173,13 +174,24 @@ __device__ __forceinline__ void reduce_problem_slots(const SketchArgs& a, int p,
     V s[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) s[u] = Vec16<T>::zero();
-    for (int q = q0; q < q1; ++q) {
-      const V* src = reinterpret_cast<const V*>(part + a.slot_off[a.pslots[q]]);
+    for (int q = q0; q < q1; q += G) {
+      const V* src[G];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int64_t e = base + t + (int64_t)u * nt;
-        if (e < nv) Vec16<T>::add(s[u], __ldcg(src + e));
-      }
+      for (int g = 0; g < G; ++g)
+        src[g] = (q + g < q1) ? reinterpret_cast<const V*>(part + a.slot_off[a.pslots[q + g]]) : nullptr;
+      V v[G][U];
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t e = base + t + (int64_t)u * nt;
+          v[g][u] = (src[g] && e < nv) ? __ldcg(src[g] + e) : Vec16<T>::zero();
+        }
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (src[g]) Vec16<T>::add(s[u], v[g][u]);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
