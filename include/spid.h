@@ -271,7 +271,7 @@ typedef struct {
                                   (batched TF32/BF16/3xBF16 plans with k_max <= 32 only) */
   int32_t error_rows;          /* CUDA-core error pass: rows per work unit, 256, 512 (default)
                                   or 1024 */
-  int32_t error_cols;          /* CUDA-core error pass: columns per work unit, 128 or 256
+  int32_t error_cols;          /* CUDA-core error pass: columns per work unit, 64, 128 or 256
                                   (default) */
   int32_t sketch_slice_major;  /* tensor-core sketch: 0 = a pack holds consecutive slices of one
                                   subdomain (default), 1 = slice j of consecutive subdomains

@@ -206,7 +206,7 @@ size_t error_smem_bytes(int k_max, int col_block, bool fp64) {
 cudaError_t launch_error(const ErrArgs& a, int units, bool fp64, cudaStream_t st) {
   if (units <= 0) return cudaSuccess;
   if (a.row_block < kErrTile || a.row_block % kErrTile ||
-      (a.col_block != 128 && a.col_block != 256))
+      (a.col_block != 64 && a.col_block != 128 && a.col_block != 256))
     return cudaErrorInvalidValue;
   const size_t smem = error_smem_bytes(a.k_max, a.col_block, fp64);
   cudaError_t e = cudaSuccess;
@@ -218,14 +218,18 @@ cudaError_t launch_error(const ErrArgs& a, int units, bool fp64, cudaStream_t st
     error_kernel<T, W, CB><<<units, 256, smem, st>>>(a);                                    \
   } while (0)
   const bool w = a.out != nullptr;
-  const bool wide = a.col_block == 256;
+#define SPID_LAUNCH_ERR_CB(T, W)                                   \
+  do {                                                             \
+    if (a.col_block == 256) SPID_LAUNCH_ERR(T, W, 256);            \
+    else if (a.col_block == 128) SPID_LAUNCH_ERR(T, W, 128);       \
+    else SPID_LAUNCH_ERR(T, W, 64);                                \
+  } while (0)
   if (fp64) {
-    if (w) { if (wide) SPID_LAUNCH_ERR(double, true, 256); else SPID_LAUNCH_ERR(double, true, 128); }
-    else { if (wide) SPID_LAUNCH_ERR(double, false, 256); else SPID_LAUNCH_ERR(double, false, 128); }
+    if (w) SPID_LAUNCH_ERR_CB(double, true); else SPID_LAUNCH_ERR_CB(double, false);
   } else {
-    if (w) { if (wide) SPID_LAUNCH_ERR(float, true, 256); else SPID_LAUNCH_ERR(float, true, 128); }
-    else { if (wide) SPID_LAUNCH_ERR(float, false, 256); else SPID_LAUNCH_ERR(float, false, 128); }
+    if (w) SPID_LAUNCH_ERR_CB(float, true); else SPID_LAUNCH_ERR_CB(float, false);
   }
+#undef SPID_LAUNCH_ERR_CB
 #undef SPID_LAUNCH_ERR
   return cudaGetLastError();
 }

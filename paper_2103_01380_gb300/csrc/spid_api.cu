@@ -628,7 +628,7 @@ spid_status get_schedule(spid_plan_t P, int col0, int ncols, Schedule** out) {
 
 // Unit shapes the tuner may choose for the CUDA-core error pass.
 constexpr int kTuneErrRows[] = {256, 512, 1024};
-constexpr int kTuneErrCols[] = {128, 256};
+constexpr int kTuneErrCols[] = {64, 128, 256};
 constexpr int kTuneMaxCtasPerSm = 4;
 
 int count_error_units(spid_plan_t P, int rows, int cols) {
@@ -1510,7 +1510,7 @@ bool valid_tuning(const spid_tuning& t) {
   return in(t.sketch_pack_slices, {1, 2, 4, 8}) && (t.sketch_stages == 0 ||
          (t.sketch_stages >= 2 && t.sketch_stages <= 8)) &&
          in(t.sketch_ctas_per_sm, {0, 1, 2, 3, 4}) && in(t.error_path, {0, 1}) &&
-         in(t.error_rows, {256, 512, 1024}) && in(t.error_cols, {128, 256}) &&
+         in(t.error_rows, {256, 512, 1024}) && in(t.error_cols, {64, 128, 256}) &&
          in(t.sketch_slice_major, {0, 1}) && in(t.sketch_slice_cols, {0, 16, 32, 64});
 }
 

@@ -178,7 +178,7 @@ def test_set_tuning_rejects_out_of_range_values():
     base = plan.tuning()
     assert base["sketch_pack_slices"] == 8 and base["error_rows"] == 512
     for key, bad in [("sketch_pack_slices", 3), ("sketch_stages", 1), ("sketch_stages", 9),
-                     ("sketch_ctas_per_sm", 5), ("error_rows", 300), ("error_cols", 64),
+                     ("sketch_ctas_per_sm", 5), ("error_rows", 300), ("error_cols", 32),
                      ("error_path", 2), ("sketch_slice_cols", 8), ("sketch_slice_major", 2)]:
         with pytest.raises(spid.SpidError) as ei:
             plan.set_tuning(dict(base, **{key: bad}))
@@ -194,7 +194,7 @@ def test_set_tuning_rejects_out_of_range_values():
 
 TUNINGS = [dict(sketch_pack_slices=ps, sketch_stages=st, error_path=0, error_rows=r, error_cols=c)
            for ps, st, r, c in [(8, 0, 512, 256), (4, 2, 256, 128), (2, 4, 1024, 256),
-                                (1, 0, 256, 256)]] + \
+                                (1, 0, 256, 256), (8, 0, 256, 64), (4, 0, 1024, 64)]] + \
           [dict(sketch_pack_slices=8, sketch_stages=3, error_path=1, error_rows=512, error_cols=256)] + \
           [dict(sketch_pack_slices=ps, sketch_stages=0, sketch_slice_cols=w, sketch_slice_major=o,
                 error_path=0, error_rows=512, error_cols=256)
