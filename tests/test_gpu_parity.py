@@ -175,6 +175,47 @@ def test_snapshot_major_layout():
                      min_prefix=0 if prec == "tf32" else 4)
 
 
+@pytest.mark.parametrize("slice_cols", [64, 32, 16])
+def test_strided_blocks_with_ragged_windows(slice_cols):
+    # subdomains of whole 32-row chunks side by side in every snapshot row
+    # (one tensor map of whole rows serves them all), window lengths that end
+    # inside a slice (those slices read through the subdomain's own map, which
+    # zero-fills past its last column), micro-batches of 48 columns, and NaN in
+    # every element no subdomain owns: a box read past a subdomain's columns
+    # into a kept result would turn it to NaN
+    m, n = [64, 96, 32, 128, 64], [100, 64, 37, 130, 81]
+    S, L, N = len(m), sum(m), max(n)
+    blocks = [inputs.separated_lowrank(m[s], n[s], 4, 60 + s, decay=0.5, noise=1e-4)
+              for s in range(S)]
+    data = np.full(L * N, np.nan, dtype=np.float32)
+    off = np.concatenate([[0], np.cumsum(m)[:-1]]).astype(np.int64)
+    win = inputs.Window(data, np.array(m), np.array(n), off, np.full(S, L, dtype=np.int64))
+    for s in range(S):
+        win.block(s)[...] = blocks[s]
+    plan = spid.Plan.for_window(win, k_max=4, p=6, precision="tf32", seed=0x5EED0001)
+    if slice_cols != 64:
+        plan.set_tuning(dict(plan.tuning(), sketch_slice_cols=slice_cols))
+    w = _dev(win)
+    for c0 in range(0, N, 48):
+        plan.sketch(w, c0, 48)
+    plan.finalize()
+    torch.cuda.synchronize()
+    Y = plan.sketches()
+    assert plan.device_status() in (0, spid.SPID_ERR_RANK)
+    ref = inputs.pack_blocks(blocks)            # the same blocks, contiguous
+    bp = spid.Plan.for_window(ref, k_max=4, p=6, precision="tf32", seed=0x5EED0001)
+    bp.sketch(_dev(ref))
+    torch.cuda.synchronize()
+    Yb = bp.sketches()
+    o = oracle_window(ref, 10, 4, 0.0, "tf32", 0x5EED0001)
+    for s in range(S):
+        assert np.all(np.isfinite(Y[s])), s
+        assert rel_fro(Y[s], Yb[s]) <= 1e-5, s     # the same TF32 products, other FP32 order
+        assert rel_fro(Y[s], o["Y"][s]) <= Y_TOL["tf32"], s
+    plan.close()
+    bp.close()
+
+
 @pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16", "bf16x3"])
 def test_edge_cases(precision):
     # n < k_max, n = 1, m < 32, k_max = 1
