@@ -724,7 +724,7 @@ def _run_insitu(args, torch, inputs, spid):
     tot = torch.zeros(4, dtype=torch.float64, device="cuda")
     plan = spid.Plan([m] * S, [n] * S, np.arange(S) * n * m, [m] * S, k_max=30, p=10,
                      precision="tf32", seed=0x5EED0005)
-    tuning = None if args.no_autotune else plan.autotune(window)
+    tuning = None if args.no_autotune else plan.autotune(window, microbatch=b)
     sk, fi, er = _stage_times(torch, plan, window, args.steps, args.warmup, err, tot, calls)
     summ = _summary(plan, tot)
     # in-situ overlap: producer writes batch i+1 while the sketch consumes batch i
@@ -951,7 +951,8 @@ def run_headline(args):
     plan = make_plan(args.precision)
     err = torch.zeros(2 * S, dtype=torch.float64, device="cuda")
     tot = torch.zeros(plan.total_len, dtype=torch.float64, device="cuda")
-    tuning = dict(plan.tuning(), cached=None) if args.no_autotune else plan.autotune(window)
+    tuning = (dict(plan.tuning(), cached=None) if args.no_autotune
+              else plan.autotune(window, microbatch=mb))
     graph = plan.graph(window, err=err, total=tot, microbatch=mb)
 
     def timed_graph(steps, warmup):

@@ -281,8 +281,9 @@ typedef struct {
                                   sketch_pack_slices x 64 columns.  Narrower slices cover fewer
                                   snapshots per chunk, which helps windows whose snapshots lie far
                                   apart (a global field).  Other precisions: 64 only. */
-  float sketch_ms;             /* spid_plan_autotune: measured whole-window sketch time of the
-                                  chosen shape (0 if the tuning was set, not measured) */
+  float sketch_ms;             /* spid_plan_autotune: measured time of the chosen shape to
+                                  sketch the whole window in the tuner's calls (0 if the
+                                  tuning was set, not measured) */
   float error_ms;              /* spid_plan_autotune: measured error-pass time */
 } spid_tuning;
 
@@ -308,6 +309,16 @@ spid_status spid_plan_set_tuning(spid_plan_t plan, const spid_tuning* tuning);
  * captured from the plan exist. */
 spid_status spid_plan_autotune(spid_plan_t plan, const void* window, spid_stream_t stream,
                                spid_tuning* best);
+
+/* spid_plan_autotune for the way the caller sketches: each sketch candidate is
+ * timed on the whole window sketched in calls of `microbatch` columns (columns
+ * [0, b), [b, 2b), ... up to the longest window; 0 = one whole-window call,
+ * which is spid_plan_autotune), since the best shape of a 64-column call
+ * differs from that of a 512-column one.  sketch_ms is the time of all those
+ * calls.  SPID_ERR_INVALID_ARG for microbatch < 0; otherwise as
+ * spid_plan_autotune. */
+spid_status spid_plan_autotune_calls(spid_plan_t plan, const void* window, int32_t microbatch,
+                                     spid_stream_t stream, spid_tuning* best);
 
 /* A text key for caching tunings across runs: the device (compute capability,
  * SM count), precision, flags, l_pad, k_max and log2 buckets of the subdomain

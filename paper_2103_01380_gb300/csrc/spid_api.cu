@@ -1624,10 +1624,32 @@ extern "C" spid_status spid_plan_set_tuning(spid_plan_t P, const spid_tuning* t)
 
 extern "C" spid_status spid_plan_autotune(spid_plan_t P, const void* window, spid_stream_t stream,
                                           spid_tuning* best) {
+  return spid_plan_autotune_calls(P, window, 0, stream, best);
+}
+
+extern "C" spid_status spid_plan_autotune_calls(spid_plan_t P, const void* window,
+                                                int32_t microbatch, spid_stream_t stream,
+                                                spid_tuning* best) {
   spid_status st = check_plan(P);
   if (st != SPID_OK) return st;
   if (!window || reinterpret_cast<uintptr_t>(window) % 16)
     return fail(SPID_ERR_INVALID_ARG, "window is NULL or not 16-byte aligned");
+  if (microbatch < 0) return fail(SPID_ERR_INVALID_ARG, "microbatch must be >= 0");
+  // the column ranges the caller sketches: the whole window, or runs of
+  // `microbatch` columns
+  std::vector<std::pair<int, int>> calls;
+  if (microbatch == 0 || microbatch >= P->n_max) calls.push_back({0, P->n_max});
+  else
+    for (int c = 0; c < P->n_max; c += microbatch) calls.push_back({c, std::min(microbatch, P->n_max - c)});
+  auto sketch_calls = [&]() -> spid_status {
+    for (const auto& cr : calls) {
+      Schedule* sc = nullptr;
+      spid_status s2 = get_schedule(P, cr.first, cr.second, &sc);
+      if (s2 == SPID_OK) s2 = launch_sketch_range(P, sc, window, P->d_tmaps, (cudaStream_t)stream);
+      if (s2 != SPID_OK) return s2;
+    }
+    return SPID_OK;
+  };
   if (P->live_graphs > 0) return fail(SPID_ERR_STATE, "graphs captured from the plan exist");
   std::lock_guard<std::mutex> g(P->tune_mu);
   cudaStream_t cs = (cudaStream_t)stream;
@@ -1664,7 +1686,8 @@ extern "C" spid_status spid_plan_autotune(spid_plan_t P, const void* window, spi
           cands.push_back(c);
         }
   } else {
-    for (int cps : {1, 2, 4}) {
+    // the default first: CTAs per SM by the register budget of each call's variant
+    for (int cps : {0, 1, 2, 3, 4}) {
       TuneCfg c = P->tune;
       c.ctas_per_sm = cps;
       cands.push_back(c);
@@ -1683,7 +1706,7 @@ extern "C" spid_status spid_plan_autotune(spid_plan_t P, const void* window, spi
       if (st != SPID_OK) return st;
     }
     Schedule* sc = nullptr;
-    st = get_schedule(P, 0, P->n_max, &sc);
+    st = get_schedule(P, calls[0].first, calls[0].second, &sc);
     if (st != SPID_OK) return st;
     // stage counts above what fits collapse onto the same launch: skip repeats
     if (P->tensor_core() && sc->stages == seen_stages && c.pack_slices == seen_pack &&
@@ -1694,8 +1717,7 @@ extern "C" spid_status spid_plan_autotune(spid_plan_t P, const void* window, spi
     seen_order = c.slice_major;
     seen_width = c.slice_cols;
     float ms = 0.f;
-    st = time_median(cs, kReps, [&] { return launch_sketch_range(P, sc, window, P->d_tmaps, cs); },
-                     &ms);
+    st = time_median(cs, kReps, sketch_calls, &ms);
     if (st != SPID_OK) return st;
     // the first candidate is the default; another must beat the best so far
     // by kTuneMargin to replace it (run-to-run noise is a few percent)
@@ -1711,13 +1733,9 @@ extern "C" spid_status spid_plan_autotune(spid_plan_t P, const void* window, spi
   st = apply_sketch_cfg(P, best_cfg);
   if (st == SPID_OK && P->tensor_core()) st = bind_window(P, window, cs);
   if (st != SPID_OK) return st;
-  {
-    Schedule* sc = nullptr;
-    st = get_schedule(P, 0, P->n_max, &sc);
-    if (st == SPID_OK) st = launch_sketch_range(P, sc, window, P->d_tmaps, cs);
-    if (st == SPID_OK) st = run_finalize(P, cs);
-    if (st != SPID_OK) return st;
-  }
+  st = sketch_calls();
+  if (st == SPID_OK) st = run_finalize(P, cs);
+  if (st != SPID_OK) return st;
   // ---- error-pass candidates
   std::vector<TuneCfg> ecands;
   {

@@ -40,7 +40,7 @@ EXPORTS = ["spid_plan_create", "spid_plan_destroy", "spid_plan_info", "spid_sket
            "spid_ts_error", "spid_ts_reconstruct", "spid_ts_get_factors",
            "spid_ts_get_block_factors", "spid_ts_device_status",
            "spid_plan_get_tuning", "spid_plan_set_tuning", "spid_plan_autotune",
-           "spid_plan_tuning_key", "spid_graph_create", "spid_graph_launch", "spid_graph_launch_host",
+           "spid_plan_autotune_calls", "spid_plan_tuning_key", "spid_graph_create", "spid_graph_launch", "spid_graph_launch_host",
            "spid_graph_destroy",
            "spid_sub_plan_create_points", "spid_producer_step"]
 GRAPH_SKETCH = 1
@@ -199,6 +199,7 @@ def load_library(path: str = LIB_PATH):
             "spid_plan_get_tuning": ([vp, c.POINTER(_Tuning)], c.c_int),
             "spid_plan_set_tuning": ([vp, c.POINTER(_Tuning)], c.c_int),
             "spid_plan_autotune": ([vp, vp, vp, c.POINTER(_Tuning)], c.c_int),
+            "spid_plan_autotune_calls": ([vp, vp, i32, vp, c.POINTER(_Tuning)], c.c_int),
             "spid_plan_tuning_key": ([vp, c.c_char_p, i32], c.c_int),
             "spid_graph_create": ([vp, vp, i32, i32, i32, u32, vp, vp, c.POINTER(vp)], c.c_int),
             "spid_graph_launch": ([vp, vp], c.c_int),
@@ -419,13 +420,14 @@ class Plan:
         _check(load_library().spid_plan_tuning_key(self._h, buf, 512), "spid_plan_tuning_key")
         return buf.value.decode()
 
-    def autotune(self, window, stream=None, cache: str | None = None) -> dict:
-        """Measure the candidate tile shapes on `window` and keep the fastest.
+    def autotune(self, window, stream=None, cache: str | None = None, microbatch: int = 0) -> dict:
+        """Measure the candidate tile shapes on `window`, sketched in calls of
+        `microbatch` columns (0: whole-window calls), and keep the fastest.
         With `cache` (a JSON file path), a tuning stored under this plan's
-        tuning key is applied instead of measuring, and a new measurement is
-        stored there."""
+        tuning key (and the call width) is applied instead of measuring, and a
+        new measurement is stored there."""
         import json
-        key = self.tuning_key()
+        key = self.tuning_key() + (f"/calls{int(microbatch)}" if microbatch else "")
         store = {}
         if cache and os.path.exists(cache):
             with open(cache) as f:
@@ -434,8 +436,9 @@ class Plan:
                 self.set_tuning(store[key])
                 return dict(store[key], cached=True)
         t = _Tuning()
-        _check(load_library().spid_plan_autotune(self._h, _ptr(window), _stream_handle(stream),
-                                                 ctypes.byref(t)), "spid_plan_autotune")
+        _check(load_library().spid_plan_autotune_calls(self._h, _ptr(window), int(microbatch),
+                                                       _stream_handle(stream), ctypes.byref(t)),
+               "spid_plan_autotune_calls")
         d = t.as_dict()
         if cache:
             store[key] = d

@@ -264,3 +264,33 @@ def test_autotune_and_cache(precision, tmp_path):
         assert plan.tuning_key() in json.load(f)
     plan.close()
     plan2.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32"])
+def test_autotune_for_micro_batched_calls(precision, tmp_path):
+    # tuning measured on the window sketched in calls of 48 columns (the way an
+    # in-situ caller sketches); the plan is left as after those calls and a
+    # finalize, so its error meets the same bar as a one-shot sketch; the cache
+    # keeps micro-batch tunings under their own key
+    win = _window(seed=91)
+    w = torch.from_numpy(win.data).cuda()
+    plan = spid.Plan.for_window(win, k_max=5, p=8, precision=precision, seed=13)
+    with pytest.raises(spid.SpidError) as ei:
+        plan.autotune(w, microbatch=-1)
+    assert ei.value.status == 1
+    cache = str(tmp_path / "tune.json")
+    t = plan.autotune(w, cache=cache, microbatch=48)
+    assert t["cached"] is False and t["sketch_ms"] > 0 and t["error_ms"] > 0
+    err = torch.zeros(2 * win.num_sub, dtype=torch.float64, device="cuda")
+    tot = torch.zeros(4, dtype=torch.float64, device="cuda")
+    plan.error(w, err, tot)
+    torch.cuda.synchronize()
+    assert plan.device_status() in STATUS_OK
+    o = oracle_window(win, 13, 5, 0.0, precision, 13)
+    rel = float(np.sqrt(tot[0].item() / tot[1].item()))
+    rel_o = float(np.sqrt(o["e2"].sum() / o["a2"].sum()))
+    assert rel <= max(2 * rel_o, 1e-3)
+    with open(cache) as f:
+        store = json.load(f)
+    assert plan.tuning_key() + "/calls48" in store and plan.tuning_key() not in store
+    plan.close()
