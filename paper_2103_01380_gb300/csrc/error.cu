@@ -121,24 +121,41 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) error_kernel(ErrA
     const int64_t rofs = boxed ? roff_s[4 * lane] : (int64_t)r;   // their element offset
     const bool full_rows = (r + 4 <= m);
     for (int cg = 4 * warp; cg < ncb; cg += 32) {   // 4 columns per warp per pass
-      T acc[4][4];
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] = T(0);
       T av[4][4];   // A(r .. r+3, col0 + cg + y)
+      const T* src0 = A + (int64_t)(col0 + cg) * ld + rofs;
+      if (full_rows && cg + 4 <= ncb) {
 #pragma unroll
-      for (int y = 0; y < 4; ++y) {
-        const int col = col0 + cg + y;
-        const T* src = A + (int64_t)col * ld + rofs;
-        if (col < n && full_rows) {
-          V4<T>::load(src, av[y]);
-        } else {
+        for (int y = 0; y < 4; ++y) V4<T>::load(src0 + y * ld, av[y]);
+      } else {
 #pragma unroll
-          for (int x = 0; x < 4; ++x) av[y][x] = (col < n && r + x < m) ? src[x] : T(0);
+        for (int y = 0; y < 4; ++y) {
+          const bool in = cg + y < ncb;
+          const T* src = src0 + y * ld;
+          if (in && full_rows) {
+            V4<T>::load(src, av[y]);
+          } else {
+#pragma unroll
+            for (int x = 0; x < 4; ++x) av[y][x] = (in && r + x < m) ? src[x] : T(0);
+          }
         }
       }
-      for (int p = 0; p < kk; ++p) {
+      // k-step 0 starts the products (no zeroing pass), steps 1.. accumulate
+      T acc[4][4];
+      if (kk > 0) {
+        T aj[4], cc[4];
+        V4<T>::lds(AJ + 4 * lane, aj);
+        V4<T>::lds(Cs + cg, cc);
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = aj[x] * cc[y];
+      } else {
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = T(0);
+      }
+      for (int p = 1; p < kk; ++p) {
         T aj[4], cc[4];
         V4<T>::lds(AJ + p * kErrTile + 4 * lane, aj);
         V4<T>::lds(Cs + p * cb + cg, cc);
