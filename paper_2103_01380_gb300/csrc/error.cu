@@ -12,7 +12,8 @@
 // 512 contiguous bytes per warp per column.
 //
 // Reductions keep FP64 off the per-element path (GB300 runs FP64 at 1/64 of
-// FP32): per-thread sums are Kahan-compensated in the working precision, warps
+// FP32): each thread sums a tile's terms plainly (at most 128) and adds the
+// tile sum to a Kahan-compensated running sum in the working precision, warps
 // reduce in the working precision, and only the per-CTA, per-subdomain and
 // window totals are FP64.  The last CTA of each subdomain (an atomic counter,
 // after a device-wide fence) sums that subdomain's unit partials in a fixed
@@ -120,6 +121,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) error_kernel(ErrA
     const int r = rt + 4 * lane;                    // this lane's 4 rows
     const int64_t rofs = boxed ? roff_s[4 * lane] : (int64_t)r;   // their element offset
     const bool full_rows = (r + 4 <= m);
+    // this tile's sums of e^2 and a^2, plain FP32 (at most 8 passes x 16
+    // terms), added to the Kahan sums once per tile
+    T te = T(0), ta = T(0);
     for (int cg = 4 * warp; cg < ncb; cg += 32) {   // 4 columns per warp per pass
       T av[4][4];   // A(r .. r+3, col0 + cg + y)
       const T* src0 = A + (int64_t)(col0 + cg) * ld + rofs;
@@ -155,6 +159,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) error_kernel(ErrA
 #pragma unroll
           for (int y = 0; y < 4; ++y) acc[x][y] = T(0);
       }
+#pragma unroll 2
       for (int p = 1; p < kk; ++p) {
         T aj[4], cc[4];
         V4<T>::lds(AJ + p * kErrTile + 4 * lane, aj);
@@ -164,7 +169,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) error_kernel(ErrA
 #pragma unroll
           for (int y = 0; y < 4; ++y) acc[x][y] = fma(aj[x], cc[y], acc[x][y]);
       }
-      T le = T(0), la = T(0);
+      T le = te, la = ta;
 #pragma unroll
       for (int y = 0; y < 4; ++y) {
 #pragma unroll
@@ -188,9 +193,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) error_kernel(ErrA
           }
         }
       }
-      kahan_add(se, ce, le);
-      kahan_add(sa, ca, la);
+      te = le;
+      ta = la;
     }
+    kahan_add(se, ce, te);
+    kahan_add(sa, ca, ta);
   }
   // warp tree in the working precision, then FP64 across the 8 warps
   T we = se - ce, wa = sa - ca;
