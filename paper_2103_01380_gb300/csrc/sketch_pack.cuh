@@ -66,14 +66,27 @@ __device__ __forceinline__ void pack_epilogue(const SketchArgs& a, const PackSeg
     last_flags[gtid] = ok && (atomicAdd(&a.prob_cnt[p], 1) == nslots - 1);
   }
   named_bar_sync(barrier_id, nthreads);
-  for (int q = 0; q < pk.nprob; ++q) {
-    if (last_flags[q]) {
-      __threadfence();
-      reduce_problem_slots<float>(a, pk.prob0 + q, gtid, nthreads);
-      if (gtid == 0) a.prob_cnt[pk.prob0 + q] = 0;
-    }
+  // the problems this segment completed are folded side by side: completed
+  // problem j of c gets threads [ceil(j N / c), ceil((j + 1) N / c)) of the N,
+  // so their slot loads are in flight together (each element still sums its
+  // slots in schedule order)
+  __shared__ int done_s[kMaxPackMembers + 1];
+  if (gtid == 0) {
+    int c = 0;
+    for (int q = 0; q < pk.nprob; ++q)
+      if (last_flags[q]) done_s[c++] = q;
+    done_s[kMaxPackMembers] = c;
   }
-  named_bar_sync(barrier_id, nthreads);   // last_flags is reused by the next segment
+  named_bar_sync(barrier_id, nthreads);
+  const int c = done_s[kMaxPackMembers];
+  if (c > 0) {
+    __threadfence();
+    const int j = gtid * c / nthreads;
+    const int t0 = (j * nthreads + c - 1) / c, t1 = ((j + 1) * nthreads + c - 1) / c;
+    reduce_problem_slots<float>(a, pk.prob0 + done_s[j], gtid - t0, t1 - t0);
+    if (gtid < c) a.prob_cnt[pk.prob0 + done_s[gtid]] = 0;
+  }
+  named_bar_sync(barrier_id, nthreads);   // last_flags and done_s are reused by the next segment
 }
 
 }  // namespace tc
