@@ -258,9 +258,12 @@ double spid_compression_factor(int32_t num_sub, const int32_t* m, const int32_t*
  * their own.  Results depend on the tuning only through the order of FP32
  * partial sums (sketch slots, error-pass units); each tuning is deterministic. */
 typedef struct {
-  int32_t sketch_pack_slices;  /* tensor-core sketch: 64-column slices of equal-shape subdomains
-                                  sharing one generated Omega chunk: 1, 2, 4 or 8 (default 8);
-                                  spid_plan_autotune also tries both sketch_slice_major orders */
+  int32_t sketch_pack_slices;  /* tensor-core and batched CUDA-core sketches: 64-column slices of
+                                  equal-shape subdomains sharing one generated Omega chunk: 1, 2,
+                                  4 or 8 (default 8, and 2 for the CUDA-core sketch, whose register
+                                  tile grows with it; its FP64 form uses at most 4);
+                                  spid_plan_autotune also tries both sketch_slice_major orders
+                                  (tensor-core sketches) */
   int32_t sketch_stages;       /* tensor-core sketch pipeline depth: 0 = as many as fit in
                                   shared memory (default), else 2..8 (capped by what fits) */
   int32_t sketch_ctas_per_sm;  /* CUDA-core (FP32/FP64) sketch: persistent CTAs per SM, 1..4;

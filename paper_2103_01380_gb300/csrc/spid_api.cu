@@ -44,7 +44,8 @@ struct Schedule {
   int nprob = 0;
   int max_tiles = 1;       // 128-column tiles of the widest problem (TF32)
   int stages = 1;          // TF32 pipeline depth
-  int simt_tj = 1;         // CUDA-core sketch: columns per thread (64 tj >= widest problem)
+  int simt_tj = 1;         // CUDA-core sketch: columns per thread (64 tj >= widest problem or pack)
+  bool packed = false;     // the tables hold pack segments (tensor-core, or batched CUDA-core)
   std::vector<int> cta_base_of_sub, prob_base_of_sub, nprob_of_sub;
   void* dev = nullptr;     // one device block holding every table below
   const Problem* probs = nullptr;
@@ -74,7 +75,7 @@ spid_status plan_create_sketch_rows(const spid_plan_desc* d, spid_stream_t strea
 
 // Tile shapes and schedules of one plan (spid_tuning without the timings).
 struct TuneCfg {
-  int pack_slices = kPackSlices;   // tensor-core sketch: 64-column slices per Omega chunk
+  int pack_slices = kPackSlices;   // 64-column slices per Omega chunk (CUDA-core plans: 2)
   int slice_major = 0;             // tensor-core sketch: packs cut slice index major
   int slice_cols = kSliceCols;     // tensor-core sketch: columns per slice (TMA box width)
   int stages = 0;                  // tensor-core sketch pipeline depth, 0 = as many as fit
@@ -212,6 +213,8 @@ namespace {
 // CUDA-core CTAs per SM: its partial-sum workspace holds a slot per CTA per
 // subdomain.
 constexpr int kPerSubMaxCtasPerSm = 2;
+// default pack width of the batched CUDA-core sketch
+constexpr int kSimtPackSlices = 2;
 constexpr int kPerSubMinChunks = 8;
 
 // Build the sketch schedule for window columns [col0, col0 + ncols).
@@ -228,7 +231,9 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   int G = P->sketch_grid();
   const bool tc = P->tensor_core();
   const int W = tc ? P->tune.slice_cols : kSliceCols;                 // slice width
-  const int pack_cap = tc ? P->tune.pack_slices * kSliceCols / W : 1;   // slices per pack
+  // slices per pack; CUDA-core packs stay within the kernel's widest column tile
+  const int pack_cap = tc ? P->tune.pack_slices * kSliceCols / W
+                          : std::min(P->tune.pack_slices, sketch_simt_group_cols(P->fp64()) / kSliceCols);
   // ---- problems, subdomain by subdomain; with packing, ordered by m
   std::vector<int> subs(P->S);
   for (int s = 0; s < P->S; ++s) subs[s] = s;
@@ -241,7 +246,7 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
     const RowGeom& g = P->geo[s];
     return std::make_tuple(P->m[s], g.ex, g.ey, g.ez);
   };
-  if (tc && !P->per_sub())
+  if (!P->per_sub())
     std::stable_sort(subs.begin(), subs.end(), [&](int x, int y) {
       return std::make_tuple(shape(x), P->off[x]) < std::make_tuple(shape(y), P->off[y]);
     });
@@ -274,7 +279,8 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   // (the fold unit) is a subdomain's run of consecutive slices inside one pack.
   // A chunk's weight counts its columns plus a fixed share for the Omega chunk
   // it regenerates.
-  const bool streamed = tc && !P->per_sub();
+  const bool streamed = !P->per_sub();
+  const bool packed = tc || streamed;   // pack segments (else one problem per segment)
   if (streamed) {
     // Packs are cut from the stream of 64-column slices of one shape class,
     // either subdomain major (all slices of one subdomain, then the next: a
@@ -387,9 +393,18 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   // CUDA-core kernels: the register tile fits the widest problem of this
   // column range, and the grid holds as many CTAs per SM as that tile allows
   if (!tc) {
-    int max_cols = 1;
-    for (const Problem& pb : probs) max_cols = std::max(max_cols, pb.ncols);
-    sc.simt_tj = sketch_simt_tj(P->fp64(), max_cols);
+    if (streamed) {
+      // packed: one 64-column group per slice, the tile fits the widest pack
+      int mx = 1;
+      for (const Pack& pk : packs) mx = std::max(mx, pk.nslices);
+      int tj = 1;
+      while (tj < mx) tj *= 2;
+      sc.simt_tj = tj;
+    } else {
+      int max_cols = 1;
+      for (const Problem& pb : probs) max_cols = std::max(max_cols, pb.ncols);
+      sc.simt_tj = sketch_simt_tj(P->fp64(), max_cols);
+    }
     int cps = P->tune.ctas_per_sm > 0 ? P->tune.ctas_per_sm
                                       : sketch_simt_ctas_per_sm(P->fp64(), P->l_pad, sc.simt_tj);
     if (P->per_sub()) cps = std::min(cps, kPerSubMaxCtasPerSm);
@@ -472,7 +487,7 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
       }
     }
     for (int c = 0; c < G; ++c) {
-      seg_ptr.push_back((int32_t)(tc ? psegs.size() : segs.size()));
+      seg_ptr.push_back((int32_t)(packed ? psegs.size() : segs.size()));
       for (const Run& r : per_cta[c]) {
         const Unit& un = units[r.unit];
         const int32_t first_slot = (int32_t)slot_off.size();
@@ -482,11 +497,11 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
           slot_off.push_back(slot_total);
           slot_total += (int64_t)probs[p].ncols * P->l_pad;
         }
-        if (tc) psegs.push_back({un.pack, r.chunk0, r.chunk1, first_slot});
+        if (packed) psegs.push_back({un.pack, r.chunk0, r.chunk1, first_slot});
         else segs.push_back({un.prob0, r.chunk0, r.chunk1, first_slot});
       }
     }
-    seg_ptr.push_back((int32_t)(tc ? psegs.size() : segs.size()));
+    seg_ptr.push_back((int32_t)(packed ? psegs.size() : segs.size()));
   };
   sc.cta_base_of_sub.assign(P->S, 0);
   sc.prob_base_of_sub.assign(P->S, 0);
@@ -515,6 +530,7 @@ spid_status build_schedule(spid_plan_t P, int col0, int ncols, Schedule& sc) {
   for (const Pack& pk : packs) max_slices = std::max(max_slices, pk.nslices);
 
   sc.grid = G;
+  sc.packed = packed;
   sc.nprob = (int)probs.size();
   sc.max_tiles = tc ? (max_slices * W + 127) / 128 : 1;
   sc.partial_elems = slot_total;
@@ -813,6 +829,7 @@ spid_status launch_sketch_range(spid_plan_t P, const Schedule* sc, const void* w
         P->bf16() ? launch_sketch_bf16(a, sc->grid, sc->stages, sc->max_tiles,
                                        P->prec == SPID_PREC_BF16X3, cs)
         : P->tensor_core() ? launch_sketch_tc(a, sc->grid, sc->stages, sc->max_tiles, cs)
+        : sc->packed       ? launch_sketch_simt_packed(a, sc->grid, P->fp64(), sc->simt_tj, cs)
                            : launch_sketch_simt(a, sc->grid, P->fp64(), sc->simt_tj, cs);
     if (e != cudaSuccess) return fail(SPID_ERR_CUDA, std::string("sketch launch: ") + cudaGetErrorString(e));
   }
@@ -1169,6 +1186,9 @@ static spid_status plan_create(const spid_plan_desc* d, spid_stream_t stream, in
                    : (int64_t)std::max(P->sketch_grid(), kTuneMaxCtasPerSm * P->num_sms);
   P->partial_cap = (ctas + nprob_full) * (int64_t)CG * P->l_pad;
   if (P->flags & SPID_FLAG_TC_ERROR) P->tune.err_path = P->err_tc_possible() ? 1 : 0;
+  // the CUDA-core sketch keeps a register tile of 64 columns per pack slice:
+  // 2 slices leave room for 3 CTAs per SM (8 allow 1)
+  if (!P->tensor_core()) P->tune.pack_slices = kSimtPackSlices;
 
 #define SPID_ALLOC(ptr, bytes)                                                            \
   do {                                                                                    \
@@ -1686,9 +1706,17 @@ extern "C" spid_status spid_plan_autotune_calls(spid_plan_t P, const void* windo
           cands.push_back(c);
         }
   } else {
-    // the default first: CTAs per SM by the register budget of each call's variant
-    for (int cps : {0, 1, 2, 3, 4}) {
+    // the default first (2-slice packs, CTAs per SM by the register budget of
+    // each call's variant), then other pack widths and CTA counts
+    for (int ps : {kSimtPackSlices, 4, 8, 1}) {
       TuneCfg c = P->tune;
+      c.pack_slices = ps;
+      c.ctas_per_sm = 0;
+      cands.push_back(c);
+    }
+    for (int cps : {1, 2, 3, 4}) {
+      TuneCfg c = P->tune;
+      c.pack_slices = kSimtPackSlices;
       c.ctas_per_sm = cps;
       cands.push_back(c);
     }

@@ -316,6 +316,9 @@ int sketch_simt_group_cols(bool fp64);
 int sketch_simt_tj(bool fp64, int max_cols);
 int sketch_simt_ctas_per_sm(bool fp64, int l_pad, int tj);
 cudaError_t launch_sketch_simt(const SketchArgs& a, int grid, bool fp64, int tj, cudaStream_t st);
+// batched plans: the pack segments of the streamed schedule (tj = slices per pack tile)
+cudaError_t launch_sketch_simt_packed(const SketchArgs& a, int grid, bool fp64, int tj,
+                                      cudaStream_t st);
 int sketch_tc_group_cols();
 size_t sketch_tc_smem_bytes(int stages, int max_tiles, int l_pad);
 int sketch_tc_max_stages();

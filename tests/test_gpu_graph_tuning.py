@@ -176,7 +176,7 @@ def test_set_tuning_rejects_out_of_range_values():
     win = _window(seed=70, m=(100,), n=(50,))
     plan = spid.Plan.for_window(win, k_max=5, p=8, precision="fp32", seed=1)
     base = plan.tuning()
-    assert base["sketch_pack_slices"] == 8 and base["error_rows"] == 512
+    assert base["sketch_pack_slices"] == 2 and base["error_rows"] == 512
     for key, bad in [("sketch_pack_slices", 3), ("sketch_stages", 1), ("sketch_stages", 9),
                      ("sketch_ctas_per_sm", 5), ("error_rows", 300), ("error_cols", 32),
                      ("error_path", 2), ("sketch_slice_cols", 8), ("sketch_slice_major", 2)]:
