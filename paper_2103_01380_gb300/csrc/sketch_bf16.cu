@@ -270,23 +270,30 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_bf16_kernel(const Bf16Args
         if (!ok) continue;
         unsigned char* ob = smem_O + (size_t)st * omega_bytes;
         const int r0 = ch * kChunkRows;
-        for (int task = gtid; task < kChunkRows * groups; task += kGenThreads) {
-          const int k = task % kChunkRows, g = task / kChunkRows;
-          float w[4] = {0.f, 0.f, 0.f, 0.f};
-          if (4 * g < a.l && r0 + k < pb.m) {
-            omega_group<float>(key, (uint32_t)(r0 + k), (uint32_t)g, w);
+        // a task makes K-rows k and k + 1 (k even) of Omega rows 4g .. 4g+3:
+        // each (row, k pair) is one 4-byte store of two adjacent BF16 values
+        for (int task = gtid; task < (kChunkRows / 2) * groups; task += kGenThreads) {
+          const int k = 2 * (task % (kChunkRows / 2)), g = task / (kChunkRows / 2);
+          float w[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (4 * g + u >= a.l) w[u] = 0.f;
-          }
+          for (int h = 0; h < 2; ++h)
+            if (4 * g < a.l && r0 + k + h < pb.m) {
+              omega_group<float>(key, (uint32_t)(r0 + k + h), (uint32_t)g, w[h]);
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (4 * g + u >= a.l) w[h][u] = 0.f;
+            }
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int i = 4 * g + u;   // row of Omega = MMA N index
-            const __nv_bfloat16 h = __float2bfloat16_rn(w[u]);
-            *reinterpret_cast<__nv_bfloat16*>(ob + sw64_offset(i, k)) = h;
-            if (SPLIT)
-              *reinterpret_cast<__nv_bfloat16*>(ob + l_pad * 64 + sw64_offset(i, k)) =
-                  __float2bfloat16_rn(w[u] - __bfloat162float(h));
+            const uint32_t off = sw64_offset(i, k);   // k even: 4-byte aligned, k + 1 next
+            const uint32_t hp = pack_bf16x2(w[0][u], w[1][u]);
+            *reinterpret_cast<uint32_t*>(ob + off) = hp;
+            if (SPLIT) {
+              const __nv_bfloat162 hv = *reinterpret_cast<const __nv_bfloat162*>(&hp);
+              *reinterpret_cast<uint32_t*>(ob + l_pad * 64 + off) =
+                  pack_bf16x2(w[0][u] - __bfloat162float(hv.x), w[1][u] - __bfloat162float(hv.y));
+            }
           }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
