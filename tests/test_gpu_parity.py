@@ -208,12 +208,22 @@ def test_strided_blocks_with_ragged_windows(slice_cols):
     torch.cuda.synchronize()
     Yb = bp.sketches()
     o = oracle_window(ref, 10, 4, 0.0, "tf32", 0x5EED0001)
+    # one launch per subdomain reads through the same shared map
+    ps = spid.Plan.for_window(win, k_max=4, p=6, precision="tf32", seed=0x5EED0001,
+                              flags=spid.FLAG_PER_SUBDOMAIN)
+    if slice_cols != 64:
+        ps.set_tuning(dict(ps.tuning(), sketch_slice_cols=slice_cols))
+    ps.sketch(w)
+    torch.cuda.synchronize()
+    Yp = ps.sketches()
     for s in range(S):
         assert np.all(np.isfinite(Y[s])), s
         assert rel_fro(Y[s], Yb[s]) <= 1e-5, s     # the same TF32 products, other FP32 order
+        assert rel_fro(Yp[s], Yb[s]) <= 1e-5, s
         assert rel_fro(Y[s], o["Y"][s]) <= Y_TOL["tf32"], s
     plan.close()
     bp.close()
+    ps.close()
 
 
 @pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16", "bf16x3"])
